@@ -1,0 +1,139 @@
+"""Seeded synthetic inputs shaped like the paper's globular-cluster knowledge base.
+
+The paper's data (Section 3) are ~2,100 patterns of 11 continuous photometric and
+morphological features with a binary GC / not-GC label.  That catalogue is not
+available, so every workload here is synthetic and seeded:
+
+* features: uniform in [-1, 1], or Gaussian with a seeded random correlation
+  matrix, scaled by 0.5 and clipped to [-1, 1];
+* labels: +-1 from the sign of a seeded hidden polynomial in the same basis
+  (median-centred for class balance), then 5% of the labels flipped;
+* a seeded 70/30 train/test split, returned with the training rows first.
+
+This module only produces inputs.  It holds none of the method's arithmetic:
+the hidden labelling function is evaluated with numpy's own Chebyshev routine
+(``numpy.polynomial.chebyshev.chebval``) or with ``np.cos`` / ``np.sin``, and
+both the CUDA path and the oracle receive the arrays it returns.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+from numpy.polynomial import chebyshev as _cheb
+
+DATA_SEED = 1304
+
+
+@dataclass
+class Dataset:
+    X: np.ndarray          # [NP, F] float32, training rows first
+    t: np.ndarray          # [NP] float32 targets (+-1)
+    n_train: int
+    basis: str
+    degree: int
+
+    @property
+    def n_patterns(self) -> int:
+        return self.X.shape[0]
+
+    @property
+    def n_features(self) -> int:
+        return self.X.shape[1]
+
+
+def _features(rng: np.random.Generator, n: int, F: int, correlated: bool) -> np.ndarray:
+    if not correlated:
+        return rng.uniform(-1.0, 1.0, size=(n, F)).astype(np.float32)
+    A = rng.standard_normal((F, F))
+    S0 = A @ A.T
+    d = np.sqrt(np.diag(S0))
+    L = np.linalg.cholesky(S0 / np.outer(d, d))
+    out = np.empty((n, F), dtype=np.float32)
+    step = 1 << 18
+    for i in range(0, n, step):
+        m = min(step, n - i)
+        z = rng.standard_normal((m, F))
+        out[i:i + m] = np.clip(0.5 * (z @ L.T), -1.0, 1.0)
+    return out
+
+
+def _hidden(rng: np.random.Generator, X: np.ndarray, basis: str, degree: int) -> np.ndarray:
+    """Value of a seeded random function of the features (coefficients uniform in [-1, 1])."""
+    n, F = X.shape
+    v = np.full(n, rng.uniform(-1.0, 1.0), dtype=np.float64)
+    for f in range(F):
+        x = X[:, f].astype(np.float64)
+        if basis == "chebyshev":
+            c = np.concatenate([[0.0], rng.uniform(-1.0, 1.0, size=degree)])
+            v += _cheb.chebval(x, c)
+        else:
+            a = rng.uniform(-1.0, 1.0, size=degree)
+            b = rng.uniform(-1.0, 1.0, size=degree)
+            for k in range(1, degree + 1):
+                v += a[k - 1] * np.cos(k * x) + b[k - 1] * np.sin(k * x)
+    return v
+
+
+def make_dataset(n_patterns: int, n_features: int, degree: int, basis: str = "chebyshev",
+                 seed: int = DATA_SEED, correlated: bool = False, flip: float = 0.05,
+                 train_frac: float = 0.7) -> Dataset:
+    rng = np.random.default_rng(seed)
+    X = _features(rng, n_patterns, n_features, correlated)
+    v = _hidden(rng, X, basis, degree)
+    t = np.where(v - np.median(v) >= 0.0, 1.0, -1.0)
+    t = np.where(rng.random(n_patterns) < flip, -t, t).astype(np.float32)
+    perm = rng.permutation(n_patterns)
+    n_train = int(round(train_frac * n_patterns))
+    return Dataset(X=np.ascontiguousarray(X[perm]), t=np.ascontiguousarray(t[perm]),
+                   n_train=n_train, basis=basis, degree=degree)
+
+
+def planted_targets(P: np.ndarray, h: np.ndarray) -> np.ndarray:
+    """Regression targets tanh(P h) for a planted chromosome h (P given by the caller)."""
+    return np.tanh(np.asarray(P, dtype=np.float64) @ np.asarray(h, dtype=np.float64))
+
+
+# --- the workloads -------------------------------------------------------------------
+
+def plain_small(seed: int = DATA_SEED) -> Dataset:
+    """2,000 patterns x 7 uniform features, Chebyshev degree 4 (29 genes)."""
+    return make_dataset(2000, 7, 4, "chebyshev", seed=seed)
+
+
+def plain_at_scale(seed: int = DATA_SEED, n_patterns: int = 1_000_000) -> Dataset:
+    """1,000,000 patterns x 32 correlated features, Chebyshev degree 8 (257 genes)."""
+    return make_dataset(n_patterns, 32, 8, "chebyshev", seed=seed, correlated=True)
+
+
+def surrogate_scale(seed: int = DATA_SEED, n_patterns: int = 2_000_000) -> Dataset:
+    """2,000,000 patterns x 48 correlated features, Chebyshev degree 6 (289 genes)."""
+    return make_dataset(n_patterns, 48, 6, "chebyshev", seed=seed, correlated=True)
+
+
+@dataclass
+class RunSpec:
+    n_patterns: int
+    n_features: int
+    degree: int
+    pop: int
+    basis: str
+    precision: str         # "fp32" | "bf16"
+    seed: int
+
+
+def batched_specs(n_runs: int = 64, seed: int = DATA_SEED) -> list[RunSpec]:
+    """Uneven run sizes: patterns log-uniform 1e4..5e5, features 5..40, degree 3..10,
+    population log-uniform 64..2048 rounded to 32; bases and precisions alternate."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_runs):
+        n = int(round(np.exp(rng.uniform(np.log(1e4), np.log(5e5)))))
+        F = int(rng.integers(5, 41))
+        d = int(rng.integers(3, 11))
+        pop = int(round(np.exp(rng.uniform(np.log(64), np.log(2048))) / 32.0)) * 32
+        pop = min(max(pop, 64), 2048)
+        out.append(RunSpec(n, F, d, pop, "chebyshev" if i % 2 == 0 else "trig",
+                           "fp32" if (i // 2) % 2 == 0 else "bf16", seed + 1 + i))
+    return out

@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark: chromosome x pattern evaluations per second of GAME training on one GB300.
+
+Workload (default): 1,000,000 patterns x 32 Gaussian-correlated features clipped
+to [-1, 1], Chebyshev degree 8 (257 genes), population 1,024, 70/30 split,
+tournament 3, single-point crossover 0.9, Gaussian mutation (0.1, 0.05),
+elitism 2, tanh output, RMSE fitness, float32 fitness.
+
+A step is one GAME generation (breed -> prepare -> fitness -> reduce + rank) on
+the device; ``value`` = population x training patterns x steps / device time of
+the K timed steps (inputs resident in HBM).  ``e2e`` times complete training runs
+through the public C ABI from pinned host buffers: game_set_data (host -> device
+copy + expansion) + game_evolve(50) + game_get_best (device -> host).
+
+``--impl reference`` times the CPU oracle (float64 numpy, the method's plain
+statement) on a bounded sample of the same workload.  Under torchrun each rank
+runs an independent GA run (its own data seed) with no collective on the data
+path (weak scaling); rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "chromosome*pattern evals/s (GAME population fitness, 1 GB300)"
+UNIT = "evals/s"
+GENS_PER_RUN = 50
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--engine", choices=["auto", "tcgen05", "simt"], default="auto")
+    ap.add_argument("--n-patterns", type=int, default=1_000_000)
+    ap.add_argument("--e2e-runs", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def workload_config(n_patterns):
+    return {"workload": "plain GAME at scale, FP32 fitness",
+            "n_patterns": n_patterns, "n_features": 32, "basis": "chebyshev", "degree": 8,
+            "n_genes": 257, "pop": 1024, "train_frac": 0.7, "tournament_k": 3,
+            "p_crossover": 0.9, "p_mutation": 0.05, "sigma_mutation": 0.1, "elitism": 2,
+            "activation": "tanh", "error": "rmse"}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), d.get("bf16_tflops"), "measured"
+    except OSError:
+        return 6800.0, 1900.0, "fallback"
+
+
+def kernel_traffic(kernel_file: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on this exact source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    src = os.path.join(ROOT, "paper_1304_0597_gb300", "csrc", kernel_file)
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel_file)
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_sha256") != sha:
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return max(n)
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+def oracle_generation_rate(ds, n_sample: int, pop: int, seconds: float, min_steps: int = 1,
+                           steps: int | None = None, warmup: int = 0):
+    """Time oracle generations (fitness + rank + breed, float64 numpy) on a sample of the rows."""
+    from oracle import game_oracle as o
+    ocfg = o.Config(basis="chebyshev", degree=8, pop=pop, seed=0)
+    P = o.expand(ds.X[:n_sample], "chebyshev", 8)
+    t = ds.t[:n_sample]
+    G = o.init_population(ocfg, P.shape[1])
+    gen = 0
+
+    def step():
+        nonlocal G, gen
+        fit = o.fitness(P, t, G, ocfg)
+        o.rank(fit)
+        G = o.breed(G, fit, ocfg, gen)
+        gen += 1
+
+    for _ in range(warmup):
+        step()
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        step()
+        n += 1
+        el = time.perf_counter() - t0
+        if steps is not None:
+            if n >= steps:
+                break
+        elif n >= min_steps and el >= seconds:
+            break
+    return pop * n_sample * n / el, n, el
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from paper_1304_0597_gb300 import synth
+    n_sample = 10_000
+    ds = synth.make_dataset(max(n_sample * 2, 20_000), 32, 8, "chebyshev", correlated=True)
+    rate, n, el = oracle_generation_rate(ds, n_sample, 1024, 0.0, steps=args.steps,
+                                         warmup=args.warmup)
+    cores = blas_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / n, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_config(args.n_patterns), sample_train_patterns=n_sample),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{n} generations (fitness+rank+breed) of pop 1024 on "
+                                   f"{n_sample} training patterns of the workload"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local_rank)
+    from paper_1304_0597_gb300 import game, synth
+
+    ds = synth.plain_at_scale(seed=synth.DATA_SEED + rank, n_patterns=args.n_patterns)
+    X_pin = torch.from_numpy(ds.X).pin_memory()
+    t_pin = torch.from_numpy(ds.t).pin_memory()
+    stream = torch.cuda.current_stream()
+    engine = {"auto": game.ENGINE_AUTO, "tcgen05": game.ENGINE_TCGEN05,
+              "simt": game.ENGINE_SIMT}[args.engine]
+    cfg = game.default_config(degree=8, pop=1024, seed=rank, stream=stream.cuda_stream,
+                              engine=engine, device=local_rank)
+    g = game.Game(cfg)
+    g.set_data(X_pin, t_pin, ds.n_train)
+    K, W = args.steps, args.warmup
+    g.evolve(W)
+    g.set_timing(True)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ran = g.evolve(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    tm = g.timing()
+    assert ran == K, f"evolution stopped after {ran} of {K} generations"
+    t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    pop, n_train, n_genes = 1024, ds.n_train, g.n_genes
+    units = pop * n_train * K * world
+    value = units / (ms_max / 1e3)
+
+    # End to end through the C ABI from pinned host memory: one training run per step.
+    g.set_timing(False)
+    e2e_t = []
+    genes = np.empty(n_genes, dtype=np.float32)
+    for i in range(args.e2e_runs + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_data(X_pin, t_pin, ds.n_train)
+        ran_e = g.evolve(GENS_PER_RUN)
+        genes[:], fit_best, test_rmse, test_acc = g.best()
+        el = time.perf_counter() - t0
+        if i > 0:
+            e2e_t.append(el)
+    e2e_value = pop * n_train * GENS_PER_RUN / statistics.median(e2e_t)
+    h2d = ds.X.nbytes + ds.t.nbytes
+    d2h = n_genes * 4 + 3 * 8 + 4 + 40
+
+    # Roofline of the dominant kernel (fitness), from its CUDA-event time in the timed region.
+    hbm, bf16_tf, peak_src = measured_peaks()
+    fit_ms = tm["ms_fitness"] / K
+    engine_used = tm["engine"]
+    flops = 2.0 * n_train * n_genes * pop
+    if engine_used == game.ENGINE_TCGEN05:
+        kfile, bound, peak, punit = "fitness_tc.cu", "tensor", bf16_tf, "TFLOP/s"
+        achieved = flops / (fit_ms / 1e3) / 1e12
+    else:
+        # float32 FFMA: 152 SMs x 128 lanes x 2 flops x max SM clock
+        kfile, bound, punit = "fitness_simt.cu", "alu", "TFLOP/s"
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        achieved = flops / (fit_ms / 1e3) / 1e12
+    traffic = kernel_traffic(kfile)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(args.n_patterns), n_train=n_train,
+                       engine={1: "tcgen05", 2: "simt"}.get(engine_used, "?"),
+                       l2="inputs larger than L2 (expansion planes of the training rows: "
+                          f"{2 * 2 * n_train * 256 / 1e6:.0f} MB)",
+                       parallelism=f"{world} independent runs (one per GPU)"),
+        "stage_ms_per_step": {"breed_prepare": tm["ms_breed"] / K, "fitness": fit_ms,
+                              "reduce_rank": tm["ms_rank"] / K},
+        "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": kfile, "peak_source": peak_src if bound == "tensor" else
+                     "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "step": f"one training run: set_data + "
+                f"{GENS_PER_RUN} generations + get_best", "runs": len(e2e_t)},
+        "gpu_launches": 4 * K + 1,
+        "clocks": clk.summary(),
+        "best": {"train_rmse": fit_best, "test_rmse": test_rmse, "test_accuracy": test_acc},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, n, el = oracle_generation_rate(ds, 10_000, pop, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": blas_threads(),
+                                "kind": "oracle",
+                                "sample": f"{n} generations (fitness+rank+breed, float64) of pop "
+                                          f"1024 on 10,000 training patterns, {el:.1f} s"}
+    g.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * game.h -- C ABI of libgame.so, a GB300 (sm_103a) engine for the population
+ * fitness evaluation of GAME, the polynomial-expansion genetic algorithm of
+ * Cavuoti et al., "Astrophysical data mining with GPU. A case study: genetic
+ * classification of globular clusters".
+ *
+ * Method (paper Section 2): every pattern pat_k = (f_1..f_N, t_k) is expanded
+ * feature by feature into a polynomial sequence (eq.1; polytrigo eq.8/eq.9, or
+ * Chebyshev T_1..T_d); a chromosome is the vector of expansion coefficients;
+ * its output on pattern k is Out(pat_k) = a_0 + sum_i sum_j a_ij g^j(f_i)
+ * (eq.2), its fitness the MSE / RMSE / threshold-MSE of the outputs against
+ * the targets (eq.3, eq.4, eq.5, eq.10).  Training (Section 4.1, steps 1-4)
+ * draws a random population, then repeats: fitness + sort, stop test,
+ * genetic operators.
+ *
+ * Conventions for every call:
+ *  - A call returns GAME_OK or a negative game_status; it never aborts the
+ *    process.  game_last_error() returns a message for the last failure on a
+ *    context (valid until the next call on that context).
+ *  - Host buffers passed in are read during the call only; the library copies
+ *    what it keeps.  Output buffers are caller-owned and caller-sized.
+ *  - "device pointer" arguments are CUDA global-memory addresses on the
+ *    context's device; the caller keeps ownership.
+ *  - All work is queued on the context's stream (game_config.stream, or the
+ *    legacy default stream when NULL); calls that return data to the host
+ *    synchronise that stream before returning.
+ *  - One context is used by one host thread at a time.
+ *  - Gene layout: gene 0 is the bias a_0; gene 1 + f*B*d + b is the b-th basis
+ *    member of feature f (B = 1 Chebyshev, b = 0..d-1 -> T_{b+1}; B = 2
+ *    polytrigo, b = 0..d-1 -> cos((b+1)x), b = d..2d-1 -> sin((b-d+1)x)),
+ *    so n_genes = B*F*d + 1 (eq.7 generalised to per-feature coefficients).
+ */
+#ifndef GAME_H
+#define GAME_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct game_ctx game_ctx;
+
+typedef enum {
+  GAME_OK = 0,
+  GAME_ERR_INVALID_ARG = -1,  /* a size, pointer or option is out of range        */
+  GAME_ERR_STATE = -2,        /* calls made in the wrong order (e.g. no data yet)   */
+  GAME_ERR_OOM = -3,          /* device allocation failed                           */
+  GAME_ERR_CUDA = -4,         /* a CUDA runtime / driver call failed                */
+  GAME_ERR_NO_DEVICE = -5,    /* no usable sm_103a device                           */
+  GAME_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up                 */
+  GAME_ERR_NUMERIC = -7,      /* NaN / Inf in the input data                        */
+  GAME_ERR_UNSUPPORTED = -8   /* valid request outside this build's limits          */
+} game_status;
+
+enum { GAME_CHEBYSHEV = 0, GAME_TRIG = 1 };                       /* basis g(x)     */
+enum { GAME_RMSE = 0, GAME_MSE = 1, GAME_TMSE = 2, GAME_TMSE_SQ = 3 };  /* error       */
+enum { GAME_TANH = 0, GAME_LINEAR = 1 };                          /* activation     */
+enum { GAME_INIT_UNIFORM_PM1 = 0, GAME_INIT_NORMAL_PM1 = 1, GAME_INIT_UNIFORM_01 = 2 };
+enum { GAME_ELITE_TOP = 0, GAME_ELITE_COPIES = 1 };               /* elitism reading */
+enum { GAME_FP32 = 0, GAME_BF16 = 1, GAME_FP8 = 2 };              /* storage of P    */
+enum { GAME_ENGINE_AUTO = 0, GAME_ENGINE_TCGEN05 = 1, GAME_ENGINE_SIMT = 2 };
+
+/*
+ * Training options.  Paper Section 2 lists the user options (error function,
+ * selection, elitism, random initialisation criteria); Section 5 gives the
+ * experiment values.  Fill with game_config_default() and override.
+ */
+typedef struct game_config {
+  int32_t basis;          /* GAME_CHEBYSHEV | GAME_TRIG (polytrigo, eq.8)                 */
+  int32_t degree;         /* d >= 1 (eq.1)                                                 */
+  int32_t pop;            /* chromosomes, 2..8192 (eq.6 gives B*N+1 as one choice)         */
+  int32_t tournament_k;   /* tournament size, 1..32, draws with replacement               */
+  float p_crossover;      /* single-point crossover probability per pair                   */
+  float p_mutation;       /* per-gene mutation probability                                 */
+  float sigma_mutation;   /* std-dev of the Gaussian mutation step                          */
+  int32_t elitism;        /* elite chromosomes copied unchanged, 0..pop                    */
+  int32_t elite_mode;     /* GAME_ELITE_TOP (top-e distinct) | GAME_ELITE_COPIES (e x best) */
+  int32_t error;          /* GAME_RMSE | GAME_MSE | GAME_TMSE (|t-Out|>R) | GAME_TMSE_SQ (eq.10 literal) */
+  float tmse_R;           /* threshold R in ]0,1[ (eq.10)                                   */
+  int32_t activation;     /* GAME_TANH | GAME_LINEAR (the paper's Out)                      */
+  int32_t init;           /* GAME_INIT_* (Section 2, three random generation criteria)     */
+  int32_t clamp_genes;    /* 1: genes clamped to [-1,1] after mutation                      */
+  double stop_error;      /* stop when the best fitness <= this (Section 5: 0.001)         */
+  uint64_t seed;          /* Philox key word 0                                              */
+  uint64_t run;           /* Philox key word 1 (independent runs with one seed)            */
+  int32_t precision;      /* GAME_FP32 | GAME_BF16 | GAME_FP8 storage of P                  */
+  int32_t elite_rescore;  /* low precision: top-n re-scored with the FP32 path each gen     */
+  int32_t surrogate_pool; /* 0 off; else offspring pool multiplier screened by the MLP      */
+  int32_t engine;         /* GAME_ENGINE_* fitness kernel choice (AUTO picks tcgen05)       */
+  int32_t device;         /* CUDA device ordinal                                            */
+  void* stream;           /* cudaStream_t, or NULL for the legacy default stream           */
+} game_config;
+
+/* Fill *cfg with defaults: Chebyshev d=4, pop 20, k=3, pc 0.9, pm 0.05, sigma 0.1,
+ * elitism 2 (top), RMSE, tanh, U[-1,1] init, clamp on, stop 0.001, seed 0, FP32. */
+void game_config_default(game_config* cfg);
+
+/* Create a context on cfg->device.  *out receives an owned handle (free with
+ * game_destroy).  Errors: INVALID_ARG (bad option), NO_DEVICE (no sm_103a GPU),
+ * CUDA. */
+game_status game_create(const game_config* cfg, game_ctx** out);
+
+/* Load the knowledge base (Section 2: patterns (f_1..f_N, t); train / test
+ * subsets) and build the expansion matrix once (Section 4.1: the sums of sines
+ * and cosines are computed in advance and kept on the device).
+ *   X: n_patterns x n_features float32, row-major; t: n_patterns float32.
+ *   The first n_train rows are the training set, the rest the test set.
+ *   device_ptrs: 0 = X and t are host pointers, 1 = device pointers.
+ * Resets the population to generation 0 (drawn from cfg->init).
+ * Errors: INVALID_ARG (sizes, n_train outside 1..n_patterns), NUMERIC (NaN/Inf
+ * in X or t), OOM, UNSUPPORTED (shape beyond this build's limits). */
+game_status game_set_data(game_ctx* ctx, const float* X, const float* t, int64_t n_patterns,
+                          int32_t n_features, int64_t n_train, int32_t device_ptrs);
+
+/* Run up to max_generations generations of Section 4.1 steps 2-4 (fitness +
+ * sort, stop test, operators).  Resumable: continues from the current
+ * population and Philox counter.  Each generation evaluates one population;
+ * every generation after the first evaluated one is bred from its parent.
+ * *generations_run (may be NULL) receives the number evaluated by this call;
+ * evolution stops early when the best fitness <= cfg->stop_error.
+ * Errors: STATE (no data), CUDA, TIMEOUT. */
+game_status game_evolve(game_ctx* ctx, int32_t max_generations, int32_t* generations_run);
+
+/* Best chromosome of the last evaluated population (Section 2 "train" use case:
+ * build and store the best population).  genes: caller buffer of cap >=
+ * game_n_genes floats (may be NULL).  train_fitness: its fitness under
+ * cfg->error on the training rows; test_rmse / test_accuracy: float64 report on
+ * the test rows (accuracy by sign with sign(0)=+1 for tanh, y>=0.5 for linear).
+ * Any output pointer may be NULL.  Errors: STATE (nothing evaluated), INVALID_ARG. */
+game_status game_get_best(game_ctx* ctx, float* genes, int32_t cap, double* train_fitness,
+                          double* test_rmse, double* test_accuracy);
+
+/* Genes per chromosome (B*F*d + 1); 0 before game_set_data. */
+int32_t game_n_genes(const game_ctx* ctx);
+
+/* Message for the last failing call on ctx (or a global message when ctx is NULL). */
+const char* game_last_error(const game_ctx* ctx);
+
+/* Release every resource of ctx.  NULL is ignored. */
+void game_destroy(game_ctx* ctx);
+
+/* ---- step-level calls (tests, trajectory replay, custom loops) ------------- */
+
+/* Replace the current population: G is pop x n_genes float32 row-major (host
+ * or device per device_ptrs).  Marks it not yet evaluated; the generation
+ * counter is unchanged.  Errors: STATE, INVALID_ARG. */
+game_status game_set_population(game_ctx* ctx, const float* G, int32_t pop, int32_t n_genes,
+                                int32_t device_ptrs);
+
+/* Copy the current population (pop x n_genes float32) to the host buffer G. */
+game_status game_get_population(game_ctx* ctx, float* G, int32_t pop, int32_t n_genes);
+
+/* Fitness of the current population on the training rows (eq.2 -> eq.3 ->
+ * eq.4/eq.5/eq.10), ranked by (fitness, index).  fitness (host, pop doubles)
+ * and rank (host, pop int32) may be NULL.  Does not breed. */
+game_status game_evaluate(game_ctx* ctx, double* fitness, int32_t* rank);
+
+/* One application of the genetic operators to the current population using
+ * the given fitness vector (host, pop doubles; NULL = the last evaluated one),
+ * with Philox counter word 0 = the current generation, which then advances by
+ * one.  Elitism, tournament selection, single-point crossover, Gaussian
+ * mutation and clamping as in Section 2 / Section 5. */
+game_status game_breed(game_ctx* ctx, const double* fitness);
+
+/* Copy expansion-matrix rows [row0, row0+n_rows) as float32 into out
+ * (n_rows x (n_genes-1), the basis columns; the bias column of ones is
+ * implicit), reconstructed from the stored precision. */
+game_status game_get_expansion(game_ctx* ctx, float* out, int64_t row0, int64_t n_rows);
+
+/* Float64 figures of merit of one chromosome (host genes, n_genes floats) on
+ * the training (split 0) or test (split 1) rows: RMSE (eq.5), accuracy,
+ * completeness (TP/(TP+FN)) and contamination (FP/(TP+FP)) with class +1 as
+ * the positive (GC) class (Section 5).  Any output may be NULL. */
+game_status game_score(game_ctx* ctx, const float* genes, int32_t split, double* rmse,
+                       double* accuracy, double* completeness, double* contamination);
+
+/* Current generation counter (number of breeding steps applied) and stop flag. */
+game_status game_get_state(game_ctx* ctx, int64_t* generation, int32_t* stopped);
+
+/* Device time of the last game_evolve call split by stage, in milliseconds
+ * (CUDA events): breed, fitness (contraction + epilogue), rank (reduce +
+ * sort).  Also the engine actually used (GAME_ENGINE_*). */
+typedef struct game_timing {
+  double ms_breed, ms_fitness, ms_rank, ms_total;
+  int32_t generations;
+  int32_t engine;
+} game_timing;
+game_status game_get_timing(game_ctx* ctx, game_timing* out);
+
+/* enabled = 1: game_evolve records CUDA events around every stage of every
+ * generation (on the context's stream) and game_get_timing reports their sums
+ * for the last call; enabled = 0 (default): only the total is timed. */
+game_status game_set_timing(game_ctx* ctx, int32_t enabled);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GAME_H */

@@ -5,14 +5,12 @@ imported lazily so that ``synth`` (seeded input generators) works on machines
 without the built library.
 """
 
+import importlib
+
 __all__ = ["game", "synth"]
 
 
 def __getattr__(name):
-    if name == "game":
-        from . import game
-        return game
-    if name == "synth":
-        from . import synth
-        return synth
+    if name in __all__:
+        return importlib.import_module(f"{__name__}.{name}")
     raise AttributeError(name)

@@ -1,0 +1,705 @@
+// C ABI of libgame.so: context, device buffers, the generation loop and the
+// step-level calls.  Every compute step runs in this library's kernels; the
+// host code only validates arguments, allocates, launches and copies.
+//
+// Loop (paper Section 4.1): (1) random initial population; (2) fitness of all
+// chromosomes and sort; (3) stop test (error threshold or iteration budget);
+// (4) genetic operators, back to (2).  One generation on the device is:
+//   breed -> prepare operands -> fitness (tensor cores or SIMT) -> reduce+rank
+// with the loop state (current buffer, generation, stop flag) kept in device
+// memory, so a generation is a fixed sequence of launches that is captured once
+// into a CUDA graph and replayed.
+#include "game_internal.h"
+#include "fitness_tc.h"
+
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+using namespace game;
+
+struct game_ctx {
+  game_config cfg{};
+  std::string err;
+  int dev = 0;
+  int n_sm = 0;
+  cudaStream_t st = nullptr;
+  bool have_data = false;
+  Shape s{};
+  Fitness fit{};
+  ExpDev e{};
+  PopDev p{};
+  double* d_fit = nullptr;
+  int* d_rank = nullptr;
+  double* d_partial = nullptr;
+  int n_part = 0;          // partial rows used by the engine in use
+  int part_rows = 0;       // partial rows allocated
+  DevState* d_state = nullptr;
+  float* d_scratch = nullptr;   // expansion column maxima
+  double* d_score_blocks = nullptr;
+  double* d_score_out = nullptr;
+  int score_nb = 0;
+  float* d_genes = nullptr;     // one chromosome (report)
+  int engine = GAME_ENGINE_SIMT;
+  TcPlan tc{};
+  cudaGraphExec_t graph = nullptr;     // one generation
+  cudaGraph_t graph_t_tmpl = nullptr;  // one generation with stage events (template kept alive)
+  cudaGraphExec_t graph_t = nullptr;
+  cudaGraphNode_t ev_node[4] = {};     // event-record nodes of graph_t, stage order
+  std::vector<cudaEvent_t> ev_pool;    // 4 events per generation of a timed call
+  bool timing_on = false;
+  game_timing timing{};
+  std::vector<void*> allocs;
+};
+
+static std::string g_global_err;
+
+static game_status fail(game_ctx* c, game_status code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_global_err = buf;
+  return code;
+}
+
+#define CUDA_OK(ctx, call)                                                                  \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? GAME_ERR_OOM : GAME_ERR_CUDA,      \
+                  "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);     \
+  } while (0)
+
+template <typename T>
+static game_status dalloc(game_ctx* c, T** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc((void**)ptr, bytes);
+  if (e != cudaSuccess)
+    return fail(c, GAME_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+  c->allocs.push_back(*ptr);
+  e = cudaMemsetAsync(*ptr, 0, bytes, c->st);
+  if (e != cudaSuccess) return fail(c, GAME_ERR_CUDA, "cudaMemset: %s", cudaGetErrorString(e));
+  return GAME_OK;
+}
+
+static void drop_graphs(game_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  if (c->graph_t) cudaGraphExecDestroy(c->graph_t);
+  if (c->graph_t_tmpl) cudaGraphDestroy(c->graph_t_tmpl);
+  c->graph = c->graph_t = nullptr;
+  c->graph_t_tmpl = nullptr;
+}
+
+static void free_all(game_ctx* c) {
+  drop_graphs(c);
+  for (void* p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+  c->have_data = false;
+}
+
+static int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+extern "C" void game_config_default(game_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->basis = GAME_CHEBYSHEV;
+  cfg->degree = 4;
+  cfg->pop = 20;
+  cfg->tournament_k = 3;
+  cfg->p_crossover = 0.9f;
+  cfg->p_mutation = 0.05f;
+  cfg->sigma_mutation = 0.1f;
+  cfg->elitism = 2;
+  cfg->elite_mode = GAME_ELITE_TOP;
+  cfg->error = GAME_RMSE;
+  cfg->tmse_R = 0.49f;
+  cfg->activation = GAME_TANH;
+  cfg->init = GAME_INIT_UNIFORM_PM1;
+  cfg->clamp_genes = 1;
+  cfg->stop_error = 0.001;
+  cfg->seed = 0;
+  cfg->run = 0;
+  cfg->precision = GAME_FP32;
+  cfg->elite_rescore = 16;
+  cfg->surrogate_pool = 0;
+  cfg->engine = GAME_ENGINE_AUTO;
+  cfg->device = 0;
+  cfg->stream = nullptr;
+}
+
+static game_status validate(game_ctx* c, const game_config* cfg) {
+  if (cfg->basis != GAME_CHEBYSHEV && cfg->basis != GAME_TRIG)
+    return fail(c, GAME_ERR_INVALID_ARG, "basis must be GAME_CHEBYSHEV or GAME_TRIG");
+  if (cfg->degree < 1 || cfg->degree > 32)
+    return fail(c, GAME_ERR_INVALID_ARG, "degree must be in 1..32 (got %d)", cfg->degree);
+  if (cfg->pop < 2 || cfg->pop > 8192)
+    return fail(c, GAME_ERR_INVALID_ARG, "pop must be in 2..8192 (got %d)", cfg->pop);
+  if (cfg->tournament_k < 1 || cfg->tournament_k > 32)
+    return fail(c, GAME_ERR_INVALID_ARG, "tournament_k must be in 1..32");
+  if (!(cfg->p_crossover >= 0.0f && cfg->p_crossover <= 1.0f) ||
+      !(cfg->p_mutation >= 0.0f && cfg->p_mutation <= 1.0f) || !(cfg->sigma_mutation >= 0.0f))
+    return fail(c, GAME_ERR_INVALID_ARG, "probabilities must be in [0,1] and sigma >= 0");
+  if (cfg->elitism < 0 || cfg->elitism > cfg->pop)
+    return fail(c, GAME_ERR_INVALID_ARG, "elitism must be in 0..pop");
+  if (cfg->elite_mode != GAME_ELITE_TOP && cfg->elite_mode != GAME_ELITE_COPIES)
+    return fail(c, GAME_ERR_INVALID_ARG, "bad elite_mode");
+  if (cfg->error < GAME_RMSE || cfg->error > GAME_TMSE_SQ)
+    return fail(c, GAME_ERR_INVALID_ARG, "bad error kind");
+  if ((cfg->error == GAME_TMSE || cfg->error == GAME_TMSE_SQ) &&
+      !(cfg->tmse_R > 0.0f && cfg->tmse_R < 1.0f))
+    return fail(c, GAME_ERR_INVALID_ARG, "tmse_R must be in ]0,1[");
+  if (cfg->activation != GAME_TANH && cfg->activation != GAME_LINEAR)
+    return fail(c, GAME_ERR_INVALID_ARG, "bad activation");
+  if (cfg->init < GAME_INIT_UNIFORM_PM1 || cfg->init > GAME_INIT_UNIFORM_01)
+    return fail(c, GAME_ERR_INVALID_ARG, "bad init mode");
+  if (cfg->precision < GAME_FP32 || cfg->precision > GAME_FP8)
+    return fail(c, GAME_ERR_INVALID_ARG, "bad precision");
+  if (cfg->engine < GAME_ENGINE_AUTO || cfg->engine > GAME_ENGINE_SIMT)
+    return fail(c, GAME_ERR_INVALID_ARG, "bad engine");
+  if (cfg->surrogate_pool < 0) return fail(c, GAME_ERR_INVALID_ARG, "bad surrogate_pool");
+  return GAME_OK;
+}
+
+extern "C" game_status game_create(const game_config* cfg, game_ctx** out) {
+  if (!cfg || !out) return fail(nullptr, GAME_ERR_INVALID_ARG, "cfg and out must be non-NULL");
+  *out = nullptr;
+  game_ctx* c = new game_ctx();
+  game_status s = validate(c, cfg);
+  if (s != GAME_OK) {
+    g_global_err = c->err;
+    delete c;
+    return s;
+  }
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0 || cfg->device < 0 || cfg->device >= n) {
+    cudaGetLastError();
+    delete c;
+    return fail(nullptr, GAME_ERR_NO_DEVICE, "no CUDA device %d", cfg->device);
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, cfg->device) != cudaSuccess) {
+    delete c;
+    return fail(nullptr, GAME_ERR_NO_DEVICE, "cannot query device %d", cfg->device);
+  }
+  if (prop.major != 10 || prop.minor != 3) {
+    delete c;
+    return fail(nullptr, GAME_ERR_NO_DEVICE,
+                "device %d is sm_%d%d; this library is built for sm_103a only", cfg->device,
+                prop.major, prop.minor);
+  }
+  c->cfg = *cfg;
+  c->dev = cfg->device;
+  c->n_sm = prop.multiProcessorCount;
+  c->st = (cudaStream_t)cfg->stream;
+  cudaSetDevice(c->dev);
+  cudaError_t e = ga_init_attributes();
+  if (e == cudaSuccess) e = tc_init_attributes();
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, GAME_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return GAME_OK;
+}
+
+extern "C" void game_destroy(game_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->dev);
+  cudaStreamSynchronize(c->st);
+  free_all(c);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+extern "C" const char* game_last_error(const game_ctx* c) {
+  return c ? c->err.c_str() : g_global_err.c_str();
+}
+
+extern "C" int32_t game_n_genes(const game_ctx* c) {
+  return (c && c->have_data) ? c->s.n_genes : 0;
+}
+
+__global__ void check_data_kernel(const float* X, long long nx, const float* t, long long nt,
+                                  long long n_train, unsigned int* flags) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned int bad = 0, notpm1 = 0;
+  for (long long k = i; k < nx; k += stride) bad |= !isfinite(X[k]);
+  for (long long k = i; k < nt; k += stride) {
+    bad |= !isfinite(t[k]);
+    if (k < n_train) notpm1 |= !(t[k] == 1.0f || t[k] == -1.0f);
+  }
+  if (bad) atomicOr(flags, 1u);
+  if (notpm1) atomicOr(flags, 2u);
+}
+
+static game_status choose_engine(game_ctx* c) {
+  int want = c->cfg.engine;
+  if (want == GAME_ENGINE_AUTO) want = tc_supported(c->s) ? GAME_ENGINE_TCGEN05 : GAME_ENGINE_SIMT;
+  if (want == GAME_ENGINE_TCGEN05) {
+    if (!tc_supported(c->s))
+      return fail(c, GAME_ERR_UNSUPPORTED, "tcgen05 engine does not support this shape");
+    cudaError_t e = tc_plan(c->s, c->e, c->p, c->n_sm, &c->tc);
+    if (e != cudaSuccess) return fail(c, GAME_ERR_CUDA, "tcgen05 plan: %s", cudaGetErrorString(e));
+    c->engine = GAME_ENGINE_TCGEN05;
+    c->n_part = c->tc.n_part;
+  } else {
+    c->engine = GAME_ENGINE_SIMT;
+    c->n_part = simt_partials(c->s, c->n_sm);
+  }
+  return GAME_OK;
+}
+
+extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t,
+                                     int64_t n_patterns, int32_t n_features, int64_t n_train,
+                                     int32_t device_ptrs) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!X || !t) return fail(c, GAME_ERR_INVALID_ARG, "X and t must be non-NULL");
+  if (n_patterns < 1 || n_features < 1 || n_train < 1 || n_train > n_patterns)
+    return fail(c, GAME_ERR_INVALID_ARG,
+                "need n_patterns >= 1, n_features >= 1, 1 <= n_train <= n_patterns");
+  cudaSetDevice(c->dev);
+  const int B = c->cfg.basis == GAME_TRIG ? 2 : 1;
+  const long long kb = (long long)B * n_features * c->cfg.degree;
+  if (kb > 4096)
+    return fail(c, GAME_ERR_UNSUPPORTED, "B*F*d = %lld basis columns exceeds 4096", kb);
+  free_all(c);
+  Shape& s = c->s;
+  s.n_patterns = n_patterns;
+  s.n_train = n_train;
+  s.n_features = n_features;
+  s.degree = c->cfg.degree;
+  s.basis = c->cfg.basis;
+  s.bd = B * c->cfg.degree;
+  s.kb = (int)kb;
+  s.kp = round_up(s.kb, c->cfg.precision == GAME_FP8 ? 32 : 16);
+  s.n_genes = s.kb + 1;
+  s.kstride = round_up(s.n_genes, 4);
+  s.pop = c->cfg.pop;
+  s.pop_pad = round_up(s.pop, 128);
+  s.precision = c->cfg.precision;
+  c->fit.error = c->cfg.error;
+  c->fit.activation = c->cfg.activation;
+  c->fit.tmse_R = c->cfg.tmse_R;
+
+  game_status r;
+  // Knowledge base on the device.
+  float* dX = nullptr;
+  const size_t xbytes = sizeof(float) * (size_t)n_patterns * n_features;
+  if ((r = dalloc(c, &dX, xbytes)) != GAME_OK) return r;
+  const long long tpad = (n_patterns + 255) / 256 * 256 + 256;
+  if ((r = dalloc(c, &c->e.t, sizeof(float) * tpad)) != GAME_OK) return r;
+  CUDA_OK(c, cudaMemcpyAsync(dX, X, xbytes, device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+  CUDA_OK(c, cudaMemcpyAsync(c->e.t, t, sizeof(float) * n_patterns,
+                             device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+  unsigned int* dflags = nullptr;
+  if ((r = dalloc(c, &dflags, sizeof(unsigned int))) != GAME_OK) return r;
+  check_data_kernel<<<4 * c->n_sm, 256, 0, c->st>>>(dX, n_patterns * n_features, c->e.t,
+                                                      n_patterns, n_train, dflags);
+  CUDA_OK(c, cudaGetLastError());
+  unsigned int flags = 0;
+  CUDA_OK(c, cudaMemcpyAsync(&flags, dflags, sizeof(flags), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  if (flags & 1u) {
+    free_all(c);
+    return fail(c, GAME_ERR_NUMERIC, "X or t holds NaN or Inf");
+  }
+  c->fit.pm1_targets = (flags & 2u) ? 0 : 1;
+
+  // Expansion matrix (Section 4.1: computed once, reused every generation).
+  const size_t esz = s.precision == GAME_FP32 ? 2 : (s.precision == GAME_BF16 ? 2 : 1);
+  const size_t pbytes = esz * (size_t)n_patterns * s.kp;
+  if ((r = dalloc(c, &c->e.p0, pbytes)) != GAME_OK) return r;
+  if (s.precision == GAME_FP32) {
+    if ((r = dalloc(c, &c->e.p1, pbytes)) != GAME_OK) return r;
+  }
+  if ((r = dalloc(c, &c->e.colscale, sizeof(float) * s.kp)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_scratch, sizeof(float) * s.kp)) != GAME_OK) return r;
+  CUDA_OK(c, launch_expand(dX, s, c->e, c->d_scratch, c->st));
+
+  // Population buffers.
+  const size_t g32b = sizeof(float) * (size_t)s.pop_pad * s.kstride;
+  for (int i = 0; i < 2; ++i)
+    if ((r = dalloc(c, &c->p.g32[i], g32b)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->p.geval, sizeof(float) * (size_t)s.pop_pad * s.kp)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->p.bias, sizeof(float) * s.pop_pad)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->p.rscale, sizeof(float) * s.pop_pad)) != GAME_OK) return r;
+  const size_t gpl = esz * (size_t)s.pop_pad * s.kp;
+  if ((r = dalloc(c, &c->p.ghi, gpl)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->p.glo, gpl)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_fit, sizeof(double) * s.pop_pad)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_rank, sizeof(int) * s.pop_pad)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_state, sizeof(DevState))) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_genes, sizeof(float) * (size_t)s.kstride)) != GAME_OK) return r;
+  c->score_nb = score_blocks(n_patterns, c->n_sm);
+  if ((r = dalloc(c, &c->d_score_blocks, sizeof(double) * 5 * c->score_nb)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_score_out, sizeof(double) * 8)) != GAME_OK) return r;
+
+  if ((r = choose_engine(c)) != GAME_OK) {
+    free_all(c);
+    return r;
+  }
+  c->part_rows = c->n_part > simt_partials(s, c->n_sm) ? c->n_part : simt_partials(s, c->n_sm);
+  if ((r = dalloc(c, &c->d_partial, sizeof(double) * (size_t)c->part_rows * s.pop_pad)) != GAME_OK)
+    return r;
+
+  CUDA_OK(c, launch_state_op(c->d_state, kStateReset, c->st));
+  CUDA_OK(c, launch_init_population(s, c->cfg.init, c->cfg.seed, c->cfg.run, c->p.g32[0], c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  // X is no longer needed once P exists.
+  for (size_t i = 0; i < c->allocs.size(); ++i)
+    if (c->allocs[i] == dX) {
+      cudaFree(dX);
+      c->allocs.erase(c->allocs.begin() + i);
+      break;
+    }
+  c->have_data = true;
+  return GAME_OK;
+}
+
+// Launch the fitness of the prepared population into the partial-sum buffer.
+static game_status launch_fitness(game_ctx* c, const DevState* state) {
+  if (c->engine == GAME_ENGINE_TCGEN05) {
+    CUDA_OK(c, tc_launch(c->tc, c->s, c->fit, c->p, c->e, c->d_partial, state, c->st));
+  } else {
+    CUDA_OK(c, launch_fitness_simt(c->s, c->fit, c->p, c->e, c->d_partial, c->n_part, state, c->st));
+  }
+  return GAME_OK;
+}
+
+// One generation: breed (if the current population was evaluated), prepare,
+// fitness, reduce + rank.  Reads and writes only device state.
+static game_status enqueue_generation(game_ctx* c, const cudaEvent_t* ev) {
+  if (ev) CUDA_OK(c, cudaEventRecordWithFlags(ev[0], c->st, cudaEventRecordExternal));
+  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 1 | 2, c->st));
+  CUDA_OK(c, launch_prepare(c->s, c->p, c->e, c->d_state, 1 | 2, c->st));
+  if (ev) CUDA_OK(c, cudaEventRecordWithFlags(ev[1], c->st, cudaEventRecordExternal));
+  game_status r = launch_fitness(c, c->d_state);
+  if (r != GAME_OK) return r;
+  if (ev) CUDA_OK(c, cudaEventRecordWithFlags(ev[2], c->st, cudaEventRecordExternal));
+  CUDA_OK(c, launch_reduce_rank(c->s, c->cfg, c->d_partial, c->n_part, c->d_fit, c->d_rank,
+                                c->d_state, kRankEvaluate | (1 << 8), c->st));
+  if (ev) CUDA_OK(c, cudaEventRecordWithFlags(ev[3], c->st, cudaEventRecordExternal));
+  return GAME_OK;
+}
+
+static game_status ensure_events(game_ctx* c, size_t n) {
+  while (c->ev_pool.size() < n) {
+    cudaEvent_t e;
+    CUDA_OK(c, cudaEventCreate(&e));
+    c->ev_pool.push_back(e);
+  }
+  return GAME_OK;
+}
+
+static game_status build_graph(game_ctx* c, bool timed) {
+  if (timed ? c->graph_t != nullptr : c->graph != nullptr) return GAME_OK;
+  if (timed) {
+    game_status r0 = ensure_events(c, 4);
+    if (r0 != GAME_OK) return r0;
+  }
+  cudaStream_t cap = c->st;
+  bool own = false;
+  if (cap == nullptr) {
+    CUDA_OK(c, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    own = true;
+  }
+  cudaStream_t saved = c->st;
+  c->st = cap;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  game_status r = GAME_OK;
+  if (e == cudaSuccess) {
+    r = enqueue_generation(c, timed ? c->ev_pool.data() : nullptr);
+    e = cudaStreamEndCapture(cap, &g);
+  }
+  c->st = saved;
+  if (own) cudaStreamDestroy(cap);
+  if (r != GAME_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) return fail(c, GAME_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  if (!timed) {
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(c, GAME_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return GAME_OK;
+  }
+  // Locate the four event-record nodes so that each replay can record into its own events.
+  size_t n = 0;
+  CUDA_OK(c, cudaGraphGetNodes(g, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  CUDA_OK(c, cudaGraphGetNodes(g, nodes.data(), &n));
+  int found = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    CUDA_OK(c, cudaGraphNodeGetType(nd, &ty));
+    if (ty != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t ev;
+    CUDA_OK(c, cudaGraphEventRecordNodeGetEvent(nd, &ev));
+    for (int j = 0; j < 4; ++j)
+      if (ev == c->ev_pool[j]) {
+        c->ev_node[j] = nd;
+        ++found;
+      }
+  }
+  if (found != 4) {
+    cudaGraphDestroy(g);
+    return fail(c, GAME_ERR_CUDA, "timed graph: found %d of 4 event nodes", found);
+  }
+  e = cudaGraphInstantiate(&c->graph_t, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(c, GAME_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  c->graph_t_tmpl = g;
+  return GAME_OK;
+}
+
+extern "C" game_status game_evolve(game_ctx* c, int32_t max_generations, int32_t* generations_run) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  if (max_generations < 0) return fail(c, GAME_ERR_INVALID_ARG, "max_generations < 0");
+  cudaSetDevice(c->dev);
+  const bool timed = c->timing_on;
+  game_status r = build_graph(c, timed);
+  if (r != GAME_OK) return r;
+  if (timed && (r = ensure_events(c, 4 * (size_t)max_generations + 4)) != GAME_OK) return r;
+  cudaEvent_t e0, e1;
+  CUDA_OK(c, cudaEventCreate(&e0));
+  CUDA_OK(c, cudaEventCreate(&e1));
+  CUDA_OK(c, launch_state_op(c->d_state, kStateBeginEvolve, c->st));
+  CUDA_OK(c, cudaEventRecord(e0, c->st));
+  for (int i = 0; i < max_generations; ++i) {
+    if (timed) {
+      for (int j = 0; j < 4; ++j)
+        CUDA_OK(c, cudaGraphExecEventRecordNodeSetEvent(c->graph_t, c->ev_node[j],
+                                                        c->ev_pool[4 + 4 * i + j]));
+      CUDA_OK(c, cudaGraphLaunch(c->graph_t, c->st));
+    } else {
+      CUDA_OK(c, cudaGraphLaunch(c->graph, c->st));
+    }
+  }
+  CUDA_OK(c, cudaEventRecord(e1, c->st));
+  DevState hs;
+  CUDA_OK(c, cudaMemcpyAsync(&hs, c->d_state, sizeof(hs), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->timing = game_timing{};
+  if (timed) {
+    // Generations skipped after a stop still record their (empty) stages.
+    for (int i = 0; i < max_generations; ++i) {
+      const cudaEvent_t* ev = &c->ev_pool[4 + 4 * i];
+      float a = 0.f, b = 0.f, d = 0.f;
+      cudaEventElapsedTime(&a, ev[0], ev[1]);
+      cudaEventElapsedTime(&b, ev[1], ev[2]);
+      cudaEventElapsedTime(&d, ev[2], ev[3]);
+      c->timing.ms_breed += a;
+      c->timing.ms_fitness += b;
+      c->timing.ms_rank += d;
+    }
+  }
+  c->timing.ms_total = ms;
+  c->timing.generations = hs.gens_run;
+  c->timing.engine = c->engine;
+  if (hs.status != 0) return fail(c, GAME_ERR_TIMEOUT, "device-side wait timed out (status %d)", hs.status);
+  if (generations_run) *generations_run = hs.gens_run;
+  return GAME_OK;
+}
+
+extern "C" game_status game_evaluate(game_ctx* c, double* fitness, int32_t* rank) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  cudaSetDevice(c->dev);
+  // A breed launch with allow = 0 records "not bred" for this evaluation.
+  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 0, c->st));
+  CUDA_OK(c, launch_prepare(c->s, c->p, c->e, c->d_state, 0, c->st));
+  game_status r = launch_fitness(c, nullptr);
+  if (r != GAME_OK) return r;
+  CUDA_OK(c, launch_reduce_rank(c->s, c->cfg, c->d_partial, c->n_part, c->d_fit, c->d_rank,
+                                c->d_state, kRankEvaluate, c->st));
+  if (fitness)
+    CUDA_OK(c, cudaMemcpyAsync(fitness, c->d_fit, sizeof(double) * c->s.pop, cudaMemcpyDeviceToHost, c->st));
+  if (rank)
+    CUDA_OK(c, cudaMemcpyAsync(rank, c->d_rank, sizeof(int) * c->s.pop, cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  return GAME_OK;
+}
+
+extern "C" game_status game_breed(game_ctx* c, const double* fitness) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  cudaSetDevice(c->dev);
+  if (fitness) {
+    CUDA_OK(c, cudaMemcpyAsync(c->d_fit, fitness, sizeof(double) * c->s.pop, cudaMemcpyHostToDevice, c->st));
+    CUDA_OK(c, launch_reduce_rank(c->s, c->cfg, nullptr, 0, c->d_fit, c->d_rank, c->d_state,
+                                  kRankSortOnly, c->st));
+  } else {
+    DevState hs;
+    CUDA_OK(c, cudaMemcpyAsync(&hs, c->d_state, sizeof(hs), cudaMemcpyDeviceToHost, c->st));
+    CUDA_OK(c, cudaStreamSynchronize(c->st));
+    if (!hs.evaluated) return fail(c, GAME_ERR_STATE, "population not evaluated; pass a fitness vector");
+  }
+  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 1, c->st));
+  CUDA_OK(c, launch_state_op(c->d_state, kStateAfterBreed, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  return GAME_OK;
+}
+
+extern "C" game_status game_set_population(game_ctx* c, const float* G, int32_t pop,
+                                           int32_t n_genes, int32_t device_ptrs) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  if (!G || pop != c->s.pop || n_genes != c->s.n_genes)
+    return fail(c, GAME_ERR_INVALID_ARG, "population must be %d x %d", c->s.pop, c->s.n_genes);
+  cudaSetDevice(c->dev);
+  DevState hs;
+  CUDA_OK(c, cudaMemcpyAsync(&hs, c->d_state, sizeof(hs), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  CUDA_OK(c, cudaMemcpy2DAsync(c->p.g32[hs.cur], sizeof(float) * c->s.kstride, G,
+                               sizeof(float) * n_genes, sizeof(float) * n_genes, pop,
+                               device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+  CUDA_OK(c, launch_state_op(c->d_state, kStatePopulationSet, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  return GAME_OK;
+}
+
+extern "C" game_status game_get_population(game_ctx* c, float* G, int32_t pop, int32_t n_genes) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  if (!G || pop != c->s.pop || n_genes != c->s.n_genes)
+    return fail(c, GAME_ERR_INVALID_ARG, "population must be %d x %d", c->s.pop, c->s.n_genes);
+  cudaSetDevice(c->dev);
+  DevState hs;
+  CUDA_OK(c, cudaMemcpyAsync(&hs, c->d_state, sizeof(hs), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  CUDA_OK(c, cudaMemcpy2DAsync(G, sizeof(float) * n_genes, c->p.g32[hs.cur],
+                               sizeof(float) * c->s.kstride, sizeof(float) * n_genes, pop,
+                               cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  return GAME_OK;
+}
+
+extern "C" game_status game_get_expansion(game_ctx* c, float* out, int64_t row0, int64_t n_rows) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  if (!out || row0 < 0 || n_rows < 0 || row0 + n_rows > c->s.n_patterns)
+    return fail(c, GAME_ERR_INVALID_ARG, "rows out of range");
+  if (n_rows == 0) return GAME_OK;
+  cudaSetDevice(c->dev);
+  float* tmp = nullptr;
+  const size_t bytes = sizeof(float) * (size_t)n_rows * c->s.kb;
+  CUDA_OK(c, cudaMalloc(&tmp, bytes));
+  cudaError_t e = launch_expand_get(c->s, c->e, row0, n_rows, tmp, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  cudaFree(tmp);
+  CUDA_OK(c, e);
+  return GAME_OK;
+}
+
+static game_status score(game_ctx* c, const float* genes_host_or_null, int split, double out[5],
+                         long long* rows) {
+  const long long r0 = split == 0 ? 0 : c->s.n_train;
+  const long long r1 = split == 0 ? c->s.n_train : c->s.n_patterns;
+  *rows = r1 - r0;
+  if (genes_host_or_null)
+    CUDA_OK(c, cudaMemcpyAsync(c->d_genes, genes_host_or_null, sizeof(float) * c->s.n_genes,
+                               cudaMemcpyHostToDevice, c->st));
+  CUDA_OK(c, launch_score(c->s, c->fit, c->e, c->d_genes, r0, r1, c->d_score_blocks, c->score_nb,
+                          c->d_score_out, c->st));
+  CUDA_OK(c, cudaMemcpyAsync(out, c->d_score_out, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  return GAME_OK;
+}
+
+static void fill_report(const double v[5], long long rows, double* rmse, double* acc,
+                        double* compl_, double* contam) {
+  const double n = rows > 0 ? (double)rows : 1.0;
+  if (rmse) *rmse = rows > 0 ? sqrt(v[0] / n) : 0.0;
+  if (acc) *acc = rows > 0 ? v[1] / n : 0.0;
+  if (compl_) *compl_ = (v[2] + v[4]) > 0 ? v[2] / (v[2] + v[4]) : 0.0;
+  if (contam) *contam = (v[2] + v[3]) > 0 ? v[3] / (v[2] + v[3]) : 0.0;
+}
+
+extern "C" game_status game_score(game_ctx* c, const float* genes, int32_t split, double* rmse,
+                                  double* accuracy, double* completeness, double* contamination) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  if (!genes || (split != 0 && split != 1)) return fail(c, GAME_ERR_INVALID_ARG, "bad genes/split");
+  cudaSetDevice(c->dev);
+  double v[5];
+  long long rows = 0;
+  game_status r = score(c, genes, split, v, &rows);
+  if (r != GAME_OK) return r;
+  fill_report(v, rows, rmse, accuracy, completeness, contamination);
+  return GAME_OK;
+}
+
+extern "C" game_status game_get_best(game_ctx* c, float* genes, int32_t cap, double* train_fitness,
+                                     double* test_rmse, double* test_accuracy) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  if (genes && cap < c->s.n_genes)
+    return fail(c, GAME_ERR_INVALID_ARG, "cap %d < n_genes %d", cap, c->s.n_genes);
+  cudaSetDevice(c->dev);
+  DevState hs;
+  CUDA_OK(c, cudaMemcpyAsync(&hs, c->d_state, sizeof(hs), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  if (!hs.evaluated) return fail(c, GAME_ERR_STATE, "no evaluated population yet");
+  int best = 0;
+  CUDA_OK(c, cudaMemcpyAsync(&best, c->d_rank, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  const float* row = c->p.g32[hs.cur] + (size_t)best * c->s.kstride;
+  CUDA_OK(c, cudaMemcpyAsync(c->d_genes, row, sizeof(float) * c->s.n_genes, cudaMemcpyDeviceToDevice, c->st));
+  if (genes)
+    CUDA_OK(c, cudaMemcpyAsync(genes, c->d_genes, sizeof(float) * c->s.n_genes, cudaMemcpyDeviceToHost, c->st));
+  if (train_fitness) {
+    CUDA_OK(c, cudaMemcpyAsync(train_fitness, c->d_fit + best, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  }
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  if (test_rmse || test_accuracy) {
+    double v[5];
+    long long rows = 0;
+    game_status r = score(c, nullptr, 1, v, &rows);
+    if (r != GAME_OK) return r;
+    fill_report(v, rows, test_rmse, test_accuracy, nullptr, nullptr);
+  }
+  return GAME_OK;
+}
+
+extern "C" game_status game_get_state(game_ctx* c, int64_t* generation, int32_t* stopped) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  cudaSetDevice(c->dev);
+  DevState hs;
+  CUDA_OK(c, cudaMemcpyAsync(&hs, c->d_state, sizeof(hs), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  if (generation) *generation = hs.gen;
+  if (stopped) *stopped = hs.stopped;
+  return GAME_OK;
+}
+
+extern "C" game_status game_set_timing(game_ctx* c, int32_t enabled) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  c->timing_on = enabled != 0;
+  return GAME_OK;
+}
+
+extern "C" game_status game_get_timing(game_ctx* c, game_timing* out) {
+  if (!c || !out) return fail(c, GAME_ERR_INVALID_ARG, "ctx and out must be non-NULL");
+  *out = c->timing;
+  out->engine = c->engine;
+  return GAME_OK;
+}

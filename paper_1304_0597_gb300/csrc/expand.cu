@@ -1,0 +1,180 @@
+// Expansion matrix P: every feature of every pattern expanded once into its
+// polynomial sequence and kept on the device for the whole run.
+//
+// Paper Section 2, eq.1 (per-feature sequence a_1 g(f_i) + ... + a_d g^d(f_i),
+// with g^j the j-th member of the basis, eq.9), eq.8 / eq.9 (polytrigo:
+// cos(m x), sin(m x), m = 1..d).  Section 4.1 computes the sines and cosines in
+// advance and reuses them every iteration, which is what this kernel does; the
+// bias a_0 multiplies a column of ones that is never stored (its gene is added
+// in the fitness epilogue).
+//
+// Values are generated in float64 by recurrences (Chebyshev: T_{k+1} = 2x T_k -
+// T_{k-1}; trig: angle addition from one sincos(x)), rounded once to float32,
+// then stored in the precision of the run:
+//   FP32: two fp16 planes, hi = fp16(v), lo = fp16(v - hi)  (v = hi + lo to ~22 bits)
+//   BF16: bf16(v / s_g), s_g = max_k |P[k,g]|          (per-column scale)
+//   FP8 : e4m3(v / s_g), s_g = max_k |P[k,g]| / 448
+#include "game_internal.h"
+
+namespace game {
+
+// Calls emit(b, v) for the bd basis values of one feature value x.
+template <typename Emit>
+__device__ __forceinline__ void basis_values(int basis, int d, double x, Emit emit) {
+  if (basis == GAME_CHEBYSHEV) {
+    double tm = 1.0, t = x;
+    for (int b = 0; b < d; ++b) {
+      emit(b, t);
+      const double tn = 2.0 * x * t - tm;
+      tm = t;
+      t = tn;
+    }
+  } else {
+    double s1, c1;
+    sincos(x, &s1, &c1);
+    double c = c1, s = s1;
+    for (int k = 0; k < d; ++k) {
+      emit(k, c);
+      emit(d + k, s);
+      const double cn = c * c1 - s * s1;
+      const double sn = s * c1 + c * s1;
+      c = cn;
+      s = sn;
+    }
+  }
+}
+
+struct ExpArgs {
+  const float* X;
+  long long n;
+  int F, d, basis, bd, kb, kp, precision;
+  void* p0;
+  void* p1;
+  const float* colscale;
+  unsigned int* colmax_bits;
+};
+
+__global__ void expand_colmax_kernel(ExpArgs a) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n * a.F) return;
+  const int f = (int)(i % a.F);
+  const double x = (double)a.X[i];
+  unsigned int* cm = a.colmax_bits + f * a.bd;
+  basis_values(a.basis, a.d, x, [&](int b, double v) {
+    atomicMax(cm + b, __float_as_uint(fabsf((float)v)));
+  });
+}
+
+__global__ void expand_scale_kernel(const unsigned int* colmax_bits, float* colscale, int kb,
+                                    int kp, float qmax) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= kp) return;
+  const float m = c < kb ? __uint_as_float(colmax_bits[c]) : 0.0f;
+  colscale[c] = m > 0.0f ? m / qmax : 1.0f;
+}
+
+__global__ void expand_kernel(ExpArgs a) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n * a.F) return;
+  const long long k = i / a.F;
+  const int f = (int)(i % a.F);
+  const double x = (double)a.X[i];
+  const long long row = k * a.kp;
+  const int col0 = f * a.bd;
+  if (a.precision == GAME_FP32) {
+    __half* hi = (__half*)a.p0 + row + col0;
+    __half* lo = (__half*)a.p1 + row + col0;
+    basis_values(a.basis, a.d, x, [&](int b, double v) {
+      const float v32 = (float)v;
+      const __half h = __float2half_rn(v32);
+      hi[b] = h;
+      lo[b] = __float2half_rn(__fsub_rn(v32, __half2float(h)));
+    });
+    if (f == a.F - 1)
+      for (int c = a.kb; c < a.kp; ++c) {
+        ((__half*)a.p0)[row + c] = __float2half_rn(0.0f);
+        ((__half*)a.p1)[row + c] = __float2half_rn(0.0f);
+      }
+  } else if (a.precision == GAME_BF16) {
+    __nv_bfloat16* q = (__nv_bfloat16*)a.p0 + row + col0;
+    const float* sc = a.colscale + col0;
+    basis_values(a.basis, a.d, x, [&](int b, double v) {
+      q[b] = __float2bfloat16_rn((float)v / sc[b]);
+    });
+    if (f == a.F - 1)
+      for (int c = a.kb; c < a.kp; ++c) ((__nv_bfloat16*)a.p0)[row + c] = __float2bfloat16_rn(0.0f);
+  } else {
+    __nv_fp8_e4m3* q = (__nv_fp8_e4m3*)a.p0 + row + col0;
+    const float* sc = a.colscale + col0;
+    basis_values(a.basis, a.d, x, [&](int b, double v) { q[b] = __nv_fp8_e4m3((float)v / sc[b]); });
+    if (f == a.F - 1)
+      for (int c = a.kb; c < a.kp; ++c) ((__nv_fp8_e4m3*)a.p0)[row + c] = __nv_fp8_e4m3(0.0f);
+  }
+}
+
+__global__ void fill_ones_kernel(float* v, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = 1.0f;
+}
+
+cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax_scratch,
+                          cudaStream_t st) {
+  ExpArgs a;
+  a.X = X;
+  a.n = s.n_patterns;
+  a.F = s.n_features;
+  a.d = s.degree;
+  a.basis = s.basis;
+  a.bd = s.bd;
+  a.kb = s.kb;
+  a.kp = s.kp;
+  a.precision = s.precision;
+  a.p0 = e.p0;
+  a.p1 = e.p1;
+  a.colscale = e.colscale;
+  a.colmax_bits = reinterpret_cast<unsigned int*>(qmax_scratch);
+  const int threads = 256;
+  const long long n = s.n_patterns * s.n_features;
+  const unsigned blocks = (unsigned)((n + threads - 1) / threads);
+  if (s.precision == GAME_FP32) {
+    fill_ones_kernel<<<(s.kp + 255) / 256, 256, 0, st>>>(e.colscale, s.kp);
+  } else {
+    cudaError_t err = cudaMemsetAsync(qmax_scratch, 0, sizeof(float) * s.kp, st);
+    if (err != cudaSuccess) return err;
+    expand_colmax_kernel<<<blocks, threads, 0, st>>>(a);
+    expand_scale_kernel<<<(s.kp + 255) / 256, 256, 0, st>>>(
+        a.colmax_bits, e.colscale, s.kb, s.kp, s.precision == GAME_BF16 ? 1.0f : 448.0f);
+  }
+  expand_kernel<<<blocks, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Float32 reconstruction of rows [row0, row0 + nrows) of P (basis columns).
+__global__ void expand_get_kernel(const void* p0, const void* p1, const float* colscale,
+                                  int precision, int kb, int kp, long long row0, long long nrows,
+                                  float* out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nrows * kb) return;
+  const long long r = row0 + i / kb;
+  const int c = (int)(i % kb);
+  const long long o = r * kp + c;
+  float v;
+  if (precision == GAME_FP32)
+    v = __half2float(((const __half*)p0)[o]) + __half2float(((const __half*)p1)[o]);
+  else if (precision == GAME_BF16)
+    v = __bfloat162float(((const __nv_bfloat16*)p0)[o]) * colscale[c];
+  else
+    v = (float)(((const __nv_fp8_e4m3*)p0)[o]) * colscale[c];
+  out[i] = v;
+}
+
+cudaError_t launch_expand_get(const Shape& s, const ExpDev& e, long long row0, long long nrows,
+                              float* out, cudaStream_t st) {
+  const long long n = nrows * s.kb;
+  if (n == 0) return cudaSuccess;
+  expand_get_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+      e.p0, e.p1, e.colscale, s.precision, s.kb, s.kp, row0, nrows, out);
+  return cudaGetLastError();
+}
+
+}  // namespace game

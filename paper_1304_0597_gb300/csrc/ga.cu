@@ -1,0 +1,581 @@
+// Genetic-algorithm side of the GAME loop on the device: counter-based random
+// numbers, population initialisation, the genetic operators, operand
+// preparation, and the reduce + rank step that closes each generation.
+//
+// Paper Section 4.1 lists the loop: (1) random initial population, (2) fitness
+// and sort of the chromosomes, (3) stop test, (4) genetic operators.  Section 2
+// names the user options (error function, selection, elitism, three random
+// generation criteria); Section 5 gives crossover, mutation, tournament and
+// elitism settings.  The paper keeps selection and the operators on the host;
+// here they run on the device so that a generation never leaves the GPU.
+#include "game_internal.h"
+
+#include <math_constants.h>
+
+namespace game {
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11).  Key = (seed, run);
+// counter = (generation, pair or chromosome, stream, block).  A block gives
+// 4 x 64 bits = 8 words of 32 bits: word w is the low (w even) or high (w odd)
+// half of lane w/2.
+// ---------------------------------------------------------------------------
+struct Key {
+  uint64_t k0, k1;
+};
+
+__device__ __forceinline__ void philox_block(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3,
+                                             Key key, uint64_t out[4]) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+  uint64_t k0 = key.k0, k1 = key.k1;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+__device__ __forceinline__ uint64_t pick_lane(const uint64_t v[4], uint32_t lane) {
+  return lane == 0 ? v[0] : lane == 1 ? v[1] : lane == 2 ? v[2] : v[3];
+}
+
+__device__ __forceinline__ uint32_t philox_word(Key key, uint64_t gen, uint64_t pair,
+                                                uint64_t stream, uint64_t word) {
+  uint64_t v[4];
+  philox_block(gen, pair, stream, word >> 3, key, v);
+  const uint64_t x = pick_lane(v, (uint32_t)(word & 7) >> 1);
+  return (word & 1) ? (uint32_t)(x >> 32) : (uint32_t)x;
+}
+
+// Both words 2w and 2w+1 (one 64-bit lane of one block).
+__device__ __forceinline__ void philox_word_pair(Key key, uint64_t gen, uint64_t pair,
+                                                 uint64_t stream, uint64_t w, uint32_t* a,
+                                                 uint32_t* b) {
+  uint64_t v[4];
+  const uint64_t word = 2 * w;
+  philox_block(gen, pair, stream, word >> 3, key, v);
+  const uint64_t x = pick_lane(v, (uint32_t)(word & 7) >> 1);
+  *a = (uint32_t)x;
+  *b = (uint32_t)(x >> 32);
+}
+
+__device__ __forceinline__ float uniform24(uint32_t w) {
+  return __fmul_rn((float)(w >> 8), 0x1p-24f);
+}
+
+__device__ __forceinline__ int index_draw(uint32_t w, int n) {
+  return (int)(((uint64_t)w * (uint64_t)n) >> 32);
+}
+
+// ---------------------------------------------------------------------------
+// Box-Muller (Box & Muller, 1958) with its own float32 logarithm and cosine,
+// evaluated with explicitly rounded operations (no FMA contraction) so that the
+// draw is the same on every IEEE-754 machine that performs the same steps.
+//   ln u:   u = m 2^e, m in [sqrt(1/2), sqrt(2)); ln m = 2 atanh(s),
+//           s = (m-1)/(m+1), series 2s(1 + s^2/3 + ... + s^10/11).
+//   cos 2 pi v: quadrant q = floor(4v), a = (4v - q) pi/2 in [0, pi/2);
+//           Taylor series of cos a (to a^16) and sin a (to a^15).
+// ---------------------------------------------------------------------------
+__device__ float ln_f32(float u) {
+  const uint32_t b = __float_as_uint(u);
+  int e = (int)((b >> 23) & 0xffu) - 126;
+  float m = __uint_as_float((b & 0x7fffffu) | 0x3f000000u);   // [0.5, 1)
+  if (m < 0x1.6a09e6p-1f) {
+    m = __fmul_rn(m, 2.0f);
+    e -= 1;
+  }
+  const float f = __fsub_rn(m, 1.0f);
+  const float s = __fdiv_rn(f, __fadd_rn(f, 2.0f));
+  const float z = __fmul_rn(s, s);
+  float p = 0x1.745d18p-4f;                       // 1/11
+  p = __fadd_rn(__fmul_rn(p, z), 0x1.c71c72p-4f);  // 1/9
+  p = __fadd_rn(__fmul_rn(p, z), 0x1.24924ap-3f);  // 1/7
+  p = __fadd_rn(__fmul_rn(p, z), 0x1.99999ap-3f);  // 1/5
+  p = __fadd_rn(__fmul_rn(p, z), 0x1.555556p-2f);  // 1/3
+  p = __fadd_rn(__fmul_rn(p, z), 1.0f);
+  float a = __fmul_rn(s, p);
+  a = __fadd_rn(a, a);
+  return __fadd_rn(__fmul_rn((float)e, 0x1.62e430p-1f), a);
+}
+
+__device__ float cos2pi_f32(float v) {
+  const float v4 = __fmul_rn(v, 4.0f);
+  const float q = floorf(v4);
+  const float a = __fmul_rn(__fsub_rn(v4, q), 0x1.921fb6p+0f);
+  const float a2 = __fmul_rn(a, a);
+  float c = 0x1.ae7f3ep-45f;
+  c = __fadd_rn(__fmul_rn(c, a2), -0x1.93974ap-37f);
+  c = __fadd_rn(__fmul_rn(c, a2), 0x1.1eed8ep-29f);
+  c = __fadd_rn(__fmul_rn(c, a2), -0x1.27e4fcp-22f);
+  c = __fadd_rn(__fmul_rn(c, a2), 0x1.a01a02p-16f);
+  c = __fadd_rn(__fmul_rn(c, a2), -0x1.6c16c2p-10f);
+  c = __fadd_rn(__fmul_rn(c, a2), 0x1.555556p-5f);
+  c = __fadd_rn(__fmul_rn(c, a2), -0x1.000000p-1f);
+  c = __fadd_rn(__fmul_rn(c, a2), 1.0f);
+  float s = -0x1.ae7f3ep-41f;
+  s = __fadd_rn(__fmul_rn(s, a2), 0x1.612462p-33f);
+  s = __fadd_rn(__fmul_rn(s, a2), -0x1.ae6456p-26f);
+  s = __fadd_rn(__fmul_rn(s, a2), 0x1.71de3ap-19f);
+  s = __fadd_rn(__fmul_rn(s, a2), -0x1.a01a02p-13f);
+  s = __fadd_rn(__fmul_rn(s, a2), 0x1.111112p-7f);
+  s = __fadd_rn(__fmul_rn(s, a2), -0x1.555556p-3f);
+  s = __fadd_rn(__fmul_rn(s, a2), 1.0f);
+  s = __fmul_rn(a, s);
+  const int qi = (int)q;
+  return qi == 0 ? c : qi == 1 ? -s : qi == 2 ? -c : s;
+}
+
+__device__ __forceinline__ float gauss_f32(uint32_t w0, uint32_t w1) {
+  const float u1 = __fmul_rn((float)((w0 >> 8) + 1u), 0x1p-24f);   // (0, 1]
+  const float u2 = uniform24(w1);                                  // [0, 1)
+  const float r = __fsqrt_rn(__fmul_rn(ln_f32(u1), -2.0f));
+  return __fmul_rn(r, cos2pi_f32(u2));
+}
+
+// ---------------------------------------------------------------------------
+// Initial population (Section 2: pseudo-random in [-1,1], normal in [-1,1],
+// pseudo-random in [0,1]).  One thread per gene.
+// ---------------------------------------------------------------------------
+__global__ void init_population_kernel(int pop, int n_genes, int kstride, int mode, Key key,
+                                       float* __restrict__ g32) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)pop * n_genes) return;
+  const int c = (int)(i / n_genes), g = (int)(i % n_genes);
+  float v;
+  if (mode == GAME_INIT_NORMAL_PM1) {
+    v = 0.0f;
+    for (int r = 0; r < 64; ++r) {
+      uint32_t w0, w1;
+      philox_word_pair(key, 0, (uint64_t)c, kStreamInitNormal,
+                       (uint64_t)r * (uint64_t)n_genes + (uint64_t)g, &w0, &w1);
+      const float x = __fmul_rn(gauss_f32(w0, w1), 0.5f);
+      if (fabsf(x) <= 1.0f) {
+        v = x;
+        break;
+      }
+      if (r == 63) v = fminf(fmaxf(x, -1.0f), 1.0f);
+    }
+  } else {
+    const float u = uniform24(philox_word(key, 0, (uint64_t)c, kStreamInit, (uint64_t)g));
+    v = (mode == GAME_INIT_UNIFORM_01) ? u : __fsub_rn(__fmul_rn(u, 2.0f), 1.0f);
+  }
+  g32[(long long)c * kstride + g] = v;
+}
+
+cudaError_t launch_init_population(const Shape& s, int init_mode, uint64_t seed, uint64_t run,
+                                   float* g32, cudaStream_t st) {
+  const long long n = (long long)s.pop * s.n_genes;
+  const int threads = 256;
+  init_population_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, st>>>(
+      s.pop, s.n_genes, s.kstride, init_mode, Key{seed, run}, g32);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Genetic operators: one warp per child pair (plus one warp per elite slot).
+// ---------------------------------------------------------------------------
+struct BreedArgs {
+  const float* g32_0;
+  const float* g32_1;
+  float* out_0;
+  float* out_1;
+  const double* fit;
+  const int* rank;
+  DevState* state;
+  Key key;
+  int pop, n_genes, kstride;
+  int tournament_k, elitism, elite_mode, clamp;
+  float p_c, p_m, sigma;
+  int allow, in_evolve;
+};
+
+__device__ __forceinline__ double fit_key(const double* fit, int i) {
+  const double f = fit[i];
+  return isnan(f) ? CUDART_INF : f;
+}
+
+__device__ __forceinline__ bool better(double fa, int ia, double fb, int ib) {
+  return fa < fb || (fa == fb && ia < ib);
+}
+
+__device__ __forceinline__ float mutate_gene(float v, Key key, uint64_t gen, uint64_t pair,
+                                             uint64_t w, float p_m, float sigma, int clamp) {
+  const float u = uniform24(philox_word(key, gen, pair, kStreamMutMask, w));
+  if (u < p_m) {
+    uint32_t a, b;
+    philox_word_pair(key, gen, pair, kStreamMutNormal, w, &a, &b);
+    v = __fadd_rn(v, __fmul_rn(sigma, gauss_f32(a, b)));
+    if (clamp) v = fminf(fmaxf(v, -1.0f), 1.0f);
+  }
+  return v;
+}
+
+__global__ void breed_kernel(BreedArgs a) {
+  DevState* st = a.state;
+  const int decision = a.allow && st->evaluated && !(a.in_evolve && st->stopped);
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->bred = decision;
+  if (!decision) return;
+  const int cur = st->cur;
+  const uint64_t gen = (uint64_t)st->gen;
+  const float* __restrict__ G = cur ? a.g32_1 : a.g32_0;
+  float* __restrict__ out = cur ? a.out_0 : a.out_1;
+  const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int e = min(a.elitism, a.pop);
+  const int n_child = a.pop - e;
+  const int n_pairs = (n_child + 1) / 2;
+  const int K = a.n_genes;
+
+  if (warp < n_pairs) {
+    const uint64_t j = (uint64_t)warp;
+    // Two tournaments of k draws with replacement; winner = min (fitness, index).
+    double bf0 = CUDART_INF, bf1 = CUDART_INF;
+    int bi0 = 0x7fffffff, bi1 = 0x7fffffff;
+    for (int i = lane; i < 2 * a.tournament_k; i += 32) {
+      const int idx = index_draw(philox_word(a.key, gen, j, kStreamTournament, (uint64_t)i), a.pop);
+      const double f = fit_key(a.fit, idx);
+      if (i < a.tournament_k) {
+        if (better(f, idx, bf0, bi0)) { bf0 = f; bi0 = idx; }
+      } else {
+        if (better(f, idx, bf1, bi1)) { bf1 = f; bi1 = idx; }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double f0 = __shfl_xor_sync(0xffffffffu, bf0, o);
+      const int i0 = __shfl_xor_sync(0xffffffffu, bi0, o);
+      const double f1 = __shfl_xor_sync(0xffffffffu, bf1, o);
+      const int i1 = __shfl_xor_sync(0xffffffffu, bi1, o);
+      if (better(f0, i0, bf0, bi0)) { bf0 = f0; bi0 = i0; }
+      if (better(f1, i1, bf1, bi1)) { bf1 = f1; bi1 = i1; }
+    }
+    const int p1 = bi0, p2 = bi1;
+    // Single-point crossover: words 0 (decision) and 1 (cut in [1, K-1]).
+    const uint32_t wc = philox_word(a.key, gen, j, kStreamCrossover, 0);
+    const uint32_t wk = philox_word(a.key, gen, j, kStreamCrossover, 1);
+    int cut = K;
+    if (uniform24(wc) < a.p_c && K >= 2) cut = 1 + index_draw(wk, K - 1);
+    const float* __restrict__ r1 = G + (long long)p1 * a.kstride;
+    const float* __restrict__ r2 = G + (long long)p2 * a.kstride;
+    const int slot_a = e + 2 * warp, slot_b = slot_a + 1;
+    float* oa = out + (long long)slot_a * a.kstride;
+    float* ob = out + (long long)slot_b * a.kstride;
+    const bool has_b = slot_b < a.pop;
+    for (int g = lane; g < K; g += 32) {
+      const bool head = g < cut;
+      float va = head ? r1[g] : r2[g];
+      float vb = head ? r2[g] : r1[g];
+      va = mutate_gene(va, a.key, gen, j, (uint64_t)g, a.p_m, a.sigma, a.clamp);
+      oa[g] = va;
+      if (has_b) {
+        vb = mutate_gene(vb, a.key, gen, j, (uint64_t)K + (uint64_t)g, a.p_m, a.sigma, a.clamp);
+        ob[g] = vb;
+      }
+    }
+  } else if (warp < n_pairs + e) {
+    const int slot = warp - n_pairs;
+    const int src = (a.elite_mode == GAME_ELITE_TOP) ? a.rank[slot] : a.rank[0];
+    const float* __restrict__ r = G + (long long)src * a.kstride;
+    float* o = out + (long long)slot * a.kstride;
+    for (int g = lane; g < K; g += 32) o[g] = r[g];
+  }
+}
+
+cudaError_t launch_breed(const Shape& s, const game_config& cfg, const PopDev& p,
+                         const double* fit, const int* rank, DevState* state, int allow,
+                         cudaStream_t st) {
+  BreedArgs a;
+  a.g32_0 = p.g32[0];
+  a.g32_1 = p.g32[1];
+  a.out_0 = p.g32[0];
+  a.out_1 = p.g32[1];
+  a.fit = fit;
+  a.rank = rank;
+  a.state = state;
+  a.key = Key{cfg.seed, cfg.run};
+  a.pop = s.pop;
+  a.n_genes = s.n_genes;
+  a.kstride = s.kstride;
+  a.tournament_k = cfg.tournament_k;
+  a.elitism = cfg.elitism;
+  a.elite_mode = cfg.elite_mode;
+  a.clamp = cfg.clamp_genes;
+  a.p_c = cfg.p_crossover;
+  a.p_m = cfg.p_mutation;
+  a.sigma = cfg.sigma_mutation;
+  a.allow = allow & 1;
+  a.in_evolve = (allow >> 1) & 1;
+  const int e = cfg.elitism < s.pop ? cfg.elitism : s.pop;
+  const int warps = (s.pop - e + 1) / 2 + e;
+  const int threads = 256;
+  const int blocks = allow & 1 ? (warps * 32 + threads - 1) / threads : 1;
+  breed_kernel<<<blocks > 0 ? blocks : 1, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Operand preparation: basis genes of the population under evaluation, in the
+// float32 layout of the SIMT path and in the tensor-core planes of the chosen
+// precision.  One warp per chromosome row (rows >= pop are zero).
+//   FP32: plane hi = fp16(g), lo = fp16(g - hi): g = hi + lo to ~22 bits.
+//   BF16 / FP8: g' = g * s_col / r_c with r_c = max_col |g * s_col| / qmax;
+//   hi = q(g'), lo = q(g' - hi); the contraction result is scaled back by r_c.
+// ---------------------------------------------------------------------------
+struct PrepArgs {
+  const float* g32_0;
+  const float* g32_1;
+  const float* colscale;
+  float* geval;
+  float* bias;
+  void* ghi;
+  void* glo;
+  float* rscale;
+  const DevState* state;
+  int pop, pop_pad, kb, kp, kstride, precision, use_bred_flag, in_evolve;
+};
+
+__global__ void prepare_kernel(PrepArgs a) {
+  const DevState* st = a.state;
+  if (a.in_evolve && st->stopped) return;
+  const int row = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= a.pop_pad) return;
+  int buf = st->cur;
+  if (a.use_bred_flag && st->bred) buf ^= 1;
+  const float* G = (buf ? a.g32_1 : a.g32_0) + (long long)row * a.kstride;
+  const bool live = row < a.pop;
+  float* ge = a.geval + (long long)row * a.kp;
+  if (lane == 0) a.bias[row] = live ? G[0] : 0.0f;
+  if (a.precision == GAME_FP32) {
+    __half* hi = (__half*)a.ghi + (long long)row * a.kp;
+    __half* lo = (__half*)a.glo + (long long)row * a.kp;
+    for (int c = lane; c < a.kp; c += 32) {
+      const float v = (live && c < a.kb) ? G[1 + c] : 0.0f;
+      ge[c] = v;
+      const __half h = __float2half_rn(v);
+      hi[c] = h;
+      lo[c] = __float2half_rn(__fsub_rn(v, __half2float(h)));
+    }
+    if (lane == 0) a.rscale[row] = 1.0f;
+    return;
+  }
+  const float qmax = a.precision == GAME_BF16 ? 1.0f : 448.0f;
+  float m = 0.0f;
+  for (int c = lane; c < a.kb; c += 32)
+    if (live) m = fmaxf(m, fabsf(G[1 + c] * a.colscale[c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const float r = m > 0.0f ? m / qmax : 1.0f;
+  if (lane == 0) a.rscale[row] = r;
+  for (int c = lane; c < a.kp; c += 32) {
+    const float v = (live && c < a.kb) ? G[1 + c] : 0.0f;
+    ge[c] = v;
+    const float w = (c < a.kb) ? (v * a.colscale[c]) / r : 0.0f;
+    if (a.precision == GAME_BF16) {
+      __nv_bfloat16* hi = (__nv_bfloat16*)a.ghi + (long long)row * a.kp;
+      __nv_bfloat16* lo = (__nv_bfloat16*)a.glo + (long long)row * a.kp;
+      const __nv_bfloat16 h = __float2bfloat16_rn(w);
+      hi[c] = h;
+      lo[c] = __float2bfloat16_rn(w - __bfloat162float(h));
+    } else {
+      __nv_fp8_e4m3* hi = (__nv_fp8_e4m3*)a.ghi + (long long)row * a.kp;
+      __nv_fp8_e4m3* lo = (__nv_fp8_e4m3*)a.glo + (long long)row * a.kp;
+      const __nv_fp8_e4m3 h(w);
+      hi[c] = h;
+      lo[c] = __nv_fp8_e4m3(w - (float)h);
+    }
+  }
+}
+
+cudaError_t launch_prepare(const Shape& s, const PopDev& p, const ExpDev& e, DevState* state,
+                           int use_bred_flag, cudaStream_t st) {
+  PrepArgs a;
+  a.g32_0 = p.g32[0];
+  a.g32_1 = p.g32[1];
+  a.colscale = e.colscale;
+  a.geval = p.geval;
+  a.bias = p.bias;
+  a.ghi = p.ghi;
+  a.glo = p.glo;
+  a.rscale = p.rscale;
+  a.state = state;
+  a.pop = s.pop;
+  a.pop_pad = s.pop_pad;
+  a.kb = s.kb;
+  a.kp = s.kp;
+  a.kstride = s.kstride;
+  a.precision = s.precision;
+  a.use_bred_flag = use_bred_flag & 1;
+  a.in_evolve = (use_bred_flag >> 1) & 1;
+  const int threads = 256;
+  const int blocks = (s.pop_pad * 32 + threads - 1) / threads;
+  prepare_kernel<<<blocks, threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Reduce + rank (one CTA): per-chromosome sums of the fitness partials in a
+// fixed order (float64), fitness (eq.4 / eq.5 / eq.10), then a bitonic sort of
+// (fitness, index) and the end-of-generation state update with the stop test
+// (Section 4.1 steps 2-3).
+// ---------------------------------------------------------------------------
+struct RankArgs {
+  const double* partial;
+  double* fit;
+  int* rank;
+  DevState* state;
+  int n_part, pop, pop_pad, n2, error, mode, in_evolve;
+  double inv_m, stop_error;
+};
+
+__global__ void __launch_bounds__(1024) reduce_rank_kernel(RankArgs a) {
+  DevState* st = a.state;
+  if (a.in_evolve && st->stopped) return;
+  extern __shared__ unsigned char smem_raw[];
+  double* key = reinterpret_cast<double*>(smem_raw);
+  int* idx = reinterpret_cast<int*>(key + a.n2);
+  const int tid = threadIdx.x;
+  for (int c = tid; c < a.n2; c += blockDim.x) {
+    double f = CUDART_INF;
+    if (c < a.pop) {
+      if (a.mode == kRankEvaluate) {
+        double sse = 0.0;
+        for (int b = 0; b < a.n_part; ++b) sse += a.partial[(long long)b * a.pop_pad + c];
+        const double mse = sse * a.inv_m;
+        f = (a.error == GAME_RMSE) ? sqrt(mse) : mse;
+        a.fit[c] = f;
+      } else {
+        f = a.fit[c];
+      }
+      if (isnan(f)) f = CUDART_INF;
+    }
+    key[c] = f;
+    idx[c] = c < a.pop ? c : 0x7fffffff;
+  }
+  __syncthreads();
+  for (int k = 2; k <= a.n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < a.n2; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const bool lt = key[l] < key[i] || (key[l] == key[i] && idx[l] < idx[i]);
+          if (lt == up) {
+            const double tk = key[i];
+            key[i] = key[l];
+            key[l] = tk;
+            const int ti = idx[i];
+            idx[i] = idx[l];
+            idx[l] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int c = tid; c < a.pop; c += blockDim.x) a.rank[c] = idx[c];
+  if (tid == 0) {
+    st->best = key[0];
+    if (a.mode == kRankEvaluate) {
+      if (st->bred) {
+        st->cur ^= 1;
+        st->gen += 1;
+      }
+      st->bred = 0;
+      st->gens_run += 1;
+      if (key[0] <= a.stop_error) st->stopped = 1;
+    }
+    st->evaluated = 1;
+  }
+}
+
+static int next_pow2(int n) {
+  int p = 2;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+cudaError_t launch_reduce_rank(const Shape& s, const game_config& cfg, const double* partial,
+                               int n_part, double* fit, int* rank, DevState* state, int mode,
+                               cudaStream_t st) {
+  RankArgs a;
+  a.partial = partial;
+  a.fit = fit;
+  a.rank = rank;
+  a.state = state;
+  a.n_part = n_part;
+  a.pop = s.pop;
+  a.pop_pad = s.pop_pad;
+  a.n2 = next_pow2(s.pop);
+  a.error = cfg.error;
+  a.mode = mode & 0xff;
+  a.in_evolve = (mode >> 8) & 1;
+  a.inv_m = 1.0 / (double)s.n_train;
+  a.stop_error = cfg.stop_error;
+  const size_t smem = (size_t)a.n2 * (sizeof(double) + sizeof(int));
+  const int threads = a.n2 < 1024 ? (a.n2 < 32 ? 32 : a.n2) : 1024;
+  reduce_rank_kernel<<<1, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t ga_init_attributes() {
+  return cudaFuncSetAttribute(reduce_rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              8192 * (int)(sizeof(double) + sizeof(int)));
+}
+
+// ---------------------------------------------------------------------------
+// Single-thread state transitions.
+// ---------------------------------------------------------------------------
+__global__ void state_kernel(DevState* st, int op) {
+  switch (op) {
+    case kStateReset:
+      st->gen = 0;
+      st->cur = 0;
+      st->evaluated = 0;
+      st->bred = 0;
+      st->stopped = 0;
+      st->gens_run = 0;
+      st->status = 0;
+      st->best = CUDART_INF;
+      break;
+    case kStatePopulationSet:
+      st->evaluated = 0;
+      st->bred = 0;
+      st->stopped = 0;
+      break;
+    case kStateBeginEvolve:
+      st->gens_run = 0;
+      break;
+    case kStateAfterBreed:
+      if (st->bred) {
+        st->cur ^= 1;
+        st->gen += 1;
+      }
+      st->bred = 0;
+      st->evaluated = 0;
+      break;
+    default:
+      break;
+  }
+}
+
+cudaError_t launch_state_op(DevState* state, int op, cudaStream_t st) {
+  state_kernel<<<1, 1, 0, st>>>(state, op);
+  return cudaGetLastError();
+}
+
+}  // namespace game

@@ -1,0 +1,129 @@
+// Internal declarations shared by the CUDA translation units of libgame.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/game.h"
+
+namespace game {
+
+// Philox stream ids (counter word 2).
+enum : uint32_t {
+  kStreamTournament = 0,
+  kStreamCrossover = 1,
+  kStreamMutMask = 2,
+  kStreamMutNormal = 3,
+  kStreamInit = 4,
+  kStreamInitNormal = 5,
+};
+
+// Device-resident loop state.  Only single-thread "state" kernels and the
+// single-CTA reduce/rank kernel write it, so every multi-CTA kernel of a
+// generation reads one consistent value.
+struct DevState {
+  long long gen;      // breeding steps applied so far (Philox counter word 0)
+  int cur;            // population buffer (0/1) holding the current population
+  int evaluated;      // the current population has a fitness vector
+  int bred;           // the breed kernel of this generation produced buf[cur^1]
+  int stopped;        // best fitness reached stop_error
+  int gens_run;       // populations evaluated since the last reset
+  int status;         // device-side error code (0 ok)
+  double best;        // best fitness of the last evaluated population
+};
+
+// Everything a kernel needs to know about the problem and population shapes.
+struct Shape {
+  long long n_patterns;   // NP
+  long long n_train;      // training rows (the first rows of P)
+  int n_features;         // F
+  int degree;             // d
+  int basis;              // GAME_CHEBYSHEV | GAME_TRIG
+  int bd;                 // basis columns per feature: B*d
+  int kb;                 // basis columns in total: F*B*d  (= n_genes - 1)
+  int kp;                 // stored columns of P / of the gene planes (kb padded)
+  int n_genes;            // kb + 1
+  int kstride;            // row stride of the float32 gene buffers (n_genes padded to 4)
+  int pop;                // population size
+  int pop_pad;            // pop padded to the 128-row MMA tile
+  int precision;          // GAME_FP32 | GAME_BF16 | GAME_FP8
+};
+
+// Population double buffer plus the operand planes of the population being evaluated.
+struct PopDev {
+  float* g32[2];          // [pop_pad x kstride] master genes (float32)
+  float* geval;           // [pop_pad x kp] basis genes of the population under evaluation
+  float* bias;            // [pop_pad] gene 0 of the population under evaluation
+  void* ghi;              // [pop_pad x kp] MMA operand plane (hi part)
+  void* glo;              // [pop_pad x kp] MMA operand plane (lo part)
+  float* rscale;          // [pop_pad] per-chromosome scale of the planes (1 for FP32)
+};
+
+// Expansion matrix P (basis columns only; the bias column of ones is implicit).
+struct ExpDev {
+  void* p0;               // FP32: fp16 hi plane; BF16: bf16 values; FP8: e4m3 values
+  void* p1;               // FP32: fp16 lo plane; otherwise unused
+  float* colscale;        // [kp] per-column scale s_g of quantised P (1 for FP32)
+  float* t;               // [n_patterns padded to 256] targets
+};
+
+struct Fitness {
+  int error;              // GAME_RMSE ...
+  int activation;         // GAME_TANH | GAME_LINEAR
+  float tmse_R;
+  int pm1_targets;        // every training target is +-1 (enables the fused tanh form)
+};
+
+// ---- launchers (each returns cudaGetLastError of its launch) ----------------
+
+cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax_scratch,
+                          cudaStream_t st);
+cudaError_t launch_expand_get(const Shape& s, const ExpDev& e, long long row0, long long nrows,
+                              float* out, cudaStream_t st);
+bool targets_pm1(const float* t_host, long long n);
+
+cudaError_t launch_init_population(const Shape& s, int init_mode, uint64_t seed, uint64_t run,
+                                   float* g32, cudaStream_t st);
+cudaError_t launch_breed(const Shape& s, const game_config& cfg, const PopDev& p,
+                         const double* fit, const int* rank, DevState* state, int allow,
+                         cudaStream_t st);
+cudaError_t launch_prepare(const Shape& s, const PopDev& p, const ExpDev& e, DevState* state,
+                           int use_bred_flag, cudaStream_t st);
+cudaError_t launch_reduce_rank(const Shape& s, const game_config& cfg, const double* partial,
+                               int n_part, double* fit, int* rank, DevState* state,
+                               int mode, cudaStream_t st);
+cudaError_t launch_state_op(DevState* state, int op, cudaStream_t st);
+cudaError_t ga_init_attributes();   // once per device, outside stream capture
+
+// State ops.
+enum : int {
+  kStateReset = 0,          // gen=0, cur=0, evaluated=0, bred=0, stopped=0, gens_run=0
+  kStatePopulationSet = 1,  // evaluated=0, bred=0, stopped=0
+  kStateBeginEvolve = 2,    // gens_run=0
+  kStateAfterBreed = 3,     // if bred: cur^=1, gen++ ; evaluated=0, bred=0
+};
+
+// reduce_rank modes
+enum : int {
+  kRankEvaluate = 0,        // reduce partials -> fitness, sort, update state
+  kRankSortOnly = 1,        // sort the given fitness vector, mark evaluated
+};
+
+// SIMT fitness (FFMA) over the training rows: partial sums [n_part x pop_pad].
+int simt_partials(const Shape& s, int n_sm);
+cudaError_t launch_fitness_simt(const Shape& s, const Fitness& f, const PopDev& p,
+                                const ExpDev& e, double* partial, int n_part,
+                                const DevState* state, cudaStream_t st);
+
+// Float64 score of one chromosome on rows [r0, r1).
+cudaError_t launch_score(const Shape& s, const Fitness& f, const ExpDev& e, const float* genes,
+                         long long r0, long long r1, double* block_out, int n_blocks,
+                         double* result, cudaStream_t st);
+int score_blocks(long long rows, int n_sm);
+
+}  // namespace game

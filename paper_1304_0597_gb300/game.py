@@ -1,0 +1,226 @@
+"""ctypes binding of libgame.so (the C ABI declared in include/game.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Host arrays are numpy; device arrays are torch CUDA tensors (passed by
+``data_ptr()`` with ``device_ptrs=1``).  Importing this module loads the
+in-tree ``_lib/libgame.so`` and raises if it is missing.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libgame.so")
+
+GAME_OK = 0
+STATUS = {0: "OK", -1: "INVALID_ARG", -2: "STATE", -3: "OOM", -4: "CUDA", -5: "NO_DEVICE",
+          -6: "TIMEOUT", -7: "NUMERIC", -8: "UNSUPPORTED"}
+
+CHEBYSHEV, TRIG = 0, 1
+RMSE, MSE, TMSE, TMSE_SQ = 0, 1, 2, 3
+TANH, LINEAR = 0, 1
+INIT_UNIFORM_PM1, INIT_NORMAL_PM1, INIT_UNIFORM_01 = 0, 1, 2
+ELITE_TOP, ELITE_COPIES = 0, 1
+FP32, BF16, FP8 = 0, 1, 2
+ENGINE_AUTO, ENGINE_TCGEN05, ENGINE_SIMT = 0, 1, 2
+
+
+class GameConfig(C.Structure):
+    _fields_ = [
+        ("basis", C.c_int32), ("degree", C.c_int32), ("pop", C.c_int32),
+        ("tournament_k", C.c_int32), ("p_crossover", C.c_float), ("p_mutation", C.c_float),
+        ("sigma_mutation", C.c_float), ("elitism", C.c_int32), ("elite_mode", C.c_int32),
+        ("error", C.c_int32), ("tmse_R", C.c_float), ("activation", C.c_int32),
+        ("init", C.c_int32), ("clamp_genes", C.c_int32), ("stop_error", C.c_double),
+        ("seed", C.c_uint64), ("run", C.c_uint64), ("precision", C.c_int32),
+        ("elite_rescore", C.c_int32), ("surrogate_pool", C.c_int32), ("engine", C.c_int32),
+        ("device", C.c_int32), ("stream", C.c_void_p),
+    ]
+
+
+class GameTiming(C.Structure):
+    _fields_ = [("ms_breed", C.c_double), ("ms_fitness", C.c_double), ("ms_rank", C.c_double),
+                ("ms_total", C.c_double), ("generations", C.c_int32), ("engine", C.c_int32)]
+
+
+class GameError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1304_0597_gb300.build "
+                          "(there is no non-CUDA fallback)")
+    lib = C.CDLL(LIB_PATH)
+    P, I32, I64, D, F = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_float
+    sig = {
+        "game_config_default": (None, [C.POINTER(GameConfig)]),
+        "game_create": (I32, [C.POINTER(GameConfig), C.POINTER(P)]),
+        "game_set_data": (I32, [P, P, P, I64, I32, I64, I32]),
+        "game_evolve": (I32, [P, I32, C.POINTER(I32)]),
+        "game_get_best": (I32, [P, P, I32, C.POINTER(D), C.POINTER(D), C.POINTER(D)]),
+        "game_n_genes": (I32, [P]),
+        "game_last_error": (C.c_char_p, [P]),
+        "game_destroy": (None, [P]),
+        "game_set_population": (I32, [P, P, I32, I32, I32]),
+        "game_get_population": (I32, [P, P, I32, I32]),
+        "game_evaluate": (I32, [P, P, P]),
+        "game_breed": (I32, [P, P]),
+        "game_get_expansion": (I32, [P, P, I64, I64]),
+        "game_score": (I32, [P, P, I32, C.POINTER(D), C.POINTER(D), C.POINTER(D), C.POINTER(D)]),
+        "game_get_state": (I32, [P, C.POINTER(I64), C.POINTER(I32)]),
+        "game_get_timing": (I32, [P, C.POINTER(GameTiming)]),
+        "game_set_timing": (I32, [P, I32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C entry points this binding expects libgame.so to export."""
+    return [n for n in dir(lib) if n.startswith("game_")]
+
+
+def default_config(**overrides) -> GameConfig:
+    cfg = GameConfig()
+    lib.game_config_default(C.byref(cfg))
+    for k, v in overrides.items():
+        if k == "stream" and v is not None and not isinstance(v, int):
+            v = int(v)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _ptr(a) -> tuple[int, int, object]:
+    """(address, device flag, keep-alive) for a numpy array or a torch tensor."""
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if a.is_cuda:
+            if not a.is_contiguous():
+                raise ValueError("device tensors must be contiguous")
+            return a.data_ptr(), 1, a
+        a = a.detach().cpu().numpy()
+    arr = np.ascontiguousarray(a, dtype=np.float32)
+    return arr.ctypes.data, 0, arr
+
+
+class Game:
+    """One GAME training context (``game_ctx``)."""
+
+    def __init__(self, config: GameConfig | None = None, **overrides):
+        cfg = config if config is not None else default_config()
+        for k, v in overrides.items():
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        h = C.c_void_p()
+        self._check(lib.game_create(C.byref(cfg), C.byref(h)), None)
+        self.h = h
+
+    def _check(self, status: int, h) -> None:
+        if status != GAME_OK:
+            raise GameError(status, lib.game_last_error(h).decode())
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lib.game_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def n_genes(self) -> int:
+        return lib.game_n_genes(self.h)
+
+    @property
+    def pop(self) -> int:
+        return self.cfg.pop
+
+    def set_data(self, X, t, n_train: int) -> None:
+        xp, xd, kx = _ptr(X)
+        tp, td, kt = _ptr(t)
+        if xd != td:
+            raise ValueError("X and t must both be host arrays or both device tensors")
+        n, F = X.shape
+        self._check(lib.game_set_data(self.h, xp, tp, n, F, n_train, xd), self.h)
+
+    def evolve(self, generations: int) -> int:
+        run = C.c_int32(0)
+        self._check(lib.game_evolve(self.h, generations, C.byref(run)), self.h)
+        return run.value
+
+    def best(self):
+        g = np.empty(self.n_genes, dtype=np.float32)
+        fit, rm, acc = C.c_double(), C.c_double(), C.c_double()
+        self._check(lib.game_get_best(self.h, g.ctypes.data, g.size, C.byref(fit), C.byref(rm),
+                                      C.byref(acc)), self.h)
+        return g, fit.value, rm.value, acc.value
+
+    def set_population(self, G) -> None:
+        gp, gd, keep = _ptr(G)
+        self._check(lib.game_set_population(self.h, gp, self.pop, self.n_genes, gd), self.h)
+
+    def population(self) -> np.ndarray:
+        G = np.empty((self.pop, self.n_genes), dtype=np.float32)
+        self._check(lib.game_get_population(self.h, G.ctypes.data, self.pop, self.n_genes),
+                    self.h)
+        return G
+
+    def evaluate(self):
+        fit = np.empty(self.pop, dtype=np.float64)
+        rank = np.empty(self.pop, dtype=np.int32)
+        self._check(lib.game_evaluate(self.h, fit.ctypes.data, rank.ctypes.data), self.h)
+        return fit, rank
+
+    def breed(self, fitness=None) -> None:
+        if fitness is None:
+            self._check(lib.game_breed(self.h, None), self.h)
+        else:
+            f = np.ascontiguousarray(fitness, dtype=np.float64)
+            self._check(lib.game_breed(self.h, f.ctypes.data), self.h)
+
+    def expansion(self, row0: int, n_rows: int) -> np.ndarray:
+        out = np.empty((n_rows, self.n_genes - 1), dtype=np.float32)
+        self._check(lib.game_get_expansion(self.h, out.ctypes.data, row0, n_rows), self.h)
+        return out
+
+    def score(self, genes, split: int) -> dict:
+        g = np.ascontiguousarray(genes, dtype=np.float32)
+        v = [C.c_double() for _ in range(4)]
+        self._check(lib.game_score(self.h, g.ctypes.data, split, *[C.byref(x) for x in v]),
+                    self.h)
+        return dict(zip(("rmse", "accuracy", "completeness", "contamination"),
+                        (x.value for x in v)))
+
+    def state(self) -> tuple[int, int]:
+        gen, stopped = C.c_int64(), C.c_int32()
+        self._check(lib.game_get_state(self.h, C.byref(gen), C.byref(stopped)), self.h)
+        return gen.value, stopped.value
+
+    def set_timing(self, enabled: bool) -> None:
+        self._check(lib.game_set_timing(self.h, int(bool(enabled))), self.h)
+
+    def timing(self) -> dict:
+        t = GameTiming()
+        self._check(lib.game_get_timing(self.h, C.byref(t)), self.h)
+        return {f: getattr(t, f) for f, _ in GameTiming._fields_}

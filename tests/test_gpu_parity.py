@@ -1,0 +1,234 @@
+"""GPU path (through the C ABI) against the CPU oracle on identical seeded inputs.
+
+Bars: expansion within 6e-7 absolute (float32 rounding of a float64 value plus
+the two-plane fp16 split, both < 2^-22 relative); FP32 fitness within 1e-5
+relative (the stated tolerance for FP32 fitness); initial population and
+genetic operators bit-for-bit.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import game_oracle as o
+from paper_1304_0597_gb300 import synth
+from tests.gpu_helpers import game_config, lib, make_game, oracle_fitness_chunked
+
+pytestmark = pytest.mark.gpu
+
+FIT_RTOL = 1e-5
+
+
+def _cfg(**kw):
+    base = dict(basis="chebyshev", degree=4, pop=20, tournament_k=3, p_crossover=0.9,
+                p_mutation=0.05, sigma_mutation=0.1, elitism=2, seed=7)
+    base.update(kw)
+    return o.Config(**base)
+
+
+# ------------------------------------------------------------------ expansion
+
+@pytest.mark.parametrize("basis,F,d", [("chebyshev", 7, 4), ("trig", 6, 5), ("chebyshev", 3, 10),
+                                       ("trig", 1, 1)])
+def test_expansion_matches_closed_form(basis, F, d):
+    ds = synth.make_dataset(1537, F, d, basis, seed=3)
+    ocfg = _cfg(basis=basis, degree=d)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    got = g.expansion(0, ds.n_patterns)
+    want = o.expand(ds.X, basis, d)[:, 1:]
+    assert got.shape == want.shape
+    np.testing.assert_allclose(got, want, rtol=0, atol=6e-7)
+
+
+def test_expansion_of_device_inputs_equals_host_inputs():
+    import torch
+    ds = synth.make_dataset(700, 5, 3, seed=4)
+    ocfg = _cfg(degree=3)
+    a = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    b = make_game(ocfg, torch.from_numpy(ds.X).cuda(), torch.from_numpy(ds.t).cuda(), ds.n_train)
+    np.testing.assert_array_equal(a.expansion(0, 700), b.expansion(0, 700))
+
+
+# ------------------------------------------------------------------- fitness
+
+@pytest.mark.parametrize("engine", ["auto", "simt"])
+@pytest.mark.parametrize("shape", [
+    dict(n=2000, F=7, d=4, pop=20, basis="chebyshev"),          # the small plain workload
+    dict(n=5003, F=9, d=5, pop=300, basis="chebyshev"),         # several tiles, ragged tails
+    dict(n=3001, F=6, d=4, pop=129, basis="trig"),              # polytrigo, pop just over a tile
+])
+def test_fitness_matches_oracle(shape, engine):
+    game = lib()
+    ds = synth.make_dataset(shape["n"], shape["F"], shape["d"], shape["basis"], seed=5)
+    ocfg = _cfg(basis=shape["basis"], degree=shape["d"], pop=shape["pop"])
+    eng = game.ENGINE_AUTO if engine == "auto" else game.ENGINE_SIMT
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=eng)
+    G = g.population()
+    fit, rank = g.evaluate()
+    P = o.expand(ds.X[:ds.n_train], shape["basis"], shape["d"])
+    want = o.fitness(P, ds.t[:ds.n_train], G, ocfg)
+    np.testing.assert_allclose(fit, want, rtol=FIT_RTOL)
+    assert list(rank) == list(o.rank(fit))
+
+
+@pytest.mark.parametrize("err,act", [("mse", "tanh"), ("tmse", "tanh"), ("tmse_sq", "tanh"),
+                                     ("rmse", "linear"), ("tmse", "linear")])
+def test_error_kinds_and_activations(err, act):
+    ds = synth.make_dataset(2500, 5, 3, seed=6)
+    t = ds.t if act == "tanh" else (ds.t > 0).astype(np.float32)   # 0/1 labels with linear Out
+    ocfg = _cfg(degree=3, pop=40, error=err, activation=act, tmse_R=0.49)
+    g = make_game(ocfg, ds.X, t, ds.n_train)
+    G = g.population()
+    fit, _ = g.evaluate()
+    P = o.expand(ds.X[:ds.n_train], "chebyshev", 3)
+    want = o.fitness(P, t[:ds.n_train], G, ocfg)
+    if err.startswith("tmse"):
+        # a pattern whose error sits within float32 rounding of R may fall on either side
+        np.testing.assert_allclose(fit, want, rtol=1e-4, atol=1e-6)
+    else:
+        np.testing.assert_allclose(fit, want, rtol=FIT_RTOL)
+
+
+def test_planted_chromosome_fits_exactly():
+    rng = np.random.default_rng(9)
+    X = rng.uniform(-1, 1, size=(4000, 6)).astype(np.float32)
+    ocfg = _cfg(degree=3, pop=33, stop_error=1e-5)
+    P = o.expand(X, "chebyshev", 3)
+    h = o.init_population(o.Config(pop=1, seed=99), P.shape[1])[0]
+    t = synth.planted_targets(P, h).astype(np.float32)
+    g = make_game(ocfg, X, t, 3000)
+    G = g.population()
+    G[5] = h
+    g.set_population(G)
+    fit, rank = g.evaluate()
+    assert rank[0] == 5
+    assert fit[5] < 2e-6
+    # the stop test ends evolution on the first generation
+    g.set_population(G)
+    assert g.evolve(20) == 1
+    assert g.state()[1] == 1
+
+
+# ----------------------------------------------------------------- operators
+
+@pytest.mark.parametrize("init", ["uniform_pm1", "normal_pm1", "uniform_01"])
+def test_initial_population_bit_exact(init):
+    ds = synth.make_dataset(300, 4, 3, seed=1)
+    ocfg = _cfg(degree=3, pop=57, init=init, seed=123, run=4)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    np.testing.assert_array_equal(g.population(), o.init_population(ocfg, g.n_genes))
+
+
+@pytest.mark.parametrize("kw", [
+    dict(),
+    dict(pop=31, elitism=3),                                  # odd slots: last child dropped
+    dict(pop=64, elite_mode="copies", tournament_k=4, p_mutation=0.2),
+    dict(pop=2, elitism=0, p_crossover=1.0),
+    dict(pop=10, elitism=10),                                 # everything elite
+    dict(pop=45, tournament_k=32, clamp_genes=False, sigma_mutation=0.7, p_mutation=0.5),
+    dict(pop=1000, degree=6),
+])
+def test_operators_bit_exact_given_fitness(kw):
+    ds = synth.make_dataset(500, 5, kw.get("degree", 4), seed=2)
+    ocfg = _cfg(**kw)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    G = g.population()
+    np.testing.assert_array_equal(G, o.init_population(ocfg, g.n_genes))
+    rng = np.random.default_rng(0)
+    for gen in range(4):
+        fit = rng.random(ocfg.pop)
+        if gen == 2:
+            fit[: ocfg.pop // 2] = 0.25                       # ties broken by index
+            fit[-1] = np.nan                                  # NaN ranks last
+        g.breed(fit)
+        want = o.breed(G, fit, ocfg, gen)
+        G = g.population()
+        np.testing.assert_array_equal(G, want)
+        assert g.state()[0] == gen + 1
+
+
+def test_trajectory_bit_exact_with_gpu_fitness():
+    """GPU evaluate + breed for 12 generations equals the oracle's operators fed the
+    GPU's fitness vectors; game_evolve reproduces the same trajectory."""
+    ds = synth.plain_small()
+    ocfg = _cfg(pop=20, degree=4, seed=0)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    G = g.population()
+    hist = []
+    for gen in range(12):
+        fit, _ = g.evaluate()
+        hist.append(fit.min())
+        if gen == 11:
+            break
+        g.breed(None)
+        want = o.breed(G, fit, ocfg, gen)
+        G = g.population()
+        np.testing.assert_array_equal(G, want)
+    assert all(b <= a for a, b in zip(hist, hist[1:]))       # elitism: best never worsens
+    h = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    assert h.evolve(12) == 12
+    np.testing.assert_array_equal(h.population(), G)
+    _, fit_best, _, _ = h.best()
+    assert fit_best == pytest.approx(hist[-1], rel=1e-12)
+
+
+def test_evolve_is_resumable():
+    ds = synth.make_dataset(1500, 5, 3, seed=8)
+    ocfg = _cfg(degree=3, pop=50)
+    a = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    b = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    assert a.evolve(9) == 9
+    assert b.evolve(4) == 4 and b.evolve(5) == 5
+    np.testing.assert_array_equal(a.population(), b.population())
+    assert a.state() == b.state() == (8, 0)
+
+
+# -------------------------------------------------------------------- report
+
+def test_score_matches_oracle_report():
+    ds = synth.plain_small()
+    ocfg = _cfg()
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    g.evolve(15)
+    genes, fit, test_rmse, test_acc = g.best()
+    P_te = o.expand(ds.X[ds.n_train:], "chebyshev", 4)
+    rep = o.report(P_te, ds.t[ds.n_train:], genes, ocfg)
+    assert test_rmse == pytest.approx(rep["rmse"], rel=1e-6)
+    assert test_acc == pytest.approx(rep["accuracy"], abs=1.0 / 600 + 1e-12)
+    s = g.score(genes, 1)
+    assert s["completeness"] == pytest.approx(rep["completeness"], abs=2.0 / 600)
+    assert s["contamination"] == pytest.approx(rep["contamination"], abs=2.0 / 600)
+    P_tr = o.expand(ds.X[:ds.n_train], "chebyshev", 4)
+    assert fit == pytest.approx(o.fitness(P_tr, ds.t[:ds.n_train], genes[None, :], ocfg)[0],
+                                rel=FIT_RTOL)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_edge_shapes():
+    game = lib()
+    # one training row, one feature, degree 1: K = 2
+    X = np.array([[0.5], [-0.25], [1.0]], dtype=np.float32)
+    t = np.array([1, -1, 1], dtype=np.float32)
+    ocfg = _cfg(degree=1, pop=2, elitism=1)
+    g = make_game(ocfg, X, t, 1)
+    G = g.population()
+    fit, _ = g.evaluate()
+    want = o.fitness(o.expand(X[:1], "chebyshev", 1), t[:1], G, ocfg)
+    np.testing.assert_allclose(fit, want, rtol=FIT_RTOL)
+    with pytest.raises(game.GameError):
+        g.set_data(X, t, 0)
+    with pytest.raises(game.GameError):
+        g.set_data(X, t, 4)
+    Xn = X.copy()
+    Xn[1, 0] = np.nan
+    with pytest.raises(game.GameError) as e:
+        g.set_data(Xn, t, 2)
+    assert e.value.status == -7
+
+
+def test_calls_out_of_order_are_state_errors():
+    game = lib()
+    g = game.Game(game_config(_cfg()))
+    with pytest.raises(game.GameError) as e:
+        g.evolve(1)
+    assert e.value.status == -2

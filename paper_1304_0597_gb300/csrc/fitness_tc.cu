@@ -1,7 +1,573 @@
+// Tensor-core fitness of the whole population on sm_103a: tcgen05.mma with the
+// accumulator in TMEM, operands staged in shared memory by TMA, fused epilogue.
+//
+// What it computes (paper Section 2): for every chromosome c and training
+// pattern k, Out = a_0 + sum_g G[c,g] P[k,g] (eq.2), E = (t_k - tanh(Out))^2
+// (eq.3; eq.10 for the threshold form), and per chromosome the sum of E over
+// the training patterns, later turned into MSE / RMSE (eq.4, eq.5).
+//
+// Layout.  D[c, k] = sum_g A[c, g] B[k, g] with A = genes of a 128-chromosome
+// slice (M = 128, TMEM lane = chromosome) and B = a tile of BN expansion rows
+// (N = BN, TMEM column = pattern); both K-major, 128-byte swizzled.  A CTA owns
+// one slice for its whole life: the slice's gene planes are loaded once and stay
+// in shared memory, while pattern tiles stream through a ring of B stages.  The
+// per-chromosome error sum is then a per-thread running sum over TMEM columns,
+// with no cross-lane reduction.
+//
+// Precision.  FP32 fitness: P = P_hi + P_lo and G = G_hi + G_lo are fp16
+// pairs (~22 significant bits) and D accumulates G_hi.P_hi + G_lo.P_hi +
+// G_hi.P_lo in float32 (kind::f16).  BF16 / FP8: one quantised P plane with
+// per-column scales folded into the genes, genes as a hi/lo pair with a
+// per-chromosome scale applied in the epilogue (kind::f16 bf16 / kind::f8f6f4).
+//
+// Roles (320 threads): warp 0 = TMA producer, warp 1 = TMEM allocator + MMA
+// issuer, warps 2..9 = epilogue (warp w reads TMEM lanes 32*(w%4) and half of
+// the columns).  Two TMEM accumulators let the epilogue of tile i overlap the
+// MMAs of tile i+1.  Every mbarrier wait is bounded (2 s of %globaltimer); on
+// a timeout the CTA records GAME_ERR_TIMEOUT in the device state, drains its
+// outstanding copies and MMAs (again bounded), frees TMEM and exits.
 #include "fitness_tc.h"
+
+#include <cudaTypedefs.h>
+
 namespace game {
-bool tc_supported(const Shape&) { return false; }
-cudaError_t tc_plan(const Shape&, const ExpDev&, const PopDev&, int, TcPlan*) { return cudaErrorNotSupported; }
-cudaError_t tc_launch(const TcPlan&, const Shape&, const Fitness&, const PopDev&, const ExpDev&, double*, const DevState*, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t tc_init_attributes() { return cudaSuccess; }
+
+namespace {
+
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr int kTileA = 128 * 128;         // bytes of one 128-row x 128-byte A tile
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+struct TcParams {
+  CUtensorMap a[2];
+  CUtensorMap b[2];
+  const float* t;
+  const float* bias;
+  const float* rscale;
+  double* partial;
+  DevState* state;
+  long long m;            // training rows
+  int n_slices, cps, n_tiles, kblocks, kp, stages, pop_pad;
+  int n_bplanes;          // FP32: 2 (P_hi, P_lo); else 1
+  int act, err, in_evolve;
+  float R;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on one phase of an mbarrier.  On timeout raises the CTA error
+// flag and the device status, and returns false.  Also returns false as soon
+// as another role of the CTA has raised the flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* err,
+                                          DevState* st) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*err) return false;
+    if (globaltimer() - t0 > kWaitNs) {
+      *err = 1;
+      atomicExch(&st->status, (int)GAME_ERR_TIMEOUT);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1 (tcgen05).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused with swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset
+  d |= (uint64_t)1 << 46;                      // version
+  d |= (uint64_t)2 << 61;                      // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: D f32, A/B format, both K-major, N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N, uint32_t ab_fmt) {
+  return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+template <int PREC>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                    uint32_t accum) {
+  if (PREC == GAME_FP8) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float general_error(float t, float s, int act, int err, float R) {
+  const float y = act == GAME_TANH ? tanhf(s) : s;
+  const float d = t - y;
+  const float e = d * d;
+  if (err == GAME_TMSE) return fabsf(d) > R ? e : 0.0f;
+  if (err == GAME_TMSE_SQ) return e > R ? e : 0.0f;
+  return e;
+}
+
+// Sum over 32 consecutive patterns of one chromosome's error.
+// FAST (targets +-1, tanh, MSE/RMSE): |t - tanh(s)| = 2 / (1 + exp(2 t s)), so
+// E = 4 r^2 with r = 1 / (1 + 2^(2 log2(e) t s)); the factor 4 is applied by the caller.
+template <bool FAST>
+__device__ __forceinline__ float chunk_error(const float v[32], const float* __restrict__ t,
+                                             long long p0, long long m, float rs, float bias,
+                                             int act, int err, float R) {
+  float sum = 0.0f;
+  const float4* t4 = reinterpret_cast<const float4*>(t + p0);
+  const bool full = p0 + 32 <= m;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 tq = __ldg(t4 + q);
+    const float tt[4] = {tq.x, tq.y, tq.z, tq.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int j = 4 * q + i;
+      const float s = fmaf(v[j], rs, bias);
+      float e;
+      if (FAST) {
+        const float E = ex2_approx(tt[i] * 2.8853900817779268f * s);
+        const float r = rcp_approx(1.0f + E);
+        e = r * r;
+      } else {
+        e = general_error(tt[i], s, act, err, R);
+      }
+      if (full || p0 + j < m) sum += e;
+    }
+  }
+  return FAST ? 4.0f * sum : sum;
+}
+
+template <int BN, int PREC, bool FAST>
+__global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_constant__ TcParams p) {
+  if (p.in_evolve && p.state->stopped) return;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~(uintptr_t)1023);
+  constexpr int kTileB = BN * 128;
+  constexpr int kKB = PREC == GAME_FP8 ? 128 : 64;    // elements per 128-byte k-block
+  constexpr int kKStep = PREC == GAME_FP8 ? 32 : 16;  // elements per MMA
+  constexpr uint32_t kFmt = PREC == GAME_BF16 ? 1u : 0u;
+  constexpr uint32_t kIdesc = make_idesc(128, BN, kFmt);
+  const int S = p.stages;
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + 2 * p.kblocks * kTileA;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + S * kTileB);
+  uint64_t* a_full = bars;
+  uint64_t* b_full = bars + 1;
+  uint64_t* b_empty = b_full + S;
+  uint64_t* acc_full = b_empty + S;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* fin = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* last_par = reinterpret_cast<int*>(tmem_slot + 2);          // [S]
+  double* red = reinterpret_cast<double*>(sB);   // [2][128], reused once the ring is idle
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int slice = blockIdx.x % p.n_slices;
+  const int member = blockIdx.x / p.n_slices;
+  const int my_tiles = member < p.n_tiles ? (p.n_tiles - 1 - member) / p.cps + 1 : 0;
+  constexpr uint32_t kTmemCols = 2 * BN;
+
+  if (threadIdx.x == 0) {
+    mbar_init(a_full, 1);
+    for (int s = 0; s < S; ++s) {
+      mbar_init(b_full + s, 1);
+      mbar_init(b_empty + s, 1);
+      last_par[s] = -1;
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(acc_full + b, 1);
+      mbar_init(acc_empty + b, kEpiWarps);
+    }
+    mbar_init(fin, 1);
+    *err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int a_steps_total = p.kp / kKStep;
+  double acc = 0.0;   // epilogue threads: this chromosome's error sum over its columns
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer ----
+      const uint32_t a_bytes = 2u * p.kblocks * kTileA;
+      mbar_expect_tx(a_full, a_bytes);
+      for (int pl = 0; pl < 2; ++pl)
+        for (int kb = 0; kb < p.kblocks; ++kb)
+          tma_load_2d(sA + (pl * p.kblocks + kb) * kTileA, &p.a[pl], kb * kKB, slice * 128,
+                      a_full);
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int it = 0; it < my_tiles && !*err; ++it) {
+        const int row0 = (member + it * p.cps) * BN;
+        for (int kb = 0; kb < p.kblocks && !*err; ++kb)
+          for (int bp = 0; bp < p.n_bplanes; ++bp) {
+            if (!mbar_wait(b_empty + stage, phase ^ 1u, err, p.state)) break;
+            mbar_expect_tx(b_full + stage, kTileB);
+            tma_load_2d(sB + stage * kTileB, &p.b[bp], kb * kKB, row0, b_full + stage);
+            last_par[stage] = (int)phase;
+            if (++stage == S) {
+              stage = 0;
+              phase ^= 1u;
+            }
+          }
+      }
+      // Drain: every issued copy has landed before the CTA may exit.
+      if (!mbar_wait(a_full, 0, err, p.state)) { /* recorded */ }
+      for (int s = 0; s < S; ++s)
+        if (last_par[s] >= 0) {
+          const unsigned long long t0 = globaltimer();
+          while (!mbar_try_wait(b_full + s, (uint32_t)last_par[s]) && globaltimer() - t0 < kWaitNs) {
+          }
+        }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      if (mbar_wait(a_full, 0, err, p.state)) {
+        fence_after();
+        int stage = 0;
+        uint32_t phase = 0;
+        for (int it = 0; it < my_tiles && !*err; ++it) {
+          const int buf = it & 1;
+          const uint32_t ap = (uint32_t)((it >> 1) & 1);
+          if (!mbar_wait(acc_empty + buf, ap ^ 1u, err, p.state)) break;
+          fence_after();
+          const uint32_t d = tmem + (uint32_t)(buf * BN);
+          uint32_t accum = 0;
+          bool ok = true;
+          for (int kb = 0; kb < p.kblocks && ok; ++kb) {
+            const int steps = min(kKB / kKStep, a_steps_total - kb * (kKB / kKStep));
+            for (int bp = 0; bp < p.n_bplanes; ++bp) {
+              if (!mbar_wait(b_full + stage, phase, err, p.state)) {
+                ok = false;
+                break;
+              }
+              fence_after();
+              const uint32_t b_base = smem_u32(sB + stage * kTileB);
+              // FP32 split: B = P_hi meets A = G_hi and G_lo; B = P_lo meets G_hi.
+              const int n_ap = (p.n_bplanes == 2 && bp == 1) ? 1 : 2;
+              for (int ai = 0; ai < n_ap; ++ai) {
+                const uint32_t a_base = smem_u32(sA + (ai * p.kblocks + kb) * kTileA);
+                for (int k = 0; k < steps; ++k) {
+                  mma<PREC>(d, sw128_desc(a_base + 32 * k), sw128_desc(b_base + 32 * k), kIdesc,
+                            accum);
+                  accum = 1;
+                }
+              }
+              mma_commit(b_empty + stage);
+              if (++stage == S) {
+                stage = 0;
+                phase ^= 1u;
+              }
+            }
+          }
+          if (!ok) break;
+          mma_commit(acc_full + buf);
+        }
+      }
+      // Drain: all issued MMAs complete before TMEM is released.
+      mma_commit(fin);
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(fin, 0) && globaltimer() - t0 < kWaitNs) {
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue ----
+    const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
+    const int c = slice * 128 + q * 32 + lane;
+    const float bias = p.bias[c];
+    const float rs = p.rscale[c];
+    for (int it = 0; it < my_tiles; ++it) {
+      const int buf = it & 1;
+      const uint32_t ap = (uint32_t)((it >> 1) & 1);
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait(acc_full + buf, ap, err, p.state);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) break;
+      fence_after();
+      const long long tile = member + (long long)it * p.cps;
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + h * (BN / 2));
+#pragma unroll 1
+      for (int ch = 0; ch < BN / 64; ++ch) {
+        float v[32];
+        tmem_ld32(tbase + ch * 32, v);
+        const long long p0 = tile * BN + h * (BN / 2) + ch * 32;
+        acc += (double)chunk_error<FAST>(v, p.t, p0, p.m, rs, bias, p.act, p.err, p.R);
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty + buf);
+    }
+  }
+  // Every copy and MMA of this CTA has completed (drained above): the B ring is
+  // free for the cross-half reduction and TMEM can be released.
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols));
+  if (warp >= 2) red[((warp - 2) >> 2) * 128 + (warp & 3) * 32 + lane] = acc;
+  __syncthreads();
+  if (threadIdx.x < 128)
+    p.partial[(long long)member * p.pop_pad + slice * 128 + threadIdx.x] =
+        red[threadIdx.x] + red[128 + threadIdx.x];
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* ptr = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  return fn;
+}
+
+cudaError_t make_map(CUtensorMap* m, const void* base, int precision, long long rows, int cols,
+                     int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const CUtensorMapDataType dt = precision == GAME_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : precision == GAME_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                          : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const int esz = precision == GAME_FP8 ? 1 : 2;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * esz};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+constexpr int kSmemMax = 232448;     // 227 KB opt-in per block on sm_103
+constexpr int kSmemMisc = 1024 + 512;   // alignment slack + barriers
+
+int kblocks_of(const Shape& s) {
+  const int kkb = s.precision == GAME_FP8 ? 128 : 64;
+  return (s.kp + kkb - 1) / kkb;
+}
+
+template <int BN, int PREC, bool FAST>
+void* kernel_ptr() {
+  return reinterpret_cast<void*>(&fitness_tc_kernel<BN, PREC, FAST>);
+}
+
+void* pick_kernel(int bn, int prec, bool fast) {
+#define GAME_TC_PICK(BNV, PV)                                                             \
+  if (bn == BNV && prec == PV) return fast ? kernel_ptr<BNV, PV, true>() : kernel_ptr<BNV, PV, false>();
+  GAME_TC_PICK(256, GAME_FP32)
+  GAME_TC_PICK(128, GAME_FP32)
+  GAME_TC_PICK(256, GAME_BF16)
+  GAME_TC_PICK(128, GAME_BF16)
+  GAME_TC_PICK(256, GAME_FP8)
+  GAME_TC_PICK(128, GAME_FP8)
+#undef GAME_TC_PICK
+  return nullptr;
+}
+
+}  // namespace
+
+cudaError_t tc_init_attributes() {
+  for (int bn : {128, 256})
+    for (int prec : {GAME_FP32, GAME_BF16, GAME_FP8})
+      for (bool fast : {false, true}) {
+        cudaError_t e = cudaFuncSetAttribute(pick_kernel(bn, prec, fast),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+        if (e != cudaSuccess) return e;
+      }
+  return cudaSuccess;
+}
+
+bool tc_supported(const Shape& s) {
+  if (!encode_fn()) return false;
+  const int a_bytes = 2 * kblocks_of(s) * kTileA;
+  // at least two B stages of 128 rows next to the resident gene planes
+  return a_bytes + 2 * 128 * 128 + kSmemMisc <= kSmemMax;
+}
+
+cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, TcPlan* plan) {
+  TcPlan& t = *plan;
+  t.kblocks = kblocks_of(s);
+  const int a_bytes = 2 * t.kblocks * kTileA;
+  const int room = kSmemMax - kSmemMisc - a_bytes;
+  const int n_bplanes = s.precision == GAME_FP32 ? 2 : 1;
+  // Prefer 256-pattern tiles when three stages fit; else 128-pattern tiles.
+  t.bn = (room >= 3 * 256 * 128) ? 256 : 128;
+  t.stages = room / (t.bn * 128);
+  if (t.stages > 8) t.stages = 8;
+  if (t.stages < 2) return cudaErrorNotSupported;
+  t.n_slices = s.pop_pad / 128;
+  t.n_tiles = (int)((s.n_train + t.bn - 1) / t.bn);
+  int cps = n_sm / t.n_slices;
+  if (cps < 1) cps = 1;
+  if (cps > t.n_tiles) cps = t.n_tiles;
+  t.ctas_per_slice = cps;
+  t.grid = t.n_slices * cps;
+  t.n_part = cps;
+  t.smem = (size_t)a_bytes + (size_t)t.stages * t.bn * 128 + kSmemMisc;
+  cudaError_t err;
+  if ((err = make_map(&t.a_map[0], p.ghi, s.precision, s.pop_pad, s.kp, 128)) != cudaSuccess) return err;
+  if ((err = make_map(&t.a_map[1], p.glo, s.precision, s.pop_pad, s.kp, 128)) != cudaSuccess) return err;
+  if ((err = make_map(&t.b_map[0], e.p0, s.precision, s.n_train, s.kp, t.bn)) != cudaSuccess) return err;
+  if (n_bplanes == 2) {
+    if ((err = make_map(&t.b_map[1], e.p1, s.precision, s.n_train, s.kp, t.bn)) != cudaSuccess) return err;
+  } else {
+    t.b_map[1] = t.b_map[0];
+  }
+  return cudaSuccess;
+}
+
+cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const PopDev& pd,
+                      const ExpDev& e, double* partial, const DevState* state, cudaStream_t st) {
+  TcParams p;
+  p.a[0] = t.a_map[0];
+  p.a[1] = t.a_map[1];
+  p.b[0] = t.b_map[0];
+  p.b[1] = t.b_map[1];
+  p.t = e.t;
+  p.bias = pd.bias;
+  p.rscale = pd.rscale;
+  p.partial = partial;
+  p.state = const_cast<DevState*>(state);
+  p.m = s.n_train;
+  p.n_slices = t.n_slices;
+  p.cps = t.ctas_per_slice;
+  p.n_tiles = t.n_tiles;
+  p.kblocks = t.kblocks;
+  p.kp = s.kp;
+  p.stages = t.stages;
+  p.pop_pad = s.pop_pad;
+  p.n_bplanes = s.precision == GAME_FP32 ? 2 : 1;
+  p.act = f.activation;
+  p.err = f.error;
+  p.R = f.tmse_R;
+  p.in_evolve = state != nullptr;
+  const bool fast = f.pm1_targets && f.activation == GAME_TANH &&
+                    (f.error == GAME_RMSE || f.error == GAME_MSE);
+  void* k = pick_kernel(t.bn, s.precision, fast);
+  if (!k) return cudaErrorNotSupported;
+  void* args[] = {&p};
+  return cudaLaunchKernel(k, dim3(t.grid), dim3(kThreads), args, t.smem, st);
+}
+
+}  // namespace game

@@ -50,18 +50,22 @@ def test_expansion_of_device_inputs_equals_host_inputs():
 
 # ------------------------------------------------------------------- fitness
 
-@pytest.mark.parametrize("engine", ["auto", "simt"])
+@pytest.mark.parametrize("engine", ["tcgen05", "simt"])
 @pytest.mark.parametrize("shape", [
     dict(n=2000, F=7, d=4, pop=20, basis="chebyshev"),          # the small plain workload
     dict(n=5003, F=9, d=5, pop=300, basis="chebyshev"),         # several tiles, ragged tails
     dict(n=3001, F=6, d=4, pop=129, basis="trig"),              # polytrigo, pop just over a tile
+    dict(n=40013, F=32, d=8, pop=1024, basis="chebyshev"),      # the at-scale gene count
+    dict(n=9000, F=24, d=12, pop=200, basis="chebyshev"),       # 288 basis columns (5 k-blocks)
 ])
 def test_fitness_matches_oracle(shape, engine):
     game = lib()
-    ds = synth.make_dataset(shape["n"], shape["F"], shape["d"], shape["basis"], seed=5)
+    ds = synth.make_dataset(shape["n"], shape["F"], shape["d"], shape["basis"], seed=5,
+                            correlated=shape["F"] >= 24)
     ocfg = _cfg(basis=shape["basis"], degree=shape["d"], pop=shape["pop"])
-    eng = game.ENGINE_AUTO if engine == "auto" else game.ENGINE_SIMT
+    eng = game.ENGINE_TCGEN05 if engine == "tcgen05" else game.ENGINE_SIMT
     g = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=eng)
+    assert g.timing()["engine"] == eng
     G = g.population()
     fit, rank = g.evaluate()
     P = o.expand(ds.X[:ds.n_train], shape["basis"], shape["d"])

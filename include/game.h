@@ -193,6 +193,33 @@ game_status game_get_timing(game_ctx* ctx, game_timing* out);
  * for the last call; enabled = 0 (default): only the total is timed. */
 game_status game_set_timing(game_ctx* ctx, int32_t enabled);
 
+/* ---- fitness without device allocation ------------------------------------ */
+
+/* Population fitness for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is a packaging of the fitness step (the same
+ * float32 CUDA-core kernel as GAME_ENGINE_SIMT) for code that must not call
+ * cudaMalloc -- work captured into a CUDA graph, a service whose device memory
+ * is a fixed arena owned by another allocator, or a latency-critical path that
+ * cannot afford cudaMalloc's device-wide synchronisation.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   P: device, n_patterns x (n_genes-1) float32 row-major: the basis columns
+ *      of the expansion (the bias column of ones is implicit), e.g. as
+ *      returned by game_get_expansion.
+ *   t: device, n_patterns float32 targets.  G: device, pop x n_genes float32
+ *      (gene 0 = bias).  fitness: device, pop float64 output (eq.4 / eq.5 /
+ *      eq.10 over the n_patterns rows for the given error and activation).
+ *   stream: cudaStream_t (NULL = legacy default); the call only enqueues work.
+ * Limits: 1 <= pop <= 4096 (else GAME_ERR_UNSUPPORTED).  Partial sums live in
+ * one file-scope device array of 32 x 4096 doubles (1 MiB) that every device
+ * loading the library keeps until exit; all calls share it and it keeps the
+ * last call's contents (each call overwrites what it reads).  Calls whose work
+ * overlaps on the GPU race on that array.  The first call on a device looks up
+ * the array's address with that device current: make it before any stream
+ * capture.  Errors also set game_last_error(NULL). */
+game_status game_fitness_noalloc(const float* P, const float* t, const float* G,
+                                 int64_t n_patterns, int32_t n_genes, int32_t pop, int32_t error,
+                                 int32_t activation, float tmse_R, double* fitness, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

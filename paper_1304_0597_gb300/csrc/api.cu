@@ -57,6 +57,10 @@ struct game_ctx {
 
 static std::string g_global_err;
 
+namespace game {
+void set_global_error(const char* msg) { g_global_err = msg; }
+}  // namespace game
+
 static game_status fail(game_ctx* c, game_status code, const char* fmt, ...) {
   char buf[512];
   va_list ap;

@@ -77,6 +77,7 @@ def _load() -> C.CDLL:
         "game_get_state": (I32, [P, C.POINTER(I64), C.POINTER(I32)]),
         "game_get_timing": (I32, [P, C.POINTER(GameTiming)]),
         "game_set_timing": (I32, [P, I32]),
+        "game_fitness_noalloc": (I32, [P, P, P, I64, I32, I32, I32, I32, F, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -535,3 +535,52 @@ def report(P: np.ndarray, t: np.ndarray, genes: np.ndarray, cfg: Config) -> dict
         "completeness": float(tp / (tp + fn)) if tp + fn else 0.0,
         "contamination": float(fp / (tp + fp)) if tp + fp else 0.0,
     }
+
+
+# ---------------------------------------------------------------------------
+# Low-precision storage of P (precision form): per-column scale, then rounding
+# to the storage format.  The paper computes in double; these functions state
+# what a reduced-precision copy of P holds, so that a fitness computed from it
+# can be compared with the exact one.
+# ---------------------------------------------------------------------------
+
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """Round float32 values to bfloat16 (round to nearest, ties to even); returned as float32."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + np.uint64(0x7FFF) + ((b >> np.uint64(16)) & np.uint64(1))) & np.uint64(0xFFFF0000)
+    return b.astype(np.uint32).view(np.float32)
+
+
+def round_e4m3(x: np.ndarray) -> np.ndarray:
+    """Round float32 values to FP8 E4M3 (OCP: 3 mantissa bits, exponent bias 7, largest
+    finite 448, subnormal step 2^-9), ties to even, saturating to +-448; returned as float32."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    _, e = np.frexp(a)                     # a = m 2^e, m in [0.5, 1)
+    expo = np.maximum(e - 1, -6)           # unbiased exponent, clamped to the subnormal range
+    step = np.ldexp(1.0, expo - 3)
+    q = np.round(a / step) * step          # numpy rounds halves to even
+    q = np.minimum(q, 448.0)
+    return (np.sign(x) * q).astype(np.float32)
+
+
+QMAX = {"bf16": 1.0, "fp8": 448.0}
+
+
+def quantize_columns(P: np.ndarray, fmt: str):
+    """P held in a low-precision format with a per-column scale: P ~ Q * s.
+
+    P is first rounded to float32 (the working precision of the expansion);
+    s_g = max_k |P[k,g]| / qmax (1 where the column is zero); Q = round(P / s)
+    in the format.  Returns (Q, s) as float32 arrays.
+    """
+    P32 = np.asarray(P, dtype=np.float32)
+    m = np.max(np.abs(P32), axis=0) if P32.shape[0] else np.zeros(P32.shape[1], np.float32)
+    s = np.where(m > 0, m / np.float32(QMAX[fmt]), np.float32(1.0)).astype(np.float32)
+    R = (P32 / s[None, :]).astype(np.float32)
+    Q = round_bf16(R) if fmt == "bf16" else round_e4m3(R)
+    return Q, s
+
+
+def dequantize_columns(Q: np.ndarray, s: np.ndarray) -> np.ndarray:
+    return np.asarray(Q, dtype=np.float64) * np.asarray(s, dtype=np.float64)[None, :]

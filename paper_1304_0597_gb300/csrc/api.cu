@@ -45,6 +45,17 @@ struct game_ctx {
   float* d_genes = nullptr;     // one chromosome (report)
   int engine = GAME_ENGINE_SIMT;
   TcPlan tc{};
+  // Precision form: FP32 copy of P and the FP32 re-score of the top elites.
+  bool lowp = false;            // P stored in BF16 / FP8
+  int n_rescore = 0;            // elites re-scored in FP32 each generation
+  Shape s32{};                  // FP32 shape of P (report, re-score)
+  ExpDev e32{};                 // FP32 planes of P (== e when precision is FP32)
+  Shape sr{};                   // shape of the re-score population (pop = n_rescore)
+  PopDev pr{};                  // gene planes of the gathered elites
+  int engine_r = GAME_ENGINE_SIMT;
+  TcPlan tc_r{};
+  int n_part_r = 0;
+  double* d_partial_r = nullptr;
   cudaGraphExec_t graph = nullptr;     // one generation
   cudaGraph_t graph_t_tmpl = nullptr;  // one generation with stage events (template kept alive)
   cudaGraphExec_t graph_t = nullptr;
@@ -244,19 +255,20 @@ __global__ void check_data_kernel(const float* X, long long nx, const float* t, 
   if (notpm1) atomicOr(flags, 2u);
 }
 
-static game_status choose_engine(game_ctx* c) {
+static game_status choose_engine(game_ctx* c, const Shape& s, const ExpDev& e, const PopDev& p,
+                                 int* engine, TcPlan* plan, int* n_part) {
   int want = c->cfg.engine;
-  if (want == GAME_ENGINE_AUTO) want = tc_supported(c->s) ? GAME_ENGINE_TCGEN05 : GAME_ENGINE_SIMT;
+  if (want == GAME_ENGINE_AUTO) want = tc_supported(s) ? GAME_ENGINE_TCGEN05 : GAME_ENGINE_SIMT;
   if (want == GAME_ENGINE_TCGEN05) {
-    if (!tc_supported(c->s))
+    if (!tc_supported(s))
       return fail(c, GAME_ERR_UNSUPPORTED, "tcgen05 engine does not support this shape");
-    cudaError_t e = tc_plan(c->s, c->e, c->p, c->n_sm, &c->tc);
-    if (e != cudaSuccess) return fail(c, GAME_ERR_CUDA, "tcgen05 plan: %s", cudaGetErrorString(e));
-    c->engine = GAME_ENGINE_TCGEN05;
-    c->n_part = c->tc.n_part;
+    cudaError_t err = tc_plan(s, e, p, c->n_sm, plan);
+    if (err != cudaSuccess) return fail(c, GAME_ERR_CUDA, "tcgen05 plan: %s", cudaGetErrorString(err));
+    *engine = GAME_ENGINE_TCGEN05;
+    *n_part = plan->n_part;
   } else {
-    c->engine = GAME_ENGINE_SIMT;
-    c->n_part = simt_partials(c->s, c->n_sm);
+    *engine = GAME_ENGINE_SIMT;
+    *n_part = simt_partials(s, c->n_sm);
   }
   return GAME_OK;
 }
@@ -327,6 +339,21 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   if ((r = dalloc(c, &c->e.colscale, sizeof(float) * s.kp)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_scratch, sizeof(float) * s.kp)) != GAME_OK) return r;
   CUDA_OK(c, launch_expand(dX, s, c->e, c->d_scratch, c->st));
+  c->lowp = s.precision != GAME_FP32;
+  c->s32 = s;
+  c->e32 = c->e;
+  if (c->lowp) {
+    // The FP32 planes serve the elite re-score and the float64 report.
+    c->s32.precision = GAME_FP32;
+    c->s32.kp = round_up(s.kb, 16);
+    c->e32 = ExpDev{};
+    c->e32.t = c->e.t;
+    const size_t b32 = sizeof(__half) * (size_t)n_patterns * c->s32.kp;
+    if ((r = dalloc(c, &c->e32.p0, b32)) != GAME_OK) return r;
+    if ((r = dalloc(c, &c->e32.p1, b32)) != GAME_OK) return r;
+    if ((r = dalloc(c, &c->e32.colscale, sizeof(float) * c->s32.kp)) != GAME_OK) return r;
+    CUDA_OK(c, launch_expand(dX, c->s32, c->e32, c->d_scratch, c->st));
+  }
 
   // Population buffers.
   const size_t g32b = sizeof(float) * (size_t)s.pop_pad * s.kstride;
@@ -346,13 +373,36 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   if ((r = dalloc(c, &c->d_score_blocks, sizeof(double) * 5 * c->score_nb)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_score_out, sizeof(double) * 8)) != GAME_OK) return r;
 
-  if ((r = choose_engine(c)) != GAME_OK) {
+  if ((r = choose_engine(c, s, c->e, c->p, &c->engine, &c->tc, &c->n_part)) != GAME_OK) {
     free_all(c);
     return r;
   }
   c->part_rows = c->n_part > simt_partials(s, c->n_sm) ? c->n_part : simt_partials(s, c->n_sm);
   if ((r = dalloc(c, &c->d_partial, sizeof(double) * (size_t)c->part_rows * s.pop_pad)) != GAME_OK)
     return r;
+  c->n_rescore = 0;
+  if (c->lowp && c->cfg.elite_rescore > 0) {
+    c->n_rescore = c->cfg.elite_rescore < s.pop ? c->cfg.elite_rescore : s.pop;
+    if (c->n_rescore > 128) c->n_rescore = 128;
+    c->sr = c->s32;
+    c->sr.pop = c->n_rescore;
+    c->sr.pop_pad = 128;
+    c->pr = PopDev{};
+    c->pr.g32[0] = c->p.g32[0];
+    c->pr.g32[1] = c->p.g32[1];
+    if ((r = dalloc(c, &c->pr.geval, sizeof(float) * 128 * (size_t)c->sr.kp)) != GAME_OK) return r;
+    if ((r = dalloc(c, &c->pr.bias, sizeof(float) * 128)) != GAME_OK) return r;
+    if ((r = dalloc(c, &c->pr.rscale, sizeof(float) * 128)) != GAME_OK) return r;
+    if ((r = dalloc(c, &c->pr.ghi, sizeof(__half) * 128 * (size_t)c->sr.kp)) != GAME_OK) return r;
+    if ((r = dalloc(c, &c->pr.glo, sizeof(__half) * 128 * (size_t)c->sr.kp)) != GAME_OK) return r;
+    if ((r = choose_engine(c, c->sr, c->e32, c->pr, &c->engine_r, &c->tc_r, &c->n_part_r)) != GAME_OK) {
+      free_all(c);
+      return r;
+    }
+    const int rows = c->n_part_r > simt_partials(c->sr, c->n_sm) ? c->n_part_r
+                                                                : simt_partials(c->sr, c->n_sm);
+    if ((r = dalloc(c, &c->d_partial_r, sizeof(double) * (size_t)rows * 128)) != GAME_OK) return r;
+  }
 
   CUDA_OK(c, launch_state_op(c->d_state, kStateReset, c->st));
   CUDA_OK(c, launch_init_population(s, c->cfg.init, c->cfg.seed, c->cfg.run, c->p.g32[0], c->st));
@@ -378,6 +428,26 @@ static game_status launch_fitness(game_ctx* c, const DevState* state) {
   return GAME_OK;
 }
 
+// Precision form: the top n_rescore chromosomes of the ranking just made are
+// re-evaluated on the FP32 planes, their fitness replaced, and the population
+// re-sorted (with the stop test on the re-scored best).
+static game_status enqueue_rescore(game_ctx* c, int in_evolve) {
+  const DevState* st = in_evolve ? c->d_state : nullptr;
+  CUDA_OK(c, launch_prepare(c->sr, c->pr, c->e32, c->d_state, in_evolve ? 2 : 0, c->st, c->d_rank,
+                            &c->p));
+  if (c->engine_r == GAME_ENGINE_TCGEN05) {
+    CUDA_OK(c, tc_launch(c->tc_r, c->sr, c->fit, c->pr, c->e32, c->d_partial_r, st, c->st));
+  } else {
+    CUDA_OK(c, launch_fitness_simt(c->sr, c->fit, c->pr, c->e32, c->d_partial_r, c->n_part_r, st,
+                                   c->st));
+  }
+  CUDA_OK(c, launch_rescore_merge(c->sr, c->cfg, c->d_partial_r, c->n_part_r, c->d_rank, c->d_fit,
+                                  c->d_state, in_evolve, c->st));
+  CUDA_OK(c, launch_reduce_rank(c->s, c->cfg, nullptr, 0, c->d_fit, c->d_rank, c->d_state,
+                                kRankResort | (in_evolve ? kRankInEvolve : 0), c->st));
+  return GAME_OK;
+}
+
 // One generation: breed (if the current population was evaluated), prepare,
 // fitness, reduce + rank.  Reads and writes only device state.
 static game_status enqueue_generation(game_ctx* c, const cudaEvent_t* ev) {
@@ -389,7 +459,13 @@ static game_status enqueue_generation(game_ctx* c, const cudaEvent_t* ev) {
   if (r != GAME_OK) return r;
   if (ev) CUDA_OK(c, cudaEventRecordWithFlags(ev[2], c->st, cudaEventRecordExternal));
   CUDA_OK(c, launch_reduce_rank(c->s, c->cfg, c->d_partial, c->n_part, c->d_fit, c->d_rank,
-                                c->d_state, kRankEvaluate | (1 << 8), c->st));
+                                c->d_state,
+                                kRankEvaluate | kRankInEvolve | (c->n_rescore ? kRankNoStop : 0),
+                                c->st));
+  if (c->n_rescore) {
+    r = enqueue_rescore(c, 1);
+    if (r != GAME_OK) return r;
+  }
   if (ev) CUDA_OK(c, cudaEventRecordWithFlags(ev[3], c->st, cudaEventRecordExternal));
   return GAME_OK;
 }
@@ -533,6 +609,10 @@ extern "C" game_status game_evaluate(game_ctx* c, double* fitness, int32_t* rank
   if (r != GAME_OK) return r;
   CUDA_OK(c, launch_reduce_rank(c->s, c->cfg, c->d_partial, c->n_part, c->d_fit, c->d_rank,
                                 c->d_state, kRankEvaluate, c->st));
+  if (c->n_rescore) {
+    r = enqueue_rescore(c, 0);
+    if (r != GAME_OK) return r;
+  }
   if (fitness)
     CUDA_OK(c, cudaMemcpyAsync(fitness, c->d_fit, sizeof(double) * c->s.pop, cudaMemcpyDeviceToHost, c->st));
   if (rank)
@@ -621,8 +701,8 @@ static game_status score(game_ctx* c, const float* genes_host_or_null, int split
   if (genes_host_or_null)
     CUDA_OK(c, cudaMemcpyAsync(c->d_genes, genes_host_or_null, sizeof(float) * c->s.n_genes,
                                cudaMemcpyHostToDevice, c->st));
-  CUDA_OK(c, launch_score(c->s, c->fit, c->e, c->d_genes, r0, r1, c->d_score_blocks, c->score_nb,
-                          c->d_score_out, c->st));
+  CUDA_OK(c, launch_score(c->s32, c->fit, c->e32, c->d_genes, r0, r1, c->d_score_blocks,
+                          c->score_nb, c->d_score_out, c->st));
   CUDA_OK(c, cudaMemcpyAsync(out, c->d_score_out, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->st));
   CUDA_OK(c, cudaStreamSynchronize(c->st));
   return GAME_OK;

@@ -8,9 +8,10 @@
 // bias a_0 multiplies a column of ones that is never stored (its gene is added
 // in the fitness epilogue).
 //
-// Values are generated in float64 by recurrences (Chebyshev: T_{k+1} = 2x T_k -
-// T_{k-1}; trig: angle addition from one sincos(x)), rounded once to float32,
-// then stored in the precision of the run:
+// Values come from recurrences carried well beyond float32 precision
+// (Chebyshev: T_{k+1} = 2x T_k - T_{k-1} in float-float; trig: angle addition
+// from one float64 sincos(x)), rounded once to float32, then stored in the
+// precision of the run:
 //   FP32: two fp16 planes, hi = fp16(v), lo = fp16(v - hi)  (v = hi + lo to ~22 bits)
 //   BF16: bf16(v / s_g), s_g = max_k |P[k,g]|          (per-column scale)
 //   FP8 : e4m3(v / s_g), s_g = max_k |P[k,g]| / 448
@@ -18,24 +19,48 @@
 
 namespace game {
 
-// Calls emit(b, v) for the bd basis values of one feature value x.
+// Error-free transformations on float32 (Dekker's product via FMA, Knuth's sum):
+// a*b = p + e and a+b = s + e exactly.
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = fmaf(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Calls emit(b, v) with the float32 rounding of the b-th basis value of x.
+// Chebyshev: T_{k+1} = 2x T_k - T_{k-1} carried as a float-float pair (about
+// 44 significant bits, all on the float32 pipes).  Trig: one float64 sincos and
+// float64 angle addition.
 template <typename Emit>
-__device__ __forceinline__ void basis_values(int basis, int d, double x, Emit emit) {
+__device__ __forceinline__ void basis_values(int basis, int d, float x, Emit emit) {
   if (basis == GAME_CHEBYSHEV) {
-    double tm = 1.0, t = x;
+    const float y = __fmul_rn(2.0f, x);          // exact
+    float mh = 1.0f, ml = 0.0f;                  // T_{k-1}
+    float th = x, tl = 0.0f;                     // T_k
     for (int b = 0; b < d; ++b) {
-      emit(b, t);
-      const double tn = 2.0 * x * t - tm;
-      tm = t;
-      t = tn;
+      emit(b, __fadd_rn(th, tl));
+      float p, pe, s, se;
+      two_prod(y, th, p, pe);
+      two_sum(p, -mh, s, se);
+      const float low = __fsub_rn(__fadd_rn(__fadd_rn(se, pe), __fmul_rn(y, tl)), ml);
+      const float nh = __fadd_rn(s, low);
+      const float nl = __fsub_rn(low, __fsub_rn(nh, s));
+      mh = th;
+      ml = tl;
+      th = nh;
+      tl = nl;
     }
   } else {
     double s1, c1;
-    sincos(x, &s1, &c1);
+    sincos((double)x, &s1, &c1);
     double c = c1, s = s1;
     for (int k = 0; k < d; ++k) {
-      emit(k, c);
-      emit(d + k, s);
+      emit(k, (float)c);
+      emit(d + k, (float)s);
       const double cn = c * c1 - s * s1;
       const double sn = s * c1 + c * s1;
       c = cn;
@@ -58,11 +83,9 @@ __global__ void expand_colmax_kernel(ExpArgs a) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n * a.F) return;
   const int f = (int)(i % a.F);
-  const double x = (double)a.X[i];
+  const float x = a.X[i];
   unsigned int* cm = a.colmax_bits + f * a.bd;
-  basis_values(a.basis, a.d, x, [&](int b, double v) {
-    atomicMax(cm + b, __float_as_uint(fabsf((float)v)));
-  });
+  basis_values(a.basis, a.d, x, [&](int b, float v) { atomicMax(cm + b, __float_as_uint(fabsf(v))); });
 }
 
 __global__ void expand_scale_kernel(const unsigned int* colmax_bits, float* colscale, int kb,
@@ -78,17 +101,16 @@ __global__ void expand_kernel(ExpArgs a) {
   if (i >= a.n * a.F) return;
   const long long k = i / a.F;
   const int f = (int)(i % a.F);
-  const double x = (double)a.X[i];
+  const float x = a.X[i];
   const long long row = k * a.kp;
   const int col0 = f * a.bd;
   if (a.precision == GAME_FP32) {
     __half* hi = (__half*)a.p0 + row + col0;
     __half* lo = (__half*)a.p1 + row + col0;
-    basis_values(a.basis, a.d, x, [&](int b, double v) {
-      const float v32 = (float)v;
-      const __half h = __float2half_rn(v32);
+    basis_values(a.basis, a.d, x, [&](int b, float v) {
+      const __half h = __float2half_rn(v);
       hi[b] = h;
-      lo[b] = __float2half_rn(__fsub_rn(v32, __half2float(h)));
+      lo[b] = __float2half_rn(__fsub_rn(v, __half2float(h)));
     });
     if (f == a.F - 1)
       for (int c = a.kb; c < a.kp; ++c) {
@@ -98,15 +120,13 @@ __global__ void expand_kernel(ExpArgs a) {
   } else if (a.precision == GAME_BF16) {
     __nv_bfloat16* q = (__nv_bfloat16*)a.p0 + row + col0;
     const float* sc = a.colscale + col0;
-    basis_values(a.basis, a.d, x, [&](int b, double v) {
-      q[b] = __float2bfloat16_rn((float)v / sc[b]);
-    });
+    basis_values(a.basis, a.d, x, [&](int b, float v) { q[b] = __float2bfloat16_rn(v / sc[b]); });
     if (f == a.F - 1)
       for (int c = a.kb; c < a.kp; ++c) ((__nv_bfloat16*)a.p0)[row + c] = __float2bfloat16_rn(0.0f);
   } else {
     __nv_fp8_e4m3* q = (__nv_fp8_e4m3*)a.p0 + row + col0;
     const float* sc = a.colscale + col0;
-    basis_values(a.basis, a.d, x, [&](int b, double v) { q[b] = __nv_fp8_e4m3((float)v / sc[b]); });
+    basis_values(a.basis, a.d, x, [&](int b, float v) { q[b] = __nv_fp8_e4m3(v / sc[b]); });
     if (f == a.F - 1)
       for (int c = a.kb; c < a.kp; ++c) ((__nv_fp8_e4m3*)a.p0)[row + c] = __nv_fp8_e4m3(0.0f);
   }

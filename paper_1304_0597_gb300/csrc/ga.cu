@@ -336,6 +336,7 @@ cudaError_t launch_breed(const Shape& s, const game_config& cfg, const PopDev& p
 //   hi = q(g'), lo = q(g' - hi); the contraction result is scaled back by r_c.
 // ---------------------------------------------------------------------------
 struct PrepArgs {
+  const int* rows;        // optional: row i takes chromosome rows[i] (i < pop), else row i
   const float* g32_0;
   const float* g32_1;
   const float* colscale;
@@ -356,8 +357,9 @@ __global__ void prepare_kernel(PrepArgs a) {
   if (row >= a.pop_pad) return;
   int buf = st->cur;
   if (a.use_bred_flag && st->bred) buf ^= 1;
-  const float* G = (buf ? a.g32_1 : a.g32_0) + (long long)row * a.kstride;
   const bool live = row < a.pop;
+  const int src = (live && a.rows) ? a.rows[row] : row;
+  const float* G = (buf ? a.g32_1 : a.g32_0) + (long long)src * a.kstride;
   float* ge = a.geval + (long long)row * a.kp;
   if (lane == 0) a.bias[row] = live ? G[0] : 0.0f;
   if (a.precision == GAME_FP32) {
@@ -402,10 +404,12 @@ __global__ void prepare_kernel(PrepArgs a) {
 }
 
 cudaError_t launch_prepare(const Shape& s, const PopDev& p, const ExpDev& e, DevState* state,
-                           int use_bred_flag, cudaStream_t st) {
+                           int use_bred_flag, cudaStream_t st, const int* rows,
+                           const PopDev* src) {
   PrepArgs a;
-  a.g32_0 = p.g32[0];
-  a.g32_1 = p.g32[1];
+  a.rows = rows;
+  a.g32_0 = src ? src->g32[0] : p.g32[0];
+  a.g32_1 = src ? src->g32[1] : p.g32[1];
   a.colscale = e.colscale;
   a.geval = p.geval;
   a.bias = p.bias;
@@ -438,16 +442,24 @@ struct RankArgs {
   double* fit;
   int* rank;
   DevState* state;
-  int n_part, pop, pop_pad, n2, error, mode, in_evolve;
+  int n_part, pop, pop_pad, n2, error, mode, in_evolve, no_stop;
   double inv_m, stop_error;
 };
+
+// Order-preserving map of a float64 (NaN already replaced by +inf) to uint64,
+// so that the sort compares integers (float64 units are scarce on this part).
+__device__ __forceinline__ unsigned long long ordered_key(double f) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(f);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
 
 __global__ void __launch_bounds__(1024) reduce_rank_kernel(RankArgs a) {
   DevState* st = a.state;
   if (a.in_evolve && st->stopped) return;
   extern __shared__ unsigned char smem_raw[];
-  double* key = reinterpret_cast<double*>(smem_raw);
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);
   int* idx = reinterpret_cast<int*>(key + a.n2);
+  __shared__ double best_f;
   const int tid = threadIdx.x;
   for (int c = tid; c < a.n2; c += blockDim.x) {
     double f = CUDART_INF;
@@ -463,7 +475,7 @@ __global__ void __launch_bounds__(1024) reduce_rank_kernel(RankArgs a) {
       }
       if (isnan(f)) f = CUDART_INF;
     }
-    key[c] = f;
+    key[c] = ordered_key(f);
     idx[c] = c < a.pop ? c : 0x7fffffff;
   }
   __syncthreads();
@@ -473,14 +485,14 @@ __global__ void __launch_bounds__(1024) reduce_rank_kernel(RankArgs a) {
         const int l = i ^ j;
         if (l > i) {
           const bool up = (i & k) == 0;
-          const bool lt = key[l] < key[i] || (key[l] == key[i] && idx[l] < idx[i]);
+          const unsigned long long ki = key[i], kl = key[l];
+          const int ii = idx[i], il = idx[l];
+          const bool lt = kl < ki || (kl == ki && il < ii);
           if (lt == up) {
-            const double tk = key[i];
-            key[i] = key[l];
-            key[l] = tk;
-            const int ti = idx[i];
-            idx[i] = idx[l];
-            idx[l] = ti;
+            key[i] = kl;
+            key[l] = ki;
+            idx[i] = il;
+            idx[l] = ii;
           }
         }
       }
@@ -489,7 +501,9 @@ __global__ void __launch_bounds__(1024) reduce_rank_kernel(RankArgs a) {
   }
   for (int c = tid; c < a.pop; c += blockDim.x) a.rank[c] = idx[c];
   if (tid == 0) {
-    st->best = key[0];
+    const double f0 = a.fit[idx[0]];
+    best_f = isnan(f0) ? CUDART_INF : f0;
+    st->best = best_f;
     if (a.mode == kRankEvaluate) {
       if (st->bred) {
         st->cur ^= 1;
@@ -497,8 +511,9 @@ __global__ void __launch_bounds__(1024) reduce_rank_kernel(RankArgs a) {
       }
       st->bred = 0;
       st->gens_run += 1;
-      if (key[0] <= a.stop_error) st->stopped = 1;
     }
+    if (a.mode != kRankSortOnly && !a.no_stop && a.in_evolve && best_f <= a.stop_error)
+      st->stopped = 1;
     st->evaluated = 1;
   }
 }
@@ -524,11 +539,34 @@ cudaError_t launch_reduce_rank(const Shape& s, const game_config& cfg, const dou
   a.error = cfg.error;
   a.mode = mode & 0xff;
   a.in_evolve = (mode >> 8) & 1;
+  a.no_stop = (mode >> 9) & 1;
   a.inv_m = 1.0 / (double)s.n_train;
   a.stop_error = cfg.stop_error;
-  const size_t smem = (size_t)a.n2 * (sizeof(double) + sizeof(int));
+  const size_t smem = (size_t)a.n2 * (sizeof(unsigned long long) + sizeof(int));
   const int threads = a.n2 < 1024 ? (a.n2 < 32 ? 32 : a.n2) : 1024;
   reduce_rank_kernel<<<1, threads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// FP32 re-score of the elites: fitness of rank[i] (i < n) from the partial sums of
+// the FP32 engine over the gathered rows.
+__global__ void rescore_merge_kernel(const double* partial, int n_part, int pop_pad, int n,
+                                     const int* rank, double* fit, double inv_m, int error,
+                                     const DevState* st, int in_evolve) {
+  if (in_evolve && st->stopped) return;
+  const int i = threadIdx.x;
+  if (i >= n) return;
+  double sse = 0.0;
+  for (int b = 0; b < n_part; ++b) sse += partial[(long long)b * pop_pad + i];
+  const double mse = sse * inv_m;
+  fit[rank[i]] = error == GAME_RMSE ? sqrt(mse) : mse;
+}
+
+cudaError_t launch_rescore_merge(const Shape& sr, const game_config& cfg, const double* partial,
+                                 int n_part, const int* rank, double* fit, const DevState* state,
+                                 int in_evolve, cudaStream_t st) {
+  rescore_merge_kernel<<<1, 128, 0, st>>>(partial, n_part, sr.pop_pad, sr.pop, rank, fit,
+                                          1.0 / (double)sr.n_train, cfg.error, state, in_evolve);
   return cudaGetLastError();
 }
 

@@ -92,8 +92,15 @@ cudaError_t launch_init_population(const Shape& s, int init_mode, uint64_t seed,
 cudaError_t launch_breed(const Shape& s, const game_config& cfg, const PopDev& p,
                          const double* fit, const int* rank, DevState* state, int allow,
                          cudaStream_t st);
+// use_bred_flag: bit 0 = read the bred buffer when this generation bred, bit 1 =
+// inside game_evolve (skip when stopped).  rows (optional): row i of the planes
+// takes chromosome rows[i] of src (default: p's own population buffers).
 cudaError_t launch_prepare(const Shape& s, const PopDev& p, const ExpDev& e, DevState* state,
-                           int use_bred_flag, cudaStream_t st);
+                           int use_bred_flag, cudaStream_t st, const int* rows = nullptr,
+                           const PopDev* src = nullptr);
+cudaError_t launch_rescore_merge(const Shape& sr, const game_config& cfg, const double* partial,
+                                 int n_part, const int* rank, double* fit, const DevState* state,
+                                 int in_evolve, cudaStream_t st);
 cudaError_t launch_reduce_rank(const Shape& s, const game_config& cfg, const double* partial,
                                int n_part, double* fit, int* rank, DevState* state,
                                int mode, cudaStream_t st);
@@ -108,10 +115,13 @@ enum : int {
   kStateAfterBreed = 3,     // if bred: cur^=1, gen++ ; evaluated=0, bred=0
 };
 
-// reduce_rank modes
+// reduce_rank modes (low byte), flags: bit 8 inside game_evolve, bit 9 no stop test
 enum : int {
   kRankEvaluate = 0,        // reduce partials -> fitness, sort, update state
   kRankSortOnly = 1,        // sort the given fitness vector, mark evaluated
+  kRankResort = 2,          // sort the (re-scored) fitness vector, stop test
+  kRankInEvolve = 1 << 8,
+  kRankNoStop = 1 << 9,
 };
 
 // SIMT fitness (FFMA) over the training rows: partial sums [n_part x pop_pad].

@@ -1,0 +1,85 @@
+"""Precision form: P stored in BF16 or FP8-E4M3 with per-column scales, genes as a
+hi/lo pair in the same format, FP32 accumulation; top elites re-scored in FP32.
+
+Tolerances, from the arithmetic of the stored operands:
+* stored P: the oracle rounds the same float32 values with the same per-column
+  scale, so the stored matrix agrees exactly except where float32 rounding of P
+  itself differs (a one-quantum difference, at most 1e-4 of the elements);
+* fitness against the oracle on its own quantised P: the only difference left is
+  the two-term split of the genes, 2^-16 relative for a bf16 pair and about
+  2^-8 for an e4m3 pair.  Over ~250 genes with |P|, |G| <= 1 the output error is
+  ~16 x 2^-16 x 0.5 (bf16) and ~16 x 2^-8 x 0.5 (fp8) for random signs, which
+  bounds the relative RMSE difference by 5e-4 and 3e-2.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import game_oracle as o
+from paper_1304_0597_gb300 import synth
+from tests.gpu_helpers import lib, make_game
+
+pytestmark = pytest.mark.gpu
+
+RTOL = {"bf16": 5e-4, "fp8": 3e-2}
+
+
+def _prec(fmt):
+    game = lib()
+    return game.BF16 if fmt == "bf16" else game.FP8
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+def test_stored_expansion_matches_oracle_quantisation(fmt):
+    ds = synth.make_dataset(3000, 9, 5, seed=31)
+    ocfg = o.Config(degree=5, pop=20)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=_prec(fmt))
+    got = g.expansion(0, ds.n_patterns).astype(np.float64)
+    Q, s = o.quantize_columns(o.expand(ds.X, "chebyshev", 5)[:, 1:], fmt)
+    want = o.dequantize_columns(Q, s)
+    diff = got != want.astype(np.float32)
+    assert diff.mean() <= 1e-4
+    quantum = np.abs(want) * (2.0 ** -7 if fmt == "bf16" else 2.0 ** -3) + s[None, :] * 2.0 ** -9
+    assert np.all(np.abs(got - want)[diff] <= quantum[diff])
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+@pytest.mark.parametrize("engine", ["tcgen05", "simt"])
+@pytest.mark.parametrize("shape", [dict(n=2000, F=7, d=4, pop=20),
+                                   dict(n=30011, F=32, d=8, pop=1024)])
+def test_low_precision_fitness_matches_oracle(fmt, engine, shape):
+    game = lib()
+    ds = synth.make_dataset(shape["n"], shape["F"], shape["d"], seed=32,
+                            correlated=shape["F"] > 16)
+    ocfg = o.Config(degree=shape["d"], pop=shape["pop"], seed=2)
+    eng = game.ENGINE_TCGEN05 if engine == "tcgen05" else game.ENGINE_SIMT
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=_prec(fmt), elite_rescore=0, engine=eng)
+    G = g.population()
+    fit, _ = g.evaluate()
+    Q, s = o.quantize_columns(o.expand(ds.X[:ds.n_train], "chebyshev", shape["d"])[:, 1:], fmt)
+    Pq = np.concatenate([np.ones((ds.n_train, 1)), o.dequantize_columns(Q, s)], axis=1)
+    want = o.fitness(Pq, ds.t[:ds.n_train], G, ocfg)
+    np.testing.assert_allclose(fit, want, rtol=RTOL[fmt])
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+def test_elites_rescored_in_fp32(fmt):
+    """The top elite_rescore chromosomes carry FP32-path fitness (1e-5 of the exact
+    float64 value); the ranking is redone on the merged vector."""
+    ds = synth.make_dataset(4000, 6, 4, seed=33)
+    ocfg = o.Config(degree=4, pop=64, seed=4)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=_prec(fmt), elite_rescore=16)
+    G = g.population()
+    fit, rank = g.evaluate()
+    P = o.expand(ds.X[:ds.n_train], "chebyshev", 4)
+    exact = o.fitness(P, ds.t[:ds.n_train], G, ocfg)
+    assert list(rank) == list(o.rank(fit))
+    # the 16 chromosomes that were on top of the low-precision ranking now hold FP32 values
+    close = np.isclose(fit, exact, rtol=1e-5, atol=0)
+    assert close.sum() >= 16
+    assert close[rank[0]]
+    # evolution keeps working and reports FP32 fitness for the best
+    g.evolve(10)
+    genes, fbest, test_rmse, acc = g.best()
+    np.testing.assert_allclose(fbest, o.fitness(P, ds.t[:ds.n_train], genes[None, :], ocfg)[0],
+                               rtol=1e-5)

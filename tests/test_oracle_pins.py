@@ -430,3 +430,41 @@ def test_stop_criterion_on_planted_solution():
     G0[3] = h
     res = o.evolve(P, t, cfg, 50, G0=G0)
     assert res.generations == 1 and res.best_fitness <= 1e-12
+
+
+# ------------------------------------------------------------ low precision
+
+def test_bf16_rounding_matches_torch():
+    import torch
+    x = np.concatenate([np.random.default_rng(13).standard_normal(100000).astype(np.float32),
+                        np.array([1.0, -1.0, 0.0, 1.00390625, 1.01171875, 3.3895314e38],
+                                 dtype=np.float32)])
+    want = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    np.testing.assert_array_equal(o.round_bf16(x), want)
+
+
+def test_e4m3_rounding_matches_torch_in_range():
+    import torch
+    rng = np.random.default_rng(14)
+    x = np.concatenate([rng.uniform(-448, 448, 50000), rng.uniform(-1, 1, 50000),
+                        rng.uniform(-0.02, 0.02, 50000)]).astype(np.float32)
+    want = torch.from_numpy(x).to(torch.float8_e4m3fn).to(torch.float32).numpy()
+    np.testing.assert_array_equal(o.round_e4m3(x), want)
+    # saturation of the format's largest finite value
+    assert o.round_e4m3(np.array([500.0, -1e6], dtype=np.float32)).tolist() == [448.0, -448.0]
+    # every representable magnitude is a fixed point
+    reps = np.unique(np.abs(o.round_e4m3(rng.uniform(-448, 448, 200000).astype(np.float32))))
+    np.testing.assert_array_equal(o.round_e4m3(reps), reps)
+    assert len(reps) <= 127
+
+
+def test_quantize_columns_bounds():
+    rng = np.random.default_rng(15)
+    P = o.expand(rng.uniform(-1, 1, size=(3000, 4)), "chebyshev", 5)[:, 1:]
+    for fmt, rel in (("bf16", 2.0 ** -8), ("fp8", 2.0 ** -4)):   # unit roundoff: 7 and 3 mantissa bits
+        Q, s = o.quantize_columns(P, fmt)
+        assert np.max(np.abs(Q)) <= o.QMAX[fmt]
+        D = o.dequantize_columns(Q, s)
+        # relative rounding bound of the format for normal values, plus the subnormal floor
+        floor = s[None, :] * (2.0 ** -9 if fmt == "fp8" else 0.0)
+        assert np.all(np.abs(D - P) <= rel * np.abs(P) + floor + 1e-7)

@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--e2e-runs", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32")
+    ap.add_argument("--precision-table", action="store_true",
+                    help="print the per-precision fitness error / accuracy table and exit")
     return ap.parse_args()
 
 
@@ -243,8 +246,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     engine = {"auto": game.ENGINE_AUTO, "tcgen05": game.ENGINE_TCGEN05,
               "simt": game.ENGINE_SIMT}[args.engine]
+    prec = {"fp32": game.FP32, "bf16": game.BF16, "fp8": game.FP8}[args.precision]
     cfg = game.default_config(degree=8, pop=1024, seed=rank, stream=stream.cuda_stream,
-                              engine=engine, device=local_rank)
+                              engine=engine, device=local_rank, precision=prec)
     g = game.Game(cfg)
     g.set_data(X_pin, t_pin, ds.n_train)
     K, W = args.steps, args.warmup
@@ -311,8 +315,10 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision],
+        "data": "synthetic",
         "config": dict(workload_config(args.n_patterns), n_train=n_train,
+                       precision=args.precision,
                        engine={1: "tcgen05", 2: "simt"}.get(engine_used, "?"),
                        l2="inputs larger than L2 (expansion planes of the training rows: "
                           f"{2 * 2 * n_train * 256 / 1e6:.0f} MB)",
@@ -343,8 +349,43 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def precision_table(args):
+    """Fitness error against the float64 report, and test accuracy, per storage precision
+    (the plain small workload: 2,000 x 7, Chebyshev d=4, pop 20, 100 generations; top-16
+    elites re-scored in FP32 for BF16 / FP8)."""
+    import torch
+    from paper_1304_0597_gb300 import game, synth
+    ds = synth.plain_small()
+    rows = []
+    for name, prec in (("fp32", game.FP32), ("bf16", game.BF16), ("fp8", game.FP8)):
+        for rescore in ((0,) if prec == game.FP32 else (0, 16)):
+            g = game.Game(game.default_config(degree=4, pop=20, seed=0, precision=prec,
+                                              elite_rescore=rescore))
+            g.set_data(ds.X, ds.t, ds.n_train)
+            G = g.population()
+            fit, _ = g.evaluate()
+            exact = np.array([g.score(G[i], 0)["rmse"] for i in range(20)])
+            rel = np.abs(fit - exact) / exact
+            g.set_timing(True)
+            g.evolve(100)
+            tm = g.timing()
+            genes, fbest, test_rmse, acc = g.best()
+            exact_best = g.score(genes, 0)["rmse"]
+            rows.append({"precision": name, "elite_rescore": rescore,
+                         "gen0_fitness_rel_err_vs_fp64": {"max": float(rel.max()),
+                                                          "median": float(np.median(rel))},
+                         "best_train_rmse_reported": fbest, "best_train_rmse_fp64": exact_best,
+                         "test_rmse": test_rmse, "test_accuracy": acc,
+                         "ms_per_generation": tm["ms_total"] / 100})
+            g.close()
+    print(json.dumps({"table": "precision form on the plain small workload", "rows": rows}))
+
+
 def main():
     args = parse()
+    if args.precision_table:
+        precision_table(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -328,6 +328,8 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
     return fail(c, GAME_ERR_NUMERIC, "X or t holds NaN or Inf");
   }
   c->fit.pm1_targets = (flags & 2u) ? 0 : 1;
+  if ((r = dalloc(c, &c->e.tcoef, sizeof(float) * tpad)) != GAME_OK) return r;
+  CUDA_OK(c, launch_target_coef(c->e.t, c->e.tcoef, n_patterns, c->st));
 
   // Expansion matrix (Section 4.1: computed once, reused every generation).
   const size_t esz = s.precision == GAME_FP32 ? 2 : (s.precision == GAME_BF16 ? 2 : 1);
@@ -348,6 +350,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
     c->s32.kp = round_up(s.kb, 16);
     c->e32 = ExpDev{};
     c->e32.t = c->e.t;
+    c->e32.tcoef = c->e.tcoef;
     const size_t b32 = sizeof(__half) * (size_t)n_patterns * c->s32.kp;
     if ((r = dalloc(c, &c->e32.p0, b32)) != GAME_OK) return r;
     if ((r = dalloc(c, &c->e32.p1, b32)) != GAME_OK) return r;

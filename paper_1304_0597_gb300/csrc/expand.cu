@@ -79,13 +79,22 @@ struct ExpArgs {
   unsigned int* colmax_bits;
 };
 
+// Column maxima of |P|: block-local maxima in shared memory (non-negative floats
+// order like their bit patterns), one global atomic per block and column.
 __global__ void expand_colmax_kernel(ExpArgs a) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n * a.F) return;
-  const int f = (int)(i % a.F);
-  const float x = a.X[i];
-  unsigned int* cm = a.colmax_bits + f * a.bd;
-  basis_values(a.basis, a.d, x, [&](int b, float v) { atomicMax(cm + b, __float_as_uint(fabsf(v))); });
+  extern __shared__ unsigned int cmax[];
+  for (int c = threadIdx.x; c < a.kb; c += blockDim.x) cmax[c] = 0u;
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n * a.F;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(i % a.F);
+    unsigned int* cm = cmax + f * a.bd;
+    basis_values(a.basis, a.d, a.X[i],
+                 [&](int b, float v) { atomicMax(cm + b, __float_as_uint(fabsf(v))); });
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < a.kb; c += blockDim.x)
+    if (cmax[c]) atomicMax(a.colmax_bits + c, cmax[c]);
 }
 
 __global__ void expand_scale_kernel(const unsigned int* colmax_bits, float* colscale, int kb,
@@ -132,6 +141,16 @@ __global__ void expand_kernel(ExpArgs a) {
   }
 }
 
+__global__ void target_coef_kernel(const float* t, float* c, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) c[i] = 2.8853900817779268f * t[i];   // 2 log2(e) t
+}
+
+cudaError_t launch_target_coef(const float* t, float* c, long long n, cudaStream_t st) {
+  target_coef_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(t, c, n);
+  return cudaGetLastError();
+}
+
 __global__ void fill_ones_kernel(float* v, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = 1.0f;
@@ -161,7 +180,8 @@ cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax
   } else {
     cudaError_t err = cudaMemsetAsync(qmax_scratch, 0, sizeof(float) * s.kp, st);
     if (err != cudaSuccess) return err;
-    expand_colmax_kernel<<<blocks, threads, 0, st>>>(a);
+    const unsigned cblocks = blocks < 1216u ? blocks : 1216u;
+    expand_colmax_kernel<<<cblocks, threads, sizeof(unsigned int) * s.kb, st>>>(a);
     expand_scale_kernel<<<(s.kp + 255) / 256, 256, 0, st>>>(
         a.colmax_bits, e.colscale, s.kb, s.kp, s.precision == GAME_BF16 ? 1.0f : 448.0f);
   }

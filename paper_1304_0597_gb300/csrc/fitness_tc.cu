@@ -20,9 +20,9 @@
 // per-column scales folded into the genes, genes as a hi/lo pair with a
 // per-chromosome scale applied in the epilogue (kind::f16 bf16 / kind::f8f6f4).
 //
-// Roles (320 threads): warp 0 = TMA producer, warp 1 = TMEM allocator + MMA
-// issuer, warps 2..9 = epilogue (warp w reads TMEM lanes 32*(w%4) and half of
-// the columns).  Two TMEM accumulators let the epilogue of tile i overlap the
+// Roles (576 threads): warp 0 = TMA producer, warp 1 = TMEM allocator + MMA
+// issuer, warps 2..17 = epilogue (warp w reads TMEM lanes 32*(w%4) and a
+// quarter of the columns).  Two TMEM accumulators let the epilogue of tile i overlap the
 // MMAs of tile i+1.  Every mbarrier wait is bounded (2 s of %globaltimer); on
 // a timeout the CTA records GAME_ERR_TIMEOUT in the device state, drains its
 // outstanding copies and MMAs (again bounded), frees TMEM and exits.
@@ -34,8 +34,9 @@ namespace game {
 
 namespace {
 
-constexpr int kThreads = 320;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kColGroups = kEpiWarps / 4;     // epilogue warps sharing one TMEM lane quadrant
 constexpr int kTileA = 128 * 128;         // bytes of one 128-row x 128-byte A tile
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
@@ -43,6 +44,7 @@ struct TcParams {
   CUtensorMap a[2];
   CUtensorMap b[2];
   const float* t;
+  const float* tcoef;     // 2 log2(e) t_k (fused +-1 / tanh path)
   const float* bias;
   const float* rscale;
   double* partial;
@@ -202,33 +204,51 @@ __device__ __forceinline__ float general_error(float t, float s, int act, int er
   return e;
 }
 
-// Sum over 32 consecutive patterns of one chromosome's error.
+// Sum over 32 consecutive patterns of one chromosome's error.  The per-pattern
+// inputs (c_k = 2 log2(e) t_k for the fused path, t_k otherwise) are loaded
+// before the TMEM read so that the two latencies overlap.
 // FAST (targets +-1, tanh, MSE/RMSE): |t - tanh(s)| = 2 / (1 + exp(2 t s)), so
-// E = 4 r^2 with r = 1 / (1 + 2^(2 log2(e) t s)); the factor 4 is applied by the caller.
+// E = 4 r^2 with r = 1 / (1 + 2^(c_k s)); the factor 4 is applied by the caller.
 template <bool FAST>
-__device__ __forceinline__ float chunk_error(const float v[32], const float* __restrict__ t,
+__device__ __forceinline__ float chunk_error(uint32_t taddr, const float* __restrict__ pk,
                                              long long p0, long long m, float rs, float bias,
                                              int act, int err, float R) {
-  float sum = 0.0f;
-  const float4* t4 = reinterpret_cast<const float4*>(t + p0);
-  const bool full = p0 + 32 <= m;
+  float cq[32];
+  const float4* c4 = reinterpret_cast<const float4*>(pk + p0);
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
-    const float4 tq = __ldg(t4 + q);
-    const float tt[4] = {tq.x, tq.y, tq.z, tq.w};
+    const float4 x = __ldg(c4 + q);
+    cq[4 * q] = x.x;
+    cq[4 * q + 1] = x.y;
+    cq[4 * q + 2] = x.z;
+    cq[4 * q + 3] = x.w;
+  }
+  float v[32];
+  tmem_ld32(taddr, v);
+  float sum = 0.0f;
+  if (p0 + 32 <= m) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int j = 4 * q + i;
+    for (int j = 0; j < 32; ++j) {
+      const float s = fmaf(v[j], rs, bias);
+      if (FAST) {
+        const float r = rcp_approx(1.0f + ex2_approx(cq[j] * s));
+        sum = fmaf(r, r, sum);
+      } else {
+        sum += general_error(cq[j], s, act, err, R);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
       const float s = fmaf(v[j], rs, bias);
       float e;
       if (FAST) {
-        const float E = ex2_approx(tt[i] * 2.8853900817779268f * s);
-        const float r = rcp_approx(1.0f + E);
+        const float r = rcp_approx(1.0f + ex2_approx(cq[j] * s));
         e = r * r;
       } else {
-        e = general_error(tt[i], s, act, err, R);
+        e = general_error(cq[j], s, act, err, R);
       }
-      if (full || p0 + j < m) sum += e;
+      if (p0 + j < m) sum += e;
     }
   }
   return FAST ? 4.0f * sum : sum;
@@ -258,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* last_par = reinterpret_cast<int*>(tmem_slot + 2);          // [S]
-  double* red = reinterpret_cast<double*>(sB);   // [2][128], reused once the ring is idle
+  double* red = reinterpret_cast<double*>(sB);   // [kColGroups][128], reused once the ring is idle
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int slice = blockIdx.x % p.n_slices;
@@ -384,7 +404,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   } else {
     // ---- epilogue ----
     const int q = warp & 3;
-    const int h = (warp - 2) >> 2;
+    const int h = (warp - 2) >> 2;                    // column group 0..kColGroups-1
+    const float* pk = FAST ? p.tcoef : p.t;
     const int c = slice * 128 + q * 32 + lane;
     const float bias = p.bias[c];
     const float rs = p.rscale[c];
@@ -397,13 +418,12 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
       if (!ok) break;
       fence_after();
       const long long tile = member + (long long)it * p.cps;
-      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + h * (BN / 2));
+      constexpr int kCols = BN / kColGroups;
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + h * kCols);
 #pragma unroll 1
-      for (int ch = 0; ch < BN / 64; ++ch) {
-        float v[32];
-        tmem_ld32(tbase + ch * 32, v);
-        const long long p0 = tile * BN + h * (BN / 2) + ch * 32;
-        acc += (double)chunk_error<FAST>(v, p.t, p0, p.m, rs, bias, p.act, p.err, p.R);
+      for (int ch = 0; ch < kCols / 32; ++ch) {
+        const long long p0 = tile * BN + h * kCols + ch * 32;
+        acc += (double)chunk_error<FAST>(tbase + ch * 32, pk, p0, p.m, rs, bias, p.act, p.err, p.R);
       }
       fence_before();
       __syncwarp();
@@ -420,9 +440,12 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
                  "r"(kTmemCols));
   if (warp >= 2) red[((warp - 2) >> 2) * 128 + (warp & 3) * 32 + lane] = acc;
   __syncthreads();
-  if (threadIdx.x < 128)
-    p.partial[(long long)member * p.pop_pad + slice * 128 + threadIdx.x] =
-        red[threadIdx.x] + red[128 + threadIdx.x];
+  if (threadIdx.x < 128) {
+    double tot = 0.0;
+#pragma unroll
+    for (int g = 0; g < kColGroups; ++g) tot += red[g * 128 + threadIdx.x];
+    p.partial[(long long)member * p.pop_pad + slice * 128 + threadIdx.x] = tot;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -545,6 +568,7 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
   p.b[0] = t.b_map[0];
   p.b[1] = t.b_map[1];
   p.t = e.t;
+  p.tcoef = e.tcoef;
   p.bias = pd.bias;
   p.rscale = pd.rscale;
   p.partial = partial;

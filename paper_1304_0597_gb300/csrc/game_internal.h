@@ -70,6 +70,7 @@ struct ExpDev {
   void* p1;               // FP32: fp16 lo plane; otherwise unused
   float* colscale;        // [kp] per-column scale s_g of quantised P (1 for FP32)
   float* t;               // [n_patterns padded to 256] targets
+  float* tcoef;           // [same] 2 log2(e) t_k, read by the fused +-1 / tanh epilogue
 };
 
 struct Fitness {
@@ -85,7 +86,7 @@ cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax
                           cudaStream_t st);
 cudaError_t launch_expand_get(const Shape& s, const ExpDev& e, long long row0, long long nrows,
                               float* out, cudaStream_t st);
-bool targets_pm1(const float* t_host, long long n);
+cudaError_t launch_target_coef(const float* t, float* c, long long n, cudaStream_t st);
 
 cudaError_t launch_init_population(const Shape& s, int init_mode, uint64_t seed, uint64_t run,
                                    float* g32, cudaStream_t st);

@@ -251,6 +251,9 @@ def run_ours(args):
                               engine=engine, device=local_rank, precision=prec)
     g = game.Game(cfg)
     g.set_data(X_pin, t_pin, ds.n_train)
+    tile = None
+    if g.timing()["engine"] == game.ENGINE_TCGEN05:
+        tile, tile_cands = g.autotune(reps=3)     # library autotuner, outside the timed region
     K, W = args.steps, args.warmup
     g.evolve(W)
     g.set_timing(True)
@@ -320,6 +323,7 @@ def run_ours(args):
         "config": dict(workload_config(args.n_patterns), n_train=n_train,
                        precision=args.precision,
                        engine={1: "tcgen05", 2: "simt"}.get(engine_used, "?"),
+                       tile=tile,
                        l2="inputs larger than L2 (expansion planes of the training rows: "
                           f"{2 * 2 * n_train * 256 / 1e6:.0f} MB)",
                        parallelism=f"{world} independent runs (one per GPU)"),

@@ -88,6 +88,9 @@ typedef struct game_config {
   int32_t elite_rescore;  /* low precision: top-n re-scored with the FP32 path each gen     */
   int32_t surrogate_pool; /* 0 off; else offspring pool multiplier screened by the MLP      */
   int32_t engine;         /* GAME_ENGINE_* fitness kernel choice (AUTO picks tcgen05)       */
+  int32_t tile_n;         /* tcgen05 tile: patterns per tile, 128 | 256 (0 = tuned / auto)  */
+  int32_t tile_stages;    /* tcgen05 tile: depth of the pattern-tile ring (0 = auto)        */
+  int32_t tile_cluster;   /* tcgen05 tile: CTAs sharing a pattern tile by multicast, 1|2|4|8 (0 = auto) */
   int32_t device;         /* CUDA device ordinal                                            */
   void* stream;           /* cudaStream_t, or NULL for the legacy default stream           */
 } game_config;
@@ -187,6 +190,27 @@ typedef struct game_timing {
   int32_t engine;
 } game_timing;
 game_status game_get_timing(game_ctx* ctx, game_timing* out);
+
+/* Tile shape of the tcgen05 fitness engine, as chosen by the autotuner. */
+typedef struct game_tile {
+  int32_t n;          /* patterns per tile (MMA N)                            */
+  int32_t stages;     /* pattern-tile ring depth                              */
+  int32_t cluster;    /* CTAs sharing each pattern tile (TMA multicast)       */
+  double ms;          /* median fitness time of this shape, milliseconds      */
+} game_tile;
+
+/* Autotuner (no paper counterpart; the paper has one fixed Thrust code path):
+ * times every valid tcgen05 tile shape for this context's problem (pattern
+ * count, genes, population, precision) on the current population, reps
+ * launches each (CUDA events on the context's stream, median), switches the
+ * context to the fastest and records it in a cache file (GAME_TUNE_CACHE, else
+ * $HOME/.cache/game_gb300_tiles.txt) that later contexts with the same shape
+ * bucket read when their tile fields are 0.  *best (may be NULL) receives the
+ * choice; candidates (may be NULL, cap entries) receives every timing and
+ * *n_candidates their number.  Errors: STATE (no data), UNSUPPORTED (the shape
+ * runs on the SIMT engine). */
+game_status game_autotune(game_ctx* ctx, int32_t reps, game_tile* best, game_tile* candidates,
+                          int32_t cap, int32_t* n_candidates);
 
 /* enabled = 1: game_evolve records CUDA events around every stage of every
  * generation (on the context's stream) and game_get_timing reports their sums

@@ -16,6 +16,11 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <math.h>
+#include <stdlib.h>
+#include <sys/stat.h>
+
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -255,6 +260,43 @@ __global__ void check_data_kernel(const float* X, long long nx, const float* t, 
   if (notpm1) atomicOr(flags, 2u);
 }
 
+// ---- tile cache of the autotuner: one line per shape bucket -------------------
+//   <kp> <pop_pad> <precision> <log2 n_train> <n> <stages> <cluster> <ms>
+static std::string tune_cache_path() {
+  const char* e = getenv("GAME_TUNE_CACHE");
+  if (e && *e) return e;
+  const char* h = getenv("HOME");
+  return std::string(h && *h ? h : "/tmp") + "/.cache/game_gb300_tiles.txt";
+}
+
+static int ntrain_bucket(long long n) { return (int)floor(log2((double)(n > 0 ? n : 1))); }
+
+static bool tune_cache_lookup(const Shape& s, TileReq* out) {
+  FILE* f = fopen(tune_cache_path().c_str(), "r");
+  if (!f) return false;
+  int kp, pp, pr, nb, n, st, cl;
+  double ms;
+  bool found = false;
+  while (fscanf(f, "%d %d %d %d %d %d %d %lf", &kp, &pp, &pr, &nb, &n, &st, &cl, &ms) == 8)
+    if (kp == s.kp && pp == s.pop_pad && pr == s.precision && nb == ntrain_bucket(s.n_train)) {
+      *out = TileReq{n, st, cl};   // the last record for a bucket wins
+      found = true;
+    }
+  fclose(f);
+  return found;
+}
+
+static void tune_cache_store(const Shape& s, const game_tile& t) {
+  const std::string path = tune_cache_path();
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
+  FILE* f = fopen(path.c_str(), "a");
+  if (!f) return;
+  fprintf(f, "%d %d %d %d %d %d %d %.6f\n", s.kp, s.pop_pad, s.precision, ntrain_bucket(s.n_train),
+          t.n, t.stages, t.cluster, t.ms);
+  fclose(f);
+}
+
 static game_status choose_engine(game_ctx* c, const Shape& s, const ExpDev& e, const PopDev& p,
                                  int* engine, TcPlan* plan, int* n_part) {
   int want = c->cfg.engine;
@@ -262,7 +304,13 @@ static game_status choose_engine(game_ctx* c, const Shape& s, const ExpDev& e, c
   if (want == GAME_ENGINE_TCGEN05) {
     if (!tc_supported(s))
       return fail(c, GAME_ERR_UNSUPPORTED, "tcgen05 engine does not support this shape");
-    cudaError_t err = tc_plan(s, e, p, c->n_sm, plan);
+    TileReq req{c->cfg.tile_n, c->cfg.tile_stages, c->cfg.tile_cluster};
+    if (!req.n && !req.stages && !req.cluster) tune_cache_lookup(s, &req);
+    cudaError_t err = tc_plan(s, e, p, c->n_sm, plan, req);
+    if (err != cudaSuccess) {
+      cudaGetLastError();
+      err = tc_plan(s, e, p, c->n_sm, plan);   // a stale cache entry falls back to the default
+    }
     if (err != cudaSuccess) return fail(c, GAME_ERR_CUDA, "tcgen05 plan: %s", cudaGetErrorString(err));
     *engine = GAME_ENGINE_TCGEN05;
     *n_part = plan->n_part;
@@ -380,7 +428,8 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
     free_all(c);
     return r;
   }
-  c->part_rows = c->n_part > simt_partials(s, c->n_sm) ? c->n_part : simt_partials(s, c->n_sm);
+  // Any tile shape uses at most one partial row per SM.
+  c->part_rows = std::max(std::max(c->n_part, simt_partials(s, c->n_sm)), c->n_sm);
   if ((r = dalloc(c, &c->d_partial, sizeof(double) * (size_t)c->part_rows * s.pop_pad)) != GAME_OK)
     return r;
   c->n_rescore = 0;
@@ -775,6 +824,67 @@ extern "C" game_status game_get_state(game_ctx* c, int64_t* generation, int32_t*
   CUDA_OK(c, cudaStreamSynchronize(c->st));
   if (generation) *generation = hs.gen;
   if (stopped) *stopped = hs.stopped;
+  return GAME_OK;
+}
+
+extern "C" game_status game_autotune(game_ctx* c, int32_t reps, game_tile* best,
+                                     game_tile* candidates, int32_t cap, int32_t* n_candidates) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  if (c->engine != GAME_ENGINE_TCGEN05)
+    return fail(c, GAME_ERR_UNSUPPORTED, "this shape runs on the SIMT engine; nothing to tune");
+  if (reps < 1) reps = 1;
+  cudaSetDevice(c->dev);
+  // Operand planes of the current population.
+  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 0, c->st));
+  CUDA_OK(c, launch_prepare(c->s, c->p, c->e, c->d_state, 0, c->st));
+  std::vector<TileReq> cands;
+  tc_candidates(c->s, &cands);
+  cudaEvent_t e0, e1;
+  CUDA_OK(c, cudaEventCreate(&e0));
+  CUDA_OK(c, cudaEventCreate(&e1));
+  game_tile bt{0, 0, 0, 1e30};
+  TcPlan best_plan{};
+  int n_done = 0;
+  for (const TileReq& rq : cands) {
+    TcPlan plan{};
+    if (tc_plan(c->s, c->e, c->p, c->n_sm, &plan, rq) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (plan.n_part > c->part_rows) continue;
+    std::vector<float> t;
+    bool ok = true;
+    for (int i = 0; i <= reps && ok; ++i) {
+      ok = cudaEventRecord(e0, c->st) == cudaSuccess &&
+           tc_launch(plan, c->s, c->fit, c->p, c->e, c->d_partial, nullptr, c->st) == cudaSuccess &&
+           cudaEventRecord(e1, c->st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+      float ms = 0.f;
+      if (ok && i > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t.push_back(ms);
+    }
+    if (!ok) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return fail(c, GAME_ERR_CUDA, "autotune launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    std::sort(t.begin(), t.end());
+    const game_tile gt{plan.bn, plan.stages, plan.cluster, t[t.size() / 2]};
+    if (candidates && n_done < cap) candidates[n_done] = gt;
+    ++n_done;
+    if (gt.ms < bt.ms) {
+      bt = gt;
+      best_plan = plan;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (n_candidates) *n_candidates = n_done < cap ? n_done : cap;
+  if (bt.n == 0) return fail(c, GAME_ERR_UNSUPPORTED, "no tile shape could be planned");
+  c->tc = best_plan;
+  c->n_part = best_plan.n_part;
+  drop_graphs(c);
+  tune_cache_store(c->s, bt);
+  if (best) *best = bt;
   return GAME_OK;
 }
 

@@ -54,6 +54,7 @@ struct TcParams {
   int n_bplanes;          // FP32: 2 (P_hi, P_lo); else 1
   int act, err, in_evolve;
   float R;
+  int cl;                 // CTAs per cluster sharing each B tile by multicast (1 = none)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -119,6 +120,28 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Multicast variant: the box lands at the same shared-memory offset in every CTA
+// of ctaMask, and completes bytes on the mbarrier at the same offset in each.
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int c0, int c1,
+                                               uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (stride byte offset), descriptor version 1 (tcgen05).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -156,6 +179,16 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(bar))
+      : "memory");
+}
+
+// Arrive (when this CTA's MMAs complete) on the mbarrier at the same offset in
+// every CTA of ctaMask.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(smem_u32(bar)),
+      "h"(mask)
       : "memory");
 }
 
@@ -290,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     mbar_init(a_full, 1);
     for (int s = 0; s < S; ++s) {
       mbar_init(b_full + s, 1);
-      mbar_init(b_empty + s, 1);
+      mbar_init(b_empty + s, p.cl);     // one MMA commit from every CTA that reads the tile
       last_par[s] = -1;
     }
     for (int b = 0; b < 2; ++b) {
@@ -311,7 +344,12 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   fence_before();
   __syncthreads();
   fence_after();
+  // Peers multicast into this CTA's ring: every barrier of the cluster exists first.
+  if (p.cl > 1) cluster_sync_all();
   const uint32_t tmem = *tmem_slot;
+  const uint32_t crank = p.cl > 1 ? cluster_rank() : 0u;
+  const uint16_t cmask = (uint16_t)((1u << p.cl) - 1u);
+  const int sub_rows = BN / p.cl;                     // rows of the B tile this CTA fetches
   const int a_steps_total = p.kp / kKStep;
   double acc = 0.0;   // epilogue threads: this chromosome's error sum over its columns
 
@@ -331,8 +369,12 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
         for (int kb = 0; kb < p.kblocks && !*err; ++kb)
           for (int bp = 0; bp < p.n_bplanes; ++bp) {
             if (!mbar_wait(b_empty + stage, phase ^ 1u, err, p.state)) break;
-            mbar_expect_tx(b_full + stage, kTileB);
-            tma_load_2d(sB + stage * kTileB, &p.b[bp], kb * kKB, row0, b_full + stage);
+            mbar_expect_tx(b_full + stage, kTileB);     // the whole tile lands here
+            if (p.cl > 1)
+              tma_load_2d_mc(sB + stage * kTileB + crank * sub_rows * 128, &p.b[bp], kb * kKB,
+                             row0 + (int)crank * sub_rows, b_full + stage, cmask);
+            else
+              tma_load_2d(sB + stage * kTileB, &p.b[bp], kb * kKB, row0, b_full + stage);
             last_par[stage] = (int)phase;
             if (++stage == S) {
               stage = 0;
@@ -383,7 +425,10 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
                   accum = 1;
                 }
               }
-              mma_commit(b_empty + stage);
+              if (p.cl > 1)
+                mma_commit_mc(b_empty + stage, cmask);
+              else
+                mma_commit(b_empty + stage);
               if (++stage == S) {
                 stage = 0;
                 phase ^= 1u;
@@ -446,6 +491,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     for (int g = 0; g < kColGroups; ++g) tot += red[g * 128 + threadIdx.x];
     p.partial[(long long)member * p.pop_pad + slice * 128 + threadIdx.x] = tot;
   }
+  // No CTA leaves while a peer may still signal its barriers.
+  if (p.cl > 1) cluster_sync_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -528,32 +575,84 @@ bool tc_supported(const Shape& s) {
   return a_bytes + 2 * 128 * 128 + kSmemMisc <= kSmemMax;
 }
 
-cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, TcPlan* plan) {
+static int max_stages(const Shape& s, int bn) {
+  const int room = kSmemMax - kSmemMisc - 2 * kblocks_of(s) * kTileA;
+  int st = room / (bn * 128);
+  return st > 8 ? 8 : st;
+}
+
+void tc_candidates(const Shape& s, std::vector<TileReq>* out) {
+  const int n_slices = s.pop_pad / 128;
+  for (int bn : {256, 128}) {
+    const int ms = max_stages(s, bn);
+    for (int st = ms; st >= 2 && st >= ms - 1; --st)
+      for (int cl : {1, 2, 4, 8})
+        if (n_slices % cl == 0 && bn / cl >= 16) out->push_back(TileReq{bn, st, cl});
+  }
+}
+
+cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, TcPlan* plan,
+                    TileReq req) {
   TcPlan& t = *plan;
   t.kblocks = kblocks_of(s);
   const int a_bytes = 2 * t.kblocks * kTileA;
-  const int room = kSmemMax - kSmemMisc - a_bytes;
   const int n_bplanes = s.precision == GAME_FP32 ? 2 : 1;
-  // Prefer 256-pattern tiles when three stages fit; else 128-pattern tiles.
-  t.bn = (room >= 3 * 256 * 128) ? 256 : 128;
-  t.stages = room / (t.bn * 128);
-  if (t.stages > 8) t.stages = 8;
-  if (t.stages < 2) return cudaErrorNotSupported;
   t.n_slices = s.pop_pad / 128;
+  // Default shape: 256-pattern tiles when three stages fit, else 128; multicast
+  // across the largest power-of-two group of slices up to 4.
+  t.bn = req.n ? req.n : (max_stages(s, 256) >= 3 ? 256 : 128);
+  if (t.bn != 128 && t.bn != 256) return cudaErrorInvalidValue;
+  const int ms = max_stages(s, t.bn);
+  t.stages = req.stages ? req.stages : ms;
+  if (t.stages < 2 || t.stages > ms) return cudaErrorNotSupported;
+  int cl = req.cluster;
+  if (!cl) {
+    cl = 1;
+    for (int c : {4, 2})
+      if (t.n_slices % c == 0) {
+        cl = c;
+        break;
+      }
+  }
+  if (t.n_slices % cl != 0 || t.bn / cl < 16 || cl > 8) return cudaErrorInvalidValue;
+  t.cluster = cl;
   t.n_tiles = (int)((s.n_train + t.bn - 1) / t.bn);
-  int cps = n_sm / t.n_slices;
+  t.smem = (size_t)a_bytes + (size_t)t.stages * t.bn * 128 + kSmemMisc;
+  // Co-resident CTAs under this cluster shape (clusters must fit in one GPC).
+  int resident = n_sm;
+  if (cl > 1) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = cl;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(cl * 64);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = t.smem;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n_clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&n_clusters, pick_kernel(t.bn, s.precision, true), &cfg) ==
+            cudaSuccess &&
+        n_clusters > 0)
+      resident = n_clusters * cl;
+    else
+      cudaGetLastError();
+  }
+  int cps = resident / t.n_slices;
   if (cps < 1) cps = 1;
   if (cps > t.n_tiles) cps = t.n_tiles;
   t.ctas_per_slice = cps;
   t.grid = t.n_slices * cps;
   t.n_part = cps;
-  t.smem = (size_t)a_bytes + (size_t)t.stages * t.bn * 128 + kSmemMisc;
   cudaError_t err;
   if ((err = make_map(&t.a_map[0], p.ghi, s.precision, s.pop_pad, s.kp, 128)) != cudaSuccess) return err;
   if ((err = make_map(&t.a_map[1], p.glo, s.precision, s.pop_pad, s.kp, 128)) != cudaSuccess) return err;
-  if ((err = make_map(&t.b_map[0], e.p0, s.precision, s.n_train, s.kp, t.bn)) != cudaSuccess) return err;
+  const int box = t.bn / cl;
+  if ((err = make_map(&t.b_map[0], e.p0, s.precision, s.n_train, s.kp, box)) != cudaSuccess) return err;
   if (n_bplanes == 2) {
-    if ((err = make_map(&t.b_map[1], e.p1, s.precision, s.n_train, s.kp, t.bn)) != cudaSuccess) return err;
+    if ((err = make_map(&t.b_map[1], e.p1, s.precision, s.n_train, s.kp, box)) != cudaSuccess) return err;
   } else {
     t.b_map[1] = t.b_map[0];
   }
@@ -586,12 +685,26 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
   p.err = f.error;
   p.R = f.tmse_R;
   p.in_evolve = state != nullptr;
+  p.cl = t.cluster;
   const bool fast = f.pm1_targets && f.activation == GAME_TANH &&
                     (f.error == GAME_RMSE || f.error == GAME_MSE);
   void* k = pick_kernel(t.bn, s.precision, fast);
   if (!k) return cudaErrorNotSupported;
   void* args[] = {&p};
-  return cudaLaunchKernel(k, dim3(t.grid), dim3(kThreads), args, t.smem, st);
+  if (t.cluster <= 1) return cudaLaunchKernel(k, dim3(t.grid), dim3(kThreads), args, t.smem, st);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = t.cluster;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.gridDim = dim3(t.grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = t.smem;
+  cfg.stream = st;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, k, args);
 }
 
 }  // namespace game

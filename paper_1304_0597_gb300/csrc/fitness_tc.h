@@ -3,6 +3,8 @@
 
 #include <cuda.h>
 
+#include <vector>
+
 #include "game_internal.h"
 
 namespace game {
@@ -18,11 +20,20 @@ struct TcPlan {
   int bn;                 // patterns per tile (MMA N)
   int kblocks;            // k-blocks of 128 bytes over kp
   int stages;             // B-operand pipeline depth
+  int cluster;            // CTAs (one per slice) sharing each B tile by TMA multicast
   size_t smem;            // dynamic shared memory bytes
 };
 
+// Requested tile shape; 0 fields are chosen automatically.
+struct TileReq {
+  int n = 0, stages = 0, cluster = 0;
+};
+
 bool tc_supported(const Shape& s);
-cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, TcPlan* plan);
+cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, TcPlan* plan,
+                    TileReq req = TileReq{});
+// Every valid explicit tile shape for this problem (for the autotuner).
+void tc_candidates(const Shape& s, std::vector<TileReq>* out);
 cudaError_t tc_launch(const TcPlan& plan, const Shape& s, const Fitness& f, const PopDev& p,
                       const ExpDev& e, double* partial, const DevState* state, cudaStream_t st);
 cudaError_t tc_init_attributes();

@@ -38,6 +38,7 @@ class GameConfig(C.Structure):
         ("init", C.c_int32), ("clamp_genes", C.c_int32), ("stop_error", C.c_double),
         ("seed", C.c_uint64), ("run", C.c_uint64), ("precision", C.c_int32),
         ("elite_rescore", C.c_int32), ("surrogate_pool", C.c_int32), ("engine", C.c_int32),
+        ("tile_n", C.c_int32), ("tile_stages", C.c_int32), ("tile_cluster", C.c_int32),
         ("device", C.c_int32), ("stream", C.c_void_p),
     ]
 
@@ -45,6 +46,10 @@ class GameConfig(C.Structure):
 class GameTiming(C.Structure):
     _fields_ = [("ms_breed", C.c_double), ("ms_fitness", C.c_double), ("ms_rank", C.c_double),
                 ("ms_total", C.c_double), ("generations", C.c_int32), ("engine", C.c_int32)]
+
+
+class GameTile(C.Structure):
+    _fields_ = [("n", C.c_int32), ("stages", C.c_int32), ("cluster", C.c_int32), ("ms", C.c_double)]
 
 
 class GameError(RuntimeError):
@@ -77,6 +82,8 @@ def _load() -> C.CDLL:
         "game_get_state": (I32, [P, C.POINTER(I64), C.POINTER(I32)]),
         "game_get_timing": (I32, [P, C.POINTER(GameTiming)]),
         "game_set_timing": (I32, [P, I32]),
+        "game_autotune": (I32, [P, I32, C.POINTER(GameTile), C.POINTER(GameTile), I32,
+                                C.POINTER(I32)]),
         "game_fitness_noalloc": (I32, [P, P, P, I64, I32, I32, I32, I32, F, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -217,6 +224,14 @@ class Game:
         gen, stopped = C.c_int64(), C.c_int32()
         self._check(lib.game_get_state(self.h, C.byref(gen), C.byref(stopped)), self.h)
         return gen.value, stopped.value
+
+    def autotune(self, reps: int = 5):
+        best = GameTile()
+        cands = (GameTile * 64)()
+        n = C.c_int32(0)
+        self._check(lib.game_autotune(self.h, reps, C.byref(best), cands, 64, C.byref(n)), self.h)
+        tile = lambda t: {"n": t.n, "stages": t.stages, "cluster": t.cluster, "ms": t.ms}
+        return tile(best), [tile(cands[i]) for i in range(n.value)]
 
     def set_timing(self, enabled: bool) -> None:
         self._check(lib.game_set_timing(self.h, int(bool(enabled))), self.h)

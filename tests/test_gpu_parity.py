@@ -236,3 +236,38 @@ def test_calls_out_of_order_are_state_errors():
     with pytest.raises(game.GameError) as e:
         g.evolve(1)
     assert e.value.status == -2
+
+
+# ------------------------------------------------------------ tile shapes
+
+@pytest.mark.parametrize("tile", [(256, 3, 1), (256, 2, 2), (256, 3, 4), (256, 3, 8), (128, 5, 1),
+                                  (128, 4, 2), (128, 5, 8)])
+def test_tcgen05_tile_shapes_agree(tile):
+    """Every tile shape (patterns per tile, ring depth, multicast cluster) gives the oracle's
+    fitness; population 1024 = 8 slices, so clusters of 2, 4 and 8 share pattern tiles."""
+    game = lib()
+    ds = synth.make_dataset(20011, 32, 8, seed=41, correlated=True)
+    ocfg = _cfg(degree=8, pop=1024, seed=3)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=game.ENGINE_TCGEN05, tile_n=tile[0],
+                  tile_stages=tile[1], tile_cluster=tile[2])
+    fit, _ = g.evaluate()
+    P = o.expand(ds.X[:ds.n_train], "chebyshev", 8)
+    np.testing.assert_allclose(fit, o.fitness(P, ds.t[:ds.n_train], g.population(), ocfg),
+                               rtol=FIT_RTOL)
+
+
+def test_autotune_picks_a_valid_shape(tmp_path, monkeypatch):
+    game = lib()
+    monkeypatch.setenv("GAME_TUNE_CACHE", str(tmp_path / "tiles.txt"))
+    ds = synth.make_dataset(30000, 16, 8, seed=42, correlated=True)
+    ocfg = _cfg(degree=8, pop=512, seed=1)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    before, _ = g.evaluate()
+    best, cands = g.autotune(reps=2)
+    assert len(cands) >= 4 and best["ms"] == min(c["ms"] for c in cands)
+    after, _ = g.evaluate()
+    np.testing.assert_allclose(after, before, rtol=1e-6)
+    assert (tmp_path / "tiles.txt").read_text().strip()
+    # a new context with the same shape bucket picks the cached shape up
+    h = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    np.testing.assert_allclose(h.evaluate()[0], before, rtol=1e-6)

@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32")
+    ap.add_argument("--gene-planes", type=int, choices=[1, 2], default=2,
+                    help="low precision: genes as one or two terms of P's format")
     ap.add_argument("--precision-table", action="store_true",
                     help="print the per-precision fitness error / accuracy table and exit")
     return ap.parse_args()
@@ -248,7 +250,8 @@ def run_ours(args):
               "simt": game.ENGINE_SIMT}[args.engine]
     prec = {"fp32": game.FP32, "bf16": game.BF16, "fp8": game.FP8}[args.precision]
     cfg = game.default_config(degree=8, pop=1024, seed=rank, stream=stream.cuda_stream,
-                              engine=engine, device=local_rank, precision=prec)
+                              engine=engine, device=local_rank, precision=prec,
+                              gene_planes=args.gene_planes)
     g = game.Game(cfg)
     g.set_data(X_pin, t_pin, ds.n_train)
     tile = None
@@ -322,6 +325,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": dict(workload_config(args.n_patterns), n_train=n_train,
                        precision=args.precision,
+                       gene_planes=args.gene_planes if args.precision != "fp32" else None,
                        engine={1: "tcgen05", 2: "simt"}.get(engine_used, "?"),
                        tile=tile,
                        l2="inputs larger than L2 (expansion planes of the training rows: "
@@ -362,9 +366,10 @@ def precision_table(args):
     ds = synth.plain_small()
     rows = []
     for name, prec in (("fp32", game.FP32), ("bf16", game.BF16), ("fp8", game.FP8)):
-        for rescore in ((0,) if prec == game.FP32 else (0, 16)):
+        for rescore, planes in (((0, 2),) if prec == game.FP32 else
+                                ((0, 2), (16, 2), (0, 1), (16, 1))):
             g = game.Game(game.default_config(degree=4, pop=20, seed=0, precision=prec,
-                                              elite_rescore=rescore))
+                                              elite_rescore=rescore, gene_planes=planes))
             g.set_data(ds.X, ds.t, ds.n_train)
             G = g.population()
             fit, _ = g.evaluate()
@@ -375,7 +380,7 @@ def precision_table(args):
             tm = g.timing()
             genes, fbest, test_rmse, acc = g.best()
             exact_best = g.score(genes, 0)["rmse"]
-            rows.append({"precision": name, "elite_rescore": rescore,
+            rows.append({"precision": name, "elite_rescore": rescore, "gene_planes": planes,
                          "gen0_fitness_rel_err_vs_fp64": {"max": float(rel.max()),
                                                           "median": float(np.median(rel))},
                          "best_train_rmse_reported": fbest, "best_train_rmse_fp64": exact_best,

@@ -86,6 +86,7 @@ typedef struct game_config {
   uint64_t run;           /* Philox key word 1 (independent runs with one seed)            */
   int32_t precision;      /* GAME_FP32 | GAME_BF16 | GAME_FP8 storage of P                  */
   int32_t elite_rescore;  /* low precision: top-n re-scored with the FP32 path each gen     */
+  int32_t gene_planes;    /* low precision: genes as 1 or 2 terms in P's format (0 = 2)     */
   int32_t surrogate_pool; /* 0 off; else offspring pool multiplier screened by the MLP      */
   int32_t engine;         /* GAME_ENGINE_* fitness kernel choice (AUTO picks tcgen05)       */
   int32_t tile_n;         /* tcgen05 tile: patterns per tile, 128 | 256 (0 = tuned / auto)  */

@@ -584,3 +584,29 @@ def quantize_columns(P: np.ndarray, fmt: str):
 
 def dequantize_columns(Q: np.ndarray, s: np.ndarray) -> np.ndarray:
     return np.asarray(Q, dtype=np.float64) * np.asarray(s, dtype=np.float64)[None, :]
+
+
+def quantize_genes(G: np.ndarray, s: np.ndarray, fmt: str, planes: int) -> np.ndarray:
+    """Genes as a low-precision contraction meets them.
+
+    With P stored as Q * s (``quantize_columns``), gene g of chromosome c meets Q
+    through g' = g s_g (float32 product); per chromosome r_c = max_g |g'| / qmax;
+    the operand holds one term hi = q(g'/r_c) or two, hi + q(g'/r_c - hi), in the
+    format.  Returns the genes the contraction effectively multiplies with the
+    dequantised P: (hi [+ lo]) r_c / s_g, with the bias (gene 0) unchanged.
+    """
+    G = np.asarray(G, dtype=np.float32)
+    s = np.asarray(s, dtype=np.float32)
+    q = round_bf16 if fmt == "bf16" else round_e4m3
+    gp = (G[:, 1:] * s[None, :]).astype(np.float32)
+    m = np.max(np.abs(gp), axis=1)
+    r = np.where(m > 0, m / np.float32(QMAX[fmt]), np.float32(1.0)).astype(np.float32)
+    w = (gp / r[:, None]).astype(np.float32)
+    hi = q(w)
+    val = hi.astype(np.float64)
+    if planes == 2:
+        val = val + q((w - hi).astype(np.float32)).astype(np.float64)
+    out = np.empty(G.shape, dtype=np.float64)
+    out[:, 0] = G[:, 0]
+    out[:, 1:] = val * r.astype(np.float64)[:, None] / s.astype(np.float64)[None, :]
+    return out

@@ -184,6 +184,8 @@ static game_status validate(game_ctx* c, const game_config* cfg) {
   if (cfg->engine < GAME_ENGINE_AUTO || cfg->engine > GAME_ENGINE_SIMT)
     return fail(c, GAME_ERR_INVALID_ARG, "bad engine");
   if (cfg->surrogate_pool < 0) return fail(c, GAME_ERR_INVALID_ARG, "bad surrogate_pool");
+  if (cfg->gene_planes < 0 || cfg->gene_planes > 2)
+    return fail(c, GAME_ERR_INVALID_ARG, "gene_planes must be 0, 1 or 2");
   return GAME_OK;
 }
 
@@ -349,6 +351,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   s.pop = c->cfg.pop;
   s.pop_pad = round_up(s.pop, 128);
   s.precision = c->cfg.precision;
+  s.gene_planes = (s.precision == GAME_FP32 || c->cfg.gene_planes != 1) ? 2 : 1;
   c->fit.error = c->cfg.error;
   c->fit.activation = c->cfg.activation;
   c->fit.tmse_R = c->cfg.tmse_R;
@@ -395,6 +398,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   if (c->lowp) {
     // The FP32 planes serve the elite re-score and the float64 report.
     c->s32.precision = GAME_FP32;
+    c->s32.gene_planes = 2;
     c->s32.kp = round_up(s.kb, 16);
     c->e32 = ExpDev{};
     c->e32.t = c->e.t;

@@ -52,6 +52,7 @@ struct TcParams {
   long long m;            // training rows
   int n_slices, cps, n_tiles, kblocks, kp, stages, pop_pad;
   int n_bplanes;          // FP32: 2 (P_hi, P_lo); else 1
+  int n_aplanes;          // gene planes resident in shared memory (1 or 2)
   int act, err, in_evolve;
   float R;
   int cl;                 // CTAs per cluster sharing each B tile by multicast (1 = none)
@@ -109,6 +110,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
       return false;
     }
   }
+}
+
+// Warp-uniform bounded wait: lane 0 polls, the outcome is broadcast.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* err,
+                                          DevState* st, int lane) {
+  int ok = 0;
+  if (lane == 0) ok = mbar_wait(bar, parity, err, st) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
@@ -228,6 +237,23 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
+// 2^u on the FMA pipe: u = j + f with j = floor(u), f in [0,1); 2^f by a
+// degree-5 polynomial fitted to 2^f on [0,1) (relative error 1.6e-7, the size
+// of the hardware ex2.approx error); 2^j added to the exponent field.  Used for
+// part of the elements so that the MUFU unit is not the only exp2 engine.
+__device__ __forceinline__ float exp2_poly(float u) {
+  u = fminf(fmaxf(u, -125.0f), 125.0f);
+  const float j = floorf(u);
+  const float f = u - j;
+  float p = 0x1.ec31c6p-10f;
+  p = fmaf(p, f, 0x1.269022p-7f);
+  p = fmaf(p, f, 0x1.c95442p-5f);
+  p = fmaf(p, f, 0x1.ebd5aap-3f);
+  p = fmaf(p, f, 0x1.62e4f6p-1f);
+  p = fmaf(p, f, 0x1.fffffep-1f);
+  return __int_as_float(__float_as_int(p) + ((int)j << 23));
+}
+
 __device__ __forceinline__ float general_error(float t, float s, int act, int err, float R) {
   const float y = act == GAME_TANH ? tanhf(s) : s;
   const float d = t - y;
@@ -264,7 +290,10 @@ __device__ __forceinline__ float chunk_error(uint32_t taddr, const float* __rest
     for (int j = 0; j < 32; ++j) {
       const float s = fmaf(v[j], rs, bias);
       if (FAST) {
-        const float r = rcp_approx(1.0f + ex2_approx(cq[j] * s));
+        // 18 of 32 exponentials on the FMA pipe, 14 on MUFU: balances the two units
+        const float u = cq[j] * s;
+        const float E = (j & 15) < 9 ? exp2_poly(u) : ex2_approx(u);
+        const float r = rcp_approx(1.0f + E);
         sum = fmaf(r, r, sum);
       } else {
         sum += general_error(cq[j], s, act, err, R);
@@ -300,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   constexpr uint32_t kIdesc = make_idesc(128, BN, kFmt);
   const int S = p.stages;
   uint8_t* sA = smem;
-  uint8_t* sB = sA + 2 * p.kblocks * kTileA;
+  uint8_t* sB = sA + p.n_aplanes * p.kblocks * kTileA;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + S * kTileB);
   uint64_t* a_full = bars;
   uint64_t* b_full = bars + 1;
@@ -354,21 +383,27 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   double acc = 0.0;   // epilogue threads: this chromosome's error sum over its columns
 
   if (warp == 0) {
+    // ---- TMA producer: the whole warp follows one control flow, lane 0 issues ----
     if (lane == 0) {
-      // ---- TMA producer ----
-      const uint32_t a_bytes = 2u * p.kblocks * kTileA;
+      const uint32_t a_bytes = (uint32_t)p.n_aplanes * p.kblocks * kTileA;
       mbar_expect_tx(a_full, a_bytes);
-      for (int pl = 0; pl < 2; ++pl)
+      for (int pl = 0; pl < p.n_aplanes; ++pl)
         for (int kb = 0; kb < p.kblocks; ++kb)
           tma_load_2d(sA + (pl * p.kblocks + kb) * kTileA, &p.a[pl], kb * kKB, slice * 128,
                       a_full);
-      int stage = 0;
-      uint32_t phase = 0;
-      for (int it = 0; it < my_tiles && !*err; ++it) {
-        const int row0 = (member + it * p.cps) * BN;
-        for (int kb = 0; kb < p.kblocks && !*err; ++kb)
-          for (int bp = 0; bp < p.n_bplanes; ++bp) {
-            if (!mbar_wait(b_empty + stage, phase ^ 1u, err, p.state)) break;
+    }
+    int stage = 0;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int it = 0; it < my_tiles && ok; ++it) {
+      const int row0 = (member + it * p.cps) * BN;
+      for (int kb = 0; kb < p.kblocks && ok; ++kb)
+        for (int bp = 0; bp < p.n_bplanes; ++bp) {
+          if (!warp_wait(b_empty + stage, phase ^ 1u, err, p.state, lane)) {
+            ok = false;
+            break;
+          }
+          if (lane == 0) {
             mbar_expect_tx(b_full + stage, kTileB);     // the whole tile lands here
             if (p.cl > 1)
               tma_load_2d_mc(sB + stage * kTileB + crank * sub_rows * 128, &p.b[bp], kb * kKB,
@@ -376,70 +411,81 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
             else
               tma_load_2d(sB + stage * kTileB, &p.b[bp], kb * kKB, row0, b_full + stage);
             last_par[stage] = (int)phase;
+          }
+          if (++stage == S) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+    }
+    // Drain: every issued copy has landed before the CTA may exit.
+    if (lane == 0) {
+      mbar_wait(a_full, 0, err, p.state);
+      for (int s2 = 0; s2 < S; ++s2)
+        if (last_par[s2] >= 0) {
+          const unsigned long long t0 = globaltimer();
+          while (!mbar_try_wait(b_full + s2, (uint32_t)last_par[s2]) && globaltimer() - t0 < kWaitNs) {
+          }
+        }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---- MMA issuer: warp-uniform loop (descriptors in uniform registers), lane 0 issues ----
+    if (warp_wait(a_full, 0, err, p.state, lane)) {
+      fence_after();
+      int stage = 0;
+      uint32_t phase = 0;
+      const uint32_t a_addr = smem_u32(sA);
+      const uint32_t b_addr = smem_u32(sB);
+      for (int it = 0; it < my_tiles; ++it) {
+        const int buf = it & 1;
+        const uint32_t ap = (uint32_t)((it >> 1) & 1);
+        if (!warp_wait(acc_empty + buf, ap ^ 1u, err, p.state, lane)) break;
+        fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * BN);
+        uint32_t accum = 0;
+        bool ok = true;
+        for (int kb = 0; kb < p.kblocks && ok; ++kb) {
+          const int steps = min(kKB / kKStep, a_steps_total - kb * (kKB / kKStep));
+          for (int bp = 0; bp < p.n_bplanes; ++bp) {
+            if (!warp_wait(b_full + stage, phase, err, p.state, lane)) {
+              ok = false;
+              break;
+            }
+            fence_after();
+            const uint64_t bdesc = sw128_desc(b_addr + (uint32_t)(stage * kTileB));
+            // FP32 split: B = P_hi meets A = G_hi and G_lo; B = P_lo meets G_hi.
+            const int n_ap = (p.n_bplanes == 2 && bp == 1) ? 1 : p.n_aplanes;
+            for (int ai = 0; ai < n_ap; ++ai) {
+              const uint64_t adesc =
+                  sw128_desc(a_addr + (uint32_t)((ai * p.kblocks + kb) * kTileA));
+#pragma unroll
+              for (int k = 0; k < kKB / kKStep; ++k) {
+                if (k < steps) {
+                  // +32 bytes along K inside the 128-byte swizzle row = +2 in the address field
+                  if (lane == 0) mma<PREC>(d, adesc + 2 * k, bdesc + 2 * k, kIdesc, accum);
+                  accum = 1;
+                }
+              }
+            }
+            if (lane == 0) {
+              if (p.cl > 1)
+                mma_commit_mc(b_empty + stage, cmask);
+              else
+                mma_commit(b_empty + stage);
+            }
             if (++stage == S) {
               stage = 0;
               phase ^= 1u;
             }
           }
-      }
-      // Drain: every issued copy has landed before the CTA may exit.
-      if (!mbar_wait(a_full, 0, err, p.state)) { /* recorded */ }
-      for (int s = 0; s < S; ++s)
-        if (last_par[s] >= 0) {
-          const unsigned long long t0 = globaltimer();
-          while (!mbar_try_wait(b_full + s, (uint32_t)last_par[s]) && globaltimer() - t0 < kWaitNs) {
-          }
         }
+        if (!ok) break;
+        if (lane == 0) mma_commit(acc_full + buf);
+      }
     }
-  } else if (warp == 1) {
+    // Drain: all issued MMAs complete before TMEM is released.
     if (lane == 0) {
-      // ---- MMA issuer ----
-      if (mbar_wait(a_full, 0, err, p.state)) {
-        fence_after();
-        int stage = 0;
-        uint32_t phase = 0;
-        for (int it = 0; it < my_tiles && !*err; ++it) {
-          const int buf = it & 1;
-          const uint32_t ap = (uint32_t)((it >> 1) & 1);
-          if (!mbar_wait(acc_empty + buf, ap ^ 1u, err, p.state)) break;
-          fence_after();
-          const uint32_t d = tmem + (uint32_t)(buf * BN);
-          uint32_t accum = 0;
-          bool ok = true;
-          for (int kb = 0; kb < p.kblocks && ok; ++kb) {
-            const int steps = min(kKB / kKStep, a_steps_total - kb * (kKB / kKStep));
-            for (int bp = 0; bp < p.n_bplanes; ++bp) {
-              if (!mbar_wait(b_full + stage, phase, err, p.state)) {
-                ok = false;
-                break;
-              }
-              fence_after();
-              const uint32_t b_base = smem_u32(sB + stage * kTileB);
-              // FP32 split: B = P_hi meets A = G_hi and G_lo; B = P_lo meets G_hi.
-              const int n_ap = (p.n_bplanes == 2 && bp == 1) ? 1 : 2;
-              for (int ai = 0; ai < n_ap; ++ai) {
-                const uint32_t a_base = smem_u32(sA + (ai * p.kblocks + kb) * kTileA);
-                for (int k = 0; k < steps; ++k) {
-                  mma<PREC>(d, sw128_desc(a_base + 32 * k), sw128_desc(b_base + 32 * k), kIdesc,
-                            accum);
-                  accum = 1;
-                }
-              }
-              if (p.cl > 1)
-                mma_commit_mc(b_empty + stage, cmask);
-              else
-                mma_commit(b_empty + stage);
-              if (++stage == S) {
-                stage = 0;
-                phase ^= 1u;
-              }
-            }
-          }
-          if (!ok) break;
-          mma_commit(acc_full + buf);
-        }
-      }
-      // Drain: all issued MMAs complete before TMEM is released.
       mma_commit(fin);
       const unsigned long long t0 = globaltimer();
       while (!mbar_try_wait(fin, 0) && globaltimer() - t0 < kWaitNs) {
@@ -457,10 +503,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     for (int it = 0; it < my_tiles; ++it) {
       const int buf = it & 1;
       const uint32_t ap = (uint32_t)((it >> 1) & 1);
-      bool ok = true;
-      if (lane == 0) ok = mbar_wait(acc_full + buf, ap, err, p.state);
-      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      if (!ok) break;
+      if (!warp_wait(acc_full + buf, ap, err, p.state, lane)) break;
       fence_after();
       const long long tile = member + (long long)it * p.cps;
       constexpr int kCols = BN / kColGroups;
@@ -570,13 +613,13 @@ cudaError_t tc_init_attributes() {
 
 bool tc_supported(const Shape& s) {
   if (!encode_fn()) return false;
-  const int a_bytes = 2 * kblocks_of(s) * kTileA;
+  const int a_bytes = s.gene_planes * kblocks_of(s) * kTileA;
   // at least two B stages of 128 rows next to the resident gene planes
   return a_bytes + 2 * 128 * 128 + kSmemMisc <= kSmemMax;
 }
 
 static int max_stages(const Shape& s, int bn) {
-  const int room = kSmemMax - kSmemMisc - 2 * kblocks_of(s) * kTileA;
+  const int room = kSmemMax - kSmemMisc - s.gene_planes * kblocks_of(s) * kTileA;
   int st = room / (bn * 128);
   return st > 8 ? 8 : st;
 }
@@ -595,7 +638,7 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
                     TileReq req) {
   TcPlan& t = *plan;
   t.kblocks = kblocks_of(s);
-  const int a_bytes = 2 * t.kblocks * kTileA;
+  const int a_bytes = s.gene_planes * t.kblocks * kTileA;
   const int n_bplanes = s.precision == GAME_FP32 ? 2 : 1;
   t.n_slices = s.pop_pad / 128;
   // Default shape: 256-pattern tiles when three stages fit, else 128; multicast
@@ -681,6 +724,7 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
   p.stages = t.stages;
   p.pop_pad = s.pop_pad;
   p.n_bplanes = s.precision == GAME_FP32 ? 2 : 1;
+  p.n_aplanes = s.gene_planes;
   p.act = f.activation;
   p.err = f.error;
   p.R = f.tmse_R;

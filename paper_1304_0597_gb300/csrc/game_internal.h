@@ -52,6 +52,7 @@ struct Shape {
   int pop;                // population size
   int pop_pad;            // pop padded to the 128-row MMA tile
   int precision;          // GAME_FP32 | GAME_BF16 | GAME_FP8
+  int gene_planes;        // terms of each gene in the operand planes (FP32: always 2)
 };
 
 // Population double buffer plus the operand planes of the population being evaluated.

@@ -37,7 +37,7 @@ class GameConfig(C.Structure):
         ("error", C.c_int32), ("tmse_R", C.c_float), ("activation", C.c_int32),
         ("init", C.c_int32), ("clamp_genes", C.c_int32), ("stop_error", C.c_double),
         ("seed", C.c_uint64), ("run", C.c_uint64), ("precision", C.c_int32),
-        ("elite_rescore", C.c_int32), ("surrogate_pool", C.c_int32), ("engine", C.c_int32),
+        ("elite_rescore", C.c_int32), ("gene_planes", C.c_int32), ("surrogate_pool", C.c_int32), ("engine", C.c_int32),
         ("tile_n", C.c_int32), ("tile_stages", C.c_int32), ("tile_cluster", C.c_int32),
         ("device", C.c_int32), ("stream", C.c_void_p),
     ]

@@ -5,11 +5,12 @@ Tolerances, from the arithmetic of the stored operands:
 * stored P: the oracle rounds the same float32 values with the same per-column
   scale, so the stored matrix agrees exactly except where float32 rounding of P
   itself differs (a one-quantum difference, at most 1e-4 of the elements);
-* fitness against the oracle on its own quantised P: the only difference left is
-  the two-term split of the genes, 2^-16 relative for a bf16 pair and about
-  2^-8 for an e4m3 pair.  Over ~250 genes with |P|, |G| <= 1 the output error is
-  ~16 x 2^-16 x 0.5 (bf16) and ~16 x 2^-8 x 0.5 (fp8) for random signs, which
-  bounds the relative RMSE difference by 5e-4 and 3e-2.
+* fitness against the oracle fed its own quantised P and quantised genes
+  (``quantize_columns``, ``quantize_genes``): the products of the format are
+  exact in float32, so what is left is float32 accumulation over the genes
+  (~sqrt(K) x 2^-24 of |Out|), well inside 1e-5 relative on the RMSE;
+* against the exact genes (one gene term): the bf16 / e4m3 rounding of the
+  genes, 2^-8 / 2^-4 relative per gene, bounds the RMSE difference by 1e-3 / 3e-2.
 """
 
 import numpy as np
@@ -21,7 +22,7 @@ from tests.gpu_helpers import lib, make_game
 
 pytestmark = pytest.mark.gpu
 
-RTOL = {"bf16": 5e-4, "fp8": 3e-2}
+RTOL1 = {"bf16": 1e-3, "fp8": 3e-2}
 
 
 def _prec(fmt):
@@ -44,22 +45,41 @@ def test_stored_expansion_matches_oracle_quantisation(fmt):
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "fp8"])
-@pytest.mark.parametrize("engine", ["tcgen05", "simt"])
+@pytest.mark.parametrize("planes", [1, 2])
 @pytest.mark.parametrize("shape", [dict(n=2000, F=7, d=4, pop=20),
                                    dict(n=30011, F=32, d=8, pop=1024)])
-def test_low_precision_fitness_matches_oracle(fmt, engine, shape):
+def test_low_precision_tcgen05_matches_oracle(fmt, planes, shape):
     game = lib()
     ds = synth.make_dataset(shape["n"], shape["F"], shape["d"], seed=32,
                             correlated=shape["F"] > 16)
     ocfg = o.Config(degree=shape["d"], pop=shape["pop"], seed=2)
-    eng = game.ENGINE_TCGEN05 if engine == "tcgen05" else game.ENGINE_SIMT
-    g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=_prec(fmt), elite_rescore=0, engine=eng)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=_prec(fmt), elite_rescore=0,
+                  engine=game.ENGINE_TCGEN05, gene_planes=planes)
     G = g.population()
     fit, _ = g.evaluate()
     Q, s = o.quantize_columns(o.expand(ds.X[:ds.n_train], "chebyshev", shape["d"])[:, 1:], fmt)
     Pq = np.concatenate([np.ones((ds.n_train, 1)), o.dequantize_columns(Q, s)], axis=1)
-    want = o.fitness(Pq, ds.t[:ds.n_train], G, ocfg)
-    np.testing.assert_allclose(fit, want, rtol=RTOL[fmt])
+    np.testing.assert_allclose(fit, o.fitness(Pq, ds.t[:ds.n_train],
+                                              o.quantize_genes(G, s, fmt, planes), ocfg),
+                               rtol=1e-5)
+    if planes == 1:
+        np.testing.assert_allclose(fit, o.fitness(Pq, ds.t[:ds.n_train], G, ocfg),
+                                   rtol=RTOL1[fmt])
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+def test_low_precision_simt_matches_oracle(fmt):
+    """The CUDA-core engine reads the quantised P with exact float32 genes."""
+    game = lib()
+    ds = synth.make_dataset(5003, 9, 5, seed=34)
+    ocfg = o.Config(degree=5, pop=100, seed=2)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=_prec(fmt), elite_rescore=0,
+                  engine=game.ENGINE_SIMT)
+    fit, _ = g.evaluate()
+    Q, s = o.quantize_columns(o.expand(ds.X[:ds.n_train], "chebyshev", 5)[:, 1:], fmt)
+    Pq = np.concatenate([np.ones((ds.n_train, 1)), o.dequantize_columns(Q, s)], axis=1)
+    np.testing.assert_allclose(fit, o.fitness(Pq, ds.t[:ds.n_train], g.population(), ocfg),
+                               rtol=1e-5)
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "fp8"])

@@ -57,8 +57,9 @@ def test_low_precision_tcgen05_matches_oracle(fmt, planes, shape):
                   engine=game.ENGINE_TCGEN05, gene_planes=planes)
     G = g.population()
     fit, _ = g.evaluate()
-    Q, s = o.quantize_columns(o.expand(ds.X[:ds.n_train], "chebyshev", shape["d"])[:, 1:], fmt)
-    Pq = np.concatenate([np.ones((ds.n_train, 1)), o.dequantize_columns(Q, s)], axis=1)
+    # column scales are taken over every stored row (training and test)
+    Q, s = o.quantize_columns(o.expand(ds.X, "chebyshev", shape["d"])[:, 1:], fmt)
+    Pq = np.concatenate([np.ones((ds.n_train, 1)), o.dequantize_columns(Q[:ds.n_train], s)], axis=1)
     np.testing.assert_allclose(fit, o.fitness(Pq, ds.t[:ds.n_train],
                                               o.quantize_genes(G, s, fmt, planes), ocfg),
                                rtol=1e-5)
@@ -76,8 +77,8 @@ def test_low_precision_simt_matches_oracle(fmt):
     g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=_prec(fmt), elite_rescore=0,
                   engine=game.ENGINE_SIMT)
     fit, _ = g.evaluate()
-    Q, s = o.quantize_columns(o.expand(ds.X[:ds.n_train], "chebyshev", 5)[:, 1:], fmt)
-    Pq = np.concatenate([np.ones((ds.n_train, 1)), o.dequantize_columns(Q, s)], axis=1)
+    Q, s = o.quantize_columns(o.expand(ds.X, "chebyshev", 5)[:, 1:], fmt)
+    Pq = np.concatenate([np.ones((ds.n_train, 1)), o.dequantize_columns(Q[:ds.n_train], s)], axis=1)
     np.testing.assert_allclose(fit, o.fitness(Pq, ds.t[:ds.n_train], g.population(), ocfg),
                                rtol=1e-5)
 

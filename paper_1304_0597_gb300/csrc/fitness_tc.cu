@@ -237,21 +237,23 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// 2^u on the FMA pipe: u = j + f with j = floor(u), f in [0,1); 2^f by a
-// degree-5 polynomial fitted to 2^f on [0,1) (relative error 1.6e-7, the size
-// of the hardware ex2.approx error); 2^j added to the exponent field.  Used for
-// part of the elements so that the MUFU unit is not the only exp2 engine.
+// 2^u without the MUFU unit: u = j + f with j = round(u) obtained by the
+// 1.5 * 2^23 rounding constant (float adds only, no conversion instructions),
+// f in [-1/2, 1/2]; 2^f by a degree-5 polynomial fitted to 2^f on that
+// interval (relative error 2.3e-7, the size of the hardware ex2.approx error);
+// 2^j added to the exponent field with an integer add.  Used for part of the
+// elements so that the MUFU unit is not the only exp2 engine.
 __device__ __forceinline__ float exp2_poly(float u) {
   u = fminf(fmaxf(u, -125.0f), 125.0f);
-  const float j = floorf(u);
-  const float f = u - j;
-  float p = 0x1.ec31c6p-10f;
-  p = fmaf(p, f, 0x1.269022p-7f);
-  p = fmaf(p, f, 0x1.c95442p-5f);
-  p = fmaf(p, f, 0x1.ebd5aap-3f);
-  p = fmaf(p, f, 0x1.62e4f6p-1f);
-  p = fmaf(p, f, 0x1.fffffep-1f);
-  return __int_as_float(__float_as_int(p) + ((int)j << 23));
+  const float t = __fadd_rn(u, 12582912.0f);
+  const float f = __fsub_rn(u, __fsub_rn(t, 12582912.0f));
+  float p = 0x1.5c08c4p-10f;
+  p = fmaf(p, f, 0x1.3d0c52p-7f);
+  p = fmaf(p, f, 0x1.c6b6e6p-5f);
+  p = fmaf(p, f, 0x1.ebf918p-3f);
+  p = fmaf(p, f, 0x1.62e428p-1f);
+  p = fmaf(p, f, 0x1.000002p+0f);
+  return __int_as_float(__float_as_int(p) + ((__float_as_int(t) - 0x4B400000) << 23));
 }
 
 __device__ __forceinline__ float general_error(float t, float s, int act, int err, float R) {

@@ -237,25 +237,6 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// 2^u without the MUFU unit: u = j + f with j = round(u) obtained by the
-// 1.5 * 2^23 rounding constant (float adds only, no conversion instructions),
-// f in [-1/2, 1/2]; 2^f by a degree-5 polynomial fitted to 2^f on that
-// interval (relative error 2.3e-7, the size of the hardware ex2.approx error);
-// 2^j added to the exponent field with an integer add.  Used for part of the
-// elements so that the MUFU unit is not the only exp2 engine.
-__device__ __forceinline__ float exp2_poly(float u) {
-  u = fminf(fmaxf(u, -125.0f), 125.0f);
-  const float t = __fadd_rn(u, 12582912.0f);
-  const float f = __fsub_rn(u, __fsub_rn(t, 12582912.0f));
-  float p = 0x1.5c08c4p-10f;
-  p = fmaf(p, f, 0x1.3d0c52p-7f);
-  p = fmaf(p, f, 0x1.c6b6e6p-5f);
-  p = fmaf(p, f, 0x1.ebf918p-3f);
-  p = fmaf(p, f, 0x1.62e428p-1f);
-  p = fmaf(p, f, 0x1.000002p+0f);
-  return __int_as_float(__float_as_int(p) + ((__float_as_int(t) - 0x4B400000) << 23));
-}
-
 __device__ __forceinline__ float general_error(float t, float s, int act, int err, float R) {
   const float y = act == GAME_TANH ? tanhf(s) : s;
   const float d = t - y;
@@ -292,10 +273,9 @@ __device__ __forceinline__ float chunk_error(uint32_t taddr, const float* __rest
     for (int j = 0; j < 32; ++j) {
       const float s = fmaf(v[j], rs, bias);
       if (FAST) {
-        // 18 of 32 exponentials on the FMA pipe, 14 on MUFU: balances the two units
-        const float u = cq[j] * s;
-        const float E = (j & 15) < 9 ? exp2_poly(u) : ex2_approx(u);
-        const float r = rcp_approx(1.0f + E);
+        // Fewest instructions per element: the MMA-issuing warp shares its
+        // scheduler with epilogue warps, so epilogue issue slots are not free.
+        const float r = rcp_approx(1.0f + ex2_approx(cq[j] * s));
         sum = fmaf(r, r, sum);
       } else {
         sum += general_error(cq[j], s, act, err, R);

@@ -160,6 +160,11 @@ game_status game_get_population(game_ctx* ctx, float* G, int32_t pop, int32_t n_
  * and rank (host, pop int32) may be NULL.  Does not breed. */
 game_status game_evaluate(game_ctx* ctx, double* fitness, int32_t* rank);
 
+/* Fitness vector and ranking of the last evaluated population (no new
+ * evaluation): host arrays of pop doubles / int32, either may be NULL.
+ * Errors: STATE (nothing evaluated yet). */
+game_status game_get_fitness(game_ctx* ctx, double* fitness, int32_t* rank);
+
 /* One application of the genetic operators to the current population using
  * the given fitness vector (host, pop doubles; NULL = the last evaluated one),
  * with Philox counter word 0 = the current generation, which then advances by
@@ -217,6 +222,37 @@ game_status game_autotune(game_ctx* ctx, int32_t reps, game_tile* best, game_til
  * generation (on the context's stream) and game_get_timing reports their sums
  * for the last call; enabled = 0 (default): only the total is timed. */
 game_status game_set_timing(game_ctx* ctx, int32_t enabled);
+
+/* ---- batched form: many independent runs ----------------------------------- */
+
+/* A batch of independent GAME runs (no paper counterpart: the paper trains one
+ * model at a time).  Each run has its own configuration, data, population and
+ * Philox key; a generation of every run is one CUDA graph whose fitness step is
+ * a single persistent grouped launch over all runs (static schedule of (run,
+ * slice, pattern-tile range) items balanced over the SMs).  A run's results are
+ * those of the same run alone, up to the order of float64 partial sums. */
+typedef struct game_batch game_batch;
+
+/* n_runs contexts from cfgs[0..n_runs); all share cfgs[0].device and .stream. */
+game_status game_batch_create(const game_config* cfgs, int32_t n_runs, game_batch** out);
+/* Data of one run (as game_set_data). */
+game_status game_batch_set_data(game_batch* b, int32_t run, const float* X, const float* t,
+                                int64_t n_patterns, int32_t n_features, int64_t n_train,
+                                int32_t device_ptrs);
+/* The context of one run (owned by the batch): game_get_best, game_score,
+ * game_get_population ... work on it; NULL for a bad index. */
+game_ctx* game_batch_run(game_batch* b, int32_t run);
+/* max_generations generations of every run; generations_run (may be NULL) is an
+ * n_runs array receiving each run's count (runs stop on their own stop test). */
+game_status game_batch_evolve(game_batch* b, int32_t max_generations, int32_t* generations_run);
+/* Work items per SM of the grouped launch (schedule granularity, default 4). */
+game_status game_batch_set_granularity(game_batch* b, int32_t items_per_sm);
+/* Autotuner of the grouped launch: times the schedule granularities 1..16 items
+ * per SM on the current populations, keeps the fastest (*items_per_sm, *ms). */
+game_status game_batch_autotune(game_batch* b, int32_t reps, int32_t* items_per_sm, double* ms);
+/* Total device time of the last game_batch_evolve (ms_total, generations). */
+game_status game_batch_get_timing(game_batch* b, game_timing* out);
+void game_batch_destroy(game_batch* b);
 
 /* ---- fitness without device allocation ------------------------------------ */
 

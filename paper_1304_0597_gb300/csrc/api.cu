@@ -223,6 +223,7 @@ extern "C" game_status game_create(const game_config* cfg, game_ctx** out) {
   cudaSetDevice(c->dev);
   cudaError_t e = ga_init_attributes();
   if (e == cudaSuccess) e = tc_init_attributes();
+  if (e == cudaSuccess) e = batch_init_attributes();
   if (e != cudaSuccess) {
     delete c;
     return fail(nullptr, GAME_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
@@ -506,22 +507,39 @@ static game_status enqueue_rescore(game_ctx* c, int in_evolve) {
 
 // One generation: breed (if the current population was evaluated), prepare,
 // fitness, reduce + rank.  Reads and writes only device state.
+// Generation steps before the fitness launch: breed (if the current population
+// was evaluated) and the operand planes of the population to evaluate.
+static game_status enqueue_pre(game_ctx* c, cudaStream_t st) {
+  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 1 | 2, st));
+  CUDA_OK(c, launch_prepare(c->s, c->p, c->e, c->d_state, 1 | 2, st));
+  return GAME_OK;
+}
+
+// Generation steps after the fitness launch: reduce + rank (+ FP32 re-score).
+static game_status enqueue_post(game_ctx* c, int n_part, cudaStream_t st) {
+  const cudaStream_t saved = c->st;
+  c->st = st;
+  game_status r = GAME_OK;
+  cudaError_t e = launch_reduce_rank(c->s, c->cfg, c->d_partial, n_part, c->d_fit, c->d_rank,
+                                     c->d_state,
+                                     kRankEvaluate | kRankInEvolve | (c->n_rescore ? kRankNoStop : 0),
+                                     st);
+  if (e != cudaSuccess) r = fail(c, GAME_ERR_CUDA, "reduce_rank: %s", cudaGetErrorString(e));
+  if (r == GAME_OK && c->n_rescore) r = enqueue_rescore(c, 1);
+  c->st = saved;
+  return r;
+}
+
 static game_status enqueue_generation(game_ctx* c, const cudaEvent_t* ev) {
   if (ev) CUDA_OK(c, cudaEventRecordWithFlags(ev[0], c->st, cudaEventRecordExternal));
-  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 1 | 2, c->st));
-  CUDA_OK(c, launch_prepare(c->s, c->p, c->e, c->d_state, 1 | 2, c->st));
+  game_status r = enqueue_pre(c, c->st);
+  if (r != GAME_OK) return r;
   if (ev) CUDA_OK(c, cudaEventRecordWithFlags(ev[1], c->st, cudaEventRecordExternal));
-  game_status r = launch_fitness(c, c->d_state);
+  r = launch_fitness(c, c->d_state);
   if (r != GAME_OK) return r;
   if (ev) CUDA_OK(c, cudaEventRecordWithFlags(ev[2], c->st, cudaEventRecordExternal));
-  CUDA_OK(c, launch_reduce_rank(c->s, c->cfg, c->d_partial, c->n_part, c->d_fit, c->d_rank,
-                                c->d_state,
-                                kRankEvaluate | kRankInEvolve | (c->n_rescore ? kRankNoStop : 0),
-                                c->st));
-  if (c->n_rescore) {
-    r = enqueue_rescore(c, 1);
-    if (r != GAME_OK) return r;
-  }
+  r = enqueue_post(c, c->n_part, c->st);
+  if (r != GAME_OK) return r;
   if (ev) CUDA_OK(c, cudaEventRecordWithFlags(ev[3], c->st, cudaEventRecordExternal));
   return GAME_OK;
 }
@@ -669,6 +687,22 @@ extern "C" game_status game_evaluate(game_ctx* c, double* fitness, int32_t* rank
     r = enqueue_rescore(c, 0);
     if (r != GAME_OK) return r;
   }
+  if (fitness)
+    CUDA_OK(c, cudaMemcpyAsync(fitness, c->d_fit, sizeof(double) * c->s.pop, cudaMemcpyDeviceToHost, c->st));
+  if (rank)
+    CUDA_OK(c, cudaMemcpyAsync(rank, c->d_rank, sizeof(int) * c->s.pop, cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  return GAME_OK;
+}
+
+extern "C" game_status game_get_fitness(game_ctx* c, double* fitness, int32_t* rank) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  cudaSetDevice(c->dev);
+  DevState hs;
+  CUDA_OK(c, cudaMemcpyAsync(&hs, c->d_state, sizeof(hs), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  if (!hs.evaluated) return fail(c, GAME_ERR_STATE, "no evaluated population yet");
   if (fitness)
     CUDA_OK(c, cudaMemcpyAsync(fitness, c->d_fit, sizeof(double) * c->s.pop, cudaMemcpyDeviceToHost, c->st));
   if (rank)
@@ -903,4 +937,311 @@ extern "C" game_status game_get_timing(game_ctx* c, game_timing* out) {
   *out = c->timing;
   out->engine = c->engine;
   return GAME_OK;
+}
+
+
+// ===========================================================================
+// Batched form: many independent runs, one persistent grouped fitness launch
+// per generation, the whole generation of every run in one CUDA graph.
+// ===========================================================================
+
+struct game_batch {
+  std::vector<game_ctx*> runs;
+  cudaStream_t st = nullptr;
+  int dev = 0, n_sm = 0;
+  std::string err;
+  bool planned = false;
+  int items_per_sm = 4;
+  int grid = 0;
+  std::vector<int> parts;          // partial rows per run (chunks * 4)
+  BatchRunDev* d_runs = nullptr;
+  WorkItem* d_items = nullptr;
+  int* d_item_off = nullptr;
+  int n_items = 0;
+  cudaGraphExec_t graph = nullptr;
+  game_timing timing{};
+};
+
+static game_status bfail(game_batch* b, game_status code, const char* msg) {
+  if (b) b->err = msg;
+  g_global_err = msg;
+  return code;
+}
+
+static void batch_free_plan(game_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  cudaFree(b->d_runs);
+  cudaFree(b->d_items);
+  cudaFree(b->d_item_off);
+  b->d_runs = nullptr;
+  b->d_items = nullptr;
+  b->d_item_off = nullptr;
+  b->planned = false;
+}
+
+extern "C" game_status game_batch_create(const game_config* cfgs, int32_t n_runs,
+                                         game_batch** out) {
+  if (!cfgs || !out || n_runs < 1 || n_runs > 4096)
+    return bfail(nullptr, GAME_ERR_INVALID_ARG, "need cfgs, out and 1 <= n_runs <= 4096");
+  *out = nullptr;
+  game_batch* b = new game_batch();
+  for (int i = 0; i < n_runs; ++i) {
+    if (cfgs[i].device != cfgs[0].device || cfgs[i].stream != cfgs[0].stream) {
+      for (game_ctx* c : b->runs) game_destroy(c);
+      delete b;
+      return bfail(nullptr, GAME_ERR_INVALID_ARG, "every run of a batch shares one device and stream");
+    }
+    game_ctx* c = nullptr;
+    game_status s = game_create(&cfgs[i], &c);
+    if (s != GAME_OK) {
+      for (game_ctx* x : b->runs) game_destroy(x);
+      delete b;
+      return s;
+    }
+    b->runs.push_back(c);
+  }
+  b->st = (cudaStream_t)cfgs[0].stream;
+  b->dev = cfgs[0].device;
+  b->n_sm = b->runs[0]->n_sm;
+  *out = b;
+  return GAME_OK;
+}
+
+extern "C" game_ctx* game_batch_run(game_batch* b, int32_t run) {
+  if (!b || run < 0 || run >= (int)b->runs.size()) return nullptr;
+  return b->runs[run];
+}
+
+extern "C" game_status game_batch_set_data(game_batch* b, int32_t run, const float* X,
+                                           const float* t, int64_t n_patterns, int32_t n_features,
+                                           int64_t n_train, int32_t device_ptrs) {
+  if (!b || run < 0 || run >= (int)b->runs.size())
+    return bfail(b, GAME_ERR_INVALID_ARG, "bad batch or run index");
+  batch_free_plan(b);
+  game_status s = game_set_data(b->runs[run], X, t, n_patterns, n_features, n_train, device_ptrs);
+  if (s != GAME_OK) b->err = b->runs[run]->err;
+  return s;
+}
+
+// Static schedule: every (run, slice) is cut into chunks of consecutive tiles of
+// about equal cost (tiles x k-blocks x MMA products), and the work items go to
+// the SM with the least work so far, largest first.
+static game_status batch_plan(game_batch* b) {
+  if (b->planned) return GAME_OK;
+  cudaSetDevice(b->dev);
+  const int nr = (int)b->runs.size();
+  const int tile = batch_tile_rows();
+  std::vector<double> tcost(nr);
+  double total = 0.0;
+  for (int r = 0; r < nr; ++r) {
+    game_ctx* c = b->runs[r];
+    if (!c->have_data) return bfail(b, GAME_ERR_STATE, "every run of the batch needs data first");
+    const Shape& s = c->s;
+    const double prods = s.precision == GAME_FP32 ? 3.0 : s.gene_planes * (s.precision == GAME_FP8 ? 0.5 : 1.0);
+    tcost[r] = (double)s.kp * prods + 64.0;   // + fixed per-tile epilogue cost
+    const long long tiles = (s.n_train + tile - 1) / tile;
+    total += tcost[r] * (double)tiles * (s.pop_pad / 128);
+  }
+  const double target = total / ((double)b->n_sm * b->items_per_sm);
+  std::vector<WorkItem> items;
+  std::vector<double> icost;
+  b->parts.assign(nr, 0);
+  for (int r = 0; r < nr; ++r) {
+    game_ctx* c = b->runs[r];
+    const int tiles = (int)((c->s.n_train + tile - 1) / tile);
+    int chunks = (int)ceil(tiles * tcost[r] / target);
+    chunks = std::max(1, std::min(chunks, std::min(tiles, c->part_rows / 4)));
+    b->parts[r] = chunks * 4;
+    for (int sl = 0; sl < c->s.pop_pad / 128; ++sl)
+      for (int k = 0; k < chunks; ++k) {
+        const int t0 = (int)((long long)tiles * k / chunks), t1 = (int)((long long)tiles * (k + 1) / chunks);
+        items.push_back(WorkItem{r, sl, t0, t1, k});
+        icost.push_back((t1 - t0) * tcost[r]);
+      }
+  }
+  std::vector<int> order(items.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return icost[x] > icost[y]; });
+  const int g = std::min<int>(b->n_sm, (int)items.size());
+  std::vector<double> load(g, 0.0);
+  std::vector<std::vector<int>> per(g);
+  for (int i : order) {
+    const int m = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[m] += icost[i];
+    per[m].push_back(i);
+  }
+  std::vector<WorkItem> flat;
+  std::vector<int> off(1, 0);
+  for (int m = 0; m < g; ++m) {
+    for (int i : per[m]) flat.push_back(items[i]);
+    off.push_back((int)flat.size());
+  }
+  std::vector<BatchRunDev> rd(nr);
+  for (int r = 0; r < nr; ++r) {
+    game_ctx* c = b->runs[r];
+    cudaError_t e = batch_make_run(c->s, c->fit, c->p, c->e, c->d_partial, c->d_state, &rd[r]);
+    if (e != cudaSuccess) return bfail(b, GAME_ERR_CUDA, "tensor maps of a batched run");
+  }
+  if (cudaMalloc(&b->d_runs, sizeof(BatchRunDev) * nr) != cudaSuccess ||
+      cudaMalloc(&b->d_items, sizeof(WorkItem) * flat.size()) != cudaSuccess ||
+      cudaMalloc(&b->d_item_off, sizeof(int) * off.size()) != cudaSuccess)
+    return bfail(b, GAME_ERR_OOM, "batch schedule allocation");
+  if (cudaMemcpy(b->d_runs, rd.data(), sizeof(BatchRunDev) * nr, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_items, flat.data(), sizeof(WorkItem) * flat.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_item_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bfail(b, GAME_ERR_CUDA, "batch schedule upload");
+  b->grid = g;
+  b->n_items = (int)flat.size();
+  b->planned = true;
+  return GAME_OK;
+}
+
+static game_status batch_enqueue_generation(game_batch* b, cudaStream_t st) {
+  for (game_ctx* c : b->runs) {
+    game_status r = enqueue_pre(c, st);
+    if (r != GAME_OK) return bfail(b, r, c->err.c_str());
+  }
+  cudaError_t e = batch_fitness_launch(b->d_runs, b->d_items, b->d_item_off, b->grid, 1, st);
+  if (e != cudaSuccess) return bfail(b, GAME_ERR_CUDA, cudaGetErrorString(e));
+  for (size_t i = 0; i < b->runs.size(); ++i) {
+    game_status r = enqueue_post(b->runs[i], b->parts[i], st);
+    if (r != GAME_OK) return bfail(b, r, b->runs[i]->err.c_str());
+  }
+  return GAME_OK;
+}
+
+static game_status batch_build_graph(game_batch* b) {
+  if (b->graph) return GAME_OK;
+  cudaStream_t cap;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
+    return bfail(b, GAME_ERR_CUDA, "stream for capture");
+  cudaGraph_t g = nullptr;
+  game_status r = GAME_OK;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    r = batch_enqueue_generation(b, cap);
+    e = cudaStreamEndCapture(cap, &g);
+  }
+  cudaStreamDestroy(cap);
+  if (r != GAME_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) return bfail(b, GAME_ERR_CUDA, cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bfail(b, GAME_ERR_CUDA, cudaGetErrorString(e));
+  return GAME_OK;
+}
+
+extern "C" game_status game_batch_evolve(game_batch* b, int32_t max_generations,
+                                         int32_t* generations_run) {
+  if (!b) return bfail(nullptr, GAME_ERR_INVALID_ARG, "batch is NULL");
+  if (max_generations < 0) return bfail(b, GAME_ERR_INVALID_ARG, "max_generations < 0");
+  cudaSetDevice(b->dev);
+  game_status r = batch_plan(b);
+  if (r != GAME_OK) return r;
+  if ((r = batch_build_graph(b)) != GAME_OK) return r;
+  for (game_ctx* c : b->runs)
+    if (launch_state_op(c->d_state, kStateBeginEvolve, b->st) != cudaSuccess)
+      return bfail(b, GAME_ERR_CUDA, "state reset");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, b->st);
+  for (int i = 0; i < max_generations; ++i)
+    if (cudaGraphLaunch(b->graph, b->st) != cudaSuccess) return bfail(b, GAME_ERR_CUDA, "graph launch");
+  cudaEventRecord(e1, b->st);
+  if (cudaStreamSynchronize(b->st) != cudaSuccess) return bfail(b, GAME_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->timing = game_timing{};
+  b->timing.ms_total = ms;
+  b->timing.engine = GAME_ENGINE_TCGEN05;
+  int status = 0;
+  for (size_t i = 0; i < b->runs.size(); ++i) {
+    DevState hs;
+    if (cudaMemcpy(&hs, b->runs[i]->d_state, sizeof(hs), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return bfail(b, GAME_ERR_CUDA, "state read");
+    if (generations_run) generations_run[i] = hs.gens_run;
+    if (hs.status) status = hs.status;
+    b->timing.generations = std::max(b->timing.generations, hs.gens_run);
+  }
+  if (status) return bfail(b, GAME_ERR_TIMEOUT, "device-side wait timed out");
+  return GAME_OK;
+}
+
+extern "C" game_status game_batch_get_timing(game_batch* b, game_timing* out) {
+  if (!b || !out) return bfail(b, GAME_ERR_INVALID_ARG, "batch and out must be non-NULL");
+  *out = b->timing;
+  return GAME_OK;
+}
+
+extern "C" game_status game_batch_set_granularity(game_batch* b, int32_t items_per_sm) {
+  if (!b || items_per_sm < 1 || items_per_sm > 64)
+    return bfail(b, GAME_ERR_INVALID_ARG, "items_per_sm must be in 1..64");
+  if (b->items_per_sm != items_per_sm) batch_free_plan(b);
+  b->items_per_sm = items_per_sm;
+  return GAME_OK;
+}
+
+extern "C" game_status game_batch_autotune(game_batch* b, int32_t reps, int32_t* items_per_sm,
+                                           double* ms) {
+  if (!b) return bfail(nullptr, GAME_ERR_INVALID_ARG, "batch is NULL");
+  if (reps < 1) reps = 1;
+  cudaSetDevice(b->dev);
+  for (game_ctx* c : b->runs) {
+    if (!c->have_data) return bfail(b, GAME_ERR_STATE, "every run of the batch needs data first");
+    if (launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 0, b->st) != cudaSuccess ||
+        launch_prepare(c->s, c->p, c->e, c->d_state, 0, b->st) != cudaSuccess)
+      return bfail(b, GAME_ERR_CUDA, "operand preparation");
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best_g = b->items_per_sm;
+  double best_ms = 1e30;
+  for (int gsz : {1, 2, 4, 8, 16}) {
+    batch_free_plan(b);
+    b->items_per_sm = gsz;
+    game_status r = batch_plan(b);
+    if (r != GAME_OK) return r;
+    std::vector<float> t;
+    for (int i = 0; i <= reps; ++i) {
+      cudaEventRecord(e0, b->st);
+      if (batch_fitness_launch(b->d_runs, b->d_items, b->d_item_off, b->grid, 0, b->st) != cudaSuccess)
+        return bfail(b, GAME_ERR_CUDA, "grouped launch");
+      cudaEventRecord(e1, b->st);
+      cudaEventSynchronize(e1);
+      float m = 0.f;
+      cudaEventElapsedTime(&m, e0, e1);
+      if (i > 0) t.push_back(m);
+    }
+    std::sort(t.begin(), t.end());
+    if (t[t.size() / 2] < best_ms) {
+      best_ms = t[t.size() / 2];
+      best_g = gsz;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  batch_free_plan(b);
+  b->items_per_sm = best_g;
+  game_status r = batch_plan(b);
+  if (r != GAME_OK) return r;
+  if (items_per_sm) *items_per_sm = best_g;
+  if (ms) *ms = best_ms;
+  return GAME_OK;
+}
+
+extern "C" void game_batch_destroy(game_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->dev);
+  cudaStreamSynchronize(b->st);
+  batch_free_plan(b);
+  for (game_ctx* c : b->runs) game_destroy(c);
+  delete b;
 }

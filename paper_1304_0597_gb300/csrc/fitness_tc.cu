@@ -27,6 +27,7 @@
 // a timeout the CTA records GAME_ERR_TIMEOUT in the device state, drains its
 // outstanding copies and MMAs (again bounded), frees TMEM and exits.
 #include "fitness_tc.h"
+#include "tc_ptx.cuh"
 
 #include <cudaTypedefs.h>
 
@@ -34,11 +35,12 @@ namespace game {
 
 namespace {
 
+using namespace tc;
+
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kColGroups = kEpiWarps / 4;     // epilogue warps sharing one TMEM lane quadrant
 constexpr int kTileA = 128 * 128;         // bytes of one 128-row x 128-byte A tile
-constexpr unsigned long long kWaitNs = 2000000000ull;
 
 struct TcParams {
   CUtensorMap a[2];
@@ -57,246 +59,6 @@ struct TcParams {
   float R;
   int cl;                 // CTAs per cluster sharing each B tile by multicast (1 = none)
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on one phase of an mbarrier.  On timeout raises the CTA error
-// flag and the device status, and returns false.  Also returns false as soon
-// as another role of the CTA has raised the flag.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* err,
-                                          DevState* st) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (*err) return false;
-    if (globaltimer() - t0 > kWaitNs) {
-      *err = 1;
-      atomicExch(&st->status, (int)GAME_ERR_TIMEOUT);
-      return false;
-    }
-  }
-}
-
-// Warp-uniform bounded wait: lane 0 polls, the outcome is broadcast.
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* err,
-                                          DevState* st, int lane) {
-  int ok = 0;
-  if (lane == 0) ok = mbar_wait(bar, parity, err, st) ? 1 : 0;
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
-                                            uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-      : "memory");
-}
-
-// Multicast variant: the box lands at the same shared-memory offset in every CTA
-// of ctaMask, and completes bytes on the mbarrier at the same offset in each.
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int c0, int c1,
-                                               uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                   : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (stride byte offset), descriptor version 1 (tcgen05).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;                      // leading byte offset (unused with swizzle)
-  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset
-  d |= (uint64_t)1 << 46;                      // version
-  d |= (uint64_t)2 << 61;                      // SWIZZLE_128B
-  return d;
-}
-
-// Instruction descriptor: D f32, A/B format, both K-major, N >> 3, M >> 4.
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N, uint32_t ab_fmt) {
-  return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
-template <int PREC>
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                    uint32_t accum) {
-  if (PREC == GAME_FP8) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accum));
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accum));
-  }
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-// Arrive (when this CTA's MMAs complete) on the mbarrier at the same offset in
-// every CTA of ctaMask.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-      " [%0], %1;" ::"r"(smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ void fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ float general_error(float t, float s, int act, int err, float R) {
-  const float y = act == GAME_TANH ? tanhf(s) : s;
-  const float d = t - y;
-  const float e = d * d;
-  if (err == GAME_TMSE) return fabsf(d) > R ? e : 0.0f;
-  if (err == GAME_TMSE_SQ) return e > R ? e : 0.0f;
-  return e;
-}
-
-// Sum over 32 consecutive patterns of one chromosome's error.  The per-pattern
-// inputs (c_k = 2 log2(e) t_k for the fused path, t_k otherwise) are loaded
-// before the TMEM read so that the two latencies overlap.
-// FAST (targets +-1, tanh, MSE/RMSE): |t - tanh(s)| = 2 / (1 + exp(2 t s)), so
-// E = 4 r^2 with r = 1 / (1 + 2^(c_k s)); the factor 4 is applied by the caller.
-template <bool FAST>
-__device__ __forceinline__ float chunk_error(uint32_t taddr, const float* __restrict__ pk,
-                                             long long p0, long long m, float rs, float bias,
-                                             int act, int err, float R) {
-  float cq[32];
-  const float4* c4 = reinterpret_cast<const float4*>(pk + p0);
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const float4 x = __ldg(c4 + q);
-    cq[4 * q] = x.x;
-    cq[4 * q + 1] = x.y;
-    cq[4 * q + 2] = x.z;
-    cq[4 * q + 3] = x.w;
-  }
-  float v[32];
-  tmem_ld32(taddr, v);
-  float sum = 0.0f;
-  if (p0 + 32 <= m) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const float s = fmaf(v[j], rs, bias);
-      if (FAST) {
-        // Fewest instructions per element: the MMA-issuing warp shares its
-        // scheduler with epilogue warps, so epilogue issue slots are not free.
-        const float r = rcp_approx(1.0f + ex2_approx(cq[j] * s));
-        sum = fmaf(r, r, sum);
-      } else {
-        sum += general_error(cq[j], s, act, err, R);
-      }
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const float s = fmaf(v[j], rs, bias);
-      float e;
-      if (FAST) {
-        const float r = rcp_approx(1.0f + ex2_approx(cq[j] * s));
-        e = r * r;
-      } else {
-        e = general_error(cq[j], s, act, err, R);
-      }
-      if (p0 + j < m) sum += e;
-    }
-  }
-  return FAST ? 4.0f * sum : sum;
-}
 
 template <int BN, int PREC, bool FAST>
 __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_constant__ TcParams p) {
@@ -537,7 +299,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 cudaError_t make_map(CUtensorMap* m, const void* base, int precision, long long rows, int cols,
-                     int box_rows) {
+                     int box_rows) {  // NOLINT
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   const CUtensorMapDataType dt = precision == GAME_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
@@ -581,6 +343,11 @@ void* pick_kernel(int bn, int prec, bool fast) {
 }
 
 }  // namespace
+
+cudaError_t tc_make_map(CUtensorMap* m, const void* base, int precision, long long rows, int cols,
+                        int box_rows) {
+  return make_map(m, base, precision, rows, cols, box_rows);
+}
 
 cudaError_t tc_init_attributes() {
   for (int bn : {128, 256})

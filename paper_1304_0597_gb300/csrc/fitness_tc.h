@@ -37,5 +37,41 @@ void tc_candidates(const Shape& s, std::vector<TileReq>* out);
 cudaError_t tc_launch(const TcPlan& plan, const Shape& s, const Fitness& f, const PopDev& p,
                       const ExpDev& e, double* partial, const DevState* state, cudaStream_t st);
 cudaError_t tc_init_attributes();
+// Tensor map of a K-major operand plane [rows x cols] in the storage type of
+// `precision`, 128-byte rows per box, 128-byte swizzle, box of box_rows rows.
+cudaError_t tc_make_map(CUtensorMap* m, const void* base, int precision, long long rows, int cols,
+                        int box_rows);
+
+// ---- batched form: many runs in one persistent grouped launch ----------------
+
+// Everything the grouped kernel needs about one run (device-resident; the tensor
+// maps must stay 64-byte aligned).
+struct alignas(64) BatchRunDev {
+  CUtensorMap a[2];       // gene planes (hi, lo)
+  CUtensorMap b[2];       // expansion planes
+  const float* pk;        // per-pattern epilogue input (2 log2(e) t, or t)
+  const float* bias;
+  const float* rscale;
+  double* partial;        // [n_chunks * 4 x pop_pad]
+  const DevState* state;
+  long long m;
+  int pop_pad, kblocks, ksteps, n_bplanes, n_aplanes, prec, fast, act, err;
+  float R;
+};
+
+// One unit of work: a slice of one run over tiles [tile0, tile1); chunk = its
+// index among the slice's items (partial rows chunk*4 .. chunk*4+3).
+struct WorkItem {
+  int run, slice, tile0, tile1, chunk;
+};
+
+cudaError_t batch_init_attributes();
+int batch_stages();
+size_t batch_smem_bytes();
+int batch_tile_rows();
+cudaError_t batch_make_run(const Shape& s, const Fitness& f, const PopDev& p, const ExpDev& e,
+                           double* partial, const DevState* state, BatchRunDev* out);
+cudaError_t batch_fitness_launch(const BatchRunDev* d_runs, const WorkItem* d_items,
+                                 const int* d_item_off, int grid, int in_evolve, cudaStream_t st);
 
 }  // namespace game

@@ -77,6 +77,7 @@ def _load() -> C.CDLL:
         "game_get_population": (I32, [P, P, I32, I32]),
         "game_evaluate": (I32, [P, P, P]),
         "game_breed": (I32, [P, P]),
+        "game_get_fitness": (I32, [P, P, P]),
         "game_get_expansion": (I32, [P, P, I64, I64]),
         "game_score": (I32, [P, P, I32, C.POINTER(D), C.POINTER(D), C.POINTER(D), C.POINTER(D)]),
         "game_get_state": (I32, [P, C.POINTER(I64), C.POINTER(I32)]),
@@ -85,6 +86,14 @@ def _load() -> C.CDLL:
         "game_autotune": (I32, [P, I32, C.POINTER(GameTile), C.POINTER(GameTile), I32,
                                 C.POINTER(I32)]),
         "game_fitness_noalloc": (I32, [P, P, P, I64, I32, I32, I32, I32, F, P, P]),
+        "game_batch_create": (I32, [C.POINTER(GameConfig), I32, C.POINTER(P)]),
+        "game_batch_set_data": (I32, [P, I32, P, P, I64, I32, I64, I32]),
+        "game_batch_run": (P, [P, I32]),
+        "game_batch_evolve": (I32, [P, I32, P]),
+        "game_batch_set_granularity": (I32, [P, I32]),
+        "game_batch_autotune": (I32, [P, I32, C.POINTER(I32), C.POINTER(D)]),
+        "game_batch_get_timing": (I32, [P, C.POINTER(GameTiming)]),
+        "game_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -200,6 +209,13 @@ class Game:
         self._check(lib.game_evaluate(self.h, fit.ctypes.data, rank.ctypes.data), self.h)
         return fit, rank
 
+    def fitness(self):
+        """Fitness and ranking of the last evaluated population (no new evaluation)."""
+        fit = np.empty(self.pop, dtype=np.float64)
+        rank = np.empty(self.pop, dtype=np.int32)
+        self._check(lib.game_get_fitness(self.h, fit.ctypes.data, rank.ctypes.data), self.h)
+        return fit, rank
+
     def breed(self, fitness=None) -> None:
         if fitness is None:
             self._check(lib.game_breed(self.h, None), self.h)
@@ -240,3 +256,70 @@ class Game:
         t = GameTiming()
         self._check(lib.game_get_timing(self.h, C.byref(t)), self.h)
         return {f: getattr(t, f) for f, _ in GameTiming._fields_}
+
+
+class _RunView(Game):
+    """A run owned by a Batch: the Game API without ownership of the context."""
+
+    def __init__(self, handle, cfg):
+        self.h = C.c_void_p(handle)
+        self.cfg = cfg
+        self._owned = False
+
+    def close(self) -> None:
+        self.h = None
+
+
+class Batch:
+    """Many independent GAME runs evolved together (``game_batch``)."""
+
+    def __init__(self, configs):
+        arr = (GameConfig * len(configs))(*configs)
+        h = C.c_void_p()
+        st = lib.game_batch_create(arr, len(configs), C.byref(h))
+        if st != GAME_OK:
+            raise GameError(st, lib.game_last_error(None).decode())
+        self.h = h
+        self.configs = list(configs)
+        self.runs = [_RunView(lib.game_batch_run(h, i), configs[i]) for i in range(len(configs))]
+
+    def _check(self, status: int) -> None:
+        if status != GAME_OK:
+            raise GameError(status, lib.game_last_error(None).decode())
+
+    def set_data(self, run: int, X, t, n_train: int) -> None:
+        xp, xd, kx = _ptr(X)
+        tp, td, kt = _ptr(t)
+        n, F = X.shape
+        self._check(lib.game_batch_set_data(self.h, run, xp, tp, n, F, n_train, xd))
+
+    def evolve(self, generations: int):
+        out = np.zeros(len(self.runs), dtype=np.int32)
+        self._check(lib.game_batch_evolve(self.h, generations, out.ctypes.data))
+        return out
+
+    def autotune(self, reps: int = 3):
+        g, ms = C.c_int32(), C.c_double()
+        self._check(lib.game_batch_autotune(self.h, reps, C.byref(g), C.byref(ms)))
+        return g.value, ms.value
+
+    def set_granularity(self, items_per_sm: int) -> None:
+        self._check(lib.game_batch_set_granularity(self.h, items_per_sm))
+
+    def timing(self) -> dict:
+        t = GameTiming()
+        self._check(lib.game_batch_get_timing(self.h, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in GameTiming._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            for r in self.runs:
+                r.h = None
+            lib.game_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

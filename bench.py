@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32")
     ap.add_argument("--gene-planes", type=int, choices=[1, 2], default=2,
                     help="low precision: genes as one or two terms of P's format")
+    ap.add_argument("--batched", action="store_true",
+                    help="the batched form: 64 uneven runs in one grouped launch per generation "
+                         "against the same runs launched one by one; prints its own JSON line")
     ap.add_argument("--precision-table", action="store_true",
                     help="print the per-precision fitness error / accuracy table and exit")
     return ap.parse_args()
@@ -390,8 +393,69 @@ def precision_table(args):
     print(json.dumps({"table": "precision form on the plain small workload", "rows": rows}))
 
 
+def batched(args):
+    """64 independent runs of uneven sizes (seeded: patterns 1e4..5e5 log-uniform, features
+    5..40, degree 3..10, population 64..2048, Chebyshev / trig and FP32 / BF16 alternating)
+    evolved together, against the sum of the same runs evolved one at a time."""
+    import torch
+    from paper_1304_0597_gb300 import game, synth
+    specs = synth.batched_specs()
+    data, cfgs = [], []
+    for sp in specs:
+        ds = synth.make_dataset(sp.n_patterns, sp.n_features, sp.degree, sp.basis, seed=sp.seed,
+                                correlated=True)
+        data.append(ds)
+        cfgs.append(game.default_config(
+            basis=game.CHEBYSHEV if sp.basis == "chebyshev" else game.TRIG, degree=sp.degree,
+            pop=sp.pop, seed=sp.seed, precision=game.FP32 if sp.precision == "fp32" else game.BF16,
+            elite_rescore=0))
+    evals_per_gen = sum(sp.pop * ds.n_train for sp, ds in zip(specs, data))
+    flops_per_gen = sum(2.0 * ds.n_train * (c.basis + 1) * sp.n_features * sp.degree * sp.pop
+                        for sp, ds, c in zip(specs, data, cfgs))
+    K, W = args.steps, args.warmup
+    b = game.Batch(cfgs)
+    for i, ds in enumerate(data):
+        b.set_data(i, ds.X, ds.t, ds.n_train)
+    gran, gran_ms = b.autotune(reps=2)
+    b.evolve(W)
+    with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gens = b.evolve(K)
+        wall = time.perf_counter() - t0
+    tb = b.timing()["ms_total"]
+    assert all(g == K for g in gens)
+    b.close()
+    single_ms = 0.0
+    engines = {"tcgen05": 0, "simt": 0}
+    for cfg, ds in zip(cfgs, data):
+        g = game.Game(cfg)
+        g.set_data(ds.X, ds.t, ds.n_train)
+        g.evolve(W)
+        g.evolve(K)
+        single_ms += g.timing()["ms_total"]
+        engines["tcgen05" if g.timing()["engine"] == game.ENGINE_TCGEN05 else "simt"] += 1
+        g.close()
+    line = {"metric": METRIC + ", batched form", "value": evals_per_gen * K / (tb / 1e3),
+            "unit": UNIT, "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": tb / K,
+            "higher_is_better": True, "data": "synthetic",
+            "config": {"workload": "64 independent runs of uneven sizes", "runs": len(specs),
+                       "evals_per_generation": evals_per_gen,
+                       "algorithmic_tflop_per_generation": flops_per_gen / 1e12,
+                       "schedule_items_per_sm": gran, "grouped_launch_ms": gran_ms},
+            "one_at_a_time": {"value": evals_per_gen * K / (single_ms / 1e3),
+                              "ms_per_step": single_ms / K, "engines": engines},
+            "speedup_vs_one_at_a_time": single_ms / tb,
+            "achieved_tflops": flops_per_gen * K / (tb / 1e3) / 1e12,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.batched:
+        batched(args)
+        return
     if args.precision_table:
         precision_table(args)
         return

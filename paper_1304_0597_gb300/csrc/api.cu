@@ -945,6 +945,8 @@ extern "C" game_status game_get_timing(game_ctx* c, game_timing* out) {
 // per generation, the whole generation of every run in one CUDA graph.
 // ===========================================================================
 
+extern "C" void game_batch_destroy(game_batch* b);
+
 struct game_batch {
   std::vector<game_ctx*> runs;
   cudaStream_t st = nullptr;
@@ -960,6 +962,8 @@ struct game_batch {
   int n_items = 0;
   cudaGraphExec_t graph = nullptr;
   game_timing timing{};
+  std::vector<cudaStream_t> side;      // capture-time branches for the per-run kernels
+  std::vector<cudaEvent_t> ev;         // fork / join events of those branches
 };
 
 static game_status bfail(game_batch* b, game_status code, const char* msg) {
@@ -1004,6 +1008,21 @@ extern "C" game_status game_batch_create(const game_config* cfgs, int32_t n_runs
   b->st = (cudaStream_t)cfgs[0].stream;
   b->dev = cfgs[0].device;
   b->n_sm = b->runs[0]->n_sm;
+  const int ns = n_runs < 16 ? n_runs : 16;
+  for (int k = 0; k < ns; ++k) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) break;
+    b->side.push_back(s);
+  }
+  for (int k = 0; k <= (int)b->side.size(); ++k) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) break;
+    b->ev.push_back(e);
+  }
+  if (b->side.empty() || b->ev.size() != b->side.size() + 1) {
+    game_batch_destroy(b);
+    return bfail(nullptr, GAME_ERR_CUDA, "streams / events of the batch");
+  }
   *out = b;
   return GAME_OK;
 }
@@ -1097,18 +1116,34 @@ static game_status batch_plan(game_batch* b) {
   return GAME_OK;
 }
 
-static game_status batch_enqueue_generation(game_batch* b, cudaStream_t st) {
-  for (game_ctx* c : b->runs) {
-    game_status r = enqueue_pre(c, st);
+// The per-run kernels of a phase run on parallel graph branches (one branch per
+// side stream, runs dealt round-robin), joined before the grouped launch and at
+// the end of the generation.
+static game_status batch_fork_join(game_batch* b, cudaStream_t st, bool post) {
+  const int ns = (int)b->side.size();
+  if (cudaEventRecord(b->ev[0], st) != cudaSuccess) return bfail(b, GAME_ERR_CUDA, "fork");
+  for (int k = 0; k < ns; ++k)
+    if (cudaStreamWaitEvent(b->side[k], b->ev[0], 0) != cudaSuccess)
+      return bfail(b, GAME_ERR_CUDA, "fork wait");
+  for (size_t i = 0; i < b->runs.size(); ++i) {
+    game_ctx* c = b->runs[i];
+    cudaStream_t s = b->side[i % ns];
+    game_status r = post ? enqueue_post(c, b->parts[i], s) : enqueue_pre(c, s);
     if (r != GAME_OK) return bfail(b, r, c->err.c_str());
   }
+  for (int k = 0; k < ns; ++k)
+    if (cudaEventRecord(b->ev[1 + k], b->side[k]) != cudaSuccess ||
+        cudaStreamWaitEvent(st, b->ev[1 + k], 0) != cudaSuccess)
+      return bfail(b, GAME_ERR_CUDA, "join");
+  return GAME_OK;
+}
+
+static game_status batch_enqueue_generation(game_batch* b, cudaStream_t st) {
+  game_status r = batch_fork_join(b, st, false);
+  if (r != GAME_OK) return r;
   cudaError_t e = batch_fitness_launch(b->d_runs, b->d_items, b->d_item_off, b->grid, 1, st);
   if (e != cudaSuccess) return bfail(b, GAME_ERR_CUDA, cudaGetErrorString(e));
-  for (size_t i = 0; i < b->runs.size(); ++i) {
-    game_status r = enqueue_post(b->runs[i], b->parts[i], st);
-    if (r != GAME_OK) return bfail(b, r, b->runs[i]->err.c_str());
-  }
-  return GAME_OK;
+  return batch_fork_join(b, st, true);
 }
 
 static game_status batch_build_graph(game_batch* b) {
@@ -1243,5 +1278,7 @@ extern "C" void game_batch_destroy(game_batch* b) {
   cudaStreamSynchronize(b->st);
   batch_free_plan(b);
   for (game_ctx* c : b->runs) game_destroy(c);
+  for (cudaStream_t s : b->side) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
   delete b;
 }

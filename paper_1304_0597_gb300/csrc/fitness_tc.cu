@@ -54,13 +54,12 @@ struct TcParams {
   long long m;            // training rows
   int n_slices, cps, n_tiles, kblocks, kp, stages, pop_pad;
   int n_bplanes;          // FP32: 2 (P_hi, P_lo); else 1
-  int n_aplanes;          // gene planes resident in shared memory (1 or 2)
   int act, err, in_evolve;
   float R;
   int cl;                 // CTAs per cluster sharing each B tile by multicast (1 = none)
 };
 
-template <int BN, int PREC, bool FAST>
+template <int BN, int PREC, bool FAST, int NA>
 __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_constant__ TcParams p) {
   if (p.in_evolve && p.state->stopped) return;
   extern __shared__ uint8_t smem_raw[];
@@ -73,7 +72,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   constexpr uint32_t kIdesc = make_idesc(128, BN, kFmt);
   const int S = p.stages;
   uint8_t* sA = smem;
-  uint8_t* sB = sA + p.n_aplanes * p.kblocks * kTileA;
+  uint8_t* sB = sA + NA * p.kblocks * kTileA;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + S * kTileB);
   uint64_t* a_full = bars;
   uint64_t* b_full = bars + 1;
@@ -129,9 +128,9 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   if (warp == 0) {
     // ---- TMA producer: the whole warp follows one control flow, lane 0 issues ----
     if (lane == 0) {
-      const uint32_t a_bytes = (uint32_t)p.n_aplanes * p.kblocks * kTileA;
+      const uint32_t a_bytes = (uint32_t)NA * p.kblocks * kTileA;
       mbar_expect_tx(a_full, a_bytes);
-      for (int pl = 0; pl < p.n_aplanes; ++pl)
+      for (int pl = 0; pl < NA; ++pl)
         for (int kb = 0; kb < p.kblocks; ++kb)
           tma_load_2d(sA + (pl * p.kblocks + kb) * kTileA, &p.a[pl], kb * kKB, slice * 128,
                       a_full);
@@ -199,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
             fence_after();
             const uint64_t bdesc = sw128_desc(b_addr + (uint32_t)(stage * kTileB));
             // FP32 split: B = P_hi meets A = G_hi and G_lo; B = P_lo meets G_hi.
-            const int n_ap = (p.n_bplanes == 2 && bp == 1) ? 1 : p.n_aplanes;
+            const int n_ap = (PREC == GAME_FP32 && bp == 1) ? 1 : NA;
             for (int ai = 0; ai < n_ap; ++ai) {
               const uint64_t adesc =
                   sw128_desc(a_addr + (uint32_t)((ai * p.kblocks + kb) * kTileA));
@@ -324,20 +323,25 @@ int kblocks_of(const Shape& s) {
   return (s.kp + kkb - 1) / kkb;
 }
 
-template <int BN, int PREC, bool FAST>
+template <int BN, int PREC, bool FAST, int NA>
 void* kernel_ptr() {
-  return reinterpret_cast<void*>(&fitness_tc_kernel<BN, PREC, FAST>);
+  return reinterpret_cast<void*>(&fitness_tc_kernel<BN, PREC, FAST, NA>);
 }
 
-void* pick_kernel(int bn, int prec, bool fast) {
-#define GAME_TC_PICK(BNV, PV)                                                             \
-  if (bn == BNV && prec == PV) return fast ? kernel_ptr<BNV, PV, true>() : kernel_ptr<BNV, PV, false>();
-  GAME_TC_PICK(256, GAME_FP32)
-  GAME_TC_PICK(128, GAME_FP32)
-  GAME_TC_PICK(256, GAME_BF16)
-  GAME_TC_PICK(128, GAME_BF16)
-  GAME_TC_PICK(256, GAME_FP8)
-  GAME_TC_PICK(128, GAME_FP8)
+void* pick_kernel(int bn, int prec, bool fast, int na = 2) {
+#define GAME_TC_PICK(BNV, PV, NAV)                                                          \
+  if (bn == BNV && prec == PV && na == NAV)                                                  \
+    return fast ? kernel_ptr<BNV, PV, true, NAV>() : kernel_ptr<BNV, PV, false, NAV>();
+  GAME_TC_PICK(256, GAME_FP32, 2)
+  GAME_TC_PICK(128, GAME_FP32, 2)
+  GAME_TC_PICK(256, GAME_BF16, 2)
+  GAME_TC_PICK(128, GAME_BF16, 2)
+  GAME_TC_PICK(256, GAME_FP8, 2)
+  GAME_TC_PICK(128, GAME_FP8, 2)
+  GAME_TC_PICK(256, GAME_BF16, 1)
+  GAME_TC_PICK(128, GAME_BF16, 1)
+  GAME_TC_PICK(256, GAME_FP8, 1)
+  GAME_TC_PICK(128, GAME_FP8, 1)
 #undef GAME_TC_PICK
   return nullptr;
 }
@@ -352,11 +356,14 @@ cudaError_t tc_make_map(CUtensorMap* m, const void* base, int precision, long lo
 cudaError_t tc_init_attributes() {
   for (int bn : {128, 256})
     for (int prec : {GAME_FP32, GAME_BF16, GAME_FP8})
-      for (bool fast : {false, true}) {
-        cudaError_t e = cudaFuncSetAttribute(pick_kernel(bn, prec, fast),
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-        if (e != cudaSuccess) return e;
-      }
+      for (bool fast : {false, true})
+        for (int na : {1, 2}) {
+          void* k = pick_kernel(bn, prec, fast, na);
+          if (!k) continue;
+          cudaError_t e =
+              cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+          if (e != cudaSuccess) return e;
+        }
   return cudaSuccess;
 }
 
@@ -425,7 +432,7 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     int n_clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&n_clusters, pick_kernel(t.bn, s.precision, true), &cfg) ==
+    if (cudaOccupancyMaxActiveClusters(&n_clusters, pick_kernel(t.bn, s.precision, true, s.gene_planes), &cfg) ==
             cudaSuccess &&
         n_clusters > 0)
       resident = n_clusters * cl;
@@ -473,7 +480,6 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
   p.stages = t.stages;
   p.pop_pad = s.pop_pad;
   p.n_bplanes = s.precision == GAME_FP32 ? 2 : 1;
-  p.n_aplanes = s.gene_planes;
   p.act = f.activation;
   p.err = f.error;
   p.R = f.tmse_R;
@@ -481,7 +487,7 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
   p.cl = t.cluster;
   const bool fast = f.pm1_targets && f.activation == GAME_TANH &&
                     (f.error == GAME_RMSE || f.error == GAME_MSE);
-  void* k = pick_kernel(t.bn, s.precision, fast);
+  void* k = pick_kernel(t.bn, s.precision, fast, s.gene_planes);
   if (!k) return cudaErrorNotSupported;
   void* args[] = {&p};
   if (t.cluster <= 1) return cudaLaunchKernel(k, dim3(t.grid), dim3(kThreads), args, t.smem, st);

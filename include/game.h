@@ -88,6 +88,11 @@ typedef struct game_config {
   int32_t elite_rescore;  /* low precision: top-n re-scored with the FP32 path each gen     */
   int32_t gene_planes;    /* low precision: genes as 1 or 2 terms in P's format (0 = 2)     */
   int32_t surrogate_pool; /* 0 off; else offspring pool multiplier screened by the MLP      */
+  int32_t surrogate_steps;  /* Adam steps per generation (0 = 8)                            */
+  int32_t surrogate_batch;  /* training batch rows (0 = 1024)                               */
+  float surrogate_lr;       /* Adam learning rate (0 = 1e-3)                                */
+  int32_t surrogate_select; /* 0: surrogate's best of the pool; 1: plain children (ablation)*/
+  int32_t surrogate_fp32;   /* 1: float32 weights in the GEMMs (checks); 0: bfloat16        */
   int32_t engine;         /* GAME_ENGINE_* fitness kernel choice (AUTO picks tcgen05)       */
   int32_t tile_n;         /* tcgen05 tile: patterns per tile, 128 | 256 (0 = tuned / auto)  */
   int32_t tile_stages;    /* tcgen05 tile: depth of the pattern-tile ring (0 = auto)        */
@@ -222,6 +227,37 @@ game_status game_autotune(game_ctx* ctx, int32_t reps, game_tile* best, game_til
  * generation (on the context's stream) and game_get_timing reports their sums
  * for the last call; enabled = 0 (default): only the total is timed. */
 game_status game_set_timing(game_ctx* ctx, int32_t enabled);
+
+/* ---- learned surrogate (no paper counterpart) ------------------------------- */
+
+/* With cfg.surrogate_pool = m > 0, every generation breeds m x (pop - elitism)
+ * children with the usual operators, scores them with an MLP (genes -> 256 ->
+ * 256 -> 1, GELU, bfloat16 weights, float32 accumulation) that predicts the
+ * standardised log fitness, keeps the pop - elitism best-scored children, and
+ * evaluates them exactly.  The exact (chromosome, fitness) pairs go to a replay
+ * ring (m x pop rows) on which the MLP takes surrogate_steps Adam steps per
+ * generation.  The Spearman correlation of predicted and exact fitness of each
+ * generation's children is recorded; below 0.1 the next generation keeps plain
+ * children instead (the fallback).  The calls below expose the network for
+ * checks and diagnostics; parameters are one flat float32 vector
+ * [W1 (256 x n_genes) | b1 | W2 (256 x 256) | b2 | w3 (256) | b3]. */
+int64_t game_surrogate_n_params(game_ctx* ctx);
+game_status game_surrogate_get_params(game_ctx* ctx, float* params);
+game_status game_surrogate_set_params(game_ctx* ctx, const float* params);
+/* y[b] for B host rows X (B x n_genes float32). */
+game_status game_surrogate_forward(game_ctx* ctx, const float* X, int32_t B, float* y);
+/* Mean squared error of the network on (X, target) and its gradient (host,
+ * n_params floats); B <= the training batch size. */
+game_status game_surrogate_grad(game_ctx* ctx, const float* X, const float* target, int32_t B,
+                                double* loss, float* grad);
+/* One Adam step (Kingma & Ba 2015; beta 0.9 / 0.999, eps 1e-8) on (X, target). */
+game_status game_surrogate_train_step(game_ctx* ctx, const float* X, const float* target,
+                                      int32_t B, float lr);
+/* Monitor: Spearman correlation of the last generation (NaN before the first
+ * prediction), last training loss, fallback flag, and up to cap past values. */
+game_status game_surrogate_monitor(game_ctx* ctx, double* rho_last, double* loss_last,
+                                   int32_t* fallback, double* history, int32_t cap,
+                                   int32_t* n_history);
 
 /* ---- batched form: many independent runs ----------------------------------- */
 

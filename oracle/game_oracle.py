@@ -610,3 +610,69 @@ def quantize_genes(G: np.ndarray, s: np.ndarray, fmt: str, planes: int) -> np.nd
     out[:, 0] = G[:, 0]
     out[:, 1:] = val * r.astype(np.float64)[:, None] / s.astype(np.float64)[None, :]
     return out
+
+
+# ---------------------------------------------------------------------------
+# Learned surrogate of the fitness (no paper counterpart): a small MLP that
+# maps a chromosome's genes to its standardised log fitness.  Float64 forward,
+# backward (chain rule written out) and the Adam update of Kingma & Ba (2015).
+# ---------------------------------------------------------------------------
+
+def gelu(z: np.ndarray) -> np.ndarray:
+    """GELU, erf form: z * Phi(z) = z/2 (1 + erf(z / sqrt 2))."""
+    from scipy.special import erf
+    return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
+
+
+def gelu_grad(z: np.ndarray) -> np.ndarray:
+    """d/dz of z Phi(z) = Phi(z) + z phi(z)."""
+    from scipy.special import erf
+    return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
+
+
+def mlp_forward(params: dict, X: np.ndarray) -> dict:
+    """y = w3 . gelu(W2 gelu(W1 x + b1) + b2) + b3 for every row x of X; keeps the
+    intermediate values the backward pass needs."""
+    X = np.asarray(X, dtype=np.float64)
+    Z1 = X @ params["W1"].T + params["b1"]
+    H1 = gelu(Z1)
+    Z2 = H1 @ params["W2"].T + params["b2"]
+    H2 = gelu(Z2)
+    y = H2 @ params["w3"] + params["b3"]
+    return {"X": X, "Z1": Z1, "H1": H1, "Z2": Z2, "H2": H2, "y": y}
+
+
+def mlp_loss_grad(params: dict, X: np.ndarray, target: np.ndarray):
+    """Mean squared error L = mean((y - target)^2) and its gradient for every parameter."""
+    f = mlp_forward(params, X)
+    B = X.shape[0]
+    dy = 2.0 * (f["y"] - np.asarray(target, dtype=np.float64)) / B
+    g = {"w3": f["H2"].T @ dy, "b3": np.array(dy.sum())}
+    dZ2 = np.outer(dy, params["w3"]) * gelu_grad(f["Z2"])
+    g["W2"] = dZ2.T @ f["H1"]
+    g["b2"] = dZ2.sum(axis=0)
+    dZ1 = (dZ2 @ params["W2"]) * gelu_grad(f["Z1"])
+    g["W1"] = dZ1.T @ f["X"]
+    g["b1"] = dZ1.sum(axis=0)
+    loss = float(np.mean((f["y"] - target) ** 2))
+    return loss, g
+
+
+def adam_update(param: np.ndarray, grad: np.ndarray, m: np.ndarray, v: np.ndarray, step: int,
+                lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """One Adam step (Kingma & Ba 2015, Algorithm 1), step counted from 1."""
+    m = beta1 * m + (1 - beta1) * grad
+    v = beta2 * v + (1 - beta2) * grad * grad
+    mh = m / (1 - beta1 ** step)
+    vh = v / (1 - beta2 ** step)
+    return param - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def spearman(a: np.ndarray, b: np.ndarray) -> float:
+    """Spearman rank correlation (no ties expected): 1 - 6 sum d^2 / (n (n^2 - 1))."""
+    n = len(a)
+    ra = np.empty(n)
+    rb = np.empty(n)
+    ra[np.argsort(a, kind="stable")] = np.arange(n)
+    rb[np.argsort(b, kind="stable")] = np.arange(n)
+    return float(1.0 - 6.0 * np.sum((ra - rb) ** 2) / (n * (n * n - 1.0)))

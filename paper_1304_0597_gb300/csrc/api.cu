@@ -11,7 +11,9 @@
 // into a CUDA graph and replayed.
 #include "game_internal.h"
 #include "fitness_tc.h"
+#include "surrogate.h"
 
+#include <math_constants.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -61,6 +63,26 @@ struct game_ctx {
   TcPlan tc_r{};
   int n_part_r = 0;
   double* d_partial_r = nullptr;
+  // Learned surrogate (cfg.surrogate_pool > 0 drives the generation; the network
+  // also exists on demand for the checking calls).
+  bool sg_alloc = false;
+  Surrogate sg{};
+  int n_pool = 0;               // children bred per generation
+  int sg_steps = 8, sg_batch = 1024;
+  float sg_lr = 1e-3f;
+  float* d_pool = nullptr;      // [n_pool x kstride]
+  float* d_score = nullptr;     // [n_pool]
+  int* d_sel = nullptr;         // [pop]
+  float* d_pred = nullptr;      // [pop_pad] surrogate score of each evaluated child
+  int* d_fallback = nullptr;
+  float* d_ring_x = nullptr;    // [ring_cap x kstride]
+  float* d_ring_f = nullptr;    // [ring_cap]
+  int* d_ring_meta = nullptr;   // head, count, evals appended, generations monitored
+  int ring_cap = 0;
+  float* d_norm = nullptr;      // mean, std of log fitness over the ring
+  double* d_monitor = nullptr;  // [4096] Spearman per generation
+  float* d_bx = nullptr;        // [batch x kstride] training rows
+  float* d_bt = nullptr;        // [batch] standardised targets
   cudaGraphExec_t graph = nullptr;     // one generation
   cudaGraph_t graph_t_tmpl = nullptr;  // one generation with stage events (template kept alive)
   cudaGraphExec_t graph_t = nullptr;
@@ -184,6 +206,9 @@ static game_status validate(game_ctx* c, const game_config* cfg) {
   if (cfg->engine < GAME_ENGINE_AUTO || cfg->engine > GAME_ENGINE_SIMT)
     return fail(c, GAME_ERR_INVALID_ARG, "bad engine");
   if (cfg->surrogate_pool < 0) return fail(c, GAME_ERR_INVALID_ARG, "bad surrogate_pool");
+  if (cfg->surrogate_steps < 0 || cfg->surrogate_batch < 0 || cfg->surrogate_batch > 65536 ||
+      !(cfg->surrogate_lr >= 0.0f) || cfg->surrogate_select < 0 || cfg->surrogate_select > 1)
+    return fail(c, GAME_ERR_INVALID_ARG, "bad surrogate settings");
   if (cfg->gene_planes < 0 || cfg->gene_planes > 2)
     return fail(c, GAME_ERR_INVALID_ARG, "gene_planes must be 0, 1 or 2");
   return GAME_OK;
@@ -224,6 +249,7 @@ extern "C" game_status game_create(const game_config* cfg, game_ctx** out) {
   cudaError_t e = ga_init_attributes();
   if (e == cudaSuccess) e = tc_init_attributes();
   if (e == cudaSuccess) e = batch_init_attributes();
+  if (e == cudaSuccess) e = surrogate_ga_init_attributes();
   if (e != cudaSuccess) {
     delete c;
     return fail(nullptr, GAME_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
@@ -321,6 +347,70 @@ static game_status choose_engine(game_ctx* c, const Shape& s, const ExpDev& e, c
     *engine = GAME_ENGINE_SIMT;
     *n_part = simt_partials(s, c->n_sm);
   }
+  return GAME_OK;
+}
+
+__global__ void fill_f32_kernel(float* p, long long n, float v) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+// Network, pool, replay ring and training buffers of the surrogate.
+static game_status alloc_surrogate(game_ctx* c) {
+  const Shape& s = c->s;
+  c->sg_steps = c->cfg.surrogate_steps > 0 ? c->cfg.surrogate_steps : 8;
+  c->sg_batch = c->cfg.surrogate_batch > 0 ? c->cfg.surrogate_batch : 1024;
+  c->sg_lr = c->cfg.surrogate_lr > 0.0f ? c->cfg.surrogate_lr : 1e-3f;
+  const int e = c->cfg.elitism < s.pop ? c->cfg.elitism : s.pop;
+  const int m = c->cfg.surrogate_pool > 0 ? c->cfg.surrogate_pool : 1;
+  c->n_pool = m * (s.pop - e);
+  if (c->n_pool < 1) c->n_pool = 1;
+  c->ring_cap = std::max(m * s.pop, c->sg_batch);
+  Surrogate& sg = c->sg;
+  sg = Surrogate{};
+  sg.D = s.n_genes;
+  sg.H = 256;
+  sg.bf16 = c->cfg.surrogate_fp32 == 0;
+  sg.max_rows = std::max(c->n_pool, c->sg_batch);
+  const size_t np = sg.n_params();
+  game_status r;
+  const size_t act = (size_t)sg.max_rows * sg.H;
+  if ((r = dalloc(c, &sg.p, sizeof(float) * np)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.g, sizeof(float) * np)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.m, sizeof(float) * np)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.v, sizeof(float) * np)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.ph, sizeof(__nv_bfloat16) * np)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.step, sizeof(int))) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.Z1, sizeof(float) * act)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.H1, sizeof(float) * act)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.Z2, sizeof(float) * act)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.H2, sizeof(float) * act)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.dZ1, sizeof(float) * act)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.dZ2, sizeof(float) * act)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.yb, sizeof(float) * sg.max_rows)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.dy, sizeof(float) * sg.max_rows)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.sq, sizeof(float) * sg.max_rows)) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.loss, sizeof(float))) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_pool, sizeof(float) * (size_t)c->n_pool * s.kstride)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_score, sizeof(float) * c->n_pool)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_sel, sizeof(int) * s.pop_pad)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_pred, sizeof(float) * s.pop_pad)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_fallback, sizeof(int))) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_ring_x, sizeof(float) * (size_t)c->ring_cap * s.kstride)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_ring_f, sizeof(float) * c->ring_cap)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_ring_meta, sizeof(int) * 8)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_norm, sizeof(float) * 2)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_monitor, sizeof(double) * 4096)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_bx, sizeof(float) * (size_t)c->sg_batch * s.kstride)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_bt, sizeof(float) * c->sg_batch)) != GAME_OK) return r;
+  fill_f32_kernel<<<(s.pop_pad + 255) / 256, 256, 0, c->st>>>(c->d_pred, s.pop_pad, NAN);
+  const int meta[8] = {0, 0, -1, 0, 0, 0, 0, 0};
+  CUDA_OK(c, cudaMemcpyAsync(c->d_ring_meta, meta, sizeof(meta), cudaMemcpyHostToDevice, c->st));
+  const float norm[2] = {0.0f, 1.0f};
+  CUDA_OK(c, cudaMemcpyAsync(c->d_norm, norm, sizeof(norm), cudaMemcpyHostToDevice, c->st));
+  CUDA_OK(c, launch_surrogate_init(sg, c->cfg.seed ^ 0x53ull, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  c->sg_alloc = true;
   return GAME_OK;
 }
 
@@ -461,6 +551,13 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
     if ((r = dalloc(c, &c->d_partial_r, sizeof(double) * (size_t)rows * 128)) != GAME_OK) return r;
   }
 
+  c->sg_alloc = false;
+  if (c->cfg.surrogate_pool > 0) {
+    if ((r = alloc_surrogate(c)) != GAME_OK) {
+      free_all(c);
+      return r;
+    }
+  }
   CUDA_OK(c, launch_state_op(c->d_state, kStateReset, c->st));
   CUDA_OK(c, launch_init_population(s, c->cfg.init, c->cfg.seed, c->cfg.run, c->p.g32[0], c->st));
   CUDA_OK(c, cudaStreamSynchronize(c->st));
@@ -510,8 +607,54 @@ static game_status enqueue_rescore(game_ctx* c, int in_evolve) {
 // Generation steps before the fitness launch: breed (if the current population
 // was evaluated) and the operand planes of the population to evaluate.
 static game_status enqueue_pre(game_ctx* c, cudaStream_t st) {
-  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 1 | 2, st));
+  if (c->cfg.surrogate_pool > 0) {
+    // Oversized pool, scored by the surrogate; its best children (or plain ones
+    // under the fallback / the ablation) form the next population.
+    PoolArgs pa;
+    pa.g32_0 = c->p.g32[0];
+    pa.g32_1 = c->p.g32[1];
+    pa.pool = c->d_pool;
+    pa.fit = c->d_fit;
+    pa.rank = c->d_rank;
+    pa.state = c->d_state;
+    pa.k0 = c->cfg.seed;
+    pa.k1 = c->cfg.run;
+    pa.pop = c->s.pop;
+    pa.n_genes = c->s.n_genes;
+    pa.kstride = c->s.kstride;
+    pa.n_pool = c->n_pool;
+    pa.tournament_k = c->cfg.tournament_k;
+    pa.clamp = c->cfg.clamp_genes;
+    pa.p_c = c->cfg.p_crossover;
+    pa.p_m = c->cfg.p_mutation;
+    pa.sigma = c->cfg.sigma_mutation;
+    const int e = std::min(c->cfg.elitism, c->s.pop);
+    CUDA_OK(c, launch_pool_breed(pa, st));
+    CUDA_OK(c, c->sg.forward(c->d_pool, c->s.kstride, c->n_pool, c->d_score, st));
+    CUDA_OK(c, launch_select(c->d_score, c->n_pool, c->s.pop - e, c->d_sel, c->d_state,
+                             c->d_fallback, c->cfg.surrogate_select, st));
+    CUDA_OK(c, launch_assemble(c->d_pool, c->d_sel, c->d_score, c->p, c->s, e,
+                               c->cfg.elite_mode == GAME_ELITE_COPIES, c->d_rank, c->d_state,
+                               c->d_pred, st));
+  } else {
+    CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 1 | 2, st));
+  }
   CUDA_OK(c, launch_prepare(c->s, c->p, c->e, c->d_state, 1 | 2, st));
+  return GAME_OK;
+}
+
+// After an exact evaluation: replay ring, monitor, and the generation's training.
+static game_status enqueue_surrogate_train(game_ctx* c, cudaStream_t st) {
+  CUDA_OK(c, launch_replay_update(c->p, c->s, std::min(c->cfg.elitism, c->s.pop), c->d_fit,
+                                  c->d_pred, c->d_state, c->d_ring_x, c->d_ring_f, c->d_ring_meta,
+                                  c->ring_cap, c->d_norm, c->d_monitor, c->d_fallback, 0.1f, st));
+  for (int k = 0; k < c->sg_steps; ++k) {
+    CUDA_OK(c, launch_sample_batch(c->d_ring_x, c->d_ring_f, c->d_ring_meta, c->s.kstride,
+                                   c->s.n_genes, c->d_norm, c->sg_batch, c->cfg.seed, c->cfg.run,
+                                   0x51ull << 32, k, c->d_state, c->d_bx, c->d_bt, st));
+    CUDA_OK(c, c->sg.backward(c->d_bx, c->s.kstride, c->sg_batch, c->d_bt, st));
+    CUDA_OK(c, c->sg.adam(c->sg_lr, st));
+  }
   return GAME_OK;
 }
 
@@ -526,6 +669,7 @@ static game_status enqueue_post(game_ctx* c, int n_part, cudaStream_t st) {
                                      st);
   if (e != cudaSuccess) r = fail(c, GAME_ERR_CUDA, "reduce_rank: %s", cudaGetErrorString(e));
   if (r == GAME_OK && c->n_rescore) r = enqueue_rescore(c, 1);
+  if (r == GAME_OK && c->cfg.surrogate_pool > 0) r = enqueue_surrogate_train(c, st);
   c->st = saved;
   return r;
 }
@@ -923,6 +1067,111 @@ extern "C" game_status game_autotune(game_ctx* c, int32_t reps, game_tile* best,
   drop_graphs(c);
   tune_cache_store(c->s, bt);
   if (best) *best = bt;
+  return GAME_OK;
+}
+
+static game_status need_surrogate(game_ctx* c) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  cudaSetDevice(c->dev);
+  if (!c->sg_alloc) return alloc_surrogate(c);
+  return GAME_OK;
+}
+
+extern "C" int64_t game_surrogate_n_params(game_ctx* c) {
+  if (need_surrogate(c) != GAME_OK) return -1;
+  return (int64_t)c->sg.n_params();
+}
+
+extern "C" game_status game_surrogate_get_params(game_ctx* c, float* params) {
+  game_status r = need_surrogate(c);
+  if (r != GAME_OK) return r;
+  if (!params) return fail(c, GAME_ERR_INVALID_ARG, "params is NULL");
+  CUDA_OK(c, cudaMemcpyAsync(params, c->sg.p, sizeof(float) * c->sg.n_params(), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  return GAME_OK;
+}
+
+extern "C" game_status game_surrogate_set_params(game_ctx* c, const float* params) {
+  game_status r = need_surrogate(c);
+  if (r != GAME_OK) return r;
+  if (!params) return fail(c, GAME_ERR_INVALID_ARG, "params is NULL");
+  CUDA_OK(c, cudaMemcpyAsync(c->sg.p, params, sizeof(float) * c->sg.n_params(), cudaMemcpyHostToDevice, c->st));
+  CUDA_OK(c, c->sg.refresh(c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  return GAME_OK;
+}
+
+static game_status upload_rows(game_ctx* c, const float* X, const float* t, int B) {
+  if (B < 1 || B > c->sg_batch) return fail(c, GAME_ERR_INVALID_ARG, "B must be in 1..%d", c->sg_batch);
+  CUDA_OK(c, cudaMemcpy2DAsync(c->d_bx, sizeof(float) * c->s.kstride, X, sizeof(float) * c->s.n_genes,
+                               sizeof(float) * c->s.n_genes, B, cudaMemcpyHostToDevice, c->st));
+  if (t) CUDA_OK(c, cudaMemcpyAsync(c->d_bt, t, sizeof(float) * B, cudaMemcpyHostToDevice, c->st));
+  return GAME_OK;
+}
+
+extern "C" game_status game_surrogate_forward(game_ctx* c, const float* X, int32_t B, float* y) {
+  game_status r = need_surrogate(c);
+  if (r != GAME_OK) return r;
+  if (!X || !y) return fail(c, GAME_ERR_INVALID_ARG, "X and y must be non-NULL");
+  if ((r = upload_rows(c, X, nullptr, B)) != GAME_OK) return r;
+  CUDA_OK(c, c->sg.forward(c->d_bx, c->s.kstride, B, c->sg.yb, c->st));
+  CUDA_OK(c, cudaMemcpyAsync(y, c->sg.yb, sizeof(float) * B, cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  return GAME_OK;
+}
+
+extern "C" game_status game_surrogate_grad(game_ctx* c, const float* X, const float* target,
+                                           int32_t B, double* loss, float* grad) {
+  game_status r = need_surrogate(c);
+  if (r != GAME_OK) return r;
+  if (!X || !target) return fail(c, GAME_ERR_INVALID_ARG, "X and target must be non-NULL");
+  if ((r = upload_rows(c, X, target, B)) != GAME_OK) return r;
+  CUDA_OK(c, c->sg.backward(c->d_bx, c->s.kstride, B, c->d_bt, c->st));
+  float l = 0.f;
+  CUDA_OK(c, cudaMemcpyAsync(&l, c->sg.loss, sizeof(float), cudaMemcpyDeviceToHost, c->st));
+  if (grad)
+    CUDA_OK(c, cudaMemcpyAsync(grad, c->sg.g, sizeof(float) * c->sg.n_params(), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  if (loss) *loss = l;
+  return GAME_OK;
+}
+
+extern "C" game_status game_surrogate_train_step(game_ctx* c, const float* X, const float* target,
+                                                 int32_t B, float lr) {
+  game_status r = need_surrogate(c);
+  if (r != GAME_OK) return r;
+  if (!X || !target) return fail(c, GAME_ERR_INVALID_ARG, "X and target must be non-NULL");
+  if ((r = upload_rows(c, X, target, B)) != GAME_OK) return r;
+  CUDA_OK(c, c->sg.backward(c->d_bx, c->s.kstride, B, c->d_bt, c->st));
+  CUDA_OK(c, c->sg.adam(lr, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  return GAME_OK;
+}
+
+extern "C" game_status game_surrogate_monitor(game_ctx* c, double* rho_last, double* loss_last,
+                                              int32_t* fallback, double* history, int32_t cap,
+                                              int32_t* n_history) {
+  game_status r = need_surrogate(c);
+  if (r != GAME_OK) return r;
+  int meta[8];
+  float l = 0.f;
+  int fb = 0;
+  CUDA_OK(c, cudaMemcpyAsync(meta, c->d_ring_meta, sizeof(meta), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaMemcpyAsync(&l, c->sg.loss, sizeof(float), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaMemcpyAsync(&fb, c->d_fallback, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  std::vector<double> hist(4096);
+  CUDA_OK(c, cudaMemcpyAsync(hist.data(), c->d_monitor, sizeof(double) * 4096, cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  const int n = std::min(meta[3], 4096);
+  if (rho_last) *rho_last = n > 0 ? hist[(meta[3] - 1) % 4096] : NAN;
+  if (loss_last) *loss_last = l;
+  if (fallback) *fallback = fb;
+  int k = 0;
+  if (history)
+    for (int i = std::max(0, meta[3] - std::min(cap, 4096)); i < meta[3] && k < cap; ++i)
+      history[k++] = hist[i % 4096];
+  if (n_history) *n_history = k;
   return GAME_OK;
 }
 

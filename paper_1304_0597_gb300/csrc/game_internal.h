@@ -34,6 +34,7 @@ struct DevState {
   int stopped;        // best fitness reached stop_error
   int gens_run;       // populations evaluated since the last reset
   int status;         // device-side error code (0 ok)
+  int evals;          // populations evaluated since game_set_data (never reset)
   double best;        // best fitness of the last evaluated population
 };
 

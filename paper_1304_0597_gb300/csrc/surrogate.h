@@ -1,0 +1,85 @@
+// Learned fitness surrogate: MLP D -> 256 -> 256 -> 1 with GELU, its online
+// training (float32 master weights, bfloat16 GEMM copies, Adam) and the kernels
+// that use it to pre-screen an oversized offspring pool.
+#pragma once
+
+#include "game_internal.h"
+
+namespace game {
+
+// GELU in the erf form, z Phi(z), and its derivative Phi(z) + z phi(z).
+__device__ __forceinline__ float gelu_f(float z) {
+  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+}
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
+         z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+struct Surrogate {
+  int D = 0;                 // input width (genes per chromosome)
+  int H = 256;               // hidden width
+  bool bf16 = true;          // GEMMs read bfloat16 weight copies
+  int max_rows = 0;          // rows of the activation workspaces
+  float* p = nullptr;        // flat parameters [W1 (HxD) | b1 | W2 (HxH) | b2 | w3 | b3]
+  float* g = nullptr;        // gradients, same layout
+  float* m = nullptr;        // Adam first moments
+  float* v = nullptr;        // Adam second moments
+  __nv_bfloat16* ph = nullptr;   // bfloat16 copy of p
+  int* step = nullptr;       // Adam step counter (device)
+  float *Z1 = nullptr, *H1 = nullptr, *Z2 = nullptr, *H2 = nullptr;   // [max_rows x H]
+  float *dZ1 = nullptr, *dZ2 = nullptr;                              // [max_rows x H]
+  float *yb = nullptr, *dy = nullptr, *sq = nullptr;                 // [max_rows]
+  float* loss = nullptr;     // last training loss (device scalar)
+
+  size_t n_params() const;
+  void views(float* base, float** W1, float** b1, float** W2, float** b2, float** w3,
+             float** b3) const;
+  // y[m] for the M rows of X (row stride ldx floats, first D columns used).
+  cudaError_t forward(const float* X, long long ldx, int M, float* y, cudaStream_t st);
+  // gradients of mean((y - t)^2) over B <= max_rows rows into g; loss into *loss.
+  cudaError_t backward(const float* X, long long ldx, int B, const float* t, cudaStream_t st);
+  cudaError_t adam(float lr, cudaStream_t st);
+  cudaError_t refresh(cudaStream_t st);     // bfloat16 copy of p
+};
+
+// Kernels of the surrogate-driven generation (surrogate_ga.cu).
+struct PoolArgs {
+  const float* g32_0;
+  const float* g32_1;
+  float* pool;              // [n_pool x kstride] children
+  const double* fit;
+  const int* rank;
+  DevState* state;
+  uint64_t k0, k1;
+  int pop, n_genes, kstride, n_pool, tournament_k, clamp;
+  float p_c, p_m, sigma;
+};
+cudaError_t launch_pool_breed(const PoolArgs& a, cudaStream_t st);
+// Selects n_sel pool rows with the lowest score (ties: lower index), or the first
+// n_sel rows when random_select (or when the monitor switched to the fallback);
+// records whether this generation breeds (bred).
+cudaError_t launch_select(const float* score, int n_pool, int n_sel, int* sel, DevState* state,
+                          const int* fallback, int random_select, cudaStream_t st);
+// Next population: elites of the current one, then the selected pool rows; the
+// surrogate's score of each selected row goes to pred (NaN for elites).
+cudaError_t launch_assemble(const float* pool, const int* sel, const float* score, const PopDev& p,
+                            const Shape& s, int elitism, int elite_copies, const int* rank,
+                            const DevState* state, float* pred, cudaStream_t st);
+// Appends the evaluated population to the replay ring, computes the monitor
+// (Spearman of predicted vs exact over the non-elite rows) and the target
+// standardisation (mean / std of log fitness over the ring).
+cudaError_t launch_replay_update(const PopDev& p, const Shape& s, int elitism, const double* fit,
+                                 const float* pred, DevState* state, float* ring_x,
+                                 float* ring_f, int* ring_meta, int ring_cap, float* norm,
+                                 double* monitor, int* fallback, float fallback_rho,
+                                 cudaStream_t st);
+// Draws a training batch from the ring (Philox) and standardises its targets.
+cudaError_t launch_sample_batch(const float* ring_x, const float* ring_f, const int* ring_meta,
+                                int kstride, int n_genes, const float* norm, int B, uint64_t k0,
+                                uint64_t k1, uint64_t gen_salt, int step, const DevState* state,
+                                float* bx, float* bt, cudaStream_t st);
+cudaError_t surrogate_ga_init_attributes();
+cudaError_t launch_surrogate_init(Surrogate& sg, uint64_t seed, cudaStream_t st);
+
+}  // namespace game

@@ -37,7 +37,9 @@ class GameConfig(C.Structure):
         ("error", C.c_int32), ("tmse_R", C.c_float), ("activation", C.c_int32),
         ("init", C.c_int32), ("clamp_genes", C.c_int32), ("stop_error", C.c_double),
         ("seed", C.c_uint64), ("run", C.c_uint64), ("precision", C.c_int32),
-        ("elite_rescore", C.c_int32), ("gene_planes", C.c_int32), ("surrogate_pool", C.c_int32), ("engine", C.c_int32),
+        ("elite_rescore", C.c_int32), ("gene_planes", C.c_int32), ("surrogate_pool", C.c_int32),
+        ("surrogate_steps", C.c_int32), ("surrogate_batch", C.c_int32), ("surrogate_lr", C.c_float),
+        ("surrogate_select", C.c_int32), ("surrogate_fp32", C.c_int32), ("engine", C.c_int32),
         ("tile_n", C.c_int32), ("tile_stages", C.c_int32), ("tile_cluster", C.c_int32),
         ("device", C.c_int32), ("stream", C.c_void_p),
     ]
@@ -86,6 +88,14 @@ def _load() -> C.CDLL:
         "game_autotune": (I32, [P, I32, C.POINTER(GameTile), C.POINTER(GameTile), I32,
                                 C.POINTER(I32)]),
         "game_fitness_noalloc": (I32, [P, P, P, I64, I32, I32, I32, I32, F, P, P]),
+        "game_surrogate_n_params": (I64, [P]),
+        "game_surrogate_get_params": (I32, [P, P]),
+        "game_surrogate_set_params": (I32, [P, P]),
+        "game_surrogate_forward": (I32, [P, P, I32, P]),
+        "game_surrogate_grad": (I32, [P, P, P, I32, C.POINTER(D), P]),
+        "game_surrogate_train_step": (I32, [P, P, P, I32, F]),
+        "game_surrogate_monitor": (I32, [P, C.POINTER(D), C.POINTER(D), C.POINTER(I32), P, I32,
+                                         C.POINTER(I32)]),
         "game_batch_create": (I32, [C.POINTER(GameConfig), I32, C.POINTER(P)]),
         "game_batch_set_data": (I32, [P, I32, P, P, I64, I32, I64, I32]),
         "game_batch_run": (P, [P, I32]),
@@ -248,6 +258,50 @@ class Game:
         self._check(lib.game_autotune(self.h, reps, C.byref(best), cands, 64, C.byref(n)), self.h)
         tile = lambda t: {"n": t.n, "stages": t.stages, "cluster": t.cluster, "ms": t.ms}
         return tile(best), [tile(cands[i]) for i in range(n.value)]
+
+    # ---- learned surrogate ----
+    def surrogate_params(self) -> np.ndarray:
+        n = lib.game_surrogate_n_params(self.h)
+        if n <= 0:
+            raise GameError(-2, lib.game_last_error(self.h).decode())
+        out = np.empty(n, dtype=np.float32)
+        self._check(lib.game_surrogate_get_params(self.h, out.ctypes.data), self.h)
+        return out
+
+    def set_surrogate_params(self, params) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(lib.game_surrogate_set_params(self.h, p.ctypes.data), self.h)
+
+    def surrogate_forward(self, X) -> np.ndarray:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.empty(X.shape[0], dtype=np.float32)
+        self._check(lib.game_surrogate_forward(self.h, X.ctypes.data, X.shape[0], y.ctypes.data),
+                    self.h)
+        return y
+
+    def surrogate_grad(self, X, target):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        t = np.ascontiguousarray(target, dtype=np.float32)
+        g = np.empty(lib.game_surrogate_n_params(self.h), dtype=np.float32)
+        loss = C.c_double()
+        self._check(lib.game_surrogate_grad(self.h, X.ctypes.data, t.ctypes.data, X.shape[0],
+                                            C.byref(loss), g.ctypes.data), self.h)
+        return loss.value, g
+
+    def surrogate_train_step(self, X, target, lr: float) -> None:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        t = np.ascontiguousarray(target, dtype=np.float32)
+        self._check(lib.game_surrogate_train_step(self.h, X.ctypes.data, t.ctypes.data,
+                                                  X.shape[0], lr), self.h)
+
+    def surrogate_monitor(self, cap: int = 4096) -> dict:
+        rho, loss = C.c_double(), C.c_double()
+        fb, n = C.c_int32(), C.c_int32()
+        hist = np.empty(cap, dtype=np.float64)
+        self._check(lib.game_surrogate_monitor(self.h, C.byref(rho), C.byref(loss), C.byref(fb),
+                                               hist.ctypes.data, cap, C.byref(n)), self.h)
+        return {"rho": rho.value, "loss": loss.value, "fallback": fb.value,
+                "history": hist[:n.value].copy()}
 
     def set_timing(self, enabled: bool) -> None:
         self._check(lib.game_set_timing(self.h, int(bool(enabled))), self.h)

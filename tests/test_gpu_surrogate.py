@@ -1,0 +1,145 @@
+"""Learned surrogate: the network's forward, gradients and Adam step against the
+float64 oracle, and the surrogate-driven generation.
+
+Tolerances: with float32 weights the kernels differ from float64 only by
+float32 rounding of the GEMMs (K <= 289 terms, |terms| ~ 1): 1e-4 relative to
+the largest output / gradient entry.  With bfloat16 weights the oracle is fed
+the same bfloat16-rounded weights, so the same bound holds.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import game_oracle as o
+from paper_1304_0597_gb300 import synth
+from tests.gpu_helpers import lib, make_game
+
+pytestmark = pytest.mark.gpu
+
+
+def _unflatten(flat, D, H=256):
+    i = 0
+    out = {}
+    for name, shape in (("W1", (H, D)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("w3", (H,)),
+                        ("b3", ())):
+        n = int(np.prod(shape)) if shape else 1
+        out[name] = np.asarray(flat[i:i + n], dtype=np.float64).reshape(shape)
+        i += n
+    return out
+
+
+def _flatten(p):
+    return np.concatenate([np.asarray(p[k], dtype=np.float64).reshape(-1)
+                           for k in ("W1", "b1", "W2", "b2", "w3", "b3")])
+
+
+def _ctx(fp32: bool, **kw):
+    ds = synth.make_dataset(1500, 12, 4, seed=51)
+    ocfg = o.Config(degree=4, pop=64, seed=5)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, surrogate_fp32=int(fp32), surrogate_batch=256,
+                  **kw)
+    return g, ds
+
+
+@pytest.mark.parametrize("fp32", [True, False])
+def test_surrogate_forward_matches_oracle(fp32):
+    g, _ = _ctx(fp32)
+    D = g.n_genes
+    flat = g.surrogate_params()
+    p = _unflatten(flat, D)
+    if not fp32:
+        for k in ("W1", "W2", "w3"):
+            p[k] = o.round_bf16(p[k].astype(np.float32)).astype(np.float64)
+    X = np.random.default_rng(1).uniform(-1, 1, size=(200, D)).astype(np.float32)
+    y = g.surrogate_forward(X)
+    want = o.mlp_forward(p, X)["y"]
+    np.testing.assert_allclose(y, want, rtol=0, atol=1e-4 * max(1.0, np.abs(want).max()))
+
+
+@pytest.mark.parametrize("fp32", [True, False])
+def test_surrogate_gradient_matches_oracle(fp32):
+    g, _ = _ctx(fp32)
+    D = g.n_genes
+    rng = np.random.default_rng(2)
+    flat = g.surrogate_params()
+    p = _unflatten(flat, D)
+    if not fp32:
+        for k in ("W1", "W2", "w3"):
+            p[k] = o.round_bf16(p[k].astype(np.float32)).astype(np.float64)
+    X = rng.uniform(-1, 1, size=(256, D)).astype(np.float32)
+    t = rng.standard_normal(256).astype(np.float32)
+    loss, grad = g.surrogate_grad(X, t)
+    want_loss, gw = o.mlp_loss_grad(p, X, t)
+    assert loss == pytest.approx(want_loss, rel=1e-4)
+    for name, got in _unflatten(grad, D).items():
+        ref = np.asarray(gw[name])
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-4 * max(1e-6, np.abs(ref).max()),
+                                   err_msg=name)
+
+
+def test_surrogate_adam_step_matches_textbook():
+    g, _ = _ctx(True)
+    D = g.n_genes
+    rng = np.random.default_rng(3)
+    p0 = g.surrogate_params().astype(np.float64)
+    X = rng.uniform(-1, 1, size=(128, D)).astype(np.float32)
+    t = rng.standard_normal(128).astype(np.float32)
+    _, grad = o.mlp_loss_grad(_unflatten(p0, D), X, t)
+    gflat = _flatten(grad)
+    g.surrogate_train_step(X, t, 1e-3)
+    want, m, v = o.adam_update(p0, gflat, np.zeros_like(p0), np.zeros_like(p0), 1, lr=1e-3)
+    got = g.surrogate_params()
+    # first Adam step moves each parameter by ~lr along -sign(grad); compare the moves
+    np.testing.assert_allclose(got - p0, want - p0, rtol=0, atol=2e-5)
+
+
+def test_surrogate_learns_on_fixed_data():
+    """Training on a fixed batch drives the loss down."""
+    g, _ = _ctx(False)
+    D = g.n_genes
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-1, 1, size=(256, D)).astype(np.float32)
+    t = (np.sin(X[:, 1] * 2) + X[:, 2] * X[:, 3]).astype(np.float32)
+    l0, _ = g.surrogate_grad(X, t)
+    for _ in range(200):
+        g.surrogate_train_step(X, t, 1e-3)
+    l1, _ = g.surrogate_grad(X, t)
+    assert l1 < 0.2 * l0
+
+
+def test_surrogate_ablation_is_the_plain_ga():
+    """Keeping the first plain children of the pool (surrogate_select = 1) reproduces the
+    GA without a surrogate bit for bit: pair j of the pool is pair j of plain breeding."""
+    game = lib()
+    ds = synth.make_dataset(3000, 8, 4, seed=52)
+    ocfg = o.Config(degree=4, pop=100, seed=6)
+    plain = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    abl = make_game(ocfg, ds.X, ds.t, ds.n_train, surrogate_pool=4, surrogate_select=1,
+                    surrogate_batch=256, surrogate_steps=2)
+    assert plain.evolve(8) == 8 and abl.evolve(8) == 8
+    np.testing.assert_array_equal(abl.population(), plain.population())
+    np.testing.assert_array_equal(abl.fitness()[0], plain.fitness()[0])
+
+
+def test_surrogate_driven_evolution():
+    """Pool of 8x, surrogate selection: elitism keeps the best, the monitor records a
+    correlation per bred generation, and the surrogate's children are better than plain
+    children drawn from the same pools (mean fitness of the evaluated children)."""
+    ds = synth.make_dataset(6000, 10, 4, seed=53)
+    ocfg = o.Config(degree=4, pop=256, seed=7)
+    sur = make_game(ocfg, ds.X, ds.t, ds.n_train, surrogate_pool=8, surrogate_batch=512,
+                    surrogate_steps=16)
+    abl = make_game(ocfg, ds.X, ds.t, ds.n_train, surrogate_pool=8, surrogate_select=1,
+                    surrogate_batch=512, surrogate_steps=16)
+    hist_s, hist_a = [], []
+    for gen in range(20):
+        sur.evolve(1)
+        abl.evolve(1)
+        hist_s.append(sur.fitness()[0].min())
+        hist_a.append(abl.fitness()[0].min())
+    assert all(b <= a for a, b in zip(hist_s, hist_s[1:]))
+    mon = sur.surrogate_monitor()
+    rho = mon["history"]
+    assert len(rho) == 20 and np.isnan(rho[0])
+    assert np.nanmean(rho[5:]) > 0.2
+    assert hist_s[-1] <= hist_a[-1]

@@ -468,3 +468,62 @@ def test_quantize_columns_bounds():
         # relative rounding bound of the format for normal values, plus the subnormal floor
         floor = s[None, :] * (2.0 ** -9 if fmt == "fp8" else 0.0)
         assert np.all(np.abs(D - P) <= rel * np.abs(P) + floor + 1e-7)
+
+
+# --------------------------------------------------------------- surrogate
+
+def _mlp(rng, d=7, h=5):
+    return {"W1": rng.standard_normal((h, d)) * 0.4, "b1": rng.standard_normal(h) * 0.1,
+            "W2": rng.standard_normal((h, h)) * 0.4, "b2": rng.standard_normal(h) * 0.1,
+            "w3": rng.standard_normal(h) * 0.4, "b3": np.array(0.05)}
+
+
+def test_gelu_against_its_definition_and_scipy():
+    from scipy import stats
+    z = np.linspace(-6, 6, 1001)
+    np.testing.assert_allclose(o.gelu(z), z * stats.norm.cdf(z), atol=1e-15)
+    # derivative by central differences
+    h = 1e-6
+    np.testing.assert_allclose(o.gelu_grad(z), (o.gelu(z + h) - o.gelu(z - h)) / (2 * h), atol=1e-8)
+
+
+def test_mlp_gradient_by_finite_differences():
+    rng = np.random.default_rng(21)
+    p = _mlp(rng)
+    X = rng.uniform(-1, 1, size=(9, 7))
+    t = rng.standard_normal(9)
+    _, g = o.mlp_loss_grad(p, X, t)
+    h = 1e-6
+    for name in ("W1", "b1", "W2", "b2", "w3", "b3"):
+        flat = p[name].reshape(-1)
+        num = np.empty(flat.size)
+        for i in range(flat.size):
+            old = flat[i]
+            flat[i] = old + h
+            lp, _ = o.mlp_loss_grad(p, X, t)
+            flat[i] = old - h
+            lm, _ = o.mlp_loss_grad(p, X, t)
+            flat[i] = old
+            num[i] = (lp - lm) / (2 * h)
+        np.testing.assert_allclose(np.asarray(g[name]).reshape(-1), num, rtol=1e-5, atol=1e-9)
+
+
+def test_adam_first_step_moves_each_parameter_by_lr():
+    """At step 1 the bias-corrected update is lr * g/(|g| + eps): size lr, against the gradient."""
+    g = np.array([0.3, -2.0, 1e-3])
+    p, m, v = o.adam_update(np.zeros(3), g, np.zeros(3), np.zeros(3), 1, lr=0.01, eps=0.0)
+    np.testing.assert_allclose(p, -0.01 * np.sign(g), rtol=1e-12)
+    # a constant gradient keeps the step size lr (bias correction exact for a constant)
+    for step in range(2, 6):
+        p, m, v = o.adam_update(p, g, m, v, step, lr=0.01, eps=0.0)
+    np.testing.assert_allclose(p, -0.05 * np.sign(g), rtol=1e-10)
+
+
+def test_spearman_known_values():
+    a = np.arange(10.0)
+    assert o.spearman(a, a) == pytest.approx(1.0)
+    assert o.spearman(a, -a) == pytest.approx(-1.0)
+    from scipy import stats
+    rng = np.random.default_rng(3)
+    x, y = rng.standard_normal(200), rng.standard_normal(200)
+    assert o.spearman(x, y) == pytest.approx(stats.spearmanr(x, y)[0], abs=1e-12)

@@ -57,6 +57,10 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="the batched form: 64 uneven runs in one grouped launch per generation "
                          "against the same runs launched one by one; prints its own JSON line")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="learned-surrogate form: time to the plain FP32 GA's final train RMSE")
+    ap.add_argument("--seeds", type=int, default=1)
+    ap.add_argument("--budget", type=int, default=200, help="plain GA generations (target run)")
     ap.add_argument("--precision-table", action="store_true",
                     help="print the per-precision fitness error / accuracy table and exit")
     return ap.parse_args()
@@ -451,8 +455,72 @@ def batched(args):
     print(json.dumps(line), flush=True)
 
 
+def surrogate_ttt(args):
+    """Time to target RMSE on 2,000,000 patterns x 48 features (Chebyshev d=6, 289 genes),
+    population 4096.  Target = final best train RMSE of the plain FP32 GA after --budget
+    generations (same seed).  Contenders: surrogate (8x pool, MLP 289-256-256-1) with FP32
+    fitness, and with BF16 P (one gene plane, top-16 elites re-scored in FP32); plus the
+    ablation (plain children of the same pools) for the gain of the network itself."""
+    import torch
+    from paper_1304_0597_gb300 import game, synth
+    ds = synth.surrogate_scale(n_patterns=args.n_patterns if args.n_patterns != 1_000_000
+                               else 2_000_000)
+    results = []
+    base = dict(degree=6, pop=4096)
+    for seed in range(args.seeds):
+        def make(**kw):
+            g = game.Game(game.default_config(**base, seed=seed, **kw))
+            g.set_data(ds.X, ds.t, ds.n_train)
+            if g.timing()["engine"] == game.ENGINE_TCGEN05:
+                g.autotune(reps=2)
+            g.set_timing(False)
+            return g
+
+        plain = make()
+        plain.evolve(args.budget)
+        t_plain = plain.timing()["ms_total"]
+        _, target, _, acc_plain = plain.best()
+        plain.close()
+        row = {"seed": seed, "target_rmse": target, "plain_fp32": {"ms": t_plain,
+               "generations": args.budget, "test_accuracy": acc_plain}}
+        for name, kw in (("surrogate_fp32", dict(surrogate_pool=8)),
+                         ("surrogate_bf16", dict(surrogate_pool=8, precision=game.BF16,
+                                                 gene_planes=1, elite_rescore=16)),
+                         ("ablation_bf16", dict(surrogate_pool=8, surrogate_select=1,
+                                                precision=game.BF16, gene_planes=1,
+                                                elite_rescore=16))):
+            g = make(**kw)
+            ms, gens, hit = 0.0, 0, False
+            while gens < 2 * args.budget:
+                g.evolve(5)
+                ms += g.timing()["ms_total"]
+                gens += 5
+                _, best, _, acc = g.best()
+                if best <= target:
+                    hit = True
+                    break
+            mon = g.surrogate_monitor()
+            rho = mon["history"]
+            row[name] = {"ms": ms, "generations": gens, "reached": hit, "best_rmse": best,
+                         "test_accuracy": acc, "speedup_vs_plain": t_plain / ms if hit else None,
+                         "spearman_mean": float(np.nanmean(rho)) if len(rho) else None}
+            g.close()
+        results.append(row)
+        print(json.dumps(row), flush=True)
+    sp = [r["surrogate_bf16"]["speedup_vs_plain"] for r in results
+          if r["surrogate_bf16"]["speedup_vs_plain"]]
+    print(json.dumps({"metric": "time-to-target-RMSE speedup vs plain FP32 GA (learned surrogate "
+                      "+ BF16 P)", "value": float(np.median(sp)) if sp else None,
+                      "unit": "x", "seeds": args.seeds, "budget_generations": args.budget,
+                      "config": {"workload": "2,000,000 patterns x 48 features, Chebyshev d=6, "
+                                             "289 genes, pop 4096, 8x pool"}}), flush=True)
+
+
 def main():
     args = parse()
+    if args.surrogate:
+        surrogate_ttt(args)
+        return
     if args.batched:
         batched(args)
         return

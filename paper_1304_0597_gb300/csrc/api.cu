@@ -391,6 +391,8 @@ static game_status alloc_surrogate(game_ctx* c) {
   if ((r = dalloc(c, &sg.dy, sizeof(float) * sg.max_rows)) != GAME_OK) return r;
   if ((r = dalloc(c, &sg.sq, sizeof(float) * sg.max_rows)) != GAME_OK) return r;
   if ((r = dalloc(c, &sg.loss, sizeof(float))) != GAME_OK) return r;
+  if ((r = dalloc(c, &sg.ws, sizeof(float) * 16 * (size_t)sg.H * std::max(sg.D, sg.H))) != GAME_OK)
+    return r;
   if ((r = dalloc(c, &c->d_pool, sizeof(float) * (size_t)c->n_pool * s.kstride)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_score, sizeof(float) * c->n_pool)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_sel, sizeof(int) * s.pop_pad)) != GAME_OK) return r;

@@ -397,9 +397,10 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
   const int a_bytes = s.gene_planes * t.kblocks * kTileA;
   const int n_bplanes = s.precision == GAME_FP32 ? 2 : 1;
   t.n_slices = s.pop_pad / 128;
-  // Default shape: 256-pattern tiles when three stages fit, else 128; multicast
+  // Default shape: 256-pattern tiles when two stages fit, else 128; multicast
   // across the largest power-of-two group of slices up to 4.
-  t.bn = req.n ? req.n : (max_stages(s, 256) >= 3 ? 256 : 128);
+  // (128-pattern tiles cost as much per MMA instruction as 256-pattern ones)
+  t.bn = req.n ? req.n : (max_stages(s, 256) >= 2 ? 256 : 128);
   if (t.bn != 128 && t.bn != 256) return cudaErrorInvalidValue;
   const int ms = max_stages(s, t.bn);
   t.stages = req.stages ? req.stages : ms;

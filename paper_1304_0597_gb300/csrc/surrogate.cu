@@ -28,21 +28,26 @@ __global__ void __launch_bounds__(256) gemm_kernel(const float* __restrict__ A, 
                                                    long long bk, long long bn, int M, int N, int K,
                                                    const float* __restrict__ bias,
                                                    float* __restrict__ C, float* __restrict__ H,
-                                                   const float* __restrict__ zaux, long long ldc) {
+                                                   const float* __restrict__ zaux, long long ldc,
+                                                   int kc, long long zstride) {
   __shared__ float As[64][17];
   __shared__ float Bs[16][65];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
   float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += 16) {
+  // split-K: this CTA covers k in [k_lo, k_hi) and writes its own partial plane
+  const int k_lo = blockIdx.z * kc;
+  const int k_hi = min(K, k_lo + kc);
+  C += blockIdx.z * zstride;
+  for (int k0 = k_lo; k0 < k_hi; k0 += 16) {
     for (int i = tid; i < 64 * 16; i += 256) {
       const int r = i >> 4, kk = i & 15;
       const int m = m0 + r, k = k0 + kk;
-      As[r][kk] = (m < M && k < K) ? A[m * am + k * ak] : 0.0f;
+      As[r][kk] = (m < M && k < k_hi) ? A[m * am + k * ak] : 0.0f;
       const int kb = i >> 6, nn = i & 63;
       const int k2 = k0 + kb, n = n0 + nn;
       float bv = 0.0f;
-      if (k2 < K && n < N) {
+      if (k2 < k_hi && n < N) {
         const long long o = k2 * bk + n * bn;
         bv = BW ? __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(Bv)[o])
                 : reinterpret_cast<const float*>(Bv)[o];
@@ -91,7 +96,31 @@ void gemm(cudaStream_t st, const float* A, long long am, long long ak, const voi
           long long bn, int M, int N, int K, const float* bias, float* C, float* H,
           const float* zaux, long long ldc) {
   dim3 grid((N + 63) / 64, (M + 63) / 64);
-  gemm_kernel<BW, EPI><<<grid, 256, 0, st>>>(A, am, ak, B, bk, bn, M, N, K, bias, C, H, zaux, ldc);
+  gemm_kernel<BW, EPI><<<grid, 256, 0, st>>>(A, am, ak, B, bk, bn, M, N, K, bias, C, H, zaux, ldc,
+                                             K, 0);
+}
+
+// out[i] = sum_z ws[z * n + i], z = 0..splits-1 in order (deterministic).
+__global__ void splitk_sum_kernel(const float* __restrict__ ws, int splits, long long n,
+                                  float* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.0f;
+  for (int z = 0; z < splits; ++z) s += ws[z * n + i];
+  out[i] = s;
+}
+
+// Weight gradients (output M x N small, K = batch rows): split K over CTAs, then
+// add the partial planes in a fixed order.
+void gemm_splitk(cudaStream_t st, const float* A, long long am, long long ak, const float* B,
+                 long long bk, long long bn, int M, int N, int K, float* C, float* ws, int splits) {
+  const int kc = ((K + splits - 1) / splits + 15) / 16 * 16;
+  const int z = (K + kc - 1) / kc;
+  dim3 grid((N + 63) / 64, (M + 63) / 64, z);
+  gemm_kernel<false, 0><<<grid, 256, 0, st>>>(A, am, ak, B, bk, bn, M, N, K, nullptr, ws, nullptr,
+                                              nullptr, N, kc, (long long)M * N);
+  const long long n = (long long)M * N;
+  splitk_sum_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ws, z, n, C);
 }
 
 // Output layer y[m] = sum_n H2[m, n] w3[n] + b3 (one warp per row).
@@ -132,14 +161,21 @@ __global__ void out_back_kernel(const float* __restrict__ y, const float* __rest
   }
 }
 
-// out[n] = sum_b X[b * ld + n] in a fixed order (column sums over the batch).
+// out[n] = sum_b X[b * ld + n]: one CTA per column, strided partial sums and a
+// fixed tree (deterministic).
 __global__ void colsum_kernel(const float* __restrict__ X, int B, int N, long long ld,
                               float* __restrict__ out) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= N) return;
+  __shared__ float red[256];
+  const int n = blockIdx.x;
   float s = 0.0f;
-  for (int b = 0; b < B; ++b) s += X[(long long)b * ld + n];
-  out[n] = s;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) s += X[(long long)b * ld + n];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = red[0];
 }
 
 // Adam (Kingma & Ba 2015) over the flat parameter vector; refreshes the bf16 copies.
@@ -171,10 +207,16 @@ __global__ void refresh_bf16_kernel(const float* __restrict__ p, __nv_bfloat16* 
 }
 
 __global__ void loss_kernel(const float* __restrict__ sq, int B, float* __restrict__ loss) {
-  if (threadIdx.x != 0) return;
+  __shared__ float red[256];
   float s = 0.0f;
-  for (int b = 0; b < B; ++b) s += sq[b];
-  *loss = s / (float)B;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) s += sq[b];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = red[0] / (float)B;
 }
 
 }  // namespace
@@ -235,21 +277,21 @@ cudaError_t Surrogate::backward(const float* X, long long ldx, int B, const floa
     out_back_kernel<true><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(yb, t, pw3, Z2, B, H, dy, dZ2, sq);
   else
     out_back_kernel<false><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(yb, t, pw3, Z2, B, H, dy, dZ2, sq);
-  loss_kernel<<<1, 32, 0, st>>>(sq, B, loss);
+  loss_kernel<<<1, 256, 0, st>>>(sq, B, loss);
   // gw3[n] = sum_b dy[b] H2[b, n];  gb3 = sum_b dy[b]
-  gemm<false, 0>(st, dy, 0, 1, H2, H, 1, 1, H, B, nullptr, gw3, nullptr, nullptr, H);
-  colsum_kernel<<<1, 32, 0, st>>>(dy, B, 1, 1, gb3);
+  gemm_splitk(st, dy, 0, 1, H2, H, 1, 1, H, B, gw3, ws, 16);
+  colsum_kernel<<<1, 256, 0, st>>>(dy, B, 1, 1, gb3);
   // gW2[i, j] = sum_b dZ2[b, i] H1[b, j]; gb2 = colsum(dZ2)
-  gemm<false, 0>(st, dZ2, 1, H, H1, H, 1, H, H, B, nullptr, gW2, nullptr, nullptr, H);
-  colsum_kernel<<<(H + 127) / 128, 128, 0, st>>>(dZ2, B, H, H, gb2);
+  gemm_splitk(st, dZ2, 1, H, H1, H, 1, H, H, B, gW2, ws, 16);
+  colsum_kernel<<<H, 256, 0, st>>>(dZ2, B, H, H, gb2);
   // dZ1 = (dZ2 W2) * gelu'(Z1): B(k, n) = W2[k * H + n]
   if (bf16)
     gemm<true, 2>(st, dZ2, H, 1, pw2, H, 1, B, H, H, nullptr, dZ1, nullptr, Z1, H);
   else
     gemm<false, 2>(st, dZ2, H, 1, pw2, H, 1, B, H, H, nullptr, dZ1, nullptr, Z1, H);
   // gW1[i, k] = sum_b dZ1[b, i] X[b, k]; gb1 = colsum(dZ1)
-  gemm<false, 0>(st, dZ1, 1, H, X, ldx, 1, H, D, B, nullptr, gW1, nullptr, nullptr, D);
-  colsum_kernel<<<(H + 127) / 128, 128, 0, st>>>(dZ1, B, H, H, gb1);
+  gemm_splitk(st, dZ1, 1, H, X, ldx, 1, H, D, B, gW1, ws, 16);
+  colsum_kernel<<<H, 256, 0, st>>>(dZ1, B, H, H, gb1);
   return cudaGetLastError();
 }
 

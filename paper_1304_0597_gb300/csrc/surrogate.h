@@ -31,6 +31,7 @@ struct Surrogate {
   float *dZ1 = nullptr, *dZ2 = nullptr;                              // [max_rows x H]
   float *yb = nullptr, *dy = nullptr, *sq = nullptr;                 // [max_rows]
   float* loss = nullptr;     // last training loss (device scalar)
+  float* ws = nullptr;       // split-K partial planes [16 x H x max(D, H)]
 
   size_t n_params() const;
   void views(float* base, float** W1, float** b1, float** W2, float** b2, float** w3,
@@ -66,9 +67,9 @@ cudaError_t launch_select(const float* score, int n_pool, int n_sel, int* sel, D
 cudaError_t launch_assemble(const float* pool, const int* sel, const float* score, const PopDev& p,
                             const Shape& s, int elitism, int elite_copies, const int* rank,
                             const DevState* state, float* pred, cudaStream_t st);
-// Appends the evaluated population to the replay ring, computes the monitor
-// (Spearman of predicted vs exact over the non-elite rows) and the target
-// standardisation (mean / std of log fitness over the ring).
+// Monitor (Spearman of predicted vs exact over the non-elite rows), then the
+// evaluated population appended to the replay ring with its log fitness
+// standardised within the generation (mean / std over that population).
 cudaError_t launch_replay_update(const PopDev& p, const Shape& s, int elitism, const double* fit,
                                  const float* pred, DevState* state, float* ring_x,
                                  float* ring_f, int* ring_meta, int ring_cap, float* norm,

@@ -131,7 +131,7 @@ __global__ void assemble_kernel(const float* __restrict__ pool, const int* __res
 __global__ void replay_copy_kernel(const float* g32_0, const float* g32_1, const double* fit,
                                    const DevState* st, int pop, int n_genes, int kstride,
                                    float* ring_x, float* ring_f, const int* ring_meta,
-                                   int ring_cap) {
+                                   int ring_cap, const float* norm) {
   if (st->evals == ring_meta[2]) return;   // nothing evaluated since the last append
   const int row = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
@@ -140,14 +140,24 @@ __global__ void replay_copy_kernel(const float* g32_0, const float* g32_1, const
   const int slot = (ring_meta[0] + row) % ring_cap;
   float* dst = ring_x + (long long)slot * kstride;
   for (int g = lane; g < n_genes; g += 32) dst[g] = G[g];
-  if (lane == 0) ring_f[slot] = (float)fit[row];
+  // target: log fitness standardised within its own generation, so that the
+  // network learns what ranks children of the same population
+  if (lane == 0)
+    ring_f[slot] = (logf(fmaxf((float)fit[row], 1e-30f)) - norm[0]) / norm[1];
 }
 
-// ---- ring bookkeeping, monitor and target standardisation (one CTA) ----
+// Ring bookkeeping after the copy (one thread).
+__global__ void replay_commit_kernel(const DevState* st, int pop, int* ring_meta, int ring_cap) {
+  if (st->evals == ring_meta[2]) return;
+  ring_meta[0] = (ring_meta[0] + pop) % ring_cap;
+  ring_meta[1] = min(ring_cap, ring_meta[1] + pop);
+  ring_meta[2] = st->evals;
+}
+
+// ---- monitor and the generation's target standardisation (one CTA) ----
 __global__ void __launch_bounds__(1024) replay_stats_kernel(const double* fit, const float* pred,
                                                             const DevState* st, int pop, int e,
-                                                            float* ring_f, int* ring_meta,
-                                                            int ring_cap, float* norm,
+                                                            int* ring_meta, float* norm,
                                                             double* monitor, int* fallback,
                                                             float fallback_rho) {
   if (st->evals == ring_meta[2]) return;
@@ -213,17 +223,10 @@ __global__ void __launch_bounds__(1024) replay_stats_kernel(const double* fit, c
       __syncthreads();
     }
   }
-  // advance the ring (the copy kernel wrote rows head..head+pop-1)
-  __shared__ int head, count;
-  if (tid == 0) {
-    head = (ring_meta[0] + pop) % ring_cap;
-    count = min(ring_cap, ring_meta[1] + pop);
-  }
-  __syncthreads();
-  // mean / std of log fitness over the ring
+  // mean / std of log fitness over this generation's population
   double s1 = 0.0, s2 = 0.0;
-  for (int i = tid; i < count; i += nt) {
-    const double l = log((double)fmaxf(ring_f[i], 1e-30f));
+  for (int i = tid; i < pop; i += nt) {
+    const double l = log(fmax(fit[i], 1e-30));
     s1 += l;
     s2 += l * l;
   }
@@ -238,13 +241,10 @@ __global__ void __launch_bounds__(1024) replay_stats_kernel(const double* fit, c
     __syncthreads();
   }
   if (tid == 0) {
-    const double mu = red[0] / count;
-    const double var = fmax(red2[0] / count - mu * mu, 1e-12);
+    const double mu = red[0] / pop;
+    const double var = fmax(red2[0] / pop - mu * mu, 1e-18);
     norm[0] = (float)mu;
     norm[1] = (float)sqrt(var);
-    ring_meta[0] = head;
-    ring_meta[1] = count;
-    ring_meta[2] = st->evals;
     const int g = ring_meta[3];
     monitor[g % 4096] = rho;
     ring_meta[3] = g + 1;
@@ -268,7 +268,7 @@ __global__ void sample_batch_kernel(const float* __restrict__ ring_x, const floa
   const float* src = ring_x + (long long)idx * kstride;
   float* dst = bx + (long long)row * kstride;
   for (int g = lane; g < n_genes; g += 32) dst[g] = src[g];
-  if (lane == 0) bt[row] = (logf(fmaxf(ring_f[idx], 1e-30f)) - norm[0]) / norm[1];
+  if (lane == 0) bt[row] = ring_f[idx];
 }
 
 // ---- initial weights: U[-a, a], a = sqrt(3 / fan_in); biases 0 ----
@@ -317,14 +317,15 @@ cudaError_t launch_replay_update(const PopDev& p, const Shape& s, int elitism, c
                                  float* ring_f, int* ring_meta, int ring_cap, float* norm,
                                  double* monitor, int* fallback, float fallback_rho,
                                  cudaStream_t st) {
-  replay_copy_kernel<<<(s.pop * 32 + 255) / 256, 256, 0, st>>>(
-      p.g32[0], p.g32[1], fit, state, s.pop, s.n_genes, s.kstride, ring_x, ring_f, ring_meta,
-      ring_cap);
   int n2 = 2;
   while (n2 < s.pop) n2 <<= 1;
   const size_t smem = (size_t)n2 * (sizeof(unsigned long long) + sizeof(int));
-  replay_stats_kernel<<<1, 1024, smem, st>>>(fit, pred, state, s.pop, elitism, ring_f, ring_meta,
-                                             ring_cap, norm, monitor, fallback, fallback_rho);
+  replay_stats_kernel<<<1, 1024, smem, st>>>(fit, pred, state, s.pop, elitism, ring_meta, norm,
+                                             monitor, fallback, fallback_rho);
+  replay_copy_kernel<<<(s.pop * 32 + 255) / 256, 256, 0, st>>>(
+      p.g32[0], p.g32[1], fit, state, s.pop, s.n_genes, s.kstride, ring_x, ring_f, ring_meta,
+      ring_cap, norm);
+  replay_commit_kernel<<<1, 1, 0, st>>>(state, s.pop, ring_meta, ring_cap);
   return cudaGetLastError();
 }
 

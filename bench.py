@@ -66,6 +66,24 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value: float, world: int) -> float:
+    """Largest value over all ranks (the job time of a weak-scaling step); the
+    process group's backend does the exchange (NCCL on GPUs, gloo on CPU)."""
+    import torch
+    import torch.distributed as dist
+    if world <= 1:
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_units(pop: int, n_train: int, steps: int, world: int) -> int:
+    """Chromosome x pattern evaluations of the whole job: every rank runs its own run."""
+    return pop * n_train * steps * world
+
+
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
             int(os.environ.get("WORLD_SIZE", 1)))
@@ -285,12 +303,9 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     tm = g.timing()
     assert ran == K, f"evolution stopped after {ran} of {K} generations"
-    t_max = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_max = float(t_max.item())
+    ms_max = max_over_ranks(ms, world)
     pop, n_train, n_genes = 1024, ds.n_train, g.n_genes
-    units = pop * n_train * K * world
+    units = job_units(pop, n_train, K, world)
     value = units / (ms_max / 1e3)
 
     # End to end through the C ABI from pinned host memory: one training run per step.

@@ -202,6 +202,14 @@ typedef struct game_timing {
 } game_timing;
 game_status game_get_timing(game_ctx* ctx, game_timing* out);
 
+/* Failure-detection self-test (no paper counterpart): a device thread waits on
+ * an mbarrier that nothing completes, with the bounded-wait code of the
+ * tensor-core kernels but a limit of wait_us microseconds; the wait gives up,
+ * records GAME_ERR_TIMEOUT in the device state and the call returns it (the
+ * state's status is cleared again, so the context stays usable).  *waited_us
+ * (may be NULL) receives the time waited.  Nothing faults, traps or hangs. */
+game_status game_selftest_timeout(game_ctx* ctx, int32_t wait_us, int32_t* waited_us);
+
 /* Tile shape of the tcgen05 fitness engine, as chosen by the autotuner. */
 typedef struct game_tile {
   int32_t n;          /* patterns per tile (MMA N)                            */

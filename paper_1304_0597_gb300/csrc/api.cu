@@ -1177,6 +1177,30 @@ extern "C" game_status game_surrogate_monitor(game_ctx* c, double* rho_last, dou
   return GAME_OK;
 }
 
+extern "C" game_status game_selftest_timeout(game_ctx* c, int32_t wait_us, int32_t* waited_us) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  if (wait_us < 1 || wait_us > 2000000) return fail(c, GAME_ERR_INVALID_ARG, "wait_us in 1..2e6");
+  cudaSetDevice(c->dev);
+  int* d_out = nullptr;
+  CUDA_OK(c, cudaMalloc(&d_out, 2 * sizeof(int)));
+  int h[2] = {0, 0};
+  cudaError_t e = tc_timeout_selftest(c->d_state, (unsigned long long)wait_us * 1000ull, d_out, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  cudaFree(d_out);
+  CUDA_OK(c, e);
+  DevState hs;
+  CUDA_OK(c, cudaMemcpy(&hs, c->d_state, sizeof(hs), cudaMemcpyDeviceToHost));
+  // clear the recorded status so the context stays usable
+  CUDA_OK(c, launch_state_op(c->d_state, kStateClearStatus, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  if (waited_us) *waited_us = h[1];
+  if (h[0] == 1 && hs.status == GAME_ERR_TIMEOUT)
+    return fail(c, GAME_ERR_TIMEOUT, "bounded wait gave up after %d us", h[1]);
+  return GAME_OK;
+}
+
 extern "C" game_status game_set_timing(game_ctx* c, int32_t enabled) {
   if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
   c->timing_on = enabled != 0;

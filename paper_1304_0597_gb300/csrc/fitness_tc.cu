@@ -353,6 +353,36 @@ cudaError_t tc_make_map(CUtensorMap* m, const void* base, int precision, long lo
   return make_map(m, base, precision, rows, cols, box_rows);
 }
 
+// Self-test of the bounded wait used by every tensor-core kernel: one thread
+// waits on an mbarrier that nothing will ever complete, with a limit of wait_ns
+// instead of the production 2 s, and records GAME_ERR_TIMEOUT in the state.
+__global__ void timeout_selftest_kernel(DevState* st, unsigned long long wait_ns, int* out) {
+  __shared__ uint64_t bar;
+  __shared__ int err;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  err = 0;
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  const unsigned long long t0 = globaltimer();
+  bool done = false;
+  while (!(done = mbar_try_wait(&bar, 0)) && globaltimer() - t0 < wait_ns) {
+  }
+  if (!done) {
+    err = 1;
+    atomicExch(&st->status, (int)GAME_ERR_TIMEOUT);
+  }
+  out[0] = done ? 0 : 1;
+  out[1] = (int)((globaltimer() - t0) / 1000ull);   // microseconds waited
+  // complete the phase so that the barrier is left consistent
+  mbar_arrive(&bar);
+}
+
+cudaError_t tc_timeout_selftest(DevState* st, unsigned long long wait_ns, int* out,
+                                cudaStream_t s) {
+  timeout_selftest_kernel<<<1, 32, 0, s>>>(st, wait_ns, out);
+  return cudaGetLastError();
+}
+
 cudaError_t tc_init_attributes() {
   for (int bn : {128, 256})
     for (int prec : {GAME_FP32, GAME_BF16, GAME_FP8})

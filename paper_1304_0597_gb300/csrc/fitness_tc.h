@@ -39,6 +39,7 @@ cudaError_t tc_launch(const TcPlan& plan, const Shape& s, const Fitness& f, cons
 cudaError_t tc_init_attributes();
 // Tensor map of a K-major operand plane [rows x cols] in the storage type of
 // `precision`, 128-byte rows per box, 128-byte swizzle, box of box_rows rows.
+cudaError_t tc_timeout_selftest(DevState* st, unsigned long long wait_ns, int* out, cudaStream_t s);
 cudaError_t tc_make_map(CUtensorMap* m, const void* base, int precision, long long rows, int cols,
                         int box_rows);
 

@@ -407,6 +407,9 @@ __global__ void state_kernel(DevState* st, int op) {
     case kStateBeginEvolve:
       st->gens_run = 0;
       break;
+    case kStateClearStatus:
+      st->status = 0;
+      break;
     case kStateAfterBreed:
       if (st->bred) {
         st->cur ^= 1;

@@ -116,6 +116,7 @@ enum : int {
   kStatePopulationSet = 1,  // evaluated=0, bred=0, stopped=0
   kStateBeginEvolve = 2,    // gens_run=0
   kStateAfterBreed = 3,     // if bred: cur^=1, gen++ ; evaluated=0, bred=0
+  kStateClearStatus = 4,    // status = 0
 };
 
 // reduce_rank modes (low byte), flags: bit 8 inside game_evolve, bit 9 no stop test

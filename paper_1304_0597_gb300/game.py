@@ -85,6 +85,7 @@ def _load() -> C.CDLL:
         "game_get_state": (I32, [P, C.POINTER(I64), C.POINTER(I32)]),
         "game_get_timing": (I32, [P, C.POINTER(GameTiming)]),
         "game_set_timing": (I32, [P, I32]),
+        "game_selftest_timeout": (I32, [P, I32, C.POINTER(I32)]),
         "game_autotune": (I32, [P, I32, C.POINTER(GameTile), C.POINTER(GameTile), I32,
                                 C.POINTER(I32)]),
         "game_fitness_noalloc": (I32, [P, P, P, I64, I32, I32, I32, I32, F, P, P]),

@@ -271,3 +271,22 @@ def test_autotune_picks_a_valid_shape(tmp_path, monkeypatch):
     # a new context with the same shape bucket picks the cached shape up
     h = make_game(ocfg, ds.X, ds.t, ds.n_train)
     np.testing.assert_allclose(h.evaluate()[0], before, rtol=1e-6)
+
+
+def test_bounded_wait_times_out_without_fault():
+    """A wait that nothing satisfies gives up after its limit and reports TIMEOUT; the
+    context keeps working afterwards."""
+    import ctypes
+    game = lib()
+    ds = synth.make_dataset(500, 4, 3, seed=61)
+    ocfg = _cfg(degree=3, pop=30)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    waited = ctypes.c_int32()
+    st = game.lib.game_selftest_timeout(g.h, 2000, ctypes.byref(waited))
+    assert st == -6
+    assert 1500 <= waited.value < 500000
+    fit, _ = g.evaluate()
+    P = o.expand(ds.X[:ds.n_train], "chebyshev", 3)
+    np.testing.assert_allclose(fit, o.fitness(P, ds.t[:ds.n_train], g.population(), ocfg),
+                               rtol=FIT_RTOL)
+    assert g.evolve(3) == 3

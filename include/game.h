@@ -215,6 +215,7 @@ typedef struct game_tile {
   int32_t n;          /* patterns per tile (MMA N)                            */
   int32_t stages;     /* pattern-tile ring depth                              */
   int32_t cluster;    /* CTAs sharing each pattern tile (TMA multicast)       */
+  int32_t prefetch;   /* 1: L2 prefetch of each CTA's next pattern tile       */
   double ms;          /* median fitness time of this shape, milliseconds      */
 } game_tile;
 

@@ -290,7 +290,7 @@ __global__ void check_data_kernel(const float* X, long long nx, const float* t, 
 }
 
 // ---- tile cache of the autotuner: one line per shape bucket -------------------
-//   <kp> <pop_pad> <precision> <log2 n_train> <n> <stages> <cluster> <ms>
+//   <kp> <pop_pad> <precision> <log2 n_train> <n> <stages> <cluster> <prefetch> <ms>
 static std::string tune_cache_path() {
   const char* e = getenv("GAME_TUNE_CACHE");
   if (e && *e) return e;
@@ -303,12 +303,12 @@ static int ntrain_bucket(long long n) { return (int)floor(log2((double)(n > 0 ? 
 static bool tune_cache_lookup(const Shape& s, TileReq* out) {
   FILE* f = fopen(tune_cache_path().c_str(), "r");
   if (!f) return false;
-  int kp, pp, pr, nb, n, st, cl;
+  int kp, pp, pr, nb, n, st, cl, pf;
   double ms;
   bool found = false;
-  while (fscanf(f, "%d %d %d %d %d %d %d %lf", &kp, &pp, &pr, &nb, &n, &st, &cl, &ms) == 8)
+  while (fscanf(f, "%d %d %d %d %d %d %d %d %lf", &kp, &pp, &pr, &nb, &n, &st, &cl, &pf, &ms) == 9)
     if (kp == s.kp && pp == s.pop_pad && pr == s.precision && nb == ntrain_bucket(s.n_train)) {
-      *out = TileReq{n, st, cl};   // the last record for a bucket wins
+      *out = TileReq{n, st, cl, pf};   // the last record for a bucket wins
       found = true;
     }
   fclose(f);
@@ -321,8 +321,8 @@ static void tune_cache_store(const Shape& s, const game_tile& t) {
   if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
   FILE* f = fopen(path.c_str(), "a");
   if (!f) return;
-  fprintf(f, "%d %d %d %d %d %d %d %.6f\n", s.kp, s.pop_pad, s.precision, ntrain_bucket(s.n_train),
-          t.n, t.stages, t.cluster, t.ms);
+  fprintf(f, "%d %d %d %d %d %d %d %d %.6f\n", s.kp, s.pop_pad, s.precision,
+          ntrain_bucket(s.n_train), t.n, t.stages, t.cluster, t.prefetch, t.ms);
   fclose(f);
 }
 
@@ -333,7 +333,7 @@ static game_status choose_engine(game_ctx* c, const Shape& s, const ExpDev& e, c
   if (want == GAME_ENGINE_TCGEN05) {
     if (!tc_supported(s))
       return fail(c, GAME_ERR_UNSUPPORTED, "tcgen05 engine does not support this shape");
-    TileReq req{c->cfg.tile_n, c->cfg.tile_stages, c->cfg.tile_cluster};
+    TileReq req{c->cfg.tile_n, c->cfg.tile_stages, c->cfg.tile_cluster, -1};
     if (!req.n && !req.stages && !req.cluster) tune_cache_lookup(s, &req);
     cudaError_t err = tc_plan(s, e, p, c->n_sm, plan, req);
     if (err != cudaSuccess) {
@@ -1027,7 +1027,7 @@ extern "C" game_status game_autotune(game_ctx* c, int32_t reps, game_tile* best,
   cudaEvent_t e0, e1;
   CUDA_OK(c, cudaEventCreate(&e0));
   CUDA_OK(c, cudaEventCreate(&e1));
-  game_tile bt{0, 0, 0, 1e30};
+  game_tile bt{0, 0, 0, 0, 1e30};
   TcPlan best_plan{};
   int n_done = 0;
   for (const TileReq& rq : cands) {
@@ -1052,7 +1052,7 @@ extern "C" game_status game_autotune(game_ctx* c, int32_t reps, game_tile* best,
       return fail(c, GAME_ERR_CUDA, "autotune launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     }
     std::sort(t.begin(), t.end());
-    const game_tile gt{plan.bn, plan.stages, plan.cluster, t[t.size() / 2]};
+    const game_tile gt{plan.bn, plan.stages, plan.cluster, plan.prefetch, t[t.size() / 2]};
     if (candidates && n_done < cap) candidates[n_done] = gt;
     ++n_done;
     if (gt.ms < bt.ms) {

@@ -57,6 +57,7 @@ struct TcParams {
   int act, err, in_evolve;
   float R;
   int cl;                 // CTAs per cluster sharing each B tile by multicast (1 = none)
+  int prefetch;           // L2 prefetch of the next tile's boxes
 };
 
 template <int BN, int PREC, bool FAST, int NA>
@@ -147,6 +148,9 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
             break;
           }
           if (lane == 0) {
+            // warm L2 with the same box of this CTA's next tile
+            if (it + 1 < my_tiles && p.prefetch)
+              tma_prefetch_2d(&p.b[bp], kb * kKB, row0 + p.cps * BN + (int)crank * sub_rows);
             mbar_expect_tx(b_full + stage, kTileB);     // the whole tile lands here
             if (p.cl > 1)
               tma_load_2d_mc(sB + stage * kTileB + crank * sub_rows * 128, &p.b[bp], kb * kKB,
@@ -416,7 +420,8 @@ void tc_candidates(const Shape& s, std::vector<TileReq>* out) {
     const int ms = max_stages(s, bn);
     for (int st = ms; st >= 2 && st >= ms - 1; --st)
       for (int cl : {1, 2, 4, 8})
-        if (n_slices % cl == 0 && bn / cl >= 16) out->push_back(TileReq{bn, st, cl});
+        if (n_slices % cl == 0 && bn / cl >= 16)
+          for (int pf : {1, 0}) out->push_back(TileReq{bn, st, cl, pf});
   }
 }
 
@@ -446,6 +451,7 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
   }
   if (t.n_slices % cl != 0 || t.bn / cl < 16 || cl > 8) return cudaErrorInvalidValue;
   t.cluster = cl;
+  t.prefetch = req.prefetch == 0 ? 0 : 1;
   t.n_tiles = (int)((s.n_train + t.bn - 1) / t.bn);
   t.smem = (size_t)a_bytes + (size_t)t.stages * t.bn * 128 + kSmemMisc;
   // Co-resident CTAs under this cluster shape (clusters must fit in one GPC).
@@ -516,6 +522,7 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
   p.R = f.tmse_R;
   p.in_evolve = state != nullptr;
   p.cl = t.cluster;
+  p.prefetch = t.prefetch;
   const bool fast = f.pm1_targets && f.activation == GAME_TANH &&
                     (f.error == GAME_RMSE || f.error == GAME_MSE);
   void* k = pick_kernel(t.bn, s.precision, fast, s.gene_planes);

@@ -21,12 +21,13 @@ struct TcPlan {
   int kblocks;            // k-blocks of 128 bytes over kp
   int stages;             // B-operand pipeline depth
   int cluster;            // CTAs (one per slice) sharing each B tile by TMA multicast
+  int prefetch = 1;       // L2 prefetch of each CTA's next pattern tile
   size_t smem;            // dynamic shared memory bytes
 };
 
 // Requested tile shape; 0 fields are chosen automatically.
 struct TileReq {
-  int n = 0, stages = 0, cluster = 0;
+  int n = 0, stages = 0, cluster = 0, prefetch = -1;   // prefetch: -1 auto (on), 0 off, 1 on
 };
 
 bool tc_supported(const Shape& s);

@@ -83,6 +83,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// L2 prefetch of one box (no shared memory, no completion): warms L2 for a load
+// issued later, so that the ring's loads see L2 rather than DRAM latency.
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int c0, int c1) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(map),
+               "r"(c0), "r"(c1)
+               : "memory");
+}
+
 // Multicast variant: the box lands at the same shared-memory offset in every CTA
 // of ctaMask, and completes bytes on the mbarrier at the same offset in each.
 __device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int c0, int c1,

@@ -51,7 +51,8 @@ class GameTiming(C.Structure):
 
 
 class GameTile(C.Structure):
-    _fields_ = [("n", C.c_int32), ("stages", C.c_int32), ("cluster", C.c_int32), ("ms", C.c_double)]
+    _fields_ = [("n", C.c_int32), ("stages", C.c_int32), ("cluster", C.c_int32),
+                ("prefetch", C.c_int32), ("ms", C.c_double)]
 
 
 class GameError(RuntimeError):
@@ -257,7 +258,8 @@ class Game:
         cands = (GameTile * 64)()
         n = C.c_int32(0)
         self._check(lib.game_autotune(self.h, reps, C.byref(best), cands, 64, C.byref(n)), self.h)
-        tile = lambda t: {"n": t.n, "stages": t.stages, "cluster": t.cluster, "ms": t.ms}
+        tile = lambda t: {"n": t.n, "stages": t.stages, "cluster": t.cluster,
+                          "prefetch": t.prefetch, "ms": t.ms}
         return tile(best), [tile(cands[i]) for i in range(n.value)]
 
     # ---- learned surrogate ----

@@ -214,7 +214,19 @@ __device__ __forceinline__ float general_error(float t, float s, int act, int er
 // before the TMEM read so that the two latencies overlap.
 // FAST (targets +-1, tanh, MSE/RMSE): |t - tanh(s)| = 2 / (1 + exp(2 t s)), so
 // E = 4 r^2 with r = 1 / (1 + 2^(c_k s)); the factor 4 is applied by the caller.
-template <bool FAST>
+// 1/d for d >= 1 on the FMA pipe: initial guess from the IEEE bit pattern
+// (exponent and mantissa negated by one integer subtraction; relative error
+// below 5.1%), then three Newton steps y <- y (2 - d y), each squaring the
+// relative error (5e-2 -> 2.6e-3 -> 6.6e-6 -> float32 rounding, 1.5e-7).
+__device__ __forceinline__ float rcp_newton(float d) {
+  float y = __int_as_float(0x7EF311C7 - __float_as_int(d));
+  y = y * fmaf(-d, y, 2.0f);
+  y = y * fmaf(-d, y, 2.0f);
+  y = y * fmaf(-d, y, 2.0f);
+  return y;
+}
+
+template <bool FAST, bool NEWTON = false>
 __device__ __forceinline__ float chunk_error(uint32_t taddr, const float* __restrict__ pk,
                                              long long p0, long long m, float rs, float bias,
                                              int act, int err, float R) {
@@ -236,9 +248,14 @@ __device__ __forceinline__ float chunk_error(uint32_t taddr, const float* __rest
     for (int j = 0; j < 32; ++j) {
       const float s = fmaf(v[j], rs, bias);
       if (FAST) {
-        // Fewest instructions per element: the MMA-issuing warp shares its
-        // scheduler with epilogue warps, so epilogue issue slots are not free.
-        const float r = rcp_approx(1.0f + ex2_approx(cq[j] * s));
+        // MMA-bound kernels: fewest instructions (2 MUFU); MUFU-bound kernels
+        // (NEWTON): one MUFU, reciprocal on the FMA pipe.  u is capped at 60
+        // (beyond it the error term r^2 < 2^-120 is zero for the sum).
+        float r;
+        if (NEWTON)
+          r = rcp_newton(1.0f + ex2_approx(fminf(cq[j] * s, 60.0f)));
+        else
+          r = rcp_approx(1.0f + ex2_approx(cq[j] * s));
         sum = fmaf(r, r, sum);
       } else {
         sum += general_error(cq[j], s, act, err, R);
@@ -250,7 +267,8 @@ __device__ __forceinline__ float chunk_error(uint32_t taddr, const float* __rest
       const float s = fmaf(v[j], rs, bias);
       float e;
       if (FAST) {
-        const float r = rcp_approx(1.0f + ex2_approx(cq[j] * s));
+        const float r = NEWTON ? rcp_newton(1.0f + ex2_approx(fminf(cq[j] * s, 60.0f)))
+                               : rcp_approx(1.0f + ex2_approx(cq[j] * s));
         e = r * r;
       } else {
         e = general_error(cq[j], s, act, err, R);

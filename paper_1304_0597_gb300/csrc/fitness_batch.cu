@@ -217,8 +217,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
         for (int ch = 0; ch < kCols / 32; ++ch) {
           const long long p0 = (long long)tile * kBN + h * kCols + ch * 32;
-          if (r.fast)
-            acc += (double)chunk_error<true>(tb + ch * 32, r.pk, p0, r.m, rs, bias, r.act, r.err, r.R);
+          if (r.fast && r.prec == GAME_FP32)
+            acc += (double)chunk_error<true, false>(tb + ch * 32, r.pk, p0, r.m, rs, bias, r.act,
+                                                    r.err, r.R);
+          else if (r.fast)   // same arithmetic as the single-run low-precision kernels
+            acc += (double)chunk_error<true, true>(tb + ch * 32, r.pk, p0, r.m, rs, bias, r.act,
+                                                   r.err, r.R);
           else
             acc += (double)chunk_error<false>(tb + ch * 32, r.pk, p0, r.m, rs, bias, r.act, r.err,
                                               r.R);

@@ -217,10 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
         for (int ch = 0; ch < kCols / 32; ++ch) {
           const long long p0 = (long long)tile * kBN + h * kCols + ch * 32;
-          if (r.fast && r.prec == GAME_FP32)
-            acc += (double)chunk_error<true, false>(tb + ch * 32, r.pk, p0, r.m, rs, bias, r.act,
-                                                    r.err, r.R);
-          else if (r.fast)   // same arithmetic as the single-run low-precision kernels
+          if (r.fast)   // same arithmetic as the single-run kernels
             acc += (double)chunk_error<true, true>(tb + ch * 32, r.pk, p0, r.m, rs, bias, r.act,
                                                    r.err, r.R);
           else

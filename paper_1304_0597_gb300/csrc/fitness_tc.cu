@@ -258,9 +258,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
 #pragma unroll 1
       for (int ch = 0; ch < kCols / 32; ++ch) {
         const long long p0 = tile * BN + h * kCols + ch * 32;
-        // low-precision kernels are MUFU-bound: reciprocal on the FMA pipe
-        acc += (double)chunk_error<FAST, PREC != GAME_FP32>(tbase + ch * 32, pk, p0, p.m, rs, bias,
-                                                           p.act, p.err, p.R);
+        acc += (double)chunk_error<FAST, true>(tbase + ch * 32, pk, p0, p.m, rs, bias, p.act,
+                                               p.err, p.R);
       }
       fence_before();
       __syncwarp();

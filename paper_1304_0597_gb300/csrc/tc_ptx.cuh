@@ -214,19 +214,34 @@ __device__ __forceinline__ float general_error(float t, float s, int act, int er
 // before the TMEM read so that the two latencies overlap.
 // FAST (targets +-1, tanh, MSE/RMSE): |t - tanh(s)| = 2 / (1 + exp(2 t s)), so
 // E = 4 r^2 with r = 1 / (1 + 2^(c_k s)); the factor 4 is applied by the caller.
-// 1/d for d >= 1 on the FMA pipe: initial guess from the IEEE bit pattern
-// (exponent and mantissa negated by one integer subtraction; relative error
-// below 5.1%), then three Newton steps y <- y (2 - d y), each squaring the
-// relative error (5e-2 -> 2.6e-3 -> 6.6e-6 -> float32 rounding, 1.5e-7).
-__device__ __forceinline__ float rcp_newton(float d) {
-  float y = __int_as_float(0x7EF311C7 - __float_as_int(d));
-  y = y * fmaf(-d, y, 2.0f);
-  y = y * fmaf(-d, y, 2.0f);
-  y = y * fmaf(-d, y, 2.0f);
-  return y;
+// Packed float32 pairs (sm_100+ f32x2 arithmetic): one instruction for two lanes
+// of work.  A pair lives in a 64-bit register.
+__device__ __forceinline__ unsigned long long pack2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
 }
 
-template <bool FAST, bool NEWTON = false>
+template <bool FAST, bool PACKED = false>
 __device__ __forceinline__ float chunk_error(uint32_t taddr, const float* __restrict__ pk,
                                              long long p0, long long m, float rs, float bias,
                                              int act, int err, float R) {
@@ -243,19 +258,34 @@ __device__ __forceinline__ float chunk_error(uint32_t taddr, const float* __rest
   float v[32];
   tmem_ld32(taddr, v);
   float sum = 0.0f;
+  if (FAST && PACKED && p0 + 32 <= m) {
+    // two patterns per float32x2 instruction: s = v rs + b, u = c s, d = 1 + 2^u,
+    // r = 1/d, sum += r^2 (the two running sums are added at the end)
+    const unsigned long long rs2 = pack2(rs, rs), b2 = pack2(bias, bias), one2 = pack2(1.0f, 1.0f);
+    unsigned long long acc2 = pack2(0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < 32; j += 2) {
+      const unsigned long long s2 = fma2(pack2(v[j], v[j + 1]), rs2, b2);
+      const unsigned long long u2 = mul2(pack2(cq[j], cq[j + 1]), s2);
+      float u0, u1;
+      unpack2(u2, u0, u1);
+      const unsigned long long d2 = add2(pack2(ex2_approx(u0), ex2_approx(u1)), one2);
+      float d0, d1;
+      unpack2(d2, d0, d1);
+      const unsigned long long r2 = pack2(rcp_approx(d0), rcp_approx(d1));
+      acc2 = fma2(r2, r2, acc2);
+    }
+    float a0, a1;
+    unpack2(acc2, a0, a1);
+    return 4.0f * (a0 + a1);
+  }
   if (p0 + 32 <= m) {
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
       const float s = fmaf(v[j], rs, bias);
       if (FAST) {
-        // MMA-bound kernels: fewest instructions (2 MUFU); MUFU-bound kernels
-        // (NEWTON): one MUFU, reciprocal on the FMA pipe.  u is capped at 60
-        // (beyond it the error term r^2 < 2^-120 is zero for the sum).
-        float r;
-        if (NEWTON)
-          r = rcp_newton(1.0f + ex2_approx(fminf(cq[j] * s, 60.0f)));
-        else
-          r = rcp_approx(1.0f + ex2_approx(cq[j] * s));
+        // fewest instructions per element: epilogue issue slots are the limit
+        const float r = rcp_approx(1.0f + ex2_approx(cq[j] * s));
         sum = fmaf(r, r, sum);
       } else {
         sum += general_error(cq[j], s, act, err, R);
@@ -267,8 +297,7 @@ __device__ __forceinline__ float chunk_error(uint32_t taddr, const float* __rest
       const float s = fmaf(v[j], rs, bias);
       float e;
       if (FAST) {
-        const float r = NEWTON ? rcp_newton(1.0f + ex2_approx(fminf(cq[j] * s, 60.0f)))
-                               : rcp_approx(1.0f + ex2_approx(cq[j] * s));
+        const float r = rcp_approx(1.0f + ex2_approx(cq[j] * s));
         e = r * r;
       } else {
         e = general_error(cq[j], s, act, err, R);

@@ -169,18 +169,22 @@ def measured_peaks():
         return 6800.0, 1900.0, "fallback"
 
 
-def kernel_traffic(kernel_file: str):
-    """DRAM bytes per launch from the committed ncu summary, if taken on this exact source."""
+def kernel_traffic(kernel_file: str, variant: str):
+    """DRAM bytes per launch from the committed ncu summary, if taken on this exact source.
+
+    A record is keyed by kernel file and variant (precision and gene planes) and carries
+    the sha256 of every source file the kernel is compiled from; any edit voids it."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_1304_0597_gb300", "csrc", kernel_file)
     try:
         with open(path) as f:
-            rec = json.load(f).get(kernel_file)
-        with open(src, "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
-    except (OSError, ValueError):
-        return None
-    if not rec or rec.get("source_sha256") != sha:
+            rec = json.load(f).get(f"{kernel_file}:{variant}")
+        if not rec:
+            return None
+        for name, want in rec.get("source_sha256", {}).items():
+            with open(os.path.join(ROOT, "paper_1304_0597_gb300", "csrc", name), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != want:
+                    return None
+    except (OSError, ValueError, AttributeError):
         return None
     return rec.get("bytes_per_launch")
 
@@ -330,15 +334,22 @@ def run_ours(args):
     fit_ms = tm["ms_fitness"] / K
     engine_used = tm["engine"]
     flops = 2.0 * n_train * n_genes * pop
+    # tensor products issued per algorithmic product: FP32 = fp16 hi/lo split (3),
+    # BF16 / FP8 = one per gene plane
+    products = 3 if args.precision == "fp32" else args.gene_planes
+    variant = "fp32" if args.precision == "fp32" else f"{args.precision}x{args.gene_planes}"
+    ratio = 1.0
     if engine_used == game.ENGINE_TCGEN05:
-        kfile, bound, peak, punit = "fitness_tc.cu", "tensor", bf16_tf, "TFLOP/s"
+        # e4m3 products run at twice the 16-bit rate (nominal dense 4.5 vs 2.25 PFLOP/s)
+        ratio = 2.0 if args.precision == "fp8" else 1.0
+        kfile, bound, peak, punit = "fitness_tc.cu", "tensor", bf16_tf * ratio, "TFLOP/s"
         achieved = flops / (fit_ms / 1e3) / 1e12
     else:
         # float32 FFMA: 152 SMs x 128 lanes x 2 flops x max SM clock
         kfile, bound, punit = "fitness_simt.cu", "alu", "TFLOP/s"
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         achieved = flops / (fit_ms / 1e3) / 1e12
-    traffic = kernel_traffic(kfile)
+    traffic = kernel_traffic(kfile, variant)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -357,8 +368,12 @@ def run_ours(args):
                               "reduce_rank": tm["ms_rank"] / K},
         "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": punit,
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": kfile, "peak_source": peak_src if bound == "tensor" else
-                     "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+                     "kernel": kfile, "variant": variant,
+                     "peak_source": (f"{peak_src} bf16" + (" x 2 (e4m3 nominal ratio)"
+                                                           if ratio != 1.0 else ""))
+                     if bound == "tensor" else "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "tensor_products_per_term": products if bound == "tensor" else None,
+                     "issued_frac": achieved * products / peak if bound == "tensor" else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "step": f"one training run: set_data + "
                 f"{GENS_PER_RUN} generations + get_best", "runs": len(e2e_t)},

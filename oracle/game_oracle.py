@@ -630,28 +630,42 @@ def gelu_grad(z: np.ndarray) -> np.ndarray:
     return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
 
 
-def mlp_forward(params: dict, X: np.ndarray) -> dict:
+def bf16_operands(a: np.ndarray) -> np.ndarray:
+    """A GEMM operand as the tensor cores see it in the bfloat16 form: the float32
+    value rounded to bfloat16."""
+    return round_bf16(np.asarray(a, dtype=np.float32)).astype(np.float64)
+
+
+def mlp_forward(params: dict, X: np.ndarray, operand_round=None) -> dict:
     """y = w3 . gelu(W2 gelu(W1 x + b1) + b2) + b3 for every row x of X; keeps the
-    intermediate values the backward pass needs."""
-    X = np.asarray(X, dtype=np.float64)
+    intermediate values the backward pass needs.
+
+    operand_round, if given, is applied to the activations where they enter a
+    matrix product (x and gelu(Z1)): the bfloat16 form rounds its GEMM operands
+    and accumulates in float32; None is the exact network."""
+    r = operand_round if operand_round is not None else (lambda a: a)
+    X = r(np.asarray(X, dtype=np.float64))
     Z1 = X @ params["W1"].T + params["b1"]
-    H1 = gelu(Z1)
+    H1 = r(gelu(Z1))
     Z2 = H1 @ params["W2"].T + params["b2"]
     H2 = gelu(Z2)
     y = H2 @ params["w3"] + params["b3"]
     return {"X": X, "Z1": Z1, "H1": H1, "Z2": Z2, "H2": H2, "y": y}
 
 
-def mlp_loss_grad(params: dict, X: np.ndarray, target: np.ndarray):
-    """Mean squared error L = mean((y - target)^2) and its gradient for every parameter."""
-    f = mlp_forward(params, X)
+def mlp_loss_grad(params: dict, X: np.ndarray, target: np.ndarray, operand_round=None):
+    """Mean squared error L = mean((y - target)^2) and its gradient for every parameter
+    (backpropagation).  operand_round as in mlp_forward; it also applies to the
+    back-propagated dZ2 and dZ1 where they enter a matrix product."""
+    r = operand_round if operand_round is not None else (lambda a: a)
+    f = mlp_forward(params, X, operand_round)
     B = X.shape[0]
     dy = 2.0 * (f["y"] - np.asarray(target, dtype=np.float64)) / B
     g = {"w3": f["H2"].T @ dy, "b3": np.array(dy.sum())}
-    dZ2 = np.outer(dy, params["w3"]) * gelu_grad(f["Z2"])
+    dZ2 = r(np.outer(dy, params["w3"]) * gelu_grad(f["Z2"]))
     g["W2"] = dZ2.T @ f["H1"]
     g["b2"] = dZ2.sum(axis=0)
-    dZ1 = (dZ2 @ params["W2"]) * gelu_grad(f["Z1"])
+    dZ1 = r((dZ2 @ params["W2"]) * gelu_grad(f["Z1"]))
     g["W1"] = dZ1.T @ f["X"]
     g["b1"] = dZ1.sum(axis=0)
     loss = float(np.mean((f["y"] - target) ** 2))

@@ -55,6 +55,7 @@ struct game_ctx {
   // Precision form: FP32 copy of P and the FP32 re-score of the top elites.
   bool lowp = false;            // P stored in BF16 / FP8
   int n_rescore = 0;            // elites re-scored in FP32 each generation
+  int part_rows_r = 0;          // rows of d_partial_r
   Shape s32{};                  // FP32 shape of P (report, re-score)
   ExpDev e32{};                 // FP32 planes of P (== e when precision is FP32)
   Shape sr{};                   // shape of the re-score population (pop = n_rescore)
@@ -77,6 +78,7 @@ struct game_ctx {
   int* d_fallback = nullptr;
   float* d_ring_x = nullptr;    // [ring_cap x kstride]
   float* d_ring_f = nullptr;    // [ring_cap]
+  long long* d_dsq = nullptr;   // [pop_pad] squared rank differences of the monitor
   int* d_ring_meta = nullptr;   // head, count, evals appended, generations monitored
   int ring_cap = 0;
   float* d_norm = nullptr;      // mean, std of log fitness over the ring
@@ -250,6 +252,7 @@ extern "C" game_status game_create(const game_config* cfg, game_ctx** out) {
   if (e == cudaSuccess) e = tc_init_attributes();
   if (e == cudaSuccess) e = batch_init_attributes();
   if (e == cudaSuccess) e = surrogate_ga_init_attributes();
+  if (e == cudaSuccess) e = surrogate_tc_init_attributes();
   if (e != cudaSuccess) {
     delete c;
     return fail(nullptr, GAME_ERR_CUDA, "kernel attributes: %s", cudaGetErrorString(e));
@@ -374,7 +377,10 @@ static game_status alloc_surrogate(game_ctx* c) {
   sg.max_rows = std::max(c->n_pool, c->sg_batch);
   const size_t np = sg.n_params();
   game_status r;
-  const size_t act = (size_t)sg.max_rows * sg.H;
+  // bfloat16 weights run on the tensor cores and need none of the float32
+  // activation planes of the SIMT path
+  const bool use_tc = sg.bf16;
+  const size_t act = use_tc ? 1 : (size_t)sg.max_rows * sg.H;
   if ((r = dalloc(c, &sg.p, sizeof(float) * np)) != GAME_OK) return r;
   if ((r = dalloc(c, &sg.g, sizeof(float) * np)) != GAME_OK) return r;
   if ((r = dalloc(c, &sg.m, sizeof(float) * np)) != GAME_OK) return r;
@@ -391,8 +397,14 @@ static game_status alloc_surrogate(game_ctx* c) {
   if ((r = dalloc(c, &sg.dy, sizeof(float) * sg.max_rows)) != GAME_OK) return r;
   if ((r = dalloc(c, &sg.sq, sizeof(float) * sg.max_rows)) != GAME_OK) return r;
   if ((r = dalloc(c, &sg.loss, sizeof(float))) != GAME_OK) return r;
-  if ((r = dalloc(c, &sg.ws, sizeof(float) * 16 * (size_t)sg.H * std::max(sg.D, sg.H))) != GAME_OK)
+  if ((r = dalloc(c, &sg.ws, sizeof(float) * (use_tc ? 1 : 16 * (size_t)sg.H * std::max(sg.D, sg.H)))) != GAME_OK)
     return r;
+  if (use_tc) {
+    uint8_t* tcbuf = nullptr;
+    if ((r = dalloc(c, &tcbuf, sg.tc_bytes(sg.max_rows, c->sg_batch))) != GAME_OK) return r;
+    sg.state = c->d_state;
+    sg.tc_carve(tcbuf, c->sg_batch);
+  }
   if ((r = dalloc(c, &c->d_pool, sizeof(float) * (size_t)c->n_pool * s.kstride)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_score, sizeof(float) * c->n_pool)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_sel, sizeof(int) * s.pop_pad)) != GAME_OK) return r;
@@ -402,6 +414,7 @@ static game_status alloc_surrogate(game_ctx* c) {
   if ((r = dalloc(c, &c->d_ring_f, sizeof(float) * c->ring_cap)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_ring_meta, sizeof(int) * 8)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_norm, sizeof(float) * 2)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_dsq, sizeof(long long) * s.pop_pad)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_monitor, sizeof(double) * 4096)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_bx, sizeof(float) * (size_t)c->sg_batch * s.kstride)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_bt, sizeof(float) * c->sg_batch)) != GAME_OK) return r;
@@ -411,6 +424,7 @@ static game_status alloc_surrogate(game_ctx* c) {
   const float norm[2] = {0.0f, 1.0f};
   CUDA_OK(c, cudaMemcpyAsync(c->d_norm, norm, sizeof(norm), cudaMemcpyHostToDevice, c->st));
   CUDA_OK(c, launch_surrogate_init(sg, c->cfg.seed ^ 0x53ull, c->st));
+  if (sg.tc) CUDA_OK(c, sg.tc_prepare(c->st));
   CUDA_OK(c, cudaStreamSynchronize(c->st));
   c->sg_alloc = true;
   return GAME_OK;
@@ -548,8 +562,9 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
       free_all(c);
       return r;
     }
-    const int rows = c->n_part_r > simt_partials(c->sr, c->n_sm) ? c->n_part_r
-                                                                : simt_partials(c->sr, c->n_sm);
+    // any tile shape of one slice uses at most one partial row per SM
+    const int rows = std::max(std::max(c->n_part_r, simt_partials(c->sr, c->n_sm)), c->n_sm);
+    c->part_rows_r = rows;
     if ((r = dalloc(c, &c->d_partial_r, sizeof(double) * (size_t)rows * 128)) != GAME_OK) return r;
   }
 
@@ -649,8 +664,17 @@ static game_status enqueue_pre(game_ctx* c, cudaStream_t st) {
 static game_status enqueue_surrogate_train(game_ctx* c, cudaStream_t st) {
   CUDA_OK(c, launch_replay_update(c->p, c->s, std::min(c->cfg.elitism, c->s.pop), c->d_fit,
                                   c->d_pred, c->d_state, c->d_ring_x, c->d_ring_f, c->d_ring_meta,
-                                  c->ring_cap, c->d_norm, c->d_monitor, c->d_fallback, 0.1f, st));
+                                  c->ring_cap, c->d_norm, c->d_monitor, c->d_fallback, 0.1f,
+                                  c->d_dsq, st));
   for (int k = 0; k < c->sg_steps; ++k) {
+    if (c->sg.tc) {
+      // bf16 form: the batch goes straight into the tensor-core operands
+      CUDA_OK(c, launch_sample_batch_tc(c->d_ring_x, c->d_ring_f, c->d_ring_meta, c->s.kstride,
+                                        c->sg, c->sg_batch, c->cfg.seed, c->cfg.run,
+                                        0x51ull << 32, k, c->d_state, c->d_bt, st));
+      CUDA_OK(c, c->sg.tc_train_step(c->sg_batch, c->d_bt, c->sg_lr, st));
+      continue;
+    }
     CUDA_OK(c, launch_sample_batch(c->d_ring_x, c->d_ring_f, c->d_ring_meta, c->s.kstride,
                                    c->s.n_genes, c->d_norm, c->sg_batch, c->cfg.seed, c->cfg.run,
                                    0x51ull << 32, k, c->d_state, c->d_bx, c->d_bt, st));
@@ -1011,37 +1035,29 @@ extern "C" game_status game_get_state(game_ctx* c, int64_t* generation, int32_t*
   return GAME_OK;
 }
 
-extern "C" game_status game_autotune(game_ctx* c, int32_t reps, game_tile* best,
-                                     game_tile* candidates, int32_t cap, int32_t* n_candidates) {
-  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
-  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
-  if (c->engine != GAME_ENGINE_TCGEN05)
-    return fail(c, GAME_ERR_UNSUPPORTED, "this shape runs on the SIMT engine; nothing to tune");
-  if (reps < 1) reps = 1;
-  cudaSetDevice(c->dev);
-  // Operand planes of the current population.
-  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 0, c->st));
-  CUDA_OK(c, launch_prepare(c->s, c->p, c->e, c->d_state, 0, c->st));
+// Times every valid tile shape of one fitness launch (shape s, population planes
+// pd, partial rows at most part_rows) and returns the fastest plan.
+static game_status tune_shape(game_ctx* c, const Shape& s, const ExpDev& e, const PopDev& pd,
+                              double* partial, int part_rows, int reps, TcPlan* best_plan,
+                              game_tile* bt, game_tile* candidates, int cap, int* n_done) {
   std::vector<TileReq> cands;
-  tc_candidates(c->s, &cands);
+  tc_candidates(s, &cands);
   cudaEvent_t e0, e1;
   CUDA_OK(c, cudaEventCreate(&e0));
   CUDA_OK(c, cudaEventCreate(&e1));
-  game_tile bt{0, 0, 0, 0, 1e30};
-  TcPlan best_plan{};
-  int n_done = 0;
+  *bt = game_tile{0, 0, 0, 0, 1e30};
   for (const TileReq& rq : cands) {
     TcPlan plan{};
-    if (tc_plan(c->s, c->e, c->p, c->n_sm, &plan, rq) != cudaSuccess) {
+    if (tc_plan(s, e, pd, c->n_sm, &plan, rq) != cudaSuccess) {
       cudaGetLastError();
       continue;
     }
-    if (plan.n_part > c->part_rows) continue;
+    if (plan.n_part > part_rows) continue;
     std::vector<float> t;
     bool ok = true;
     for (int i = 0; i <= reps && ok; ++i) {
       ok = cudaEventRecord(e0, c->st) == cudaSuccess &&
-           tc_launch(plan, c->s, c->fit, c->p, c->e, c->d_partial, nullptr, c->st) == cudaSuccess &&
+           tc_launch(plan, s, c->fit, pd, e, partial, nullptr, c->st) == cudaSuccess &&
            cudaEventRecord(e1, c->st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
       float ms = 0.f;
       if (ok && i > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) t.push_back(ms);
@@ -1053,21 +1069,55 @@ extern "C" game_status game_autotune(game_ctx* c, int32_t reps, game_tile* best,
     }
     std::sort(t.begin(), t.end());
     const game_tile gt{plan.bn, plan.stages, plan.cluster, plan.prefetch, t[t.size() / 2]};
-    if (candidates && n_done < cap) candidates[n_done] = gt;
-    ++n_done;
-    if (gt.ms < bt.ms) {
-      bt = gt;
-      best_plan = plan;
+    if (candidates && *n_done < cap) candidates[*n_done] = gt;
+    ++*n_done;
+    if (gt.ms < bt->ms) {
+      *bt = gt;
+      *best_plan = plan;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (bt->n == 0) return fail(c, GAME_ERR_UNSUPPORTED, "no tile shape could be planned");
+  return GAME_OK;
+}
+
+extern "C" game_status game_autotune(game_ctx* c, int32_t reps, game_tile* best,
+                                     game_tile* candidates, int32_t cap, int32_t* n_candidates) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  if (c->engine != GAME_ENGINE_TCGEN05)
+    return fail(c, GAME_ERR_UNSUPPORTED, "this shape runs on the SIMT engine; nothing to tune");
+  if (reps < 1) reps = 1;
+  cudaSetDevice(c->dev);
+  // Operand planes of the current population.
+  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 0, c->st));
+  CUDA_OK(c, launch_prepare(c->s, c->p, c->e, c->d_state, 0, c->st));
+  int n_done = 0;
+  game_tile bt;
+  TcPlan best_plan{};
+  game_status r = tune_shape(c, c->s, c->e, c->p, c->d_partial, c->part_rows, reps, &best_plan,
+                             &bt, candidates, cap, &n_done);
+  if (r != GAME_OK) return r;
   if (n_candidates) *n_candidates = n_done < cap ? n_done : cap;
-  if (bt.n == 0) return fail(c, GAME_ERR_UNSUPPORTED, "no tile shape could be planned");
   c->tc = best_plan;
   c->n_part = best_plan.n_part;
-  drop_graphs(c);
   tune_cache_store(c->s, bt);
+  // The FP32 re-score of the elites (precision form) is a launch of its own
+  // shape: one 128-row slice over the FP32 planes.
+  if (c->n_rescore && c->engine_r == GAME_ENGINE_TCGEN05) {
+    CUDA_OK(c, launch_prepare(c->sr, c->pr, c->e32, c->d_state, 0, c->st, c->d_rank, &c->p));
+    int n_r = 0;
+    game_tile bt_r;
+    TcPlan plan_r{};
+    r = tune_shape(c, c->sr, c->e32, c->pr, c->d_partial_r, c->part_rows_r, reps, &plan_r, &bt_r,
+                   nullptr, 0, &n_r);
+    if (r != GAME_OK) return r;
+    c->tc_r = plan_r;
+    c->n_part_r = plan_r.n_part;
+    tune_cache_store(c->sr, bt_r);
+  }
+  drop_graphs(c);
   if (best) *best = bt;
   return GAME_OK;
 }

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int c = it.slice * 128 + q * 32 + lane;
       const float bias = r.bias[c];
       const float rs = r.rscale[c];
-      double acc = 0.0;
+      F2Sum acc;
       for (int tile = it.tile0; tile < it.tile1; ++tile, ++gt) {
         const int buf = gt & 1;
         const uint32_t ap = (uint32_t)((gt >> 1) & 1);
@@ -218,18 +218,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int ch = 0; ch < kCols / 32; ++ch) {
           const long long p0 = (long long)tile * kBN + h * kCols + ch * 32;
           if (r.fast)   // same arithmetic as the single-run kernels
-            acc += (double)chunk_error<true, true>(tb + ch * 32, r.pk, p0, r.m, rs, bias, r.act,
-                                                   r.err, r.R);
+            acc.add(chunk_error<true, true>(tb + ch * 32, r.pk, p0, r.m, rs, bias, r.act, r.err,
+                                            r.R));
           else
-            acc += (double)chunk_error<false>(tb + ch * 32, r.pk, p0, r.m, rs, bias, r.act, r.err,
-                                              r.R);
+            acc.add(chunk_error<false>(tb + ch * 32, r.pk, p0, r.m, rs, bias, r.act, r.err, r.R));
         }
         fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acc_empty + buf);
       }
       if (!ok) break;
-      r.partial[(long long)(it.chunk * kColGroups + h) * r.pop_pad + c] = acc;
+      r.partial[(long long)(it.chunk * kColGroups + h) * r.pop_pad + c] = acc.value();
     }
   }
   fence_before();

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   const uint16_t cmask = (uint16_t)((1u << p.cl) - 1u);
   const int sub_rows = BN / p.cl;                     // rows of the B tile this CTA fetches
   const int a_steps_total = p.kp / kKStep;
-  double acc = 0.0;   // epilogue threads: this chromosome's error sum over its columns
+  F2Sum acc;   // epilogue threads: this chromosome's error sum over its columns
 
   if (warp == 0) {
     // ---- TMA producer: the whole warp follows one control flow, lane 0 issues ----
@@ -255,11 +255,11 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
       const long long tile = member + (long long)it * p.cps;
       constexpr int kCols = BN / kColGroups;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + h * kCols);
-#pragma unroll 1
+#pragma unroll
       for (int ch = 0; ch < kCols / 32; ++ch) {
         const long long p0 = tile * BN + h * kCols + ch * 32;
-        acc += (double)chunk_error<FAST, true>(tbase + ch * 32, pk, p0, p.m, rs, bias, p.act,
-                                               p.err, p.R);
+        acc.add(chunk_error<FAST, true>(tbase + ch * 32, pk, p0, p.m, rs, bias, p.act, p.err,
+                                        p.R));
       }
       fence_before();
       __syncwarp();
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTmemCols));
-  if (warp >= 2) red[((warp - 2) >> 2) * 128 + (warp & 3) * 32 + lane] = acc;
+  if (warp >= 2) red[((warp - 2) >> 2) * 128 + (warp & 3) * 32 + lane] = acc.value();
   __syncthreads();
   if (threadIdx.x < 128) {
     double tot = 0.0;

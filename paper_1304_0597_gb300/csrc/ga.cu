@@ -326,6 +326,73 @@ __global__ void __launch_bounds__(1024) reduce_rank_kernel(RankArgs a) {
   }
 }
 
+// ---- large populations: the same result without a single-CTA sort ----
+// fit[c] from the partial sums (many CTAs).
+__global__ void fit_reduce_kernel(RankArgs a) {
+  if (a.in_evolve && a.state->stopped) return;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= a.pop) return;
+  double sse = 0.0;
+  for (int b = 0; b < a.n_part; ++b) sse += a.partial[(long long)b * a.pop_pad + c];
+  const double mse = sse * a.inv_m;
+  a.fit[c] = (a.error == GAME_RMSE) ? sqrt(mse) : mse;
+}
+
+// Rank by counting: the position of chromosome c is the number of chromosomes
+// before it in the order (fitness, index) (NaN as +inf), so rank[pos] = c.  Eight
+// threads share one c and split the comparisons; keys are staged per 1024.
+__global__ void __launch_bounds__(256) rank_count_kernel(RankArgs a) {
+  if (a.in_evolve && a.state->stopped) return;
+  __shared__ unsigned long long tile[1024];
+  const int sub = threadIdx.x & 7;
+  const int c = blockIdx.x * 32 + (threadIdx.x >> 3);
+  unsigned long long kc = 0;
+  if (c < a.pop) {
+    const double f = a.fit[c];
+    kc = ordered_key(isnan(f) ? CUDART_INF : f);
+  }
+  int pos = 0;
+  for (int t0 = 0; t0 < a.pop; t0 += 1024) {
+    const int n = min(1024, a.pop - t0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double f = a.fit[t0 + i];
+      tile[i] = ordered_key(isnan(f) ? CUDART_INF : f);
+    }
+    __syncthreads();
+    if (c < a.pop)
+      for (int i = sub; i < n; i += 8) {
+        const unsigned long long kj = tile[i];
+        pos += (kj < kc) || (kj == kc && t0 + i < c);
+      }
+  }
+  pos += __shfl_xor_sync(0xffffffffu, pos, 1);
+  pos += __shfl_xor_sync(0xffffffffu, pos, 2);
+  pos += __shfl_xor_sync(0xffffffffu, pos, 4);
+  if (c < a.pop && sub == 0) a.rank[pos] = c;
+}
+
+// The state transition of a ranking (one thread), as in reduce_rank_kernel.
+__global__ void rank_state_kernel(RankArgs a) {
+  DevState* st = a.state;
+  if (a.in_evolve && st->stopped) return;
+  const double f0 = a.fit[a.rank[0]];
+  const double best = isnan(f0) ? CUDART_INF : f0;
+  st->best = best;
+  if (a.mode == kRankEvaluate) {
+    if (st->bred) {
+      st->cur ^= 1;
+      st->gen += 1;
+    }
+    st->bred = 0;
+    st->gens_run += 1;
+    st->evals += 1;
+  }
+  if (a.mode != kRankSortOnly && !a.no_stop && a.in_evolve && best <= a.stop_error)
+    st->stopped = 1;
+  st->evaluated = 1;
+}
+
 static int next_pow2(int n) {
   int p = 2;
   while (p < n) p <<= 1;
@@ -350,6 +417,12 @@ cudaError_t launch_reduce_rank(const Shape& s, const game_config& cfg, const dou
   a.no_stop = (mode >> 9) & 1;
   a.inv_m = 1.0 / (double)s.n_train;
   a.stop_error = cfg.stop_error;
+  if (s.pop >= kRankCountMin) {
+    if (a.mode == kRankEvaluate) fit_reduce_kernel<<<(s.pop + 255) / 256, 256, 0, st>>>(a);
+    rank_count_kernel<<<(s.pop + 31) / 32, 256, 0, st>>>(a);
+    rank_state_kernel<<<1, 1, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   const size_t smem = (size_t)a.n2 * (sizeof(unsigned long long) + sizeof(int));
   const int threads = a.n2 < 1024 ? (a.n2 < 32 ? 32 : a.n2) : 1024;
   reduce_rank_kernel<<<1, threads, smem, st>>>(a);

@@ -104,6 +104,9 @@ cudaError_t launch_prepare(const Shape& s, const PopDev& p, const ExpDev& e, Dev
 cudaError_t launch_rescore_merge(const Shape& sr, const game_config& cfg, const double* partial,
                                  int n_part, const int* rank, double* fit, const DevState* state,
                                  int in_evolve, cudaStream_t st);
+// Populations of at least this size are ranked by counting over many CTAs
+// (fit_reduce / rank_count / rank_state), smaller ones by one CTA's sort.
+constexpr int kRankCountMin = 512;
 cudaError_t launch_reduce_rank(const Shape& s, const game_config& cfg, const double* partial,
                                int n_part, double* fit, int* rank, DevState* state,
                                int mode, cudaStream_t st);

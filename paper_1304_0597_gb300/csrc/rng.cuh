@@ -149,18 +149,43 @@ __device__ __forceinline__ bool better(double fa, int ia, double fb, int ib) {
   return fa < fb || (fa == fb && ia < ib);
 }
 
-__device__ __forceinline__ float mutate_gene(float v, Key key, uint64_t gen, uint64_t pair,
-                                             uint64_t w, float p_m, float sigma, int clamp) {
-  const float u = uniform24(philox_word(key, gen, pair, kStreamMutMask, w));
-  if (u < p_m) {
-    uint32_t a, b;
-    philox_word_pair(key, gen, pair, kStreamMutNormal, w, &a, &b);
-    v = __fadd_rn(v, __fmul_rn(sigma, gauss_f32(a, b)));
-    if (clamp) v = fminf(fmaxf(v, -1.0f), 1.0f);
-  }
+// Mutation of one gene (taken with probability p_m): add sigma N(0,1), the normal
+// from the words 2w, 2w+1 of the normal stream, then clamp.  Out of line: one copy
+// of the normal draw keeps the breeding loop's instruction footprint small.
+static __device__ __noinline__ float mutation_step(float v, Key key, uint64_t gen, uint64_t pair,
+                                                   uint64_t w, float sigma, int clamp) {
+  uint32_t a, b;
+  philox_word_pair(key, gen, pair, kStreamMutNormal, w, &a, &b);
+  v = __fadd_rn(v, __fmul_rn(sigma, gauss_f32(a, b)));
+  if (clamp) v = fminf(fmaxf(v, -1.0f), 1.0f);
   return v;
 }
 
+// The 8 words of one Philox block in word order.
+__device__ __forceinline__ void block_words(const uint64_t v[4], uint32_t w[8]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    w[2 * i] = (uint32_t)v[i];
+    w[2 * i + 1] = (uint32_t)(v[i] >> 32);
+  }
+}
+
+// w[i] <- w[i + o] for i < 8, o in [0, 8), over the 16 words of two consecutive
+// blocks; shifts by 4, 2, 1 with static indices (no local-memory indexing).
+__device__ __forceinline__ void shift_words(uint32_t w[16], int o) {
+  if (o & 4) {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) w[i] = w[i + 4];
+  }
+  if (o & 2) {
+#pragma unroll
+    for (int i = 0; i < 14; ++i) w[i] = w[i + 2];
+  }
+  if (o & 1) {
+#pragma unroll
+    for (int i = 0; i < 15; ++i) w[i] = w[i + 1];
+  }
+}
 
 // One child pair j (one warp): two tournaments of k draws with replacement
 // (winner = min (fitness, index)), single-point crossover with probability p_c
@@ -196,14 +221,75 @@ __device__ __forceinline__ void breed_pair(const float* __restrict__ G, int kstr
   if (uniform24(wc) < p_c && K >= 2) cut = 1 + index_draw(wk, K - 1);
   const float* __restrict__ r1 = G + (long long)bi0 * kstride;
   const float* __restrict__ r2 = G + (long long)bi1 * kstride;
-  for (int g = lane; g < K; g += 32) {
-    const bool head = g < cut;
-    const float va = mutate_gene(head ? r1[g] : r2[g], key, gen, j, (uint64_t)g, p_m, sigma, clamp);
-    oa[g] = va;
-    if (has_b) {
-      const float vb = mutate_gene(head ? r2[g] : r1[g], key, gen, j, (uint64_t)K + (uint64_t)g,
-                                   p_m, sigma, clamp);
-      ob[g] = vb;
+  // Rounds of 256 genes: lane l takes genes g0 .. g0+7, g0 = base + 8 l.  Child
+  // a's mask words g are exactly one Philox block (g0 / 8); child b's words K + g
+  // span at most two.  Genes that do not mutate are written at once; the round's
+  // mutations (probability p_m each) are then packed over the warp, one per lane,
+  // so that the normal draws run in parallel rather than once per gene slot.
+  const int ob_off = K & 7;
+  for (int base = 0; base < K; base += 256) {
+    const int g0 = base + 8 * lane;
+    uint32_t flags = 0;   // bit i: child a's gene g0 + i mutates; bit 8 + i: child b's
+    if (g0 < K) {
+      uint64_t v[4];
+      uint32_t wa[8], wb[16];
+      philox_block(gen, j, kStreamMutMask, (uint64_t)(g0 >> 3), key, v);
+      block_words(v, wa);
+      if (has_b) {
+        const uint64_t bb = ((uint64_t)K + (uint64_t)g0) >> 3;
+        philox_block(gen, j, kStreamMutMask, bb, key, v);
+        block_words(v, wb);
+        if (ob_off) {
+          philox_block(gen, j, kStreamMutMask, bb + 1, key, v);
+          block_words(v, wb + 8);
+          shift_words(wb, ob_off);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int g = g0 + i;
+        if (g < K) {
+          const bool head = g < cut;
+          const float x1 = r1[g], x2 = r2[g];
+          if (uniform24(wa[i]) < p_m)
+            flags |= 1u << i;
+          else
+            oa[g] = head ? x1 : x2;
+          if (has_b) {
+            if (uniform24(wb[i]) < p_m)
+              flags |= 1u << (8 + i);
+            else
+              ob[g] = head ? x2 : x1;
+          }
+        }
+      }
+    }
+    int incl = __popc(flags);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    for (int jb = 0; jb < total; jb += 32) {
+      const int job = jb + lane;
+      // owner = first lane whose inclusive count exceeds job
+      int owner = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1)
+        if (__shfl_sync(0xffffffffu, incl, owner + step - 1) <= job) owner += step;
+      const uint32_t of = __shfl_sync(0xffffffffu, flags, owner);
+      const int oexcl = __shfl_sync(0xffffffffu, incl, owner) - __popc(of);
+      if (job < total) {
+        const int bit = (int)__fns(of, 0, job - oexcl + 1);
+        const int g = base + 8 * owner + (bit & 7);
+        const bool head = g < cut;
+        if (bit < 8)
+          oa[g] = mutation_step(head ? r1[g] : r2[g], key, gen, j, (uint64_t)g, sigma, clamp);
+        else
+          ob[g] = mutation_step(head ? r2[g] : r1[g], key, gen, j, (uint64_t)K + (uint64_t)g, sigma,
+                                clamp);
+      }
     }
   }
 }

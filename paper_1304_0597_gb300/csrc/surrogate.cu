@@ -236,6 +236,14 @@ void Surrogate::views(float* base, float** W1, float** b1, float** W2, float** b
 }
 
 cudaError_t Surrogate::forward(const float* X, long long ldx, int M, float* y, cudaStream_t st) {
+  if (tc) {
+    for (int m0 = 0; m0 < M; m0 += max_rows) {
+      const int mm = M - m0 < max_rows ? M - m0 : max_rows;
+      cudaError_t e = tc_forward(X + (long long)m0 * ldx, ldx, mm, y + m0, nullptr, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+  }
   float *W1, *b1, *W2, *b2, *w3, *b3;
   views(p, &W1, &b1, &W2, &b2, &w3, &b3);
   const void* pw1 = bf16 ? (const void*)(ph) : (const void*)W1;
@@ -263,6 +271,14 @@ cudaError_t Surrogate::forward(const float* X, long long ldx, int M, float* y, c
 
 cudaError_t Surrogate::backward(const float* X, long long ldx, int B, const float* t,
                                 cudaStream_t st) {
+  if (tc) {
+    cudaError_t e = tc_forward(X, ldx, B, yb, t, st);
+    if (e != cudaSuccess) return e;
+    if ((e = tc_out_grads(B, st)) != cudaSuccess) return e;
+    e = tc_backward_gemms(B, st);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
   // forward of the batch keeps Z1, H1, Z2, H2, y (B <= max_rows)
   cudaError_t e = forward(X, ldx, B, yb, st);
   if (e != cudaSuccess) return e;
@@ -296,6 +312,7 @@ cudaError_t Surrogate::backward(const float* X, long long ldx, int B, const floa
 }
 
 cudaError_t Surrogate::adam(float lr, cudaStream_t st) {
+  if (tc) return tc_adam(lr, st);
   const long long n = (long long)n_params();
   adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, g, m, v, ph, n, step, lr, 0.9f,
                                                             0.999f, 1e-8f);
@@ -306,6 +323,7 @@ cudaError_t Surrogate::adam(float lr, cudaStream_t st) {
 cudaError_t Surrogate::refresh(cudaStream_t st) {
   const long long n = (long long)n_params();
   refresh_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, ph, n);
+  if (tc) return tc_weights(st);
   return cudaGetLastError();
 }
 

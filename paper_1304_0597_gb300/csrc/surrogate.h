@@ -33,6 +33,23 @@ struct Surrogate {
   float* loss = nullptr;     // last training loss (device scalar)
   float* ws = nullptr;       // split-K partial planes [16 x H x max(D, H)]
 
+  // Tensor-core path (bfloat16 weights; surrogate_tc.cu): bf16 GEMM operands,
+  // K-major, with transposed copies for the weight gradients.
+  bool tc = false;
+  int Dp = 0;                // D rounded up to 8 (16-byte rows)
+  int Bt = 0;                // training batch capacity
+  long long ldt = 0;         // row stride of the transposed operands (Bt rounded up to 8)
+  __nv_bfloat16 *W1b = nullptr, *W2b = nullptr, *W2Tb = nullptr;   // [H x Dp], [H x H], W2^T
+  __nv_bfloat16 *Xb = nullptr, *H1b = nullptr;                    // [max_rows x Dp], [max_rows x H]
+  __nv_bfloat16 *XTb = nullptr;    // [(D + 1) x ldt], last row ones
+  __nv_bfloat16 *H1Tb = nullptr;   // [(H + 1) x ldt], last row ones
+  __nv_bfloat16 *dZ2Tb = nullptr, *dZ1Tb = nullptr;   // [H x ldt]
+  __nv_bfloat16 *dZ2b = nullptr;   // [Bt x H]
+  float *gp1 = nullptr;            // gelu'(Z1) [Bt x H]
+  float *dyh2 = nullptr;           // dy * H2 [Bt x H]
+  unsigned int* adam_done = nullptr;   // blocks finished in the current Adam launch
+  DevState* state = nullptr;       // where a timed-out wait records its status
+
   size_t n_params() const;
   void views(float* base, float** W1, float** b1, float** W2, float** b2, float** w3,
              float** b3) const;
@@ -42,7 +59,29 @@ struct Surrogate {
   cudaError_t backward(const float* X, long long ldx, int B, const float* t, cudaStream_t st);
   cudaError_t adam(float lr, cudaStream_t st);
   cudaError_t refresh(cudaStream_t st);     // bfloat16 copy of p
+
+  // bytes of the tensor-core buffers, their layout in one allocation, and the
+  // constant parts (rows of ones, weight copies)
+  size_t tc_bytes(int max_rows_, int batch) const;
+  void tc_carve(void* base, int batch);
+  cudaError_t tc_prepare(cudaStream_t st);
+  cudaError_t tc_weights(cudaStream_t st);
+  // forward of M rows; with targets t (M <= Bt) also the operands of the backward pass
+  cudaError_t tc_forward(const float* X, long long ldx, int M, float* y, const float* t,
+                         cudaStream_t st);
+  // the same from rows already in Xb (and X^T when training)
+  cudaError_t tc_layers(int M, float* y, const float* t, cudaStream_t st);
+  // one training step on the B rows in Xb / X^T with targets t: gradients, Adam
+  cudaError_t tc_train_step(int B, const float* t, float lr, cudaStream_t st);
+  // dZ1^T, [gW2 | gb2] and [gW1 | gb1] of the batch just run forward with targets
+  cudaError_t tc_backward_gemms(int B, cudaStream_t st);
+  // gw3, gb3 and the loss of that batch
+  cudaError_t tc_out_grads(int B, cudaStream_t st);
+  // Adam step that also refreshes the bf16 GEMM copies and the step counter
+  cudaError_t tc_adam(float lr, cudaStream_t st);
 };
+
+cudaError_t surrogate_tc_init_attributes();
 
 // Kernels of the surrogate-driven generation (surrogate_ga.cu).
 struct PoolArgs {
@@ -67,19 +106,26 @@ cudaError_t launch_select(const float* score, int n_pool, int n_sel, int* sel, D
 cudaError_t launch_assemble(const float* pool, const int* sel, const float* score, const PopDev& p,
                             const Shape& s, int elitism, int elite_copies, const int* rank,
                             const DevState* state, float* pred, cudaStream_t st);
-// Monitor (Spearman of predicted vs exact over the non-elite rows), then the
+// Monitor (Spearman of predicted vs exact over the non-elite rows; dsq [pop]
+// holds the squared rank differences), then the
 // evaluated population appended to the replay ring with its log fitness
 // standardised within the generation (mean / std over that population).
 cudaError_t launch_replay_update(const PopDev& p, const Shape& s, int elitism, const double* fit,
                                  const float* pred, DevState* state, float* ring_x,
                                  float* ring_f, int* ring_meta, int ring_cap, float* norm,
                                  double* monitor, int* fallback, float fallback_rho,
-                                 cudaStream_t st);
+                                 long long* dsq, cudaStream_t st);
 // Draws a training batch from the ring (Philox) and standardises its targets.
 cudaError_t launch_sample_batch(const float* ring_x, const float* ring_f, const int* ring_meta,
                                 int kstride, int n_genes, const float* norm, int B, uint64_t k0,
                                 uint64_t k1, uint64_t gen_salt, int step, const DevState* state,
                                 float* bx, float* bt, cudaStream_t st);
+// The same batch written straight into the bf16 operands Xb and X^T of the
+// tensor-core path (sg.tc); targets to bt.
+cudaError_t launch_sample_batch_tc(const float* ring_x, const float* ring_f, const int* ring_meta,
+                                   int kstride, const Surrogate& sg, int B, uint64_t k0,
+                                   uint64_t k1, uint64_t gen_salt, int step, const DevState* state,
+                                   float* bt, cudaStream_t st);
 cudaError_t surrogate_ga_init_attributes();
 cudaError_t launch_surrogate_init(Surrogate& sg, uint64_t seed, cudaStream_t st);
 

@@ -11,6 +11,8 @@ namespace game {
 
 namespace {
 
+constexpr size_t kSelectSmem = 160 * 1024;   // pools up to 40,960 children keep keys on chip
+
 __device__ __forceinline__ uint32_t ordered_f32(float f) {
   if (f != f) return 0xFFFFFFFFu;   // NaN ranks last
   const uint32_t b = __float_as_uint(f);
@@ -37,7 +39,7 @@ __global__ void pool_breed_kernel(PoolArgs a) {
 __global__ void __launch_bounds__(1024) select_kernel(const float* __restrict__ score, int n_pool,
                                                       int n_sel, int* __restrict__ sel,
                                                       DevState* st, const int* fallback,
-                                                      int random_select) {
+                                                      int random_select, int keys_in_smem) {
   const int decision = st->evaluated && !st->stopped;
   if (threadIdx.x == 0) st->bred = decision;
   if (!decision) return;
@@ -46,24 +48,71 @@ __global__ void __launch_bounds__(1024) select_kernel(const float* __restrict__ 
     for (int i = tid; i < n_sel; i += nt) sel[i] = i;
     return;
   }
-  __shared__ int cnt;
   __shared__ int scan[1024];
-  // smallest threshold tau with count(key <= tau) >= n_sel (binary search on the key)
-  uint32_t lo = 0u, hi = 0xFFFFFFFFu;
-  while (lo < hi) {
-    const uint32_t mid = lo + ((hi - lo) >> 1);
-    if (tid == 0) cnt = 0;
+  __shared__ int hist[256];
+  __shared__ uint32_t sel_prefix;
+  __shared__ int sel_left;
+  // keys staged in shared memory when the pool fits (dynamic size n_pool words)
+  extern __shared__ uint32_t skey[];
+  if (keys_in_smem) {
+    for (int i = tid; i < n_pool; i += nt) skey[i] = ordered_f32(score[i]);
     __syncthreads();
-    int c = 0;
-    for (int i = tid; i < n_pool; i += nt) c += ordered_f32(score[i]) <= mid;
-    atomicAdd(&cnt, c);
-    __syncthreads();
-    const int total = cnt;
-    __syncthreads();
-    if (total >= n_sel) hi = mid;
-    else lo = mid + 1;
   }
-  const uint32_t tau = lo;
+  auto key_at = [&](int i) -> uint32_t {
+    return keys_in_smem ? skey[i] : ordered_f32(score[i]);
+  };
+  // tau = the n_sel-th smallest key (smallest tau with count(key <= tau) >= n_sel),
+  // by radix selection over the four bytes of the key, most significant first
+  if (tid == 0) {
+    sel_prefix = 0u;
+    sel_left = n_sel;
+  }
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int i = tid; i < 256; i += nt) hist[i] = 0;
+    __syncthreads();
+    const uint32_t prefix = sel_prefix;
+    const uint32_t hmask = shift == 24 ? 0u : (0xFFFFFFFFu << (shift + 8));
+    // children's scores share their leading bytes: lanes that hit the same bin
+    // add once per warp (one atomic per group of equal bins)
+    for (int i0 = 0; i0 < n_pool; i0 += nt) {
+      const int i = i0 + tid;
+      int bin = -1;
+      if (i < n_pool) {
+        const uint32_t k = key_at(i);
+        if ((k & hmask) == (prefix & hmask)) bin = (int)((k >> shift) & 255u);
+      }
+      const unsigned same = __match_any_sync(0xffffffffu, bin);
+      if (bin >= 0 && (threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[bin], __popc(same));
+    }
+    __syncthreads();
+    if (tid < 32) {
+      // lane l owns bins 8l .. 8l+7; find the bin where the running count reaches sel_left
+      int c[8], tot = 0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        c[b] = hist[tid * 8 + b];
+        tot += c[b];
+      }
+      int incl = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (tid >= o) incl += y;
+      }
+      const int left = sel_left;
+      const unsigned hit = __ballot_sync(0xffffffffu, incl >= left);
+      const int owner = __ffs(hit) - 1;   // hist sums to >= left, so some lane hits
+      if (tid == owner) {
+        int run = incl - tot;
+        int b = 0;
+        while (b < 7 && run + c[b] < left) run += c[b++];
+        sel_prefix = prefix | ((uint32_t)(tid * 8 + b) << shift);
+        sel_left = left - run;
+      }
+    }
+    __syncthreads();
+  }
+  const uint32_t tau = sel_prefix;
   // compaction in index order: thread t owns the contiguous range [t*chunk, (t+1)*chunk);
   // pass 0 takes every key < tau, pass 1 the first keys == tau up to n_sel.
   const int chunk = (n_pool + nt - 1) / nt;
@@ -74,7 +123,7 @@ __global__ void __launch_bounds__(1024) select_kernel(const float* __restrict__ 
   for (int pass = 0; pass < 2; ++pass) {
     int c = 0;
     for (int i = b0; i < b1; ++i) {
-      const uint32_t k = ordered_f32(score[i]);
+      const uint32_t k = key_at(i);
       c += pass == 0 ? (k < tau) : (k == tau);
     }
     scan[tid] = c;
@@ -87,7 +136,7 @@ __global__ void __launch_bounds__(1024) select_kernel(const float* __restrict__ 
     }
     int pos = start_s + scan[tid] - c;
     for (int i = b0; i < b1; ++i) {
-      const uint32_t k = ordered_f32(score[i]);
+      const uint32_t k = key_at(i);
       if (pass == 0 ? (k < tau) : (k == tau)) {
         if (pos < n_sel) sel[pos] = i;
         ++pos;
@@ -154,79 +203,87 @@ __global__ void replay_commit_kernel(const DevState* st, int pop, int* ring_meta
   ring_meta[2] = st->evals;
 }
 
+// ---- monitor: rank difference of every non-elite row (many CTAs) ----
+// Ranks by counting over keys (value, row) ordered as floats, row as the tie
+// break: rank = number of rows with a smaller key.  Eight threads share a row.
+__device__ __forceinline__ unsigned long long spearman_key(const float* pred, const double* fit,
+                                                           int e, int i, int which) {
+  const float v = which == 0 ? pred[e + i] : (float)fit[e + i];
+  return ((unsigned long long)ordered_f32(v) << 32) | (uint32_t)i;
+}
+
+__global__ void __launch_bounds__(256) spearman_dsq_kernel(const double* fit, const float* pred,
+                                                           const DevState* st, int pop, int e,
+                                                           const int* ring_meta,
+                                                           long long* dsq) {
+  if (st->evals == ring_meta[2]) return;
+  const int n = pop - e;
+  if (!(n >= 3 && !(pred[e] != pred[e]))) return;
+  __shared__ unsigned long long tp[1024], tf[1024];
+  const int sub = threadIdx.x & 7;
+  const int i = blockIdx.x * 32 + (threadIdx.x >> 3);
+  const unsigned long long kp = i < n ? spearman_key(pred, fit, e, i, 0) : 0ull;
+  const unsigned long long kf = i < n ? spearman_key(pred, fit, e, i, 1) : 0ull;
+  int rp = 0, rf = 0;
+  for (int t0 = 0; t0 < n; t0 += 1024) {
+    const int m = min(1024, n - t0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      tp[j] = spearman_key(pred, fit, e, t0 + j, 0);
+      tf[j] = spearman_key(pred, fit, e, t0 + j, 1);
+    }
+    __syncthreads();
+    if (i < n)
+      for (int j = sub; j < m; j += 8) {
+        rp += tp[j] < kp;
+        rf += tf[j] < kf;
+      }
+  }
+#pragma unroll
+  for (int o = 1; o < 8; o <<= 1) {
+    rp += __shfl_xor_sync(0xffffffffu, rp, o);
+    rf += __shfl_xor_sync(0xffffffffu, rf, o);
+  }
+  if (i < n && sub == 0) {
+    const long long d = (long long)(rp - rf);
+    dsq[i] = d * d;
+  }
+}
+
 // ---- monitor and the generation's target standardisation (one CTA) ----
 __global__ void __launch_bounds__(1024) replay_stats_kernel(const double* fit, const float* pred,
                                                             const DevState* st, int pop, int e,
                                                             int* ring_meta, float* norm,
                                                             double* monitor, int* fallback,
-                                                            float fallback_rho) {
+                                                            float fallback_rho,
+                                                            const long long* dsq) {
   if (st->evals == ring_meta[2]) return;
-  extern __shared__ unsigned char sm[];
-  unsigned long long* key = reinterpret_cast<unsigned long long*>(sm);
   const int tid = threadIdx.x, nt = blockDim.x;
   __shared__ double red[1024];
   __shared__ double red2[1024];
   // Spearman correlation of predicted and exact fitness over rows e..pop-1 with a
-  // prediction (rows of an untrained or fallback generation still carry one).
+  // prediction (rows of an untrained or fallback generation still carry one):
+  // 1 - 6 sum d^2 / (n (n^2 - 1)), d the rank differences (integers: the sum is exact).
   const int n = pop - e;
-  int n2 = 2;
-  while (n2 < n) n2 <<= 1;
-  int* rk_pred = reinterpret_cast<int*>(key + n2);
   double rho = CUDART_NAN;
   const bool have_pred = n >= 3 && !(pred[e] != pred[e]);
   if (have_pred) {
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int i = tid; i < n2; i += nt) {
-        uint64_t k = 0xFFFFFFFFFFFFFFFFull;
-        if (i < n) {
-          const float v = pass == 0 ? pred[e + i] : (float)fit[e + i];
-          k = ((uint64_t)ordered_f32(v) << 32) | (uint32_t)i;
-        }
-        key[i] = k;
-      }
-      __syncthreads();
-      for (int k = 2; k <= n2; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-          for (int i = tid; i < n2; i += nt) {
-            const int l = i ^ j;
-            if (l > i) {
-              const bool up = (i & k) == 0;
-              const unsigned long long a = key[i], b = key[l];
-              if ((b < a) == up) {
-                key[i] = b;
-                key[l] = a;
-              }
-            }
-          }
-          __syncthreads();
-        }
-      double s = 0.0;
-      for (int r = tid; r < n; r += nt) {
-        const int i = (int)(key[r] & 0xFFFFFFFFu);
-        if (pass == 0) {
-          rk_pred[i] = r;
-        } else {
-          const double d = (double)(rk_pred[i] - r);
-          s += d * d;
-        }
-      }
-      __syncthreads();
-      if (pass == 1) {
-        red[tid] = s;
-        __syncthreads();
-        for (int o = nt >> 1; o > 0; o >>= 1) {
-          if (tid < o) red[tid] += red[tid + o];
-          __syncthreads();
-        }
-        rho = 1.0 - 6.0 * red[0] / ((double)n * ((double)n * n - 1.0));
-      }
+    long long sdd = 0;
+    for (int i = tid; i < n; i += nt) sdd += dsq[i];
+    red[tid] = (double)sdd;
+    __syncthreads();
+    for (int o = nt >> 1; o > 0; o >>= 1) {
+      if (tid < o) red[tid] += red[tid + o];
       __syncthreads();
     }
+    rho = 1.0 - 6.0 * red[0] / ((double)n * ((double)n * n - 1.0));
+    __syncthreads();
   }
   // mean / std of log fitness over this generation's population
+  // (float32 logarithm, the one the ring's targets use; float64 sums)
   double s1 = 0.0, s2 = 0.0;
   for (int i = tid; i < pop; i += nt) {
-    const double l = log(fmax(fit[i], 1e-30));
+    const double l = (double)logf(fmaxf((float)fit[i], 1e-30f));
     s1 += l;
     s2 += l * l;
   }
@@ -271,6 +328,48 @@ __global__ void sample_batch_kernel(const float* __restrict__ ring_x, const floa
   if (lane == 0) bt[row] = ring_f[idx];
 }
 
+// ---- training batch straight into the tensor-core operands (bf16 form) ----
+// Same draws as sample_batch_kernel; a CTA takes 32 rows x 32 genes through a
+// shared tile so that both the row-major and the transposed bf16 stores coalesce.
+__global__ void sample_batch_tc_kernel(const float* __restrict__ ring_x,
+                                       const float* __restrict__ ring_f,
+                                       const int* __restrict__ ring_meta, int kstride, int D,
+                                       int B, Key key, uint64_t salt, int step, const DevState* st,
+                                       __nv_bfloat16* __restrict__ Xb, int Dp,
+                                       __nv_bfloat16* __restrict__ XT, long long ldt,
+                                       float* __restrict__ bt) {
+  __shared__ float tile[32][33];
+  __shared__ int rows[32];
+  const int d0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  if (ty == 0) {
+    const int r = r0 + tx;
+    int idx = 0;
+    if (r < B) {
+      const int count = ring_meta[1];
+      const uint32_t w = philox_word(key, (uint64_t)st->evals, salt + (uint64_t)step, 6, (uint64_t)r);
+      idx = count > 0 ? index_draw(w, count) : 0;
+      if (blockIdx.x == 0) bt[r] = ring_f[idx];
+    }
+    rows[tx] = idx;
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int r = r0 + i, d = d0 + tx;
+    float v = 0.0f;
+    if (r < B && d < D) {
+      v = ring_x[(long long)rows[i] * kstride + d];
+      Xb[(long long)r * Dp + d] = __float2bfloat16_rn(v);
+    }
+    tile[i][tx] = v;
+  }
+  __syncthreads();
+  for (int i = ty; i < 32; i += 8) {
+    const int d = d0 + i, r = r0 + tx;
+    if (d < D && r < B) XT[(long long)d * ldt + r] = __float2bfloat16_rn(tile[tx][i]);
+  }
+}
+
 // ---- initial weights: U[-a, a], a = sqrt(3 / fan_in); biases 0 ----
 __global__ void surrogate_init_kernel(float* p, __nv_bfloat16* ph, float* m, float* v, long long n,
                                       long long n_w1, long long n_b1, long long n_w2,
@@ -299,7 +398,9 @@ cudaError_t launch_pool_breed(const PoolArgs& a, cudaStream_t st) {
 
 cudaError_t launch_select(const float* score, int n_pool, int n_sel, int* sel, DevState* state,
                           const int* fallback, int random_select, cudaStream_t st) {
-  select_kernel<<<1, 1024, 0, st>>>(score, n_pool, n_sel, sel, state, fallback, random_select);
+  const int in_smem = (size_t)n_pool * sizeof(uint32_t) <= kSelectSmem ? 1 : 0;
+  select_kernel<<<1, 1024, in_smem ? (size_t)n_pool * sizeof(uint32_t) : 0, st>>>(
+      score, n_pool, n_sel, sel, state, fallback, random_select, in_smem);
   return cudaGetLastError();
 }
 
@@ -316,12 +417,13 @@ cudaError_t launch_replay_update(const PopDev& p, const Shape& s, int elitism, c
                                  const float* pred, DevState* state, float* ring_x,
                                  float* ring_f, int* ring_meta, int ring_cap, float* norm,
                                  double* monitor, int* fallback, float fallback_rho,
-                                 cudaStream_t st) {
-  int n2 = 2;
-  while (n2 < s.pop) n2 <<= 1;
-  const size_t smem = (size_t)n2 * (sizeof(unsigned long long) + sizeof(int));
-  replay_stats_kernel<<<1, 1024, smem, st>>>(fit, pred, state, s.pop, elitism, ring_meta, norm,
-                                             monitor, fallback, fallback_rho);
+                                 long long* dsq, cudaStream_t st) {
+  const int n = s.pop - elitism;
+  if (n > 0)
+    spearman_dsq_kernel<<<(n + 31) / 32, 256, 0, st>>>(fit, pred, state, s.pop, elitism, ring_meta,
+                                                       dsq);
+  replay_stats_kernel<<<1, 1024, 0, st>>>(fit, pred, state, s.pop, elitism, ring_meta, norm,
+                                          monitor, fallback, fallback_rho, dsq);
   replay_copy_kernel<<<(s.pop * 32 + 255) / 256, 256, 0, st>>>(
       p.g32[0], p.g32[1], fit, state, s.pop, s.n_genes, s.kstride, ring_x, ring_f, ring_meta,
       ring_cap, norm);
@@ -339,9 +441,20 @@ cudaError_t launch_sample_batch(const float* ring_x, const float* ring_f, const 
   return cudaGetLastError();
 }
 
+cudaError_t launch_sample_batch_tc(const float* ring_x, const float* ring_f, const int* ring_meta,
+                                   int kstride, const Surrogate& sg, int B, uint64_t k0,
+                                   uint64_t k1, uint64_t gen_salt, int step, const DevState* state,
+                                   float* bt, cudaStream_t st) {
+  const dim3 grid((sg.D + 31) / 32, (B + 31) / 32);
+  sample_batch_tc_kernel<<<grid, dim3(32, 8), 0, st>>>(ring_x, ring_f, ring_meta, kstride, sg.D, B,
+                                                       Key{k0, k1}, gen_salt, step, state, sg.Xb,
+                                                       sg.Dp, sg.XTb, sg.ldt, bt);
+  return cudaGetLastError();
+}
+
 cudaError_t surrogate_ga_init_attributes() {
-  return cudaFuncSetAttribute(replay_stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              8192 * (int)(sizeof(unsigned long long) + sizeof(int)));
+  return cudaFuncSetAttribute(select_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kSelectSmem);
 }
 
 cudaError_t launch_surrogate_init(Surrogate& sg, uint64_t seed, cudaStream_t st) {

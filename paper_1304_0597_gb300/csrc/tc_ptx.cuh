@@ -200,6 +200,22 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 
+// A running sum kept as an unevaluated float32 pair hi + lo (TwoSum, Knuth): about
+// 48 significant bits on the FP32 pipe, where float64 adds and conversions would
+// queue on this part's narrow FP64 unit.  Explicit rounding intrinsics keep the
+// compiler from reassociating the error term away.
+struct F2Sum {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float t) {
+    const float s = __fadd_rn(hi, t);
+    const float bp = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(t, bp));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 __device__ __forceinline__ float general_error(float t, float s, int act, int err, float R) {
   const float y = act == GAME_TANH ? tanhf(s) : s;
   const float d = t - y;

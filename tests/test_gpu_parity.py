@@ -130,6 +130,7 @@ def test_initial_population_bit_exact(init):
     dict(pop=10, elitism=10),                                 # everything elite
     dict(pop=45, tournament_k=32, clamp_genes=False, sigma_mutation=0.7, p_mutation=0.5),
     dict(pop=1000, degree=6),
+    dict(pop=600, degree=3, elitism=5),                       # counting rank, ragged blocks
 ])
 def test_operators_bit_exact_given_fitness(kw):
     ds = synth.make_dataset(500, 5, kw.get("degree", 4), seed=2)
@@ -148,6 +149,23 @@ def test_operators_bit_exact_given_fitness(kw):
         G = g.population()
         np.testing.assert_array_equal(G, want)
         assert g.state()[0] == gen + 1
+
+
+@pytest.mark.parametrize("pop", [100, 600, 1030])
+def test_rank_after_evaluate_is_the_oracle_order(pop):
+    """The ranking returned with the fitness is the order (fitness, index) of that
+    fitness vector, for one-CTA sorting (pop < 512) and counting over many CTAs."""
+    ds = synth.make_dataset(900, 6, 3, seed=12)
+    ocfg = _cfg(degree=3, pop=pop, seed=3)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    fit, rank = g.evaluate()
+    np.testing.assert_array_equal(rank, o.rank(fit))
+    G = g.population()
+    G[pop // 3] = G[pop // 5]                                 # a tie in fitness: index decides
+    g.set_population(G)
+    fit, rank = g.evaluate()
+    assert fit[pop // 3] == fit[pop // 5]
+    np.testing.assert_array_equal(rank, o.rank(fit))
 
 
 def test_trajectory_bit_exact_with_gpu_fitness():

@@ -1,10 +1,14 @@
 """Learned surrogate: the network's forward, gradients and Adam step against the
 float64 oracle, and the surrogate-driven generation.
 
-Tolerances: with float32 weights the kernels differ from float64 only by
-float32 rounding of the GEMMs (K <= 289 terms, |terms| ~ 1): 1e-4 relative to
-the largest output / gradient entry.  With bfloat16 weights the oracle is fed
-the same bfloat16-rounded weights, so the same bound holds.
+Tolerances: with float32 weights (SIMT kernels) the kernels differ from float64
+only by float32 rounding of the GEMMs (K <= 289 terms, |terms| ~ 1): 1e-4
+relative to the largest output / gradient entry.  The bfloat16 form runs on the
+tensor cores with bfloat16 weights and bfloat16 GEMM operands (x, gelu(Z1), dZ2,
+dZ1) and float32 accumulation; the oracle is fed the same bfloat16 weights and
+rounds the same operands.  What remains is float32 accumulation order, which can
+flip a bfloat16 rounding by one unit (2^-8 relative) for a few operands: 3e-3
+relative to the largest entry.
 """
 
 import numpy as np
@@ -52,8 +56,9 @@ def test_surrogate_forward_matches_oracle(fp32):
             p[k] = o.round_bf16(p[k].astype(np.float32)).astype(np.float64)
     X = np.random.default_rng(1).uniform(-1, 1, size=(200, D)).astype(np.float32)
     y = g.surrogate_forward(X)
-    want = o.mlp_forward(p, X)["y"]
-    np.testing.assert_allclose(y, want, rtol=0, atol=1e-4 * max(1.0, np.abs(want).max()))
+    want = o.mlp_forward(p, X, None if fp32 else o.bf16_operands)["y"]
+    tol = 1e-4 if fp32 else 3e-3
+    np.testing.assert_allclose(y, want, rtol=0, atol=tol * max(1.0, np.abs(want).max()))
 
 
 @pytest.mark.parametrize("fp32", [True, False])
@@ -69,11 +74,39 @@ def test_surrogate_gradient_matches_oracle(fp32):
     X = rng.uniform(-1, 1, size=(256, D)).astype(np.float32)
     t = rng.standard_normal(256).astype(np.float32)
     loss, grad = g.surrogate_grad(X, t)
-    want_loss, gw = o.mlp_loss_grad(p, X, t)
-    assert loss == pytest.approx(want_loss, rel=1e-4)
+    want_loss, gw = o.mlp_loss_grad(p, X, t, None if fp32 else o.bf16_operands)
+    tol = 1e-4 if fp32 else 3e-3
+    assert loss == pytest.approx(want_loss, rel=tol)
     for name, got in _unflatten(grad, D).items():
         ref = np.asarray(gw[name])
-        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-4 * max(1e-6, np.abs(ref).max()),
+        np.testing.assert_allclose(got, ref, rtol=0, atol=tol * max(1e-6, np.abs(ref).max()),
+                                   err_msg=name)
+
+
+def test_surrogate_tc_shapes_against_oracle():
+    """bfloat16 form at a shape with several k-blocks and a ragged one (145 genes),
+    three row tiles in the batch (384 rows: weight-gradient K = 384), a ragged
+    forward (300 rows) and the bias column of [gW1 | gb1] in a second tile."""
+    ds = synth.make_dataset(1500, 24, 6, seed=54)
+    ocfg = o.Config(degree=6, pop=64, seed=8)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, surrogate_batch=384)
+    D = g.n_genes
+    assert D == 145
+    p = _unflatten(g.surrogate_params(), D)
+    for k in ("W1", "W2", "w3"):
+        p[k] = o.round_bf16(p[k].astype(np.float32)).astype(np.float64)
+    rng = np.random.default_rng(9)
+    X = rng.uniform(-1, 1, size=(384, D)).astype(np.float32)
+    t = rng.standard_normal(384).astype(np.float32)
+    y = g.surrogate_forward(X[:300])
+    want = o.mlp_forward(p, X[:300], o.bf16_operands)["y"]
+    np.testing.assert_allclose(y, want, rtol=0, atol=3e-3 * max(1.0, np.abs(want).max()))
+    loss, grad = g.surrogate_grad(X, t)
+    want_loss, gw = o.mlp_loss_grad(p, X, t, o.bf16_operands)
+    assert loss == pytest.approx(want_loss, rel=3e-3)
+    for name, got in _unflatten(grad, D).items():
+        ref = np.asarray(gw[name])
+        np.testing.assert_allclose(got, ref, rtol=0, atol=3e-3 * max(1e-6, np.abs(ref).max()),
                                    err_msg=name)
 
 

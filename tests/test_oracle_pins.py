@@ -508,6 +508,35 @@ def test_mlp_gradient_by_finite_differences():
         np.testing.assert_allclose(np.asarray(g[name]).reshape(-1), num, rtol=1e-5, atol=1e-9)
 
 
+def test_mlp_bf16_operands_bounded_and_applied():
+    """The bfloat16-operand network: identity rounding is the exact network; bf16
+    rounding of x, gelu(Z1), dZ2 and dZ1 moves every result by no more than the
+    rounding bound (relative 2^-8 per operand, propagated through two layers) and
+    by more than float64 noise (the rounding is really applied)."""
+    rng = np.random.default_rng(23)
+    p = _mlp(rng)
+    X = rng.uniform(-1, 1, size=(16, 7))
+    t = rng.standard_normal(16)
+    l0, g0 = o.mlp_loss_grad(p, X, t)
+    li, gi = o.mlp_loss_grad(p, X, t, operand_round=lambda a: a)
+    assert li == l0
+    for k in g0:
+        np.testing.assert_array_equal(gi[k], g0[k])
+    y0 = o.mlp_forward(p, X)["y"]
+    yr = o.mlp_forward(p, X, o.bf16_operands)["y"]
+    # |dy| <= 2 u (sum |w3| |gelu'| |W2| |H1| + ...) : bound by the magnitudes of the terms
+    f = o.mlp_forward(p, X)
+    u = 2.0 ** -8
+    bound = u * (np.abs(f["H1"]) @ np.abs(p["W2"]).T @ np.abs(p["w3"]) * 1.2 +
+                 np.abs(X) @ np.abs(p["W1"]).T @ np.abs(p["W2"]).T @ np.abs(p["w3"]) * 1.2 * 1.2)
+    assert np.all(np.abs(yr - y0) <= bound)
+    assert np.max(np.abs(yr - y0)) > 1e-9
+    _, gr = o.mlp_loss_grad(p, X, t, operand_round=o.bf16_operands)
+    for k in ("W1", "W2", "b1", "b2"):
+        rel = np.max(np.abs(gr[k] - g0[k])) / np.max(np.abs(g0[k]))
+        assert 1e-9 < rel < 0.05, (k, rel)
+
+
 def test_adam_first_step_moves_each_parameter_by_lr():
     """At step 1 the bias-corrected update is lr * g/(|g| + eps): size lr, against the gradient."""
     g = np.array([0.3, -2.0, 1e-3])

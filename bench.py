@@ -59,7 +59,7 @@ def parse():
                          "against the same runs launched one by one; prints its own JSON line")
     ap.add_argument("--surrogate", action="store_true",
                     help="learned-surrogate form: time to the plain FP32 GA's final train RMSE")
-    ap.add_argument("--seeds", type=int, default=1)
+    ap.add_argument("--seeds", type=int, default=3)
     ap.add_argument("--budget", type=int, default=200, help="plain GA generations (target run)")
     ap.add_argument("--precision-table", action="store_true",
                     help="print the per-precision fitness error / accuracy table and exit")
@@ -488,21 +488,34 @@ def batched(args):
 def surrogate_ttt(args):
     """Time to target RMSE on 2,000,000 patterns x 48 features (Chebyshev d=6, 289 genes),
     population 4096.  Target = final best train RMSE of the plain FP32 GA after --budget
-    generations (same seed).  Contenders: surrogate (8x pool, MLP 289-256-256-1) with FP32
-    fitness, and with BF16 P (one gene plane, top-16 elites re-scored in FP32); plus the
-    ablation (plain children of the same pools) for the gain of the network itself."""
+    generations (same seed).  Contenders: the surrogate (MLP 289-256-256-1, 8x pool, top
+    1/8 evaluated exactly) with FP8 and with BF16 P (one gene plane, top-16 elites
+    re-scored in FP32); the same with a 4x pool; FP8 P alone (no surrogate); and the
+    ablation (plain children of the same 8x pools) for the gain of the network itself.
+    Every contender is timed on the device (CUDA events around each generation)."""
     import torch
     from paper_1304_0597_gb300 import game, synth
     ds = synth.surrogate_scale(n_patterns=args.n_patterns if args.n_patterns != 1_000_000
                                else 2_000_000)
+    lowp = dict(gene_planes=1, elite_rescore=16)
+    contenders = (
+        ("surrogate_fp8", dict(surrogate_pool=8, precision=game.FP8, **lowp)),
+        ("surrogate_bf16", dict(surrogate_pool=8, precision=game.BF16, **lowp)),
+        ("surrogate_fp8_pool4", dict(surrogate_pool=4, precision=game.FP8, **lowp)),
+        ("fp8_only", dict(precision=game.FP8, **lowp)),
+        ("ablation_fp8", dict(surrogate_pool=8, surrogate_select=1, precision=game.FP8, **lowp)),
+    )
+    tuned = set()
     results = []
     base = dict(degree=6, pop=4096)
     for seed in range(args.seeds):
         def make(**kw):
             g = game.Game(game.default_config(**base, seed=seed, **kw))
             g.set_data(ds.X, ds.t, ds.n_train)
-            if g.timing()["engine"] == game.ENGINE_TCGEN05:
-                g.autotune(reps=2)
+            key = (kw.get("precision", game.FP32), kw.get("gene_planes", 2))
+            if key not in tuned and g.timing()["engine"] == game.ENGINE_TCGEN05:
+                g.autotune(reps=2)      # the tile cache serves the later contexts
+                tuned.add(key)
             g.set_timing(False)
             return g
 
@@ -513,12 +526,7 @@ def surrogate_ttt(args):
         plain.close()
         row = {"seed": seed, "target_rmse": target, "plain_fp32": {"ms": t_plain,
                "generations": args.budget, "test_accuracy": acc_plain}}
-        for name, kw in (("surrogate_fp32", dict(surrogate_pool=8)),
-                         ("surrogate_bf16", dict(surrogate_pool=8, precision=game.BF16,
-                                                 gene_planes=1, elite_rescore=16)),
-                         ("ablation_bf16", dict(surrogate_pool=8, surrogate_select=1,
-                                                precision=game.BF16, gene_planes=1,
-                                                elite_rescore=16))):
+        for name, kw in contenders:
             g = make(**kw)
             ms, gens, hit = 0.0, 0, False
             while gens < 2 * args.budget:
@@ -529,21 +537,33 @@ def surrogate_ttt(args):
                 if best <= target:
                     hit = True
                     break
-            mon = g.surrogate_monitor()
-            rho = mon["history"]
-            row[name] = {"ms": ms, "generations": gens, "reached": hit, "best_rmse": best,
-                         "test_accuracy": acc, "speedup_vs_plain": t_plain / ms if hit else None,
-                         "spearman_mean": float(np.nanmean(rho)) if len(rho) else None}
+            rec = {"ms": ms, "generations": gens, "reached": hit, "best_rmse": best,
+                   "test_accuracy": acc, "speedup_vs_plain": t_plain / ms if hit else None}
+            if kw.get("surrogate_pool"):
+                rho = g.surrogate_monitor()["history"]
+                rec["spearman_mean"] = float(np.nanmean(rho)) if len(rho) else None
+            row[name] = rec
             g.close()
         results.append(row)
         print(json.dumps(row), flush=True)
-    sp = [r["surrogate_bf16"]["speedup_vs_plain"] for r in results
-          if r["surrogate_bf16"]["speedup_vs_plain"]]
-    print(json.dumps({"metric": "time-to-target-RMSE speedup vs plain FP32 GA (learned surrogate "
-                      "+ BF16 P)", "value": float(np.median(sp)) if sp else None,
-                      "unit": "x", "seeds": args.seeds, "budget_generations": args.budget,
-                      "config": {"workload": "2,000,000 patterns x 48 features, Chebyshev d=6, "
-                                             "289 genes, pop 4096, 8x pool"}}), flush=True)
+
+    def med(name):
+        v = [r[name]["speedup_vs_plain"] for r in results if r[name]["speedup_vs_plain"]]
+        return float(np.median(v)) if v else None
+
+    def dacc(name):
+        return float(np.mean([r[name]["test_accuracy"] - r["plain_fp32"]["test_accuracy"]
+                              for r in results]))
+
+    print(json.dumps({
+        "metric": "time-to-target-RMSE speedup vs plain FP32 GA (learned surrogate + FP8 P)",
+        "value": med("surrogate_fp8"), "unit": "x", "higher_is_better": True,
+        "seeds": args.seeds, "budget_generations": args.budget,
+        "median_speedup": {name: med(name) for name, _ in contenders},
+        "mean_test_accuracy_delta": {name: dacc(name) for name, _ in contenders},
+        "config": {"workload": "2,000,000 patterns x 48 features, Chebyshev d=6, 289 genes, "
+                               "pop 4096, 8x pool, surrogate MLP 289-256-256-1 (bf16, tcgen05)",
+                   "surrogate_steps_per_generation": 4, "surrogate_batch": 1024}}), flush=True)
 
 
 def main():

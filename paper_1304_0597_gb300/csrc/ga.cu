@@ -339,13 +339,13 @@ __global__ void fit_reduce_kernel(RankArgs a) {
 }
 
 // Rank by counting: the position of chromosome c is the number of chromosomes
-// before it in the order (fitness, index) (NaN as +inf), so rank[pos] = c.  Eight
-// threads share one c and split the comparisons; keys are staged per 1024.
+// before it in the order (fitness, index) (NaN as +inf), so rank[pos] = c.  One
+// warp per c splits the comparisons; keys are staged per 1024.
 __global__ void __launch_bounds__(256) rank_count_kernel(RankArgs a) {
   if (a.in_evolve && a.state->stopped) return;
   __shared__ unsigned long long tile[1024];
-  const int sub = threadIdx.x & 7;
-  const int c = blockIdx.x * 32 + (threadIdx.x >> 3);
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + (threadIdx.x >> 5);
   unsigned long long kc = 0;
   if (c < a.pop) {
     const double f = a.fit[c];
@@ -361,15 +361,14 @@ __global__ void __launch_bounds__(256) rank_count_kernel(RankArgs a) {
     }
     __syncthreads();
     if (c < a.pop)
-      for (int i = sub; i < n; i += 8) {
+      for (int i = lane; i < n; i += 32) {
         const unsigned long long kj = tile[i];
         pos += (kj < kc) || (kj == kc && t0 + i < c);
       }
   }
-  pos += __shfl_xor_sync(0xffffffffu, pos, 1);
-  pos += __shfl_xor_sync(0xffffffffu, pos, 2);
-  pos += __shfl_xor_sync(0xffffffffu, pos, 4);
-  if (c < a.pop && sub == 0) a.rank[pos] = c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
+  if (c < a.pop && lane == 0) a.rank[pos] = c;
 }
 
 // The state transition of a ranking (one thread), as in reduce_rank_kernel.
@@ -419,7 +418,7 @@ cudaError_t launch_reduce_rank(const Shape& s, const game_config& cfg, const dou
   a.stop_error = cfg.stop_error;
   if (s.pop >= kRankCountMin) {
     if (a.mode == kRankEvaluate) fit_reduce_kernel<<<(s.pop + 255) / 256, 256, 0, st>>>(a);
-    rank_count_kernel<<<(s.pop + 31) / 32, 256, 0, st>>>(a);
+    rank_count_kernel<<<(s.pop + 7) / 8, 256, 0, st>>>(a);
     rank_state_kernel<<<1, 1, 0, st>>>(a);
     return cudaGetLastError();
   }

@@ -215,8 +215,8 @@ __device__ __forceinline__ void breed_pair(const float* __restrict__ G, int kstr
     if (better(f0, i0, bf0, bi0)) { bf0 = f0; bi0 = i0; }
     if (better(f1, i1, bf1, bi1)) { bf1 = f1; bi1 = i1; }
   }
-  const uint32_t wc = philox_word(key, gen, j, kStreamCrossover, 0);
-  const uint32_t wk = philox_word(key, gen, j, kStreamCrossover, 1);
+  uint32_t wc, wk;   // crossover decision and cut: words 0 and 1 of one block
+  philox_word_pair(key, gen, j, kStreamCrossover, 0, &wc, &wk);
   int cut = K;
   if (uniform24(wc) < p_c && K >= 2) cut = 1 + index_draw(wk, K - 1);
   const float* __restrict__ r1 = G + (long long)bi0 * kstride;

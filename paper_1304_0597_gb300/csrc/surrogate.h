@@ -47,6 +47,7 @@ struct Surrogate {
   __nv_bfloat16 *dZ2b = nullptr;   // [Bt x H]
   float *gp1 = nullptr;            // gelu'(Z1) [Bt x H]
   float *dyh2 = nullptr;           // dy * H2 [Bt x H]
+  float *gws = nullptr;            // split-K partial gradient planes [4 x n_params]
   unsigned int* adam_done = nullptr;   // blocks finished in the current Adam launch
   DevState* state = nullptr;       // where a timed-out wait records its status
 

@@ -36,6 +36,36 @@ __global__ void pool_breed_kernel(PoolArgs a) {
 }
 
 // ---- selection (one CTA): the n_sel lowest scores, ties by lower index ----
+// Block-wide exclusive scan of one int per thread (1024 threads); returns the
+// total.  wt holds 32 + 1 ints of shared scratch.
+__device__ __forceinline__ int block_excl_scan(int v, int* wt, int* excl) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wt[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int t = lane < (int)(blockDim.x >> 5) ? wt[lane] : 0;
+    int ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= o) ti += y;
+    }
+    wt[lane] = ti - t;
+    if (lane == 31) wt[32] = ti;
+  }
+  __syncthreads();
+  *excl = wt[warp] + incl - v;
+  const int total = wt[32];
+  __syncthreads();   // wt is reused by the next call
+  return total;
+}
+
 __global__ void __launch_bounds__(1024) select_kernel(const float* __restrict__ score, int n_pool,
                                                       int n_sel, int* __restrict__ sel,
                                                       DevState* st, const int* fallback,
@@ -48,15 +78,14 @@ __global__ void __launch_bounds__(1024) select_kernel(const float* __restrict__ 
     for (int i = tid; i < n_sel; i += nt) sel[i] = i;
     return;
   }
-  __shared__ int scan[1024];
   __shared__ int hist[256];
+  __shared__ int wt[33];
   __shared__ uint32_t sel_prefix;
   __shared__ int sel_left;
   // keys staged in shared memory when the pool fits (dynamic size n_pool words)
   extern __shared__ uint32_t skey[];
   if (keys_in_smem) {
     for (int i = tid; i < n_pool; i += nt) skey[i] = ordered_f32(score[i]);
-    __syncthreads();
   }
   auto key_at = [&](int i) -> uint32_t {
     return keys_in_smem ? skey[i] : ordered_f32(score[i]);
@@ -72,18 +101,20 @@ __global__ void __launch_bounds__(1024) select_kernel(const float* __restrict__ 
     __syncthreads();
     const uint32_t prefix = sel_prefix;
     const uint32_t hmask = shift == 24 ? 0u : (0xFFFFFFFFu << (shift + 8));
-    // children's scores share their leading bytes: lanes that hit the same bin
-    // add once per warp (one atomic per group of equal bins)
-    for (int i0 = 0; i0 < n_pool; i0 += nt) {
-      const int i = i0 + tid;
-      int bin = -1;
-      if (i < n_pool) {
-        const uint32_t k = key_at(i);
-        if ((k & hmask) == (prefix & hmask)) bin = (int)((k >> shift) & 255u);
+    // children's scores share their leading bytes: a thread adds each run of equal
+    // bins with one atomic
+    int prev = -1, run = 0;
+    for (int i = tid; i < n_pool; i += nt) {
+      const uint32_t k = key_at(i);
+      const int bin = (k & hmask) == (prefix & hmask) ? (int)((k >> shift) & 255u) : -1;
+      if (bin != prev) {
+        if (run) atomicAdd(&hist[prev], run);
+        prev = bin;
+        run = 0;
       }
-      const unsigned same = __match_any_sync(0xffffffffu, bin);
-      if (bin >= 0 && (threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&hist[bin], __popc(same));
+      if (bin >= 0) ++run;
     }
+    if (run) atomicAdd(&hist[prev], run);
     __syncthreads();
     if (tid < 32) {
       // lane l owns bins 8l .. 8l+7; find the bin where the running count reaches sel_left
@@ -103,48 +134,46 @@ __global__ void __launch_bounds__(1024) select_kernel(const float* __restrict__ 
       const unsigned hit = __ballot_sync(0xffffffffu, incl >= left);
       const int owner = __ffs(hit) - 1;   // hist sums to >= left, so some lane hits
       if (tid == owner) {
-        int run = incl - tot;
+        int run2 = incl - tot;
         int b = 0;
-        while (b < 7 && run + c[b] < left) run += c[b++];
+        while (b < 7 && run2 + c[b] < left) run2 += c[b++];
         sel_prefix = prefix | ((uint32_t)(tid * 8 + b) << shift);
-        sel_left = left - run;
+        sel_left = left - run2;
       }
     }
     __syncthreads();
   }
   const uint32_t tau = sel_prefix;
-  // compaction in index order: thread t owns the contiguous range [t*chunk, (t+1)*chunk);
-  // pass 0 takes every key < tau, pass 1 the first keys == tau up to n_sel.
-  const int chunk = (n_pool + nt - 1) / nt;
-  const int b0 = min(n_pool, tid * chunk), b1 = min(n_pool, b0 + chunk);
-  __shared__ int start_s;
-  if (tid == 0) start_s = 0;
-  __syncthreads();
+  // Ordered compaction, 4 consecutive keys per thread per chunk of 4 nt: pass 0
+  // takes every key < tau, pass 1 the first keys == tau until n_sel are taken.
+  int start = 0;
   for (int pass = 0; pass < 2; ++pass) {
-    int c = 0;
-    for (int i = b0; i < b1; ++i) {
-      const uint32_t k = key_at(i);
-      c += pass == 0 ? (k < tau) : (k == tau);
-    }
-    scan[tid] = c;
-    __syncthreads();
-    for (int o = 1; o < nt; o <<= 1) {
-      const int v = tid >= o ? scan[tid - o] : 0;
-      __syncthreads();
-      scan[tid] += v;
-      __syncthreads();
-    }
-    int pos = start_s + scan[tid] - c;
-    for (int i = b0; i < b1; ++i) {
-      const uint32_t k = key_at(i);
-      if (pass == 0 ? (k < tau) : (k == tau)) {
-        if (pos < n_sel) sel[pos] = i;
-        ++pos;
+    for (int c0 = 0; c0 < n_pool; c0 += 4 * nt) {
+      const int i0 = c0 + 4 * tid;
+      bool pr[4];
+      int cnt = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + q;
+        bool p = false;
+        if (i < n_pool) {
+          const uint32_t k = key_at(i);
+          p = pass == 0 ? (k < tau) : (k == tau);
+        }
+        pr[q] = p;
+        cnt += p;
       }
+      int excl;
+      const int total = block_excl_scan(cnt, wt, &excl);
+      int pos = start + excl;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (pr[q]) {
+          if (pos < n_sel) sel[pos] = i0 + q;
+          ++pos;
+        }
+      start += total;
     }
-    __syncthreads();
-    if (tid == 0) start_s += scan[nt - 1];
-    __syncthreads();
   }
 }
 
@@ -205,7 +234,7 @@ __global__ void replay_commit_kernel(const DevState* st, int pop, int* ring_meta
 
 // ---- monitor: rank difference of every non-elite row (many CTAs) ----
 // Ranks by counting over keys (value, row) ordered as floats, row as the tie
-// break: rank = number of rows with a smaller key.  Eight threads share a row.
+// break: rank = number of rows with a smaller key.  One warp per row.
 __device__ __forceinline__ unsigned long long spearman_key(const float* pred, const double* fit,
                                                            int e, int i, int which) {
   const float v = which == 0 ? pred[e + i] : (float)fit[e + i];
@@ -220,8 +249,8 @@ __global__ void __launch_bounds__(256) spearman_dsq_kernel(const double* fit, co
   const int n = pop - e;
   if (!(n >= 3 && !(pred[e] != pred[e]))) return;
   __shared__ unsigned long long tp[1024], tf[1024];
-  const int sub = threadIdx.x & 7;
-  const int i = blockIdx.x * 32 + (threadIdx.x >> 3);
+  const int sub = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   const unsigned long long kp = i < n ? spearman_key(pred, fit, e, i, 0) : 0ull;
   const unsigned long long kf = i < n ? spearman_key(pred, fit, e, i, 1) : 0ull;
   int rp = 0, rf = 0;
@@ -234,13 +263,13 @@ __global__ void __launch_bounds__(256) spearman_dsq_kernel(const double* fit, co
     }
     __syncthreads();
     if (i < n)
-      for (int j = sub; j < m; j += 8) {
+      for (int j = sub; j < m; j += 32) {
         rp += tp[j] < kp;
         rf += tf[j] < kf;
       }
   }
 #pragma unroll
-  for (int o = 1; o < 8; o <<= 1) {
+  for (int o = 1; o < 32; o <<= 1) {
     rp += __shfl_xor_sync(0xffffffffu, rp, o);
     rf += __shfl_xor_sync(0xffffffffu, rf, o);
   }
@@ -420,7 +449,7 @@ cudaError_t launch_replay_update(const PopDev& p, const Shape& s, int elitism, c
                                  long long* dsq, cudaStream_t st) {
   const int n = s.pop - elitism;
   if (n > 0)
-    spearman_dsq_kernel<<<(n + 31) / 32, 256, 0, st>>>(fit, pred, state, s.pop, elitism, ring_meta,
+    spearman_dsq_kernel<<<(n + 7) / 8, 256, 0, st>>>(fit, pred, state, s.pop, elitism, ring_meta,
                                                        dsq);
   replay_stats_kernel<<<1, 1024, 0, st>>>(fit, pred, state, s.pop, elitism, ring_meta, norm,
                                           monitor, fallback, fallback_rho, dsq);

@@ -37,6 +37,7 @@ constexpr int kEpiWarpsTc = 16;
 constexpr int kThreadsTc = 64 + 32 * kEpiWarpsTc;   // warp 0 TMA, warp 1 MMA, then the epilogue
 constexpr int kStagesTc = 4;
 constexpr int kTileA = 128 * 128;    // 128 rows x 64 bf16
+constexpr int kGradSplits = 4;       // K slices of the weight-gradient GEMMs
 
 struct MlpParams {
   CUtensorMap a, b;
@@ -58,6 +59,8 @@ struct MlpParams {
   float* g_bias;               // GRAD: bias gradient [M] (column n_main)
   int n_main;
   long long ld_main;
+  int kbps;                    // k-blocks per split (blockIdx.z); kblocks when unsplit
+  long long zstride;           // GRAD: floats between the partial planes of the splits
   DevState* state;
 };
 
@@ -99,6 +102,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * 128, n0 = blockIdx.y * BN;
+  // split K: this CTA reduces k-blocks [kb0, kb1) (never empty)
+  const int kb0 = blockIdx.z * p.kbps;
+  const int kb1 = min(p.kblocks, kb0 + p.kbps);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStagesTc; ++s) {
@@ -127,7 +133,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
     // ---- TMA producer ----
     int stage = 0;
     uint32_t phase = 0;
-    for (int kb = 0; kb < p.kblocks; ++kb) {
+    for (int kb = kb0; kb < kb1; ++kb) {
       if (!warp_wait(empty + stage, phase ^ 1u, err, p.state, lane)) break;
       if (lane == 0) {
         uint8_t* sa = smem + stage * kStage;
@@ -156,7 +162,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
     uint32_t phase = 0;
     uint32_t accum = 0;
     bool ok = true;
-    for (int kb = 0; kb < p.kblocks; ++kb) {
+    for (int kb = kb0; kb < kb1; ++kb) {
       if (!warp_wait(full + stage, phase, err, p.state, lane)) {
         ok = false;
         break;
@@ -297,6 +303,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
       // weight-gradient rows: each warp turns its 32 x 32 block around in shared
       // memory (the idle ring) so that the global stores run along a row
       float* tile = reinterpret_cast<float*>(smem) + (warp - 2) * (32 * 33);
+      float* gm = p.g_main + blockIdx.z * p.zstride;
+      float* gb = p.g_bias + blockIdx.z * p.zstride;
       if (ok) {
 #pragma unroll 1
         for (int ch = 0; ch < kCols / 32; ++ch) {
@@ -310,9 +318,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
             if (rr < p.M) {
               const float w = tile[i * 33 + lane];
               if (n < p.n_main)
-                p.g_main[(long long)rr * p.ld_main + n] = w;
+                gm[(long long)rr * p.ld_main + n] = w;
               else if (n == p.n_main)
-                p.g_bias[rr] = w;
+                gb[rr] = w;
             }
           }
           __syncwarp();
@@ -494,10 +502,22 @@ cudaError_t bf16_map(CUtensorMap* m, const void* base, long long rows, long long
 }
 
 template <int BN, int EPI>
-cudaError_t launch_mlp(const MlpParams& p, int grid_m, int grid_n, cudaStream_t st) {
-  void* args[] = {const_cast<MlpParams*>(&p)};
-  return cudaLaunchKernel(reinterpret_cast<void*>(&mlp_tc_kernel<BN, EPI>), dim3(grid_m, grid_n),
-                          dim3(kThreadsTc), args, smem_bytes<BN>(), st);
+cudaError_t launch_mlp(MlpParams& p, int grid_m, int grid_n, cudaStream_t st, int splits = 1) {
+  if (splits <= 1) p.kbps = p.kblocks;
+  void* args[] = {&p};
+  return cudaLaunchKernel(reinterpret_cast<void*>(&mlp_tc_kernel<BN, EPI>),
+                          dim3(grid_m, grid_n, splits), dim3(kThreadsTc), args, smem_bytes<BN>(),
+                          st);
+}
+
+// g[i] = sum over the splits z of ws[z * n + i], in order (deterministic).
+__global__ void grad_sum_kernel(const float* __restrict__ ws, int splits, long long n,
+                                float* __restrict__ g) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = ws[i];
+  for (int z = 1; z < splits; ++z) s += ws[z * n + i];
+  g[i] = s;
 }
 
 int ceil_div(long long a, int b) { return (int)((a + b - 1) / b); }
@@ -525,7 +545,7 @@ size_t Surrogate::tc_bytes(int max_rows_, int batch) const {
   const size_t b16 = sizeof(__nv_bfloat16);
   return b16 * ((size_t)H * dp + 2 * (size_t)H * H + (size_t)max_rows_ * (dp + H) +
                 ((size_t)D + 1 + (size_t)H + 1 + 2 * (size_t)H) * ldt_ + (size_t)batch * H) +
-         sizeof(float) * 2 * (size_t)batch * H + 16;
+         sizeof(float) * (2 * (size_t)batch * H + (size_t)kGradSplits * n_params()) + 16;
 }
 
 void Surrogate::tc_carve(void* base, int batch) {
@@ -559,6 +579,8 @@ void Surrogate::tc_carve(void* base, int batch) {
   f += (size_t)Bt * H;
   dyh2 = f;
   f += (size_t)Bt * H;
+  gws = f;
+  f += (size_t)kGradSplits * n_params();
   adam_done = reinterpret_cast<unsigned int*>(f);
   tc = true;
 }
@@ -650,8 +672,6 @@ cudaError_t Surrogate::tc_adam(float lr, cudaStream_t st) {
 }
 
 cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st) {
-  float *gW1, *gb1, *gW2, *gb2, *gw3, *gb3;
-  views(g, &gW1, &gb1, &gW2, &gb2, &gw3, &gb3);
   cudaError_t e;
   MlpParams a = {};
   a.state = state;
@@ -665,6 +685,15 @@ cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st) {
   a.out_t = dZ1Tb;
   a.gp = gp1;
   if ((e = launch_mlp<128, kEpiB1>(a, ceil_div(B, 128), H / 128, st)) != cudaSuccess) return e;
+  // The weight gradients reduce over the batch (K = B): split K into up to
+  // kGradSplits slices, each writing a partial plane laid out like the flat
+  // parameters [W1 | b1 | W2 | b2] (workspace gws), then add the planes in order.
+  const long long n12 = (long long)H * D + H + (long long)H * H + H;
+  const int kblocks = ceil_div(B, 64);
+  const int kbps = ceil_div(kblocks, kGradSplits);
+  const int splits = ceil_div(kblocks, kbps);
+  float *wW1, *wb1, *wW2, *wb2, *ww3, *wb3;
+  views(gws, &wW1, &wb1, &wW2, &wb2, &ww3, &wb3);
   // [gW2 | gb2] = dZ2^T [H1 | 1] : A = dZ2^T [H x B], B operand = [H1^T ; 1] [(H + 1) x B]
   MlpParams w = {};
   w.state = state;
@@ -672,23 +701,30 @@ cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st) {
   if ((e = bf16_map(&w.b, H1Tb, H + 1, B, ldt, 128)) != cudaSuccess) return e;
   w.M = H;
   w.N = H + 1;
-  w.kblocks = ceil_div(B, 64);
-  w.g_main = gW2;
-  w.g_bias = gb2;
+  w.kblocks = kblocks;
+  w.kbps = kbps;
+  w.zstride = n12;
+  w.g_main = wW2;
+  w.g_bias = wb2;
   w.n_main = H;
   w.ld_main = H;
-  if ((e = launch_mlp<128, kEpiGrad>(w, ceil_div(H, 128), ceil_div(H + 1, 128), st)) != cudaSuccess)
+  if ((e = launch_mlp<128, kEpiGrad>(w, ceil_div(H, 128), ceil_div(H + 1, 128), st, splits)) !=
+      cudaSuccess)
     return e;
   // [gW1 | gb1] = dZ1^T [X | 1] : A = dZ1^T [H x B], B operand = [X^T ; 1] [(D + 1) x B]
   MlpParams v = w;
   if ((e = bf16_map(&v.a, dZ1Tb, H, B, ldt, 128)) != cudaSuccess) return e;
   if ((e = bf16_map(&v.b, XTb, D + 1, B, ldt, 128)) != cudaSuccess) return e;
   v.N = D + 1;
-  v.g_main = gW1;
-  v.g_bias = gb1;
+  v.g_main = wW1;
+  v.g_bias = wb1;
   v.n_main = D;
   v.ld_main = D;
-  return launch_mlp<128, kEpiGrad>(v, ceil_div(H, 128), ceil_div(D + 1, 128), st);
+  if ((e = launch_mlp<128, kEpiGrad>(v, ceil_div(H, 128), ceil_div(D + 1, 128), st, splits)) !=
+      cudaSuccess)
+    return e;
+  grad_sum_kernel<<<ceil_div(n12, 256), 256, 0, st>>>(gws, splits, n12, g);
+  return cudaGetLastError();
 }
 
 }  // namespace game

@@ -250,7 +250,12 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     for (int it = 0; it < my_tiles; ++it) {
       const int buf = it & 1;
       const uint32_t ap = (uint32_t)((it >> 1) & 1);
-      if (!warp_wait(acc_full + buf, ap, err, p.state, lane)) break;
+      // FP32 (three products per term) is MMA-bound: the accumulator wait sleeps
+      // between polls so that the issue slots go to the MMA warp on the same
+      // sub-partition.  The low-precision forms are epilogue-bound and poll.
+      const bool got = PREC == GAME_FP32 ? warp_wait_backoff(acc_full + buf, ap, err, p.state, lane)
+                                         : warp_wait(acc_full + buf, ap, err, p.state, lane);
+      if (!got) break;
       fence_after();
       const long long tile = member + (long long)it * p.cps;
       constexpr int kCols = BN / kColGroups;

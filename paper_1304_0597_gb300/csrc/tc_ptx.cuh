@@ -66,6 +66,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   }
 }
 
+// Bounded wait with a growing sleep between polls (32 ns up to 512 ns), for
+// waiters whose reaction time does not matter: it leaves the issue slots of the
+// sub-partition to the warps that do the work.
+__device__ __forceinline__ bool mbar_wait_backoff(uint64_t* bar, uint32_t parity, volatile int* err,
+                                                  DevState* st) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  unsigned ns = 32;
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*err) return false;
+    if (globaltimer() - t0 > kWaitNs) {
+      *err = 1;
+      atomicExch(&st->status, (int)GAME_ERR_TIMEOUT);
+      return false;
+    }
+    __nanosleep(ns);
+    if (ns < 512) ns <<= 1;
+  }
+}
+
+__device__ __forceinline__ bool warp_wait_backoff(uint64_t* bar, uint32_t parity, volatile int* err,
+                                                  DevState* st, int lane) {
+  int ok = 0;
+  if (lane == 0) ok = mbar_wait_backoff(bar, parity, err, st) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
 // Warp-uniform bounded wait: lane 0 polls, the outcome is broadcast.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* err,
                                           DevState* st, int lane) {

@@ -97,6 +97,7 @@ typedef struct game_config {
   int32_t tile_n;         /* tcgen05 tile: patterns per tile, 128 | 256 (0 = tuned / auto)  */
   int32_t tile_stages;    /* tcgen05 tile: depth of the pattern-tile ring (0 = auto)        */
   int32_t tile_cluster;   /* tcgen05 tile: CTAs sharing a pattern tile by multicast, 1|2|4|8 (0 = auto) */
+  int32_t tile_slices;    /* tcgen05 tile: 128-chromosome slices per CTA, 1 | 2 (2 needs tile_n 128; 0 = auto) */
   int32_t device;         /* CUDA device ordinal                                            */
   void* stream;           /* cudaStream_t, or NULL for the legacy default stream           */
 } game_config;
@@ -216,6 +217,7 @@ typedef struct game_tile {
   int32_t stages;     /* pattern-tile ring depth                              */
   int32_t cluster;    /* CTAs sharing each pattern tile (TMA multicast)       */
   int32_t prefetch;   /* 1: L2 prefetch of each CTA's next pattern tile       */
+  int32_t slices;     /* 128-chromosome slices per CTA fed by each pattern tile */
   double ms;          /* median fitness time of this shape, milliseconds      */
 } game_tile;
 

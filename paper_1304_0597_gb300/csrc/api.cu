@@ -207,6 +207,10 @@ static game_status validate(game_ctx* c, const game_config* cfg) {
     return fail(c, GAME_ERR_INVALID_ARG, "bad precision");
   if (cfg->engine < GAME_ENGINE_AUTO || cfg->engine > GAME_ENGINE_SIMT)
     return fail(c, GAME_ERR_INVALID_ARG, "bad engine");
+  if ((cfg->tile_n != 0 && cfg->tile_n != 128 && cfg->tile_n != 256) || cfg->tile_stages < 0 ||
+      cfg->tile_cluster < 0 || cfg->tile_slices < 0 || cfg->tile_slices > 2 ||
+      (cfg->tile_slices == 2 && cfg->tile_n == 256))
+    return fail(c, GAME_ERR_INVALID_ARG, "bad tile request");
   if (cfg->surrogate_pool < 0) return fail(c, GAME_ERR_INVALID_ARG, "bad surrogate_pool");
   if (cfg->surrogate_steps < 0 || cfg->surrogate_batch < 0 || cfg->surrogate_batch > 65536 ||
       !(cfg->surrogate_lr >= 0.0f) || cfg->surrogate_select < 0 || cfg->surrogate_select > 1)
@@ -293,7 +297,8 @@ __global__ void check_data_kernel(const float* X, long long nx, const float* t, 
 }
 
 // ---- tile cache of the autotuner: one line per shape bucket -------------------
-//   <kp> <pop_pad> <precision> <log2 n_train> <n> <stages> <cluster> <prefetch> <ms>
+//   <kp> <pop_pad> <precision> <log2 n_train> <n> <stages> <cluster> <prefetch> <slices> <ms>
+// (lines of any other form are skipped)
 static std::string tune_cache_path() {
   const char* e = getenv("GAME_TUNE_CACHE");
   if (e && *e) return e;
@@ -306,12 +311,15 @@ static int ntrain_bucket(long long n) { return (int)floor(log2((double)(n > 0 ? 
 static bool tune_cache_lookup(const Shape& s, TileReq* out) {
   FILE* f = fopen(tune_cache_path().c_str(), "r");
   if (!f) return false;
-  int kp, pp, pr, nb, n, st, cl, pf;
+  int kp, pp, pr, nb, n, st, cl, pf, sp;
   double ms;
   bool found = false;
-  while (fscanf(f, "%d %d %d %d %d %d %d %d %lf", &kp, &pp, &pr, &nb, &n, &st, &cl, &pf, &ms) == 9)
-    if (kp == s.kp && pp == s.pop_pad && pr == s.precision && nb == ntrain_bucket(s.n_train)) {
-      *out = TileReq{n, st, cl, pf};   // the last record for a bucket wins
+  char line[256];
+  while (fgets(line, sizeof(line), f))
+    if (sscanf(line, "%d %d %d %d %d %d %d %d %d %lf", &kp, &pp, &pr, &nb, &n, &st, &cl, &pf, &sp,
+               &ms) == 10 &&
+        kp == s.kp && pp == s.pop_pad && pr == s.precision && nb == ntrain_bucket(s.n_train)) {
+      *out = TileReq{n, st, cl, pf, sp};   // the last record for a bucket wins
       found = true;
     }
   fclose(f);
@@ -324,8 +332,8 @@ static void tune_cache_store(const Shape& s, const game_tile& t) {
   if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
   FILE* f = fopen(path.c_str(), "a");
   if (!f) return;
-  fprintf(f, "%d %d %d %d %d %d %d %d %.6f\n", s.kp, s.pop_pad, s.precision,
-          ntrain_bucket(s.n_train), t.n, t.stages, t.cluster, t.prefetch, t.ms);
+  fprintf(f, "%d %d %d %d %d %d %d %d %d %.6f\n", s.kp, s.pop_pad, s.precision,
+          ntrain_bucket(s.n_train), t.n, t.stages, t.cluster, t.prefetch, t.slices, t.ms);
   fclose(f);
 }
 
@@ -336,8 +344,8 @@ static game_status choose_engine(game_ctx* c, const Shape& s, const ExpDev& e, c
   if (want == GAME_ENGINE_TCGEN05) {
     if (!tc_supported(s))
       return fail(c, GAME_ERR_UNSUPPORTED, "tcgen05 engine does not support this shape");
-    TileReq req{c->cfg.tile_n, c->cfg.tile_stages, c->cfg.tile_cluster, -1};
-    if (!req.n && !req.stages && !req.cluster) tune_cache_lookup(s, &req);
+    TileReq req{c->cfg.tile_n, c->cfg.tile_stages, c->cfg.tile_cluster, -1, c->cfg.tile_slices};
+    if (!req.n && !req.stages && !req.cluster && !req.sp) tune_cache_lookup(s, &req);
     cudaError_t err = tc_plan(s, e, p, c->n_sm, plan, req);
     if (err != cudaSuccess) {
       cudaGetLastError();
@@ -1045,7 +1053,7 @@ static game_status tune_shape(game_ctx* c, const Shape& s, const ExpDev& e, cons
   cudaEvent_t e0, e1;
   CUDA_OK(c, cudaEventCreate(&e0));
   CUDA_OK(c, cudaEventCreate(&e1));
-  *bt = game_tile{0, 0, 0, 0, 1e30};
+  *bt = game_tile{0, 0, 0, 0, 0, 1e30};
   for (const TileReq& rq : cands) {
     TcPlan plan{};
     if (tc_plan(s, e, pd, c->n_sm, &plan, rq) != cudaSuccess) {
@@ -1068,7 +1076,8 @@ static game_status tune_shape(game_ctx* c, const Shape& s, const ExpDev& e, cons
       return fail(c, GAME_ERR_CUDA, "autotune launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     }
     std::sort(t.begin(), t.end());
-    const game_tile gt{plan.bn, plan.stages, plan.cluster, plan.prefetch, t[t.size() / 2]};
+    const game_tile gt{plan.bn, plan.stages, plan.cluster, plan.prefetch, plan.sp,
+                       t[t.size() / 2]};
     if (candidates && *n_done < cap) candidates[*n_done] = gt;
     ++*n_done;
     if (gt.ms < bt->ms) {

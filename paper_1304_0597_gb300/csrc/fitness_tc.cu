@@ -9,8 +9,9 @@
 // Layout.  D[c, k] = sum_g A[c, g] B[k, g] with A = genes of a 128-chromosome
 // slice (M = 128, TMEM lane = chromosome) and B = a tile of BN expansion rows
 // (N = BN, TMEM column = pattern); both K-major, 128-byte swizzled.  A CTA owns
-// one slice for its whole life: the slice's gene planes are loaded once and stay
-// in shared memory, while pattern tiles stream through a ring of B stages.  The
+// SP slices (1, or 2 with 128-pattern tiles) for its whole life: their gene
+// planes are loaded once and stay in shared memory, while pattern tiles stream
+// through a ring of B stages and each tile feeds the MMAs of every slice.  The
 // per-chromosome error sum is then a per-thread running sum over TMEM columns,
 // with no cross-lane reduction.
 //
@@ -52,7 +53,7 @@ struct TcParams {
   double* partial;
   DevState* state;
   long long m;            // training rows
-  int n_slices, cps, n_tiles, kblocks, kp, stages, pop_pad;
+  int n_groups, cps, n_tiles, kblocks, kp, stages, pop_pad;   // group = SP slices
   int n_bplanes;          // FP32: 2 (P_hi, P_lo); else 1
   int act, err, in_evolve;
   float R;
@@ -60,8 +61,9 @@ struct TcParams {
   int prefetch;           // L2 prefetch of the next tile's boxes
 };
 
-template <int BN, int PREC, bool FAST, int NA>
+template <int BN, int PREC, bool FAST, int NA, int SP>
 __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_constant__ TcParams p) {
+  static_assert(SP == 1 || (SP == 2 && BN == 128), "two slices per CTA use 128-pattern tiles");
   if (p.in_evolve && p.state->stopped) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   constexpr uint32_t kIdesc = make_idesc(128, BN, kFmt);
   const int S = p.stages;
   uint8_t* sA = smem;
-  uint8_t* sB = sA + NA * p.kblocks * kTileA;
+  uint8_t* sB = sA + SP * NA * p.kblocks * kTileA;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + S * kTileB);
   uint64_t* a_full = bars;
   uint64_t* b_full = bars + 1;
@@ -84,13 +86,13 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* last_par = reinterpret_cast<int*>(tmem_slot + 2);          // [S]
-  double* red = reinterpret_cast<double*>(sB);   // [kColGroups][128], reused once the ring is idle
+  double* red = reinterpret_cast<double*>(sB);   // [SP][kColGroups][128], once the ring is idle
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int slice = blockIdx.x % p.n_slices;
-  const int member = blockIdx.x / p.n_slices;
+  const int group = blockIdx.x % p.n_groups;      // slices group*SP .. group*SP+SP-1
+  const int member = blockIdx.x / p.n_groups;
   const int my_tiles = member < p.n_tiles ? (p.n_tiles - 1 - member) / p.cps + 1 : 0;
-  constexpr uint32_t kTmemCols = 2 * BN;
+  constexpr uint32_t kTmemCols = 2 * SP * BN;      // [buffer][slice] accumulators of BN columns
 
   if (threadIdx.x == 0) {
     mbar_init(a_full, 1);
@@ -124,17 +126,18 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   const uint16_t cmask = (uint16_t)((1u << p.cl) - 1u);
   const int sub_rows = BN / p.cl;                     // rows of the B tile this CTA fetches
   const int a_steps_total = p.kp / kKStep;
-  F2Sum acc;   // epilogue threads: this chromosome's error sum over its columns
+  F2Sum acc[SP];   // epilogue threads: each slice's chromosome error sum over its columns
 
   if (warp == 0) {
     // ---- TMA producer: the whole warp follows one control flow, lane 0 issues ----
     if (lane == 0) {
-      const uint32_t a_bytes = (uint32_t)NA * p.kblocks * kTileA;
+      const uint32_t a_bytes = (uint32_t)SP * NA * p.kblocks * kTileA;
       mbar_expect_tx(a_full, a_bytes);
-      for (int pl = 0; pl < NA; ++pl)
-        for (int kb = 0; kb < p.kblocks; ++kb)
-          tma_load_2d(sA + (pl * p.kblocks + kb) * kTileA, &p.a[pl], kb * kKB, slice * 128,
-                      a_full);
+      for (int sp = 0; sp < SP; ++sp)
+        for (int pl = 0; pl < NA; ++pl)
+          for (int kb = 0; kb < p.kblocks; ++kb)
+            tma_load_2d(sA + ((sp * NA + pl) * p.kblocks + kb) * kTileA, &p.a[pl], kb * kKB,
+                        (group * SP + sp) * 128, a_full);
     }
     int stage = 0;
     uint32_t phase = 0;
@@ -189,8 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
         const uint32_t ap = (uint32_t)((it >> 1) & 1);
         if (!warp_wait(acc_empty + buf, ap ^ 1u, err, p.state, lane)) break;
         fence_after();
-        const uint32_t d = tmem + (uint32_t)(buf * BN);
-        uint32_t accum = 0;
+        uint32_t accum = 0;   // the first k-step of a tile starts every slice's accumulator
         bool ok = true;
         for (int kb = 0; kb < p.kblocks && ok; ++kb) {
           const int steps = min(kKB / kKStep, a_steps_total - kb * (kKB / kKStep));
@@ -203,17 +205,23 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
             const uint64_t bdesc = sw128_desc(b_addr + (uint32_t)(stage * kTileB));
             // FP32 split: B = P_hi meets A = G_hi and G_lo; B = P_lo meets G_hi.
             const int n_ap = (PREC == GAME_FP32 && bp == 1) ? 1 : NA;
-            for (int ai = 0; ai < n_ap; ++ai) {
-              const uint64_t adesc =
-                  sw128_desc(a_addr + (uint32_t)((ai * p.kblocks + kb) * kTileA));
 #pragma unroll
-              for (int k = 0; k < kKB / kKStep; ++k) {
-                if (k < steps) {
-                  // +32 bytes along K inside the 128-byte swizzle row = +2 in the address field
-                  if (lane == 0) mma<PREC>(d, adesc + 2 * k, bdesc + 2 * k, kIdesc, accum);
-                  accum = 1;
+            for (int sp = 0; sp < SP; ++sp) {
+              const uint32_t d = tmem + (uint32_t)((buf * SP + sp) * BN);
+              uint32_t acc_sp = accum;
+              for (int ai = 0; ai < n_ap; ++ai) {
+                const uint64_t adesc =
+                    sw128_desc(a_addr + (uint32_t)(((sp * NA + ai) * p.kblocks + kb) * kTileA));
+#pragma unroll
+                for (int k = 0; k < kKB / kKStep; ++k) {
+                  if (k < steps) {
+                    // +32 bytes along K inside the 128-byte swizzle row = +2 in the address field
+                    if (lane == 0) mma<PREC>(d, adesc + 2 * k, bdesc + 2 * k, kIdesc, acc_sp);
+                    acc_sp = 1;
+                  }
                 }
               }
+              if (sp == SP - 1) accum = acc_sp;
             }
             if (lane == 0) {
               if (p.cl > 1)
@@ -244,9 +252,13 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     const int q = warp & 3;
     const int h = (warp - 2) >> 2;                    // column group 0..kColGroups-1
     const float* pk = FAST ? p.tcoef : p.t;
-    const int c = slice * 128 + q * 32 + lane;
-    const float bias = p.bias[c];
-    const float rs = p.rscale[c];
+    float bias[SP], rs[SP];
+#pragma unroll
+    for (int sp = 0; sp < SP; ++sp) {
+      const int c = (group * SP + sp) * 128 + q * 32 + lane;
+      bias[sp] = p.bias[c];
+      rs[sp] = p.rscale[c];
+    }
     for (int it = 0; it < my_tiles; ++it) {
       const int buf = it & 1;
       const uint32_t ap = (uint32_t)((it >> 1) & 1);
@@ -259,12 +271,16 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
       fence_after();
       const long long tile = member + (long long)it * p.cps;
       constexpr int kCols = BN / kColGroups;
-      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN + h * kCols);
 #pragma unroll
-      for (int ch = 0; ch < kCols / 32; ++ch) {
-        const long long p0 = tile * BN + h * kCols + ch * 32;
-        acc.add(chunk_error<FAST, true>(tbase + ch * 32, pk, p0, p.m, rs, bias, p.act, p.err,
-                                        p.R));
+      for (int sp = 0; sp < SP; ++sp) {
+        const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) +
+                               (uint32_t)((buf * SP + sp) * BN + h * kCols);
+#pragma unroll
+        for (int ch = 0; ch < kCols / 32; ++ch) {
+          const long long p0 = tile * BN + h * kCols + ch * 32;
+          acc[sp].add(chunk_error<FAST, true>(tbase + ch * 32, pk, p0, p.m, rs[sp], bias[sp],
+                                              p.act, p.err, p.R));
+        }
       }
       fence_before();
       __syncwarp();
@@ -279,13 +295,18 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTmemCols));
-  if (warp >= 2) red[((warp - 2) >> 2) * 128 + (warp & 3) * 32 + lane] = acc.value();
+  if (warp >= 2) {
+#pragma unroll
+    for (int sp = 0; sp < SP; ++sp)
+      red[(sp * kColGroups + ((warp - 2) >> 2)) * 128 + (warp & 3) * 32 + lane] = acc[sp].value();
+  }
   __syncthreads();
-  if (threadIdx.x < 128) {
+  if (threadIdx.x < SP * 128) {
+    const int sp = threadIdx.x >> 7, r = threadIdx.x & 127;
     double tot = 0.0;
 #pragma unroll
-    for (int g = 0; g < kColGroups; ++g) tot += red[g * 128 + threadIdx.x];
-    p.partial[(long long)member * p.pop_pad + slice * 128 + threadIdx.x] = tot;
+    for (int g = 0; g < kColGroups; ++g) tot += red[(sp * kColGroups + g) * 128 + r];
+    p.partial[(long long)member * p.pop_pad + (group * SP + sp) * 128 + r] = tot;
   }
   // No CTA leaves while a peer may still signal its barriers.
   if (p.cl > 1) cluster_sync_all();
@@ -333,25 +354,31 @@ int kblocks_of(const Shape& s) {
   return (s.kp + kkb - 1) / kkb;
 }
 
-template <int BN, int PREC, bool FAST, int NA>
+template <int BN, int PREC, bool FAST, int NA, int SP>
 void* kernel_ptr() {
-  return reinterpret_cast<void*>(&fitness_tc_kernel<BN, PREC, FAST, NA>);
+  return reinterpret_cast<void*>(&fitness_tc_kernel<BN, PREC, FAST, NA, SP>);
 }
 
-void* pick_kernel(int bn, int prec, bool fast, int na = 2) {
-#define GAME_TC_PICK(BNV, PV, NAV)                                                          \
-  if (bn == BNV && prec == PV && na == NAV)                                                  \
-    return fast ? kernel_ptr<BNV, PV, true, NAV>() : kernel_ptr<BNV, PV, false, NAV>();
-  GAME_TC_PICK(256, GAME_FP32, 2)
-  GAME_TC_PICK(128, GAME_FP32, 2)
-  GAME_TC_PICK(256, GAME_BF16, 2)
-  GAME_TC_PICK(128, GAME_BF16, 2)
-  GAME_TC_PICK(256, GAME_FP8, 2)
-  GAME_TC_PICK(128, GAME_FP8, 2)
-  GAME_TC_PICK(256, GAME_BF16, 1)
-  GAME_TC_PICK(128, GAME_BF16, 1)
-  GAME_TC_PICK(256, GAME_FP8, 1)
-  GAME_TC_PICK(128, GAME_FP8, 1)
+void* pick_kernel(int bn, int prec, bool fast, int na, int sp) {
+#define GAME_TC_PICK(BNV, PV, NAV, SPV)                                                     \
+  if (bn == BNV && prec == PV && na == NAV && sp == SPV)                                     \
+    return fast ? kernel_ptr<BNV, PV, true, NAV, SPV>() : kernel_ptr<BNV, PV, false, NAV, SPV>();
+  GAME_TC_PICK(256, GAME_FP32, 2, 1)
+  GAME_TC_PICK(128, GAME_FP32, 2, 1)
+  GAME_TC_PICK(256, GAME_BF16, 2, 1)
+  GAME_TC_PICK(128, GAME_BF16, 2, 1)
+  GAME_TC_PICK(256, GAME_FP8, 2, 1)
+  GAME_TC_PICK(128, GAME_FP8, 2, 1)
+  GAME_TC_PICK(256, GAME_BF16, 1, 1)
+  GAME_TC_PICK(128, GAME_BF16, 1, 1)
+  GAME_TC_PICK(256, GAME_FP8, 1, 1)
+  GAME_TC_PICK(128, GAME_FP8, 1, 1)
+  // two slices per CTA (128-pattern tiles)
+  GAME_TC_PICK(128, GAME_FP32, 2, 2)
+  GAME_TC_PICK(128, GAME_BF16, 2, 2)
+  GAME_TC_PICK(128, GAME_FP8, 2, 2)
+  GAME_TC_PICK(128, GAME_BF16, 1, 2)
+  GAME_TC_PICK(128, GAME_FP8, 1, 2)
 #undef GAME_TC_PICK
   return nullptr;
 }
@@ -397,13 +424,14 @@ cudaError_t tc_init_attributes() {
   for (int bn : {128, 256})
     for (int prec : {GAME_FP32, GAME_BF16, GAME_FP8})
       for (bool fast : {false, true})
-        for (int na : {1, 2}) {
-          void* k = pick_kernel(bn, prec, fast, na);
-          if (!k) continue;
-          cudaError_t e =
-              cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-          if (e != cudaSuccess) return e;
-        }
+        for (int na : {1, 2})
+          for (int sp : {1, 2}) {
+            void* k = pick_kernel(bn, prec, fast, na, sp);
+            if (!k) continue;
+            cudaError_t e =
+                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+            if (e != cudaSuccess) return e;
+          }
   return cudaSuccess;
 }
 
@@ -414,48 +442,55 @@ bool tc_supported(const Shape& s) {
   return a_bytes + 2 * 128 * 128 + kSmemMisc <= kSmemMax;
 }
 
-static int max_stages(const Shape& s, int bn) {
-  const int room = kSmemMax - kSmemMisc - s.gene_planes * kblocks_of(s) * kTileA;
+static int max_stages(const Shape& s, int bn, int sp) {
+  const int room = kSmemMax - kSmemMisc - sp * s.gene_planes * kblocks_of(s) * kTileA;
   int st = room / (bn * 128);
   return st > 8 ? 8 : st;
 }
 
 void tc_candidates(const Shape& s, std::vector<TileReq>* out) {
   const int n_slices = s.pop_pad / 128;
-  for (int bn : {256, 128}) {
-    const int ms = max_stages(s, bn);
-    for (int st = ms; st >= 2 && st >= ms - 1; --st)
-      for (int cl : {1, 2, 4, 8})
-        if (n_slices % cl == 0 && bn / cl >= 16)
-          for (int pf : {1, 0}) out->push_back(TileReq{bn, st, cl, pf});
-  }
+  for (int sp : {1, 2})
+    for (int bn : {256, 128}) {
+      if (sp == 2 && (bn != 128 || n_slices % 2 != 0)) continue;
+      const int n_groups = n_slices / sp;
+      const int ms = max_stages(s, bn, sp);
+      for (int st = ms; st >= 2 && st >= ms - 1; --st)
+        for (int cl : {1, 2, 4, 8})
+          if (n_groups % cl == 0 && bn / cl >= 16)
+            for (int pf : {1, 0}) out->push_back(TileReq{bn, st, cl, pf, sp});
+    }
 }
 
 cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, TcPlan* plan,
                     TileReq req) {
   TcPlan& t = *plan;
   t.kblocks = kblocks_of(s);
-  const int a_bytes = s.gene_planes * t.kblocks * kTileA;
   const int n_bplanes = s.precision == GAME_FP32 ? 2 : 1;
   t.n_slices = s.pop_pad / 128;
+  t.sp = req.sp ? req.sp : 1;
+  if (t.sp != 1 && t.sp != 2) return cudaErrorInvalidValue;
+  if (t.sp == 2 && (t.n_slices % 2 != 0 || (req.n && req.n != 128))) return cudaErrorInvalidValue;
+  t.n_groups = t.n_slices / t.sp;
+  const int a_bytes = t.sp * s.gene_planes * t.kblocks * kTileA;
   // Default shape: 256-pattern tiles when two stages fit, else 128; multicast
   // across the largest power-of-two group of slices up to 4.
   // (128-pattern tiles cost as much per MMA instruction as 256-pattern ones)
-  t.bn = req.n ? req.n : (max_stages(s, 256) >= 2 ? 256 : 128);
+  t.bn = t.sp == 2 ? 128 : (req.n ? req.n : (max_stages(s, 256, 1) >= 2 ? 256 : 128));
   if (t.bn != 128 && t.bn != 256) return cudaErrorInvalidValue;
-  const int ms = max_stages(s, t.bn);
+  const int ms = max_stages(s, t.bn, t.sp);
   t.stages = req.stages ? req.stages : ms;
   if (t.stages < 2 || t.stages > ms) return cudaErrorNotSupported;
   int cl = req.cluster;
   if (!cl) {
     cl = 1;
     for (int c : {4, 2})
-      if (t.n_slices % c == 0) {
+      if (t.n_groups % c == 0) {
         cl = c;
         break;
       }
   }
-  if (t.n_slices % cl != 0 || t.bn / cl < 16 || cl > 8) return cudaErrorInvalidValue;
+  if (t.n_groups % cl != 0 || t.bn / cl < 16 || cl > 8) return cudaErrorInvalidValue;
   t.cluster = cl;
   t.prefetch = req.prefetch == 0 ? 0 : 1;
   t.n_tiles = (int)((s.n_train + t.bn - 1) / t.bn);
@@ -475,18 +510,20 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     int n_clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&n_clusters, pick_kernel(t.bn, s.precision, true, s.gene_planes), &cfg) ==
+    if (cudaOccupancyMaxActiveClusters(&n_clusters,
+                                       pick_kernel(t.bn, s.precision, true, s.gene_planes, t.sp),
+                                       &cfg) ==
             cudaSuccess &&
         n_clusters > 0)
       resident = n_clusters * cl;
     else
       cudaGetLastError();
   }
-  int cps = resident / t.n_slices;
+  int cps = resident / t.n_groups;
   if (cps < 1) cps = 1;
   if (cps > t.n_tiles) cps = t.n_tiles;
   t.ctas_per_slice = cps;
-  t.grid = t.n_slices * cps;
+  t.grid = t.n_groups * cps;
   t.n_part = cps;
   cudaError_t err;
   if ((err = make_map(&t.a_map[0], p.ghi, s.precision, s.pop_pad, s.kp, 128)) != cudaSuccess) return err;
@@ -515,7 +552,7 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
   p.partial = partial;
   p.state = const_cast<DevState*>(state);
   p.m = s.n_train;
-  p.n_slices = t.n_slices;
+  p.n_groups = t.n_groups;
   p.cps = t.ctas_per_slice;
   p.n_tiles = t.n_tiles;
   p.kblocks = t.kblocks;
@@ -531,7 +568,7 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
   p.prefetch = t.prefetch;
   const bool fast = f.pm1_targets && f.activation == GAME_TANH &&
                     (f.error == GAME_RMSE || f.error == GAME_MSE);
-  void* k = pick_kernel(t.bn, s.precision, fast, s.gene_planes);
+  void* k = pick_kernel(t.bn, s.precision, fast, s.gene_planes, t.sp);
   if (!k) return cudaErrorNotSupported;
   void* args[] = {&p};
   if (t.cluster <= 1) return cudaLaunchKernel(k, dim3(t.grid), dim3(kThreads), args, t.smem, st);

@@ -13,14 +13,16 @@ struct TcPlan {
   CUtensorMap a_map[2];   // gene planes (hi, lo): A operand, chromosomes x genes
   CUtensorMap b_map[2];   // expansion planes (FP32: hi, lo; BF16/FP8: one): B operand
   int n_slices;           // 128-chromosome slices of the population
-  int ctas_per_slice;     // CTAs that share one slice (each takes every n-th pattern tile)
+  int sp = 1;             // slices per CTA (2: both fed by every 128-pattern tile)
+  int n_groups;           // n_slices / sp
+  int ctas_per_slice;     // CTAs that share one group (each takes every n-th pattern tile)
   int n_tiles;            // pattern tiles of BN rows over the training rows
-  int grid;               // n_slices * ctas_per_slice
+  int grid;               // n_groups * ctas_per_slice
   int n_part;             // partial-sum rows written (= ctas_per_slice)
   int bn;                 // patterns per tile (MMA N)
   int kblocks;            // k-blocks of 128 bytes over kp
   int stages;             // B-operand pipeline depth
-  int cluster;            // CTAs (one per slice) sharing each B tile by TMA multicast
+  int cluster;            // CTAs (one per group) sharing each B tile by TMA multicast
   int prefetch = 1;       // L2 prefetch of each CTA's next pattern tile
   size_t smem;            // dynamic shared memory bytes
 };
@@ -28,6 +30,7 @@ struct TcPlan {
 // Requested tile shape; 0 fields are chosen automatically.
 struct TileReq {
   int n = 0, stages = 0, cluster = 0, prefetch = -1;   // prefetch: -1 auto (on), 0 off, 1 on
+  int sp = 0;                                          // slices per CTA: 0 auto (1), 1, 2
 };
 
 bool tc_supported(const Shape& s);

@@ -41,7 +41,7 @@ class GameConfig(C.Structure):
         ("surrogate_steps", C.c_int32), ("surrogate_batch", C.c_int32), ("surrogate_lr", C.c_float),
         ("surrogate_select", C.c_int32), ("surrogate_fp32", C.c_int32), ("engine", C.c_int32),
         ("tile_n", C.c_int32), ("tile_stages", C.c_int32), ("tile_cluster", C.c_int32),
-        ("device", C.c_int32), ("stream", C.c_void_p),
+        ("tile_slices", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
     ]
 
 
@@ -52,7 +52,7 @@ class GameTiming(C.Structure):
 
 class GameTile(C.Structure):
     _fields_ = [("n", C.c_int32), ("stages", C.c_int32), ("cluster", C.c_int32),
-                ("prefetch", C.c_int32), ("ms", C.c_double)]
+                ("prefetch", C.c_int32), ("slices", C.c_int32), ("ms", C.c_double)]
 
 
 class GameError(RuntimeError):
@@ -259,7 +259,7 @@ class Game:
         n = C.c_int32(0)
         self._check(lib.game_autotune(self.h, reps, C.byref(best), cands, 64, C.byref(n)), self.h)
         tile = lambda t: {"n": t.n, "stages": t.stages, "cluster": t.cluster,
-                          "prefetch": t.prefetch, "ms": t.ms}
+                          "prefetch": t.prefetch, "slices": t.slices, "ms": t.ms}
         return tile(best), [tile(cands[i]) for i in range(n.value)]
 
     # ---- learned surrogate ----

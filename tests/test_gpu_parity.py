@@ -258,16 +258,18 @@ def test_calls_out_of_order_are_state_errors():
 
 # ------------------------------------------------------------ tile shapes
 
-@pytest.mark.parametrize("tile", [(256, 3, 1), (256, 2, 2), (256, 3, 4), (256, 3, 8), (128, 5, 1),
-                                  (128, 4, 2), (128, 5, 8)])
+@pytest.mark.parametrize("tile", [(256, 3, 1, 1), (256, 2, 2, 1), (256, 3, 4, 1), (256, 3, 8, 1),
+                                  (128, 5, 1, 1), (128, 4, 2, 1), (128, 5, 8, 1), (128, 2, 1, 2),
+                                  (128, 2, 4, 2)])
 def test_tcgen05_tile_shapes_agree(tile):
-    """Every tile shape (patterns per tile, ring depth, multicast cluster) gives the oracle's
-    fitness; population 1024 = 8 slices, so clusters of 2, 4 and 8 share pattern tiles."""
+    """Every tile shape (patterns per tile, ring depth, multicast cluster, slices per CTA)
+    gives the oracle's fitness; population 1024 = 8 slices, so clusters of 2, 4 and 8
+    share pattern tiles (4 groups of two slices with two slices per CTA)."""
     game = lib()
     ds = synth.make_dataset(20011, 32, 8, seed=41, correlated=True)
     ocfg = _cfg(degree=8, pop=1024, seed=3)
     g = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=game.ENGINE_TCGEN05, tile_n=tile[0],
-                  tile_stages=tile[1], tile_cluster=tile[2])
+                  tile_stages=tile[1], tile_cluster=tile[2], tile_slices=tile[3])
     fit, _ = g.evaluate()
     P = o.expand(ds.X[:ds.n_train], "chebyshev", 8)
     np.testing.assert_allclose(fit, o.fitness(P, ds.t[:ds.n_train], g.population(), ocfg),

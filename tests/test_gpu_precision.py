@@ -69,6 +69,26 @@ def test_low_precision_tcgen05_matches_oracle(fmt, planes, shape):
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+@pytest.mark.parametrize("planes", [1, 2])
+def test_low_precision_two_slices_per_cta(fmt, planes):
+    """Two 128-chromosome slices per CTA (both fed by each 128-pattern tile) give the
+    same fitness as the oracle on the quantised operands; population 1280 = 10 slices
+    = 5 groups of two, training rows 21,007 (a ragged last tile)."""
+    game = lib()
+    ds = synth.make_dataset(30011, 32, 8, seed=35, correlated=True)
+    ocfg = o.Config(degree=8, pop=1280, seed=4)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=_prec(fmt), elite_rescore=0,
+                  engine=game.ENGINE_TCGEN05, gene_planes=planes, tile_n=128, tile_slices=2)
+    G = g.population()
+    fit, _ = g.evaluate()
+    Q, s = o.quantize_columns(o.expand(ds.X, "chebyshev", 8)[:, 1:], fmt)
+    Pq = np.concatenate([np.ones((ds.n_train, 1)), o.dequantize_columns(Q[:ds.n_train], s)], axis=1)
+    np.testing.assert_allclose(fit, o.fitness(Pq, ds.t[:ds.n_train],
+                                              o.quantize_genes(G, s, fmt, planes), ocfg),
+                               rtol=1e-5)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
 def test_low_precision_simt_matches_oracle(fmt):
     """The CUDA-core engine reads the quantised P with exact float32 genes."""
     game = lib()

@@ -59,7 +59,7 @@ def parse():
                          "against the same runs launched one by one; prints its own JSON line")
     ap.add_argument("--surrogate", action="store_true",
                     help="learned-surrogate form: time to the plain FP32 GA's final train RMSE")
-    ap.add_argument("--seeds", type=int, default=3)
+    ap.add_argument("--seeds", type=int, default=5)
     ap.add_argument("--budget", type=int, default=200, help="plain GA generations (target run)")
     ap.add_argument("--precision-table", action="store_true",
                     help="print the per-precision fitness error / accuracy table and exit")
@@ -563,7 +563,9 @@ def surrogate_ttt(args):
         "mean_test_accuracy_delta": {name: dacc(name) for name, _ in contenders},
         "config": {"workload": "2,000,000 patterns x 48 features, Chebyshev d=6, 289 genes, "
                                "pop 4096, 8x pool, surrogate MLP 289-256-256-1 (bf16, tcgen05)",
-                   "surrogate_steps_per_generation": 4, "surrogate_batch": 1024}}), flush=True)
+                   "surrogate_steps_per_generation": 4, "surrogate_batch": 1024,
+                   "surrogate_lr": 2e-3, "replay_ring": "latest population (4096 pairs)",
+                   "inputs": "genes standardised by running per-gene statistics"}}), flush=True)
 
 
 def main():

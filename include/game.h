@@ -90,7 +90,7 @@ typedef struct game_config {
   int32_t surrogate_pool; /* 0 off; else offspring pool multiplier screened by the MLP      */
   int32_t surrogate_steps;  /* Adam steps per generation (0 = 4)                            */
   int32_t surrogate_batch;  /* training batch rows (0 = 1024)                               */
-  float surrogate_lr;       /* Adam learning rate (0 = 1e-3)                                */
+  float surrogate_lr;       /* Adam learning rate (0 = 2e-3)                                */
   int32_t surrogate_select; /* 0: surrogate's best of the pool; 1: plain children (ablation)*/
   int32_t surrogate_fp32;   /* 1: float32 weights in the GEMMs (checks); 0: bfloat16        */
   int32_t engine;         /* GAME_ENGINE_* fitness kernel choice (AUTO picks tcgen05)       */
@@ -243,10 +243,11 @@ game_status game_set_timing(game_ctx* ctx, int32_t enabled);
 
 /* With cfg.surrogate_pool = m > 0, every generation breeds m x (pop - elitism)
  * children with the usual operators, scores them with an MLP (genes -> 256 ->
- * 256 -> 1, GELU, bfloat16 weights, float32 accumulation) that predicts the
- * standardised log fitness, keeps the pop - elitism best-scored children, and
- * evaluates them exactly.  The exact (chromosome, fitness) pairs go to a replay
- * ring (m x pop rows) on which the MLP takes surrogate_steps Adam steps per
+ * 256 -> 1, GELU, bfloat16 weights and GEMM operands, float32 accumulation; the
+ * genes standardised by running per-gene statistics of the evaluated
+ * populations) that predicts the standardised log fitness, keeps the
+ * pop - elitism best-scored children, and evaluates them exactly.  The exact (chromosome, fitness) pairs go to a replay
+ * ring (the latest population, pop rows) on which the MLP takes surrogate_steps Adam steps per
  * generation.  The Spearman correlation of predicted and exact fitness of each
  * generation's children is recorded; below 0.1 the next generation keeps plain
  * children instead (the fallback).  The calls below expose the network for

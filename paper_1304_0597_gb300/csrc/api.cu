@@ -70,7 +70,7 @@ struct game_ctx {
   Surrogate sg{};
   int n_pool = 0;               // children bred per generation
   int sg_steps = 4, sg_batch = 1024;
-  float sg_lr = 1e-3f;
+  float sg_lr = 2e-3f;
   float* d_pool = nullptr;      // [n_pool x kstride]
   float* d_score = nullptr;     // [n_pool]
   int* d_sel = nullptr;         // [pop]
@@ -371,12 +371,14 @@ static game_status alloc_surrogate(game_ctx* c) {
   const Shape& s = c->s;
   c->sg_steps = c->cfg.surrogate_steps > 0 ? c->cfg.surrogate_steps : 4;
   c->sg_batch = c->cfg.surrogate_batch > 0 ? c->cfg.surrogate_batch : 1024;
-  c->sg_lr = c->cfg.surrogate_lr > 0.0f ? c->cfg.surrogate_lr : 1e-3f;
+  c->sg_lr = c->cfg.surrogate_lr > 0.0f ? c->cfg.surrogate_lr : 2e-3f;
   const int e = c->cfg.elitism < s.pop ? c->cfg.elitism : s.pop;
   const int m = c->cfg.surrogate_pool > 0 ? c->cfg.surrogate_pool : 1;
   c->n_pool = m * (s.pop - e);
   if (c->n_pool < 1) c->n_pool = 1;
-  c->ring_cap = std::max(m * s.pop, c->sg_batch);
+  // the replay ring holds the latest evaluated population (at least one batch):
+  // older generations' pairs describe a landscape the GA has left
+  c->ring_cap = std::max(s.pop, c->sg_batch);
   Surrogate& sg = c->sg;
   sg = Surrogate{};
   sg.D = s.n_genes;
@@ -670,6 +672,7 @@ static game_status enqueue_pre(game_ctx* c, cudaStream_t st) {
 
 // After an exact evaluation: replay ring, monitor, and the generation's training.
 static game_status enqueue_surrogate_train(game_ctx* c, cudaStream_t st) {
+  if (c->sg.tc) CUDA_OK(c, launch_gene_stats(c->p, c->s, c->d_state, c->d_ring_meta, c->sg, st));
   CUDA_OK(c, launch_replay_update(c->p, c->s, std::min(c->cfg.elitism, c->s.pop), c->d_fit,
                                   c->d_pred, c->d_state, c->d_ring_x, c->d_ring_f, c->d_ring_meta,
                                   c->ring_cap, c->d_norm, c->d_monitor, c->d_fallback, 0.1f,

@@ -49,6 +49,7 @@ struct Surrogate {
   float *dyh2 = nullptr;           // dy * H2 [Bt x H]
   float *gws = nullptr;            // split-K partial gradient planes [4 x n_params]
   unsigned int* adam_done = nullptr;   // blocks finished in the current Adam launch
+  float* gnorm = nullptr;          // input standardisation [shift D | scale D | var D]
   DevState* state = nullptr;       // where a timed-out wait records its status
 
   size_t n_params() const;
@@ -123,6 +124,10 @@ cudaError_t launch_sample_batch(const float* ring_x, const float* ring_f, const 
                                 float* bx, float* bt, cudaStream_t st);
 // The same batch written straight into the bf16 operands Xb and X^T of the
 // tensor-core path (sg.tc); targets to bt.
+// Running per-gene mean / variance of the evaluated populations (exponential
+// average) that standardise the network's inputs in the bf16 form.
+cudaError_t launch_gene_stats(const PopDev& p, const Shape& s, const DevState* state,
+                              const int* ring_meta, Surrogate& sg, cudaStream_t st);
 cudaError_t launch_sample_batch_tc(const float* ring_x, const float* ring_f, const int* ring_meta,
                                    int kstride, const Surrogate& sg, int B, uint64_t k0,
                                    uint64_t k1, uint64_t gen_salt, int step, const DevState* state,

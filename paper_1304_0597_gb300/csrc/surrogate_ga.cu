@@ -357,6 +357,45 @@ __global__ void sample_batch_kernel(const float* __restrict__ ring_x, const floa
   if (lane == 0) bt[row] = ring_f[idx];
 }
 
+// ---- input standardisation of the bf16 form: running per-gene statistics ----
+constexpr float kStatsWeight = 0.3f;   // weight of the newest population in the running average
+// Block of 32 genes x 32 row groups; the mean and variance of the population just
+// evaluated enter an exponential average (weight 0.3; the first generation sets
+// it), and scale = 1 / sqrt(var + 1e-6).
+__global__ void gene_stats_kernel(const float* g32_0, const float* g32_1, const DevState* st,
+                                  const int* ring_meta, int pop, int D, int kstride,
+                                  float* gnorm) {
+  if (st->evals == ring_meta[2]) return;   // nothing evaluated since the last update
+  __shared__ float s1[32][33], s2[32][33];
+  const float* G = st->cur ? g32_1 : g32_0;
+  const int d = blockIdx.x * 32 + threadIdx.x;
+  float a = 0.0f, b = 0.0f;
+  if (d < D)
+    for (int r = threadIdx.y; r < pop; r += 32) {
+      const float v = G[(long long)r * kstride + d];
+      a += v;
+      b += v * v;
+    }
+  s1[threadIdx.y][threadIdx.x] = a;
+  s2[threadIdx.y][threadIdx.x] = b;
+  __syncthreads();
+  if (threadIdx.y == 0 && d < D) {
+    float ta = 0.0f, tb = 0.0f;
+    for (int i = 0; i < 32; ++i) {
+      ta += s1[i][threadIdx.x];
+      tb += s2[i][threadIdx.x];
+    }
+    const float mu = ta / (float)pop;
+    const float var = fmaxf(tb / (float)pop - mu * mu, 0.0f);
+    const float w = ring_meta[3] > 0 ? kStatsWeight : 1.0f;   // monitor's generation count (read only)
+    const float m2 = (1.0f - w) * gnorm[d] + w * mu;
+    const float v2 = (1.0f - w) * gnorm[2 * D + d] + w * var;
+    gnorm[d] = m2;
+    gnorm[2 * D + d] = v2;
+    gnorm[D + d] = rsqrtf(v2 + 1e-6f);
+  }
+}
+
 // ---- training batch straight into the tensor-core operands (bf16 form) ----
 // Same draws as sample_batch_kernel; a CTA takes 32 rows x 32 genes through a
 // shared tile so that both the row-major and the transposed bf16 stores coalesce.
@@ -366,7 +405,7 @@ __global__ void sample_batch_tc_kernel(const float* __restrict__ ring_x,
                                        int B, Key key, uint64_t salt, int step, const DevState* st,
                                        __nv_bfloat16* __restrict__ Xb, int Dp,
                                        __nv_bfloat16* __restrict__ XT, long long ldt,
-                                       float* __restrict__ bt) {
+                                       float* __restrict__ bt, const float* __restrict__ gnorm) {
   __shared__ float tile[32][33];
   __shared__ int rows[32];
   const int d0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
@@ -388,6 +427,7 @@ __global__ void sample_batch_tc_kernel(const float* __restrict__ ring_x,
     float v = 0.0f;
     if (r < B && d < D) {
       v = ring_x[(long long)rows[i] * kstride + d];
+      v = (v - gnorm[d]) * gnorm[D + d];   // running per-gene standardisation
       Xb[(long long)r * Dp + d] = __float2bfloat16_rn(v);
     }
     tile[i][tx] = v;
@@ -477,7 +517,14 @@ cudaError_t launch_sample_batch_tc(const float* ring_x, const float* ring_f, con
   const dim3 grid((sg.D + 31) / 32, (B + 31) / 32);
   sample_batch_tc_kernel<<<grid, dim3(32, 8), 0, st>>>(ring_x, ring_f, ring_meta, kstride, sg.D, B,
                                                        Key{k0, k1}, gen_salt, step, state, sg.Xb,
-                                                       sg.Dp, sg.XTb, sg.ldt, bt);
+                                                       sg.Dp, sg.XTb, sg.ldt, bt, sg.gnorm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gene_stats(const PopDev& p, const Shape& s, const DevState* state,
+                              const int* ring_meta, Surrogate& sg, cudaStream_t st) {
+  gene_stats_kernel<<<(s.n_genes + 31) / 32, dim3(32, 32), 0, st>>>(
+      p.g32[0], p.g32[1], state, ring_meta, s.pop, s.n_genes, s.kstride, sg.gnorm);
   return cudaGetLastError();
 }
 

@@ -346,14 +346,18 @@ constexpr size_t smem_bytes() {
 // shared memory so that both stores are coalesced.
 __global__ void cast_rows_kernel(const float* __restrict__ X, long long ldx, int M, int D,
                                  __nv_bfloat16* __restrict__ Xb, int Dp,
-                                 __nv_bfloat16* __restrict__ XT, long long ldt) {
+                                 __nv_bfloat16* __restrict__ XT, long long ldt,
+                                 const float* __restrict__ gnorm) {
   __shared__ float tile[32][33];
   const int d0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
   for (int i = ty; i < 32; i += 8) {
     const int r = r0 + i, d = d0 + tx;
     float v = 0.0f;
-    if (r < M && d < D) v = X[(long long)r * ldx + d];
+    if (r < M && d < D) {
+      v = X[(long long)r * ldx + d];
+      v = (v - gnorm[d]) * gnorm[D + d];   // running per-gene standardisation
+    }
     tile[i][tx] = v;
     if (r < M && d < D) Xb[(long long)r * Dp + d] = __float2bfloat16_rn(v);
   }
@@ -363,6 +367,11 @@ __global__ void cast_rows_kernel(const float* __restrict__ X, long long ldx, int
     const int d = d0 + i, r = r0 + tx;
     if (d < D && r < M) XT[(long long)d * ldt + r] = __float2bfloat16_rn(tile[tx][i]);
   }
+}
+
+__global__ void fill_f32_tc_kernel(float* p, long long n, float v) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
 }
 
 __global__ void fill_bf16_kernel(__nv_bfloat16* p, long long n, float v) {
@@ -545,7 +554,9 @@ size_t Surrogate::tc_bytes(int max_rows_, int batch) const {
   const size_t b16 = sizeof(__nv_bfloat16);
   return b16 * ((size_t)H * dp + 2 * (size_t)H * H + (size_t)max_rows_ * (dp + H) +
                 ((size_t)D + 1 + (size_t)H + 1 + 2 * (size_t)H) * ldt_ + (size_t)batch * H) +
-         sizeof(float) * (2 * (size_t)batch * H + (size_t)kGradSplits * n_params()) + 16;
+         sizeof(float) * (2 * (size_t)batch * H + (size_t)kGradSplits * n_params() +
+                          3 * (size_t)D + 4) +
+         16;
 }
 
 void Surrogate::tc_carve(void* base, int batch) {
@@ -581,6 +592,8 @@ void Surrogate::tc_carve(void* base, int batch) {
   f += (size_t)Bt * H;
   gws = f;
   f += (size_t)kGradSplits * n_params();
+  gnorm = f;
+  f += 3 * (size_t)D + 4;
   adam_done = reinterpret_cast<unsigned int*>(f);
   tc = true;
 }
@@ -590,6 +603,8 @@ cudaError_t Surrogate::tc_prepare(cudaStream_t st) {
   // gradients come out of the weight-gradient GEMMs as one more column
   fill_bf16_kernel<<<ceil_div(ldt, 256), 256, 0, st>>>(XTb + (size_t)D * ldt, ldt, 1.0f);
   fill_bf16_kernel<<<ceil_div(ldt, 256), 256, 0, st>>>(H1Tb + (size_t)H * ldt, ldt, 1.0f);
+  // input standardisation starts as the identity (shift 0, scale 1, count 0)
+  fill_f32_tc_kernel<<<ceil_div(D, 256), 256, 0, st>>>(gnorm + D, D, 1.0f);
   return tc_weights(st);
 }
 
@@ -604,7 +619,7 @@ cudaError_t Surrogate::tc_forward(const float* X, long long ldx, int M, float* y
   const bool train = t != nullptr;
   if (M < 1 || M > max_rows || (train && M > Bt)) return cudaErrorInvalidValue;
   cast_rows_kernel<<<dim3(ceil_div(D, 32), ceil_div(M, 32)), dim3(32, 8), 0, st>>>(
-      X, ldx, M, D, Xb, Dp, train ? XTb : nullptr, ldt);
+      X, ldx, M, D, Xb, Dp, train ? XTb : nullptr, ldt, gnorm);
   return tc_layers(M, y, t, st);
 }
 

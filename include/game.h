@@ -81,6 +81,8 @@ typedef struct game_config {
   int32_t activation;     /* GAME_TANH | GAME_LINEAR (the paper's Out)                      */
   int32_t init;           /* GAME_INIT_* (Section 2, three random generation criteria)     */
   int32_t clamp_genes;    /* 1: genes clamped to [-1,1] after mutation                      */
+  int32_t immigrants;     /* random chromosomes replacing the last children of every bred
+                             generation (Section 4.1), 0..pop - elitism; default 0          */
   double stop_error;      /* stop when the best fitness <= this (Section 5: 0.001)         */
   uint64_t seed;          /* Philox key word 0                                              */
   uint64_t run;           /* Philox key word 1 (independent runs with one seed)            */
@@ -202,6 +204,30 @@ typedef struct game_timing {
   int32_t engine;
 } game_timing;
 game_status game_get_timing(game_ctx* ctx, game_timing* out);
+
+/* Outputs of a chromosome on new patterns, the paper's test and run use cases
+ * (Section 2: a trained chromosome applied to data outside the training set):
+ * out[k] = activation(g_0 + sum_f sum_b genes[1 + f*B*d + b] g_b(X[k][f])), eq.2
+ * with the context's basis (eq.8 / eq.9 family, per-feature coefficients), degree
+ * and activation, the expansion computed on the fly in float64.  X: n x n_features
+ * float32 row-major, out: n float32; both host memory (device_ptrs = 0) or both
+ * device memory (1); genes: host or device, n_genes = B*n_features*d + 1.  Needs
+ * no game_set_data.  Errors: INVALID_ARG (sizes), CUDA. */
+game_status game_predict(game_ctx* ctx, const float* genes, int32_t n_genes, const float* X,
+                         int64_t n, int32_t n_features, float* out, int32_t device_ptrs);
+
+/* Checkpoint of the GA (Section 2: the population is stored and training can
+ * resume): the current population, its fitness and ranking and the loop state
+ * (the generation that keys the counter-based random numbers), so that
+ * game_evolve after game_load continues exactly as without the interruption.
+ * game_save writes at most cap bytes to buf (host) and the needed size to *size;
+ * buf = NULL only asks the size.  game_load takes a buffer of a context with the
+ * same configuration (population, genes, basis, degree, seed, run) and data
+ * shape.  Contexts with the learned surrogate return UNSUPPORTED (its network
+ * and replay state are not part of the checkpoint).  Errors: STATE (no data),
+ * INVALID_ARG (buffer size, foreign checkpoint), UNSUPPORTED, CUDA. */
+game_status game_save(game_ctx* ctx, void* buf, int64_t cap, int64_t* size);
+game_status game_load(game_ctx* ctx, const void* buf, int64_t size);
 
 /* Failure-detection self-test (no paper counterpart): a device thread waits on
  * an mbarrier that nothing completes, with the bounded-wait code of the

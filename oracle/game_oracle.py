@@ -80,6 +80,7 @@ class Config:
     stop_error: float = 0.001
     seed: int = 0
     run: int = 0                     # second Philox key word (independent runs)
+    immigrants: int = 0              # random chromosomes replacing the last children
 
 
 def basis_multiplier(basis: str) -> int:
@@ -221,6 +222,7 @@ _PHILOX_W1 = 0xBB67AE8584CAA73B   # sqrt(3) - 1
 
 STREAM_TOURNAMENT, STREAM_CROSSOVER, STREAM_MUT_MASK, STREAM_MUT_NORMAL = 0, 1, 2, 3
 STREAM_INIT, STREAM_INIT_NORMAL = 4, 5
+STREAM_IMMIGRANT, STREAM_IMMIGRANT_NORMAL = 8, 9   # (6, 7 belong to the surrogate)
 
 
 def _mulhilo64(a: int, b: np.ndarray):
@@ -365,18 +367,20 @@ def gauss_f32(w0: np.ndarray, w1: np.ndarray) -> np.ndarray:
 # Population initialisation (Section 2: three random generation criteria)
 # ---------------------------------------------------------------------------
 
-def init_population(cfg: Config, K: int) -> np.ndarray:
-    """Generation-0 genes [pop x K] float32: U[-1,1], N(0,0.5^2) truncated to [-1,1], or U[0,1]."""
-    key = (cfg.seed, cfg.run)
-    c = np.arange(cfg.pop, dtype=np.uint64)[:, None]
+def draw_chromosomes(key, gen: int, rows: np.ndarray, K: int, init: str, stream_u: int,
+                     stream_n: int) -> np.ndarray:
+    """Random chromosomes [len(rows) x K] float32 of the init distribution, row r drawn
+    with the Philox counter (gen, r, stream, word): U[-1,1], N(0,0.5^2) truncated to
+    [-1,1] by resampling (64 rounds, then clamp), or U[0,1]."""
+    c = np.asarray(rows, dtype=np.uint64)[:, None]
     g = np.arange(K, dtype=np.uint64)[None, :]
-    if cfg.init == "normal_pm1":
-        out = np.zeros((cfg.pop, K), dtype=np.float32)
-        done = np.zeros((cfg.pop, K), dtype=bool)
+    if init == "normal_pm1":
+        out = np.zeros((c.shape[0], K), dtype=np.float32)
+        done = np.zeros((c.shape[0], K), dtype=bool)
         for r in range(64):
             w = _U64(2) * (_U64(r) * _U64(K) + g)
-            z = gauss_f32(philox_words(key, 0, c, STREAM_INIT_NORMAL, w),
-                          philox_words(key, 0, c, STREAM_INIT_NORMAL, w + _U64(1)))
+            z = gauss_f32(philox_words(key, gen, c, stream_n, w),
+                          philox_words(key, gen, c, stream_n, w + _U64(1)))
             v = z * _F(0.5)
             ok = (~done) & (np.abs(v) <= _F(1.0))
             out = np.where(ok, v, out)
@@ -384,10 +388,16 @@ def init_population(cfg: Config, K: int) -> np.ndarray:
                 out = np.where(done | ok, out, np.clip(v, _F(-1.0), _F(1.0)))
             done |= ok
         return out
-    u = uniform24(philox_words(key, 0, c, STREAM_INIT, g))
-    if cfg.init == "uniform_01":
+    u = uniform24(philox_words(key, gen, c, stream_u, g))
+    if init == "uniform_01":
         return u
     return (u * _F(2.0) - _F(1.0)).astype(np.float32)
+
+
+def init_population(cfg: Config, K: int) -> np.ndarray:
+    """Generation-0 genes [pop x K] float32 (Section 2: the first population is random)."""
+    return draw_chromosomes((cfg.seed, cfg.run), 0, np.arange(cfg.pop), K, cfg.init,
+                            STREAM_INIT, STREAM_INIT_NORMAL)
 
 
 # ---------------------------------------------------------------------------
@@ -435,7 +445,7 @@ def breed(G: np.ndarray, fit: np.ndarray, cfg: Config, gen: int) -> np.ndarray:
     n_child = pop - e
     n_pairs = (n_child + 1) // 2
     if n_pairs == 0:
-        return out
+        return immigrate(out, cfg, gen)
     j = np.arange(n_pairs, dtype=np.uint64)
     p1 = tournament(key, gen, j, 0, cfg.tournament_k, fit)
     p2 = tournament(key, gen, j, cfg.tournament_k, cfg.tournament_k, fit)
@@ -460,7 +470,23 @@ def breed(G: np.ndarray, fit: np.ndarray, cfg: Config, gen: int) -> np.ndarray:
     slots = np.empty((2 * n_pairs, K), dtype=np.float32)
     slots[0::2], slots[1::2] = ca, cb
     out[e:] = slots[:n_child]
-    return out
+    return immigrate(out, cfg, gen)
+
+
+def immigrate(G: np.ndarray, cfg: Config, gen: int) -> np.ndarray:
+    """Random immigrants (Section 4.1: a number of chromosomes are generated at random
+    to replace older individuals): the last cfg.immigrants rows of the population bred
+    at step gen are replaced by chromosomes of the init distribution, drawn with the
+    counter of the new generation gen + 1 on streams of their own."""
+    n = min(cfg.immigrants, G.shape[0])
+    if n <= 0:
+        return G
+    pop, K = G.shape
+    rows = np.arange(pop - n, pop)
+    G = G.copy()
+    G[rows] = draw_chromosomes((cfg.seed, cfg.run), gen + 1, rows, K, cfg.init,
+                               STREAM_IMMIGRANT, STREAM_IMMIGRANT_NORMAL)
+    return G
 
 
 # ---------------------------------------------------------------------------

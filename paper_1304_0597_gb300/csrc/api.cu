@@ -207,6 +207,8 @@ static game_status validate(game_ctx* c, const game_config* cfg) {
     return fail(c, GAME_ERR_INVALID_ARG, "bad precision");
   if (cfg->engine < GAME_ENGINE_AUTO || cfg->engine > GAME_ENGINE_SIMT)
     return fail(c, GAME_ERR_INVALID_ARG, "bad engine");
+  if (cfg->immigrants < 0 || cfg->immigrants > cfg->pop - (cfg->elitism < cfg->pop ? cfg->elitism : cfg->pop))
+    return fail(c, GAME_ERR_INVALID_ARG, "immigrants must be in 0..pop - elitism");
   if ((cfg->tile_n != 0 && cfg->tile_n != 128 && cfg->tile_n != 256) || cfg->tile_stages < 0 ||
       cfg->tile_cluster < 0 || cfg->tile_slices < 0 || cfg->tile_slices > 2 ||
       (cfg->tile_slices == 2 && cfg->tile_n == 256))
@@ -663,6 +665,7 @@ static game_status enqueue_pre(game_ctx* c, cudaStream_t st) {
     CUDA_OK(c, launch_assemble(c->d_pool, c->d_sel, c->d_score, c->p, c->s, e,
                                c->cfg.elite_mode == GAME_ELITE_COPIES, c->d_rank, c->d_state,
                                c->d_pred, st));
+    CUDA_OK(c, launch_immigrants(c->s, c->cfg, c->p, c->d_state, st));
   } else {
     CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 1 | 2, st));
   }
@@ -1031,6 +1034,138 @@ extern "C" game_status game_get_best(game_ctx* c, float* genes, int32_t cap, dou
     if (r != GAME_OK) return r;
     fill_report(v, rows, test_rmse, test_accuracy, nullptr, nullptr);
   }
+  return GAME_OK;
+}
+
+extern "C" game_status game_predict(game_ctx* c, const float* genes, int32_t n_genes,
+                                    const float* X, int64_t n, int32_t n_features, float* out,
+                                    int32_t device_ptrs) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  const int B = c->cfg.basis == GAME_TRIG ? 2 : 1;
+  if (!genes || !X || !out || n < 0 || n_features < 1 ||
+      n_genes != B * n_features * c->cfg.degree + 1)
+    return fail(c, GAME_ERR_INVALID_ARG, "genes must hold B*F*d+1 = %d values for F = %d",
+                B * n_features * c->cfg.degree + 1, n_features);
+  if (n == 0) return GAME_OK;
+  cudaSetDevice(c->dev);
+  float *dg = nullptr, *dX = nullptr, *dy = nullptr;
+  auto release = [&]() {
+    if (dg) cudaFree(dg);
+    if (!device_ptrs) {
+      if (dX) cudaFree(dX);
+      if (dy) cudaFree(dy);
+    }
+  };
+  cudaError_t e = cudaMalloc((void**)&dg, sizeof(float) * n_genes);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dg, genes, sizeof(float) * n_genes, cudaMemcpyDefault, c->st);
+  if (e == cudaSuccess && !device_ptrs) {
+    e = cudaMalloc((void**)&dX, sizeof(float) * (size_t)n * n_features);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&dy, sizeof(float) * (size_t)n);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dX, X, sizeof(float) * (size_t)n * n_features, cudaMemcpyHostToDevice,
+                          c->st);
+  } else if (e == cudaSuccess) {
+    dX = const_cast<float*>(X);
+    dy = out;
+  }
+  if (e == cudaSuccess)
+    e = launch_predict(dX, n, n_features, dg, n_genes, c->cfg.basis, c->cfg.degree,
+                       c->cfg.activation, dy, c->st);
+  if (e == cudaSuccess && !device_ptrs)
+    e = cudaMemcpyAsync(out, dy, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  release();
+  if (e != cudaSuccess) return fail(c, GAME_ERR_CUDA, "predict: %s", cudaGetErrorString(e));
+  return GAME_OK;
+}
+
+// ---- checkpoint of the GA state -------------------------------------------
+namespace {
+struct SaveHeader {
+  uint32_t magic;          // "GAMS"
+  uint32_t version;        // 1
+  int32_t pop, n_genes, basis, degree;
+  uint64_t seed, run;
+  int64_t gen;             // Philox counter word 0 of the next breeding
+  int32_t evaluated, stopped, gens_run, evals;
+  double best;
+};
+constexpr uint32_t kSaveMagic = 0x534D4147u;   // 'G' 'A' 'M' 'S'
+}  // namespace
+
+static int64_t save_bytes(const game_ctx* c) {
+  return (int64_t)sizeof(SaveHeader) + (int64_t)c->s.pop * c->s.n_genes * 4 +
+         (int64_t)c->s.pop * 8 + (int64_t)c->s.pop * 4;
+}
+
+extern "C" game_status game_save(game_ctx* c, void* buf, int64_t cap, int64_t* size) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  if (c->cfg.surrogate_pool > 0)
+    return fail(c, GAME_ERR_UNSUPPORTED, "the surrogate's state is not part of a checkpoint");
+  const int64_t need = save_bytes(c);
+  if (size) *size = need;
+  if (!buf) return GAME_OK;
+  if (cap < need) return fail(c, GAME_ERR_INVALID_ARG, "buffer holds %lld of %lld bytes",
+                              (long long)cap, (long long)need);
+  cudaSetDevice(c->dev);
+  DevState hs;
+  CUDA_OK(c, cudaMemcpyAsync(&hs, c->d_state, sizeof(hs), cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  SaveHeader h{kSaveMagic, 1u, c->s.pop, c->s.n_genes, c->cfg.basis, c->cfg.degree,
+               c->cfg.seed, c->cfg.run, hs.gen, hs.evaluated, hs.stopped, hs.gens_run,
+               hs.evals, hs.best};
+  uint8_t* b = static_cast<uint8_t*>(buf);
+  memcpy(b, &h, sizeof(h));
+  b += sizeof(h);
+  const int pop = c->s.pop, K = c->s.n_genes;
+  CUDA_OK(c, cudaMemcpy2DAsync(b, sizeof(float) * K, c->p.g32[hs.cur], sizeof(float) * c->s.kstride,
+                               sizeof(float) * K, pop, cudaMemcpyDeviceToHost, c->st));
+  b += (size_t)pop * K * 4;
+  CUDA_OK(c, cudaMemcpyAsync(b, c->d_fit, sizeof(double) * pop, cudaMemcpyDeviceToHost, c->st));
+  b += (size_t)pop * 8;
+  CUDA_OK(c, cudaMemcpyAsync(b, c->d_rank, sizeof(int) * pop, cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  return GAME_OK;
+}
+
+extern "C" game_status game_load(game_ctx* c, const void* buf, int64_t size) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  if (c->cfg.surrogate_pool > 0)
+    return fail(c, GAME_ERR_UNSUPPORTED, "the surrogate's state is not part of a checkpoint");
+  if (!buf || size < (int64_t)sizeof(SaveHeader))
+    return fail(c, GAME_ERR_INVALID_ARG, "not a checkpoint");
+  SaveHeader h;
+  memcpy(&h, buf, sizeof(h));
+  if (h.magic != kSaveMagic || h.version != 1u || size != save_bytes(c))
+    return fail(c, GAME_ERR_INVALID_ARG, "not a checkpoint of this version and size");
+  if (h.pop != c->s.pop || h.n_genes != c->s.n_genes || h.basis != c->cfg.basis ||
+      h.degree != c->cfg.degree || h.seed != c->cfg.seed || h.run != c->cfg.run)
+    return fail(c, GAME_ERR_INVALID_ARG,
+                "checkpoint of another configuration (population, genes, basis, seed or run)");
+  cudaSetDevice(c->dev);
+  const uint8_t* b = static_cast<const uint8_t*>(buf) + sizeof(h);
+  const int pop = c->s.pop, K = c->s.n_genes;
+  CUDA_OK(c, cudaMemcpy2DAsync(c->p.g32[0], sizeof(float) * c->s.kstride, b, sizeof(float) * K,
+                               sizeof(float) * K, pop, cudaMemcpyHostToDevice, c->st));
+  b += (size_t)pop * K * 4;
+  CUDA_OK(c, cudaMemcpyAsync(c->d_fit, b, sizeof(double) * pop, cudaMemcpyHostToDevice, c->st));
+  b += (size_t)pop * 8;
+  CUDA_OK(c, cudaMemcpyAsync(c->d_rank, b, sizeof(int) * pop, cudaMemcpyHostToDevice, c->st));
+  DevState hs{};
+  hs.gen = h.gen;
+  hs.cur = 0;
+  hs.evaluated = h.evaluated;
+  hs.bred = 0;
+  hs.stopped = h.stopped;
+  hs.gens_run = h.gens_run;
+  hs.status = 0;
+  hs.evals = h.evals;
+  hs.best = h.best;
+  CUDA_OK(c, cudaMemcpyAsync(c->d_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
   return GAME_OK;
 }
 

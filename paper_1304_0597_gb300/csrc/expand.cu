@@ -217,4 +217,61 @@ cudaError_t launch_expand_get(const Shape& s, const ExpDev& e, long long row0, l
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Prediction on new patterns (the paper's test / run use of a trained
+// chromosome): Out(x) = a_0 + sum_f sum_b g[1 + f B d + b] g_b(x_f) (eq.2, eq.8,
+// eq.9 with per-feature coefficients), then the activation.  One thread per
+// pattern; the expansion is computed on the fly in float64 (Chebyshev
+// recurrence; cos / sin of (b+1) x by angle addition from one sincos).
+// ---------------------------------------------------------------------------
+__global__ void predict_kernel(const float* __restrict__ X, long long n, int F,
+                               const float* __restrict__ genes, int K, int basis, int degree,
+                               int activation, float* __restrict__ out) {
+  extern __shared__ float gs[];
+  for (int i = threadIdx.x; i < K; i += blockDim.x) gs[i] = genes[i];
+  __syncthreads();
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float* x = X + k * F;
+  double s = (double)gs[0];
+  if (basis == GAME_CHEBYSHEV) {
+    for (int f = 0; f < F; ++f) {
+      const double v = (double)x[f];
+      const float* g = gs + 1 + f * degree;
+      double tm = 1.0, t = v;                     // T_0, T_1
+      for (int b = 0; b < degree; ++b) {
+        s = fma((double)g[b], t, s);
+        const double tn = 2.0 * v * t - tm;
+        tm = t;
+        t = tn;
+      }
+    }
+  } else {
+    for (int f = 0; f < F; ++f) {
+      const double v = (double)x[f];
+      const float* g = gs + 1 + f * 2 * degree;
+      double s1, c1;
+      sincos(v, &s1, &c1);
+      double c = c1, sn = s1;                     // cos((b+1) v), sin((b+1) v)
+      for (int b = 0; b < degree; ++b) {
+        s = fma((double)g[b], c, s);
+        s = fma((double)g[degree + b], sn, s);
+        const double cn = c * c1 - sn * s1;
+        sn = sn * c1 + c * s1;
+        c = cn;
+      }
+    }
+  }
+  out[k] = (float)(activation == GAME_TANH ? tanh(s) : s);
+}
+
+cudaError_t launch_predict(const float* X, long long n, int F, const float* genes, int K,
+                           int basis, int degree, int activation, float* out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int threads = 256;
+  predict_kernel<<<(unsigned)((n + threads - 1) / threads), threads, sizeof(float) * K, st>>>(
+      X, n, F, genes, K, basis, degree, activation, out);
+  return cudaGetLastError();
+}
+
 }  // namespace game

@@ -19,30 +19,57 @@ namespace game {
 // Initial population (Section 2: pseudo-random in [-1,1], normal in [-1,1],
 // pseudo-random in [0,1]).  One thread per gene.
 // ---------------------------------------------------------------------------
+// Gene g of a random chromosome c of the init distribution, Philox counter
+// (gen, c, stream, word): U[-1,1], N(0,0.5^2) resampled into [-1,1] (64 rounds,
+// then clamp), or U[0,1].
+__device__ __forceinline__ float draw_gene(Key key, uint64_t gen, int c, int g, int n_genes,
+                                           int mode, uint64_t stream_u, uint64_t stream_n) {
+  if (mode == GAME_INIT_NORMAL_PM1) {
+    for (int r = 0; r < 64; ++r) {
+      uint32_t w0, w1;
+      philox_word_pair(key, gen, (uint64_t)c, stream_n,
+                       (uint64_t)r * (uint64_t)n_genes + (uint64_t)g, &w0, &w1);
+      const float x = __fmul_rn(gauss_f32(w0, w1), 0.5f);
+      if (fabsf(x) <= 1.0f) return x;
+      if (r == 63) return fminf(fmaxf(x, -1.0f), 1.0f);
+    }
+    return 0.0f;
+  }
+  const float u = uniform24(philox_word(key, gen, (uint64_t)c, stream_u, (uint64_t)g));
+  return (mode == GAME_INIT_UNIFORM_01) ? u : __fsub_rn(__fmul_rn(u, 2.0f), 1.0f);
+}
+
 __global__ void init_population_kernel(int pop, int n_genes, int kstride, int mode, Key key,
                                        float* __restrict__ g32) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (long long)pop * n_genes) return;
   const int c = (int)(i / n_genes), g = (int)(i % n_genes);
-  float v;
-  if (mode == GAME_INIT_NORMAL_PM1) {
-    v = 0.0f;
-    for (int r = 0; r < 64; ++r) {
-      uint32_t w0, w1;
-      philox_word_pair(key, 0, (uint64_t)c, kStreamInitNormal,
-                       (uint64_t)r * (uint64_t)n_genes + (uint64_t)g, &w0, &w1);
-      const float x = __fmul_rn(gauss_f32(w0, w1), 0.5f);
-      if (fabsf(x) <= 1.0f) {
-        v = x;
-        break;
-      }
-      if (r == 63) v = fminf(fmaxf(x, -1.0f), 1.0f);
-    }
-  } else {
-    const float u = uniform24(philox_word(key, 0, (uint64_t)c, kStreamInit, (uint64_t)g));
-    v = (mode == GAME_INIT_UNIFORM_01) ? u : __fsub_rn(__fmul_rn(u, 2.0f), 1.0f);
-  }
-  g32[(long long)c * kstride + g] = v;
+  g32[(long long)c * kstride + g] =
+      draw_gene(key, 0, c, g, n_genes, mode, kStreamInit, kStreamInitNormal);
+}
+
+// Random immigrants (Section 4.1): the last n rows of the population just bred
+// (buffer cur ^ 1) are replaced by fresh chromosomes, counter generation gen + 1.
+__global__ void immigrants_kernel(const DevState* st, float* g32_0, float* g32_1, int pop, int n,
+                                  int n_genes, int kstride, int mode, Key key) {
+  if (!st->bred) return;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)n * n_genes) return;
+  const int c = pop - n + (int)(i / n_genes), g = (int)(i % n_genes);
+  float* out = st->cur ? g32_0 : g32_1;
+  out[(long long)c * kstride + g] = draw_gene(key, (uint64_t)st->gen + 1, c, g, n_genes, mode,
+                                              kStreamImmigrant, kStreamImmigrantNormal);
+}
+
+cudaError_t launch_immigrants(const Shape& s, const game_config& cfg, const PopDev& p,
+                              const DevState* state, cudaStream_t st) {
+  const int n = cfg.immigrants < s.pop ? cfg.immigrants : s.pop;
+  if (n <= 0) return cudaSuccess;
+  const long long total = (long long)n * s.n_genes;
+  immigrants_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(
+      state, p.g32[0], p.g32[1], s.pop, n, s.n_genes, s.kstride, cfg.init,
+      Key{cfg.seed, cfg.run});
+  return cudaGetLastError();
 }
 
 cudaError_t launch_init_population(const Shape& s, int init_mode, uint64_t seed, uint64_t run,
@@ -131,6 +158,7 @@ cudaError_t launch_breed(const Shape& s, const game_config& cfg, const PopDev& p
   const int threads = 256;
   const int blocks = allow & 1 ? (warps * 32 + threads - 1) / threads : 1;
   breed_kernel<<<blocks > 0 ? blocks : 1, threads, 0, st>>>(a);
+  if ((allow & 1) && cfg.immigrants > 0) return launch_immigrants(s, cfg, p, state, st);
   return cudaGetLastError();
 }
 

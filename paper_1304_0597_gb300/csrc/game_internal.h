@@ -21,6 +21,8 @@ enum : uint32_t {
   kStreamMutNormal = 3,
   kStreamInit = 4,
   kStreamInitNormal = 5,
+  kStreamImmigrant = 8,        // (6, 7: the surrogate's sampling and initial weights)
+  kStreamImmigrantNormal = 9,
 };
 
 // Device-resident loop state.  Only single-thread "state" kernels and the
@@ -86,6 +88,9 @@ struct Fitness {
 
 cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax_scratch,
                           cudaStream_t st);
+// Outputs of one chromosome on n new patterns X [n x F] (device buffers).
+cudaError_t launch_predict(const float* X, long long n, int F, const float* genes, int K,
+                           int basis, int degree, int activation, float* out, cudaStream_t st);
 cudaError_t launch_expand_get(const Shape& s, const ExpDev& e, long long row0, long long nrows,
                               float* out, cudaStream_t st);
 cudaError_t launch_target_coef(const float* t, float* c, long long n, cudaStream_t st);
@@ -107,6 +112,9 @@ cudaError_t launch_rescore_merge(const Shape& sr, const game_config& cfg, const 
 // Populations of at least this size are ranked by counting over many CTAs
 // (fit_reduce / rank_count / rank_state), smaller ones by one CTA's sort.
 constexpr int kRankCountMin = 512;
+// Random immigrants: the last cfg.immigrants rows of a bred population replaced.
+cudaError_t launch_immigrants(const Shape& s, const game_config& cfg, const PopDev& p,
+                              const DevState* state, cudaStream_t st);
 cudaError_t launch_reduce_rank(const Shape& s, const game_config& cfg, const double* partial,
                                int n_part, double* fit, int* rank, DevState* state,
                                int mode, cudaStream_t st);

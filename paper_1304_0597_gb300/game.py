@@ -35,7 +35,8 @@ class GameConfig(C.Structure):
         ("tournament_k", C.c_int32), ("p_crossover", C.c_float), ("p_mutation", C.c_float),
         ("sigma_mutation", C.c_float), ("elitism", C.c_int32), ("elite_mode", C.c_int32),
         ("error", C.c_int32), ("tmse_R", C.c_float), ("activation", C.c_int32),
-        ("init", C.c_int32), ("clamp_genes", C.c_int32), ("stop_error", C.c_double),
+        ("init", C.c_int32), ("clamp_genes", C.c_int32), ("immigrants", C.c_int32),
+        ("stop_error", C.c_double),
         ("seed", C.c_uint64), ("run", C.c_uint64), ("precision", C.c_int32),
         ("elite_rescore", C.c_int32), ("gene_planes", C.c_int32), ("surrogate_pool", C.c_int32),
         ("surrogate_steps", C.c_int32), ("surrogate_batch", C.c_int32), ("surrogate_lr", C.c_float),
@@ -84,6 +85,9 @@ def _load() -> C.CDLL:
         "game_get_expansion": (I32, [P, P, I64, I64]),
         "game_score": (I32, [P, P, I32, C.POINTER(D), C.POINTER(D), C.POINTER(D), C.POINTER(D)]),
         "game_get_state": (I32, [P, C.POINTER(I64), C.POINTER(I32)]),
+        "game_predict": (I32, [P, P, I32, P, I64, I32, P, I32]),
+        "game_save": (I32, [P, P, I64, C.POINTER(I64)]),
+        "game_load": (I32, [P, P, I64]),
         "game_get_timing": (I32, [P, C.POINTER(GameTiming)]),
         "game_set_timing": (I32, [P, I32]),
         "game_selftest_timeout": (I32, [P, I32, C.POINTER(I32)]),
@@ -247,6 +251,34 @@ class Game:
                     self.h)
         return dict(zip(("rmse", "accuracy", "completeness", "contamination"),
                         (x.value for x in v)))
+
+    def predict(self, genes, X) -> np.ndarray:
+        """Outputs of one chromosome on patterns X [n x F] (host arrays or CUDA tensors;
+        a CUDA X gives a CUDA result)."""
+        g = np.ascontiguousarray(genes, dtype=np.float32)
+        if hasattr(X, "is_cuda") and X.is_cuda:
+            import torch
+            Xd = X.contiguous()
+            out = torch.empty(Xd.shape[0], dtype=torch.float32, device=Xd.device)
+            self._check(lib.game_predict(self.h, g.ctypes.data, g.size, Xd.data_ptr(),
+                                         Xd.shape[0], Xd.shape[1], out.data_ptr(), 1), self.h)
+            return out
+        Xh = np.ascontiguousarray(X, dtype=np.float32)
+        out = np.empty(Xh.shape[0], dtype=np.float32)
+        self._check(lib.game_predict(self.h, g.ctypes.data, g.size, Xh.ctypes.data, Xh.shape[0],
+                                     Xh.shape[1], out.ctypes.data, 0), self.h)
+        return out
+
+    def save(self) -> bytes:
+        """Checkpoint of the GA state (population, fitness, ranking, generation)."""
+        n = C.c_int64(0)
+        self._check(lib.game_save(self.h, None, 0, C.byref(n)), self.h)
+        buf = C.create_string_buffer(n.value)
+        self._check(lib.game_save(self.h, buf, n.value, C.byref(n)), self.h)
+        return buf.raw
+
+    def load(self, data: bytes) -> None:
+        self._check(lib.game_load(self.h, data, len(data)), self.h)
 
     def state(self) -> tuple[int, int]:
         gen, stopped = C.c_int64(), C.c_int32()

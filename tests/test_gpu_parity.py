@@ -131,6 +131,8 @@ def test_initial_population_bit_exact(init):
     dict(pop=45, tournament_k=32, clamp_genes=False, sigma_mutation=0.7, p_mutation=0.5),
     dict(pop=1000, degree=6),
     dict(pop=600, degree=3, elitism=5),                       # counting rank, ragged blocks
+    dict(pop=64, immigrants=20),                              # random immigrants
+    dict(pop=50, immigrants=48, init="normal_pm1"),           # all non-elite slots immigrate
 ])
 def test_operators_bit_exact_given_fitness(kw):
     ds = synth.make_dataset(500, 5, kw.get("degree", 4), seed=2)
@@ -202,6 +204,57 @@ def test_evolve_is_resumable():
     assert b.evolve(4) == 4 and b.evolve(5) == 5
     np.testing.assert_array_equal(a.population(), b.population())
     assert a.state() == b.state() == (8, 0)
+
+
+# ------------------------------------------------------- predict / checkpoint
+
+@pytest.mark.parametrize("basis,F,d", [("chebyshev", 7, 4), ("trig", 5, 3), ("chebyshev", 3, 10)])
+@pytest.mark.parametrize("act", ["tanh", "linear"])
+def test_predict_matches_oracle(basis, F, d, act):
+    """A chromosome applied to new patterns (no data set on the context)."""
+    import torch
+    game = lib()
+    ds = synth.make_dataset(2501, F, d, basis, seed=61)
+    ocfg = _cfg(basis=basis, degree=d, activation=act)
+    g = game.Game(game_config(ocfg))
+    K = o.n_genes(basis, F, d)
+    genes = np.random.default_rng(3).uniform(-1, 1, size=K).astype(np.float32)
+    y = g.predict(genes, ds.X)
+    want = o.activate(o.outputs(o.expand(ds.X, basis, d), genes[None, :].astype(np.float64)),
+                      act)[0]
+    np.testing.assert_allclose(y, want, rtol=1e-6, atol=1e-6)
+    yd = g.predict(genes, torch.from_numpy(ds.X).cuda())
+    np.testing.assert_array_equal(yd.cpu().numpy(), y)
+    assert g.predict(genes, ds.X[:0]).shape == (0,)
+    with pytest.raises(game.GameError):
+        g.predict(genes[:-1], ds.X)
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(precision=1, gene_planes=1), dict(engine=2)])
+def test_checkpoint_resumes_exactly(kw):
+    """evolve 6, save, evolve 5 on one context == load into a fresh context, evolve 5:
+    same population, fitness and generation (random immigrants on)."""
+    game = lib()
+    ds = synth.make_dataset(3000, 6, 4, seed=62)
+    ocfg = _cfg(pop=64, degree=4, seed=5, immigrants=4)
+    a = make_game(ocfg, ds.X, ds.t, ds.n_train, **kw)
+    assert a.evolve(6) == 6
+    buf = a.save()
+    assert a.evolve(5) == 5
+    b = make_game(ocfg, ds.X, ds.t, ds.n_train, **kw)
+    b.load(buf)
+    assert b.evolve(5) == 5
+    np.testing.assert_array_equal(b.population(), a.population())
+    np.testing.assert_array_equal(b.fitness()[0], a.fitness()[0])
+    assert b.state() == a.state()
+    other = make_game(_cfg(pop=64, degree=4, seed=6, immigrants=4), ds.X, ds.t, ds.n_train, **kw)
+    with pytest.raises(game.GameError) as e:
+        other.load(buf)
+    assert e.value.status == -1
+    sur = make_game(ocfg, ds.X, ds.t, ds.n_train, surrogate_pool=2)
+    with pytest.raises(game.GameError) as e:
+        sur.save()
+    assert e.value.status == -8
 
 
 # -------------------------------------------------------------------- report

@@ -390,6 +390,38 @@ def test_elitism_keeps_top_and_best_never_worsens():
             np.testing.assert_array_equal(child[:2], G[[order[0], order[0]]])
 
 
+def test_immigrants_replace_the_last_children_with_fresh_draws():
+    """Immigrants: rows pop-I..pop-1 are replaced, every other row is the plain breed;
+    the new rows follow the init distribution (moments), differ between generations
+    and from generation 0, and elites survive (I <= pop - elitism)."""
+    rng = np.random.default_rng(31)
+    K, pop, I = 40, 300, 120
+    G = rng.uniform(-1, 1, size=(pop, K)).astype(np.float32)
+    fit = rng.random(pop)
+    base = o.Config(pop=pop, elitism=3, seed=9)
+    plain = o.breed(G, fit, base, 5)
+    imm = o.breed(G, fit, o.Config(pop=pop, elitism=3, seed=9, immigrants=I), 5)
+    np.testing.assert_array_equal(imm[:pop - I], plain[:pop - I])
+    new = imm[pop - I:]
+    assert not np.any(new == plain[pop - I:])
+    assert new.min() >= -1 and new.max() <= 1
+    assert abs(new.mean()) < 0.03 and abs(new.var() - 1 / 3) < 0.02          # U[-1, 1]
+    imm6 = o.breed(G, fit, o.Config(pop=pop, elitism=3, seed=9, immigrants=I), 6)
+    assert not np.any(imm6[pop - I:] == new)
+    g0 = o.init_population(o.Config(pop=pop, seed=9), K)
+    assert not np.any(g0[pop - I:] == new)
+    order = o.rank(fit)
+    np.testing.assert_array_equal(imm[:3], G[order[:3]])
+    u01 = o.breed(G, fit, o.Config(pop=pop, elitism=3, seed=9, immigrants=I, init="uniform_01"), 5)
+    assert u01[pop - I:].min() >= 0 and abs(u01[pop - I:].mean() - 0.5) < 0.02
+    nrm = o.breed(G, fit, o.Config(pop=pop, elitism=3, seed=9, immigrants=I, init="normal_pm1"), 5)
+    v = nrm[pop - I:]
+    # N(0, 0.5^2) truncated to [-1, 1] = +-2 sigma: std = 0.5 sqrt(1 - 4 phi(2) / (2 Phi(2) - 1))
+    from scipy import stats
+    sd = 0.5 * np.sqrt(1 - 4 * stats.norm.pdf(2) / (2 * stats.norm.cdf(2) - 1))
+    assert np.abs(v).max() <= 1 and abs(v.mean()) < 0.02 and abs(v.std() - sd) < 0.01
+
+
 def test_clamp_keeps_genes_in_range():
     G = np.full((50, 10), 0.99, dtype=np.float32)
     cfg = _cfg(pop=50, elitism=0, p_mutation=1.0, sigma_mutation=1.0)

@@ -58,6 +58,8 @@ enum { GAME_RMSE = 0, GAME_MSE = 1, GAME_TMSE = 2, GAME_TMSE_SQ = 3 };  /* error
 enum { GAME_TANH = 0, GAME_LINEAR = 1 };                          /* activation     */
 enum { GAME_INIT_UNIFORM_PM1 = 0, GAME_INIT_NORMAL_PM1 = 1, GAME_INIT_UNIFORM_01 = 2 };
 enum { GAME_ELITE_TOP = 0, GAME_ELITE_COPIES = 1 };               /* elitism reading */
+enum { GAME_COEF_PER_FEATURE = 0, GAME_COEF_SHARED = 1 };         /* eq.2 coefficients */
+enum { GAME_SEL_TOURNAMENT = 0, GAME_SEL_ROULETTE = 1, GAME_SEL_RANKING = 2 };   /* selection */
 enum { GAME_FP32 = 0, GAME_BF16 = 1, GAME_FP8 = 2 };              /* storage of P    */
 enum { GAME_ENGINE_AUTO = 0, GAME_ENGINE_TCGEN05 = 1, GAME_ENGINE_SIMT = 2 };
 
@@ -69,8 +71,13 @@ enum { GAME_ENGINE_AUTO = 0, GAME_ENGINE_TCGEN05 = 1, GAME_ENGINE_SIMT = 2 };
 typedef struct game_config {
   int32_t basis;          /* GAME_CHEBYSHEV | GAME_TRIG (polytrigo, eq.8)                 */
   int32_t degree;         /* d >= 1 (eq.1)                                                 */
+  int32_t coefficients;   /* GAME_COEF_PER_FEATURE: B*F*d+1 genes, one coefficient per feature
+                             and basis member; GAME_COEF_SHARED: B*d+1 genes shared by all
+                             features, the paper's eq.2 / eq.9 form (expansion summed over f) */
   int32_t pop;            /* chromosomes, 2..8192 (eq.6 gives B*N+1 as one choice)         */
   int32_t tournament_k;   /* tournament size, 1..32, draws with replacement               */
+  int32_t selection;      /* GAME_SEL_TOURNAMENT (k draws) | GAME_SEL_ROULETTE (weight
+                             1/(1e-12 + fitness)) | GAME_SEL_RANKING (linear ranking) (Sec. 2) */
   float p_crossover;      /* single-point crossover probability per pair                   */
   float p_mutation;       /* per-gene mutation probability                                 */
   float sigma_mutation;   /* std-dev of the Gaussian mutation step                          */

@@ -81,6 +81,8 @@ class Config:
     seed: int = 0
     run: int = 0                     # second Philox key word (independent runs)
     immigrants: int = 0              # random chromosomes replacing the last children
+    coefficients: str = "per_feature"  # "per_feature" | "shared" (eq.2 / eq.9)
+    selection: str = "tournament"    # "tournament" | "roulette" | "ranking"
 
 
 def basis_multiplier(basis: str) -> int:
@@ -88,9 +90,10 @@ def basis_multiplier(basis: str) -> int:
     return 2 if basis == TRIG else 1
 
 
-def n_genes(basis: str, n_features: int, degree: int) -> int:
-    """Genes per chromosome with per-feature coefficients: B*F*d + 1 (bias a0)."""
-    return basis_multiplier(basis) * n_features * degree + 1
+def n_genes(basis: str, n_features: int, degree: int, shared: bool = False) -> int:
+    """Genes per chromosome: B*F*d + 1 with per-feature coefficients, B*d + 1 when the
+    coefficients are shared by all features (eq.7 / eq.9: 2d + 1 for polytrigo)."""
+    return basis_multiplier(basis) * (1 if shared else n_features) * degree + 1
 
 
 # ---------------------------------------------------------------------------
@@ -123,11 +126,13 @@ def basis_value(basis: str, degree: int, b: int, x: np.ndarray) -> np.ndarray:
     return np.sin((b - degree + 1) * x)
 
 
-def expand(X: np.ndarray, basis: str, degree: int) -> np.ndarray:
+def expand(X: np.ndarray, basis: str, degree: int, shared: bool = False) -> np.ndarray:
     """Expansion matrix P [NP x K] (eq.1 written out per feature, eq.9 for polytrigo).
 
     Column 0 is the bias (a_0 multiplies 1); column 1 + f*B*d + b holds the
-    b-th basis member of feature f.
+    b-th basis member of feature f.  With shared coefficients (eq.2 / eq.9, one
+    a_j for every feature) column 1 + b is the sum over the features of the b-th
+    basis member.
     """
     X = np.asarray(X, dtype=np.float64)
     n, F = X.shape
@@ -137,6 +142,8 @@ def expand(X: np.ndarray, basis: str, degree: int) -> np.ndarray:
     for f in range(F):
         for b in range(Bd):
             P[:, 1 + f * Bd + b] = basis_value(basis, degree, b, X[:, f])
+    if shared:
+        return np.concatenate([P[:, :1], P[:, 1:].reshape(n, F, Bd).sum(axis=1)], axis=1)
     return P
 
 
@@ -420,6 +427,43 @@ def tournament(key, gen: int, pairs: np.ndarray, first_word: int, k: int,
     return best
 
 
+ROULETTE_EPS = 1e-12
+
+
+def selection_weights(fit: np.ndarray, cfg: Config) -> np.ndarray:
+    """Integer selection weights (Section 2: ranking and roulette selection).
+
+    roulette: w_c = 1 / (1e-12 + f_c) in float64, quantised q_c = floor(2^24 w_c / max w)
+    (fitness-proportionate selection for an error to minimise; NaN weighs 0);
+    ranking: linear ranking with expected values from 1.1 (best) to 0.9 (worst),
+    q = 9 (N - 1) + 2 (N - 1 - r) for rank position r.
+    Integers make the cumulative sums exact in any order of addition."""
+    fit = np.asarray(fit, dtype=np.float64)
+    pop = fit.shape[0]
+    if cfg.selection == "ranking":
+        q = np.empty(pop, dtype=np.uint64)
+        q[rank(fit)] = (_U64(9 * (pop - 1)) +
+                        _U64(2) * (_U64(pop - 1) - np.arange(pop, dtype=np.uint64)))
+        return q
+    w = np.where(np.isnan(fit), 0.0, 1.0 / (ROULETTE_EPS + np.where(np.isnan(fit), 0.0, fit)))
+    wmax = w.max() if pop else 0.0
+    if not wmax > 0:
+        return np.zeros(pop, dtype=np.uint64)
+    return np.floor(w / wmax * float(1 << 24)).astype(np.uint64)
+
+
+def wheel_draw(cum: np.ndarray, words: np.ndarray) -> np.ndarray:
+    """Parent of each 32-bit word: t = (u24 Q) >> 24 with u24 the top 24 bits and Q
+    the total weight; the first index whose inclusive cumulative weight exceeds t.
+    A zero total falls back to a uniform index draw."""
+    pop = cum.shape[0]
+    total = cum[-1]
+    if total == 0:
+        return index_draw(words, pop)
+    t = ((np.asarray(words, dtype=np.uint64) >> _U64(8)) * total) >> _U64(24)
+    return np.searchsorted(cum, t, side="right").astype(np.int64)
+
+
 def breed(G: np.ndarray, fit: np.ndarray, cfg: Config, gen: int) -> np.ndarray:
     """One application of the genetic operators: population ``gen`` -> ``gen + 1``.
 
@@ -447,8 +491,13 @@ def breed(G: np.ndarray, fit: np.ndarray, cfg: Config, gen: int) -> np.ndarray:
     if n_pairs == 0:
         return immigrate(out, cfg, gen)
     j = np.arange(n_pairs, dtype=np.uint64)
-    p1 = tournament(key, gen, j, 0, cfg.tournament_k, fit)
-    p2 = tournament(key, gen, j, cfg.tournament_k, cfg.tournament_k, fit)
+    if cfg.selection == "tournament":
+        p1 = tournament(key, gen, j, 0, cfg.tournament_k, fit)
+        p2 = tournament(key, gen, j, cfg.tournament_k, cfg.tournament_k, fit)
+    else:
+        cum = np.cumsum(selection_weights(fit, cfg), dtype=np.uint64)
+        p1 = wheel_draw(cum, philox_words(key, gen, j, STREAM_TOURNAMENT, 0))
+        p2 = wheel_draw(cum, philox_words(key, gen, j, STREAM_TOURNAMENT, 1))
     u_c = uniform24(philox_words(key, gen, j, STREAM_CROSSOVER, 0))
     cut = 1 + index_draw(philox_words(key, gen, j, STREAM_CROSSOVER, 1), max(K - 1, 1))
     do_x = (u_c < _F(cfg.p_crossover)) & (K >= 2)

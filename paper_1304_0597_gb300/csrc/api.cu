@@ -79,6 +79,7 @@ struct game_ctx {
   float* d_ring_x = nullptr;    // [ring_cap x kstride]
   float* d_ring_f = nullptr;    // [ring_cap]
   long long* d_dsq = nullptr;   // [pop_pad] squared rank differences of the monitor
+  unsigned long long* d_cum = nullptr;   // [pop_pad] roulette / ranking cumulative weights
   int* d_ring_meta = nullptr;   // head, count, evals appended, generations monitored
   int ring_cap = 0;
   float* d_norm = nullptr;      // mean, std of log fitness over the ring
@@ -207,6 +208,10 @@ static game_status validate(game_ctx* c, const game_config* cfg) {
     return fail(c, GAME_ERR_INVALID_ARG, "bad precision");
   if (cfg->engine < GAME_ENGINE_AUTO || cfg->engine > GAME_ENGINE_SIMT)
     return fail(c, GAME_ERR_INVALID_ARG, "bad engine");
+  if (cfg->coefficients < GAME_COEF_PER_FEATURE || cfg->coefficients > GAME_COEF_SHARED)
+    return fail(c, GAME_ERR_INVALID_ARG, "bad coefficients");
+  if (cfg->selection < GAME_SEL_TOURNAMENT || cfg->selection > GAME_SEL_RANKING)
+    return fail(c, GAME_ERR_INVALID_ARG, "bad selection");
   if (cfg->immigrants < 0 || cfg->immigrants > cfg->pop - (cfg->elitism < cfg->pop ? cfg->elitism : cfg->pop))
     return fail(c, GAME_ERR_INVALID_ARG, "immigrants must be in 0..pop - elitism");
   if ((cfg->tile_n != 0 && cfg->tile_n != 128 && cfg->tile_n != 256) || cfg->tile_stages < 0 ||
@@ -452,9 +457,10 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
                 "need n_patterns >= 1, n_features >= 1, 1 <= n_train <= n_patterns");
   cudaSetDevice(c->dev);
   const int B = c->cfg.basis == GAME_TRIG ? 2 : 1;
-  const long long kb = (long long)B * n_features * c->cfg.degree;
+  const int shared = c->cfg.coefficients == GAME_COEF_SHARED;
+  const long long kb = (long long)B * (shared ? 1 : n_features) * c->cfg.degree;
   if (kb > 4096)
-    return fail(c, GAME_ERR_UNSUPPORTED, "B*F*d = %lld basis columns exceeds 4096", kb);
+    return fail(c, GAME_ERR_UNSUPPORTED, "%lld basis columns exceed 4096", kb);
   free_all(c);
   Shape& s = c->s;
   s.n_patterns = n_patterns;
@@ -463,6 +469,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   s.degree = c->cfg.degree;
   s.basis = c->cfg.basis;
   s.bd = B * c->cfg.degree;
+  s.shared = shared;
   s.kb = (int)kb;
   s.kp = round_up(s.kb, c->cfg.precision == GAME_FP8 ? 32 : 16);
   s.n_genes = s.kb + 1;
@@ -541,6 +548,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   if ((r = dalloc(c, &c->p.glo, gpl)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_fit, sizeof(double) * s.pop_pad)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_rank, sizeof(int) * s.pop_pad)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_cum, sizeof(unsigned long long) * s.pop_pad)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_state, sizeof(DevState))) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_genes, sizeof(float) * (size_t)s.kstride)) != GAME_OK) return r;
   c->score_nb = score_blocks(n_patterns, c->n_sm);
@@ -658,6 +666,8 @@ static game_status enqueue_pre(game_ctx* c, cudaStream_t st) {
     pa.p_m = c->cfg.p_mutation;
     pa.sigma = c->cfg.sigma_mutation;
     const int e = std::min(c->cfg.elitism, c->s.pop);
+    pa.cum = c->cfg.selection != GAME_SEL_TOURNAMENT ? c->d_cum : nullptr;
+    CUDA_OK(c, launch_selection_weights(c->cfg, c->s, c->d_fit, c->d_rank, c->d_cum, st));
     CUDA_OK(c, launch_pool_breed(pa, st));
     CUDA_OK(c, c->sg.forward(c->d_pool, c->s.kstride, c->n_pool, c->d_score, st));
     CUDA_OK(c, launch_select(c->d_score, c->n_pool, c->s.pop - e, c->d_sel, c->d_state,
@@ -667,7 +677,7 @@ static game_status enqueue_pre(game_ctx* c, cudaStream_t st) {
                                c->d_pred, st));
     CUDA_OK(c, launch_immigrants(c->s, c->cfg, c->p, c->d_state, st));
   } else {
-    CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 1 | 2, st));
+    CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 1 | 2, st, c->d_cum));
   }
   CUDA_OK(c, launch_prepare(c->s, c->p, c->e, c->d_state, 1 | 2, st));
   return GAME_OK;
@@ -861,7 +871,7 @@ extern "C" game_status game_evaluate(game_ctx* c, double* fitness, int32_t* rank
   if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
   cudaSetDevice(c->dev);
   // A breed launch with allow = 0 records "not bred" for this evaluation.
-  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 0, c->st));
+  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 0, c->st, c->d_cum));
   CUDA_OK(c, launch_prepare(c->s, c->p, c->e, c->d_state, 0, c->st));
   game_status r = launch_fitness(c, nullptr);
   if (r != GAME_OK) return r;
@@ -909,7 +919,7 @@ extern "C" game_status game_breed(game_ctx* c, const double* fitness) {
     CUDA_OK(c, cudaStreamSynchronize(c->st));
     if (!hs.evaluated) return fail(c, GAME_ERR_STATE, "population not evaluated; pass a fitness vector");
   }
-  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 1, c->st));
+  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 1, c->st, c->d_cum));
   CUDA_OK(c, launch_state_op(c->d_state, kStateAfterBreed, c->st));
   CUDA_OK(c, cudaStreamSynchronize(c->st));
   return GAME_OK;
@@ -1042,10 +1052,10 @@ extern "C" game_status game_predict(game_ctx* c, const float* genes, int32_t n_g
                                     int32_t device_ptrs) {
   if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
   const int B = c->cfg.basis == GAME_TRIG ? 2 : 1;
-  if (!genes || !X || !out || n < 0 || n_features < 1 ||
-      n_genes != B * n_features * c->cfg.degree + 1)
-    return fail(c, GAME_ERR_INVALID_ARG, "genes must hold B*F*d+1 = %d values for F = %d",
-                B * n_features * c->cfg.degree + 1, n_features);
+  const int shared = c->cfg.coefficients == GAME_COEF_SHARED;
+  const int want = B * (shared ? 1 : n_features) * c->cfg.degree + 1;
+  if (!genes || !X || !out || n < 0 || n_features < 1 || n_genes != want)
+    return fail(c, GAME_ERR_INVALID_ARG, "genes must hold %d values for F = %d", want, n_features);
   if (n == 0) return GAME_OK;
   cudaSetDevice(c->dev);
   float *dg = nullptr, *dX = nullptr, *dy = nullptr;
@@ -1070,7 +1080,7 @@ extern "C" game_status game_predict(game_ctx* c, const float* genes, int32_t n_g
     dy = out;
   }
   if (e == cudaSuccess)
-    e = launch_predict(dX, n, n_features, dg, n_genes, c->cfg.basis, c->cfg.degree,
+    e = launch_predict(dX, n, n_features, dg, n_genes, c->cfg.basis, c->cfg.degree, shared,
                        c->cfg.activation, dy, c->st);
   if (e == cudaSuccess && !device_ptrs)
     e = cudaMemcpyAsync(out, dy, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, c->st);
@@ -1238,7 +1248,7 @@ extern "C" game_status game_autotune(game_ctx* c, int32_t reps, game_tile* best,
   if (reps < 1) reps = 1;
   cudaSetDevice(c->dev);
   // Operand planes of the current population.
-  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 0, c->st));
+  CUDA_OK(c, launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 0, c->st, c->d_cum));
   CUDA_OK(c, launch_prepare(c->s, c->p, c->e, c->d_state, 0, c->st));
   int n_done = 0;
   game_tile bt;
@@ -1702,7 +1712,7 @@ extern "C" game_status game_batch_autotune(game_batch* b, int32_t reps, int32_t*
   cudaSetDevice(b->dev);
   for (game_ctx* c : b->runs) {
     if (!c->have_data) return bfail(b, GAME_ERR_STATE, "every run of the batch needs data first");
-    if (launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 0, b->st) != cudaSuccess ||
+    if (launch_breed(c->s, c->cfg, c->p, c->d_fit, c->d_rank, c->d_state, 0, b->st, c->d_cum) != cudaSuccess ||
         launch_prepare(c->s, c->p, c->e, c->d_state, 0, b->st) != cudaSuccess)
       return bfail(b, GAME_ERR_CUDA, "operand preparation");
   }

@@ -72,7 +72,7 @@ __device__ __forceinline__ void basis_values(int basis, int d, float x, Emit emi
 struct ExpArgs {
   const float* X;
   long long n;
-  int F, d, basis, bd, kb, kp, precision;
+  int F, d, basis, bd, kb, kp, precision, shared;
   void* p0;
   void* p1;
   const float* colscale;
@@ -141,6 +141,44 @@ __global__ void expand_kernel(ExpArgs a) {
   }
 }
 
+// Shared coefficients (the paper's eq.2 / eq.9 form): column b of pattern k is the
+// sum over the features of the b-th basis value, the float32 values of the
+// per-feature expansion added in float64 and rounded once.
+__device__ __forceinline__ float shared_value(const ExpArgs& a, long long k, int b) {
+  double acc = 0.0;
+  const float* x = a.X + k * a.F;
+  for (int f = 0; f < a.F; ++f)
+    basis_values(a.basis, a.d, x[f], [&](int bb, float v) {
+      if (bb == b) acc += (double)v;
+    });
+  return (float)acc;
+}
+
+__global__ void expand_shared_colmax_kernel(ExpArgs a) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n * a.kb) return;
+  const int b = (int)(i % a.kb);
+  atomicMax(a.colmax_bits + b, __float_as_uint(fabsf(shared_value(a, i / a.kb, b))));
+}
+
+__global__ void expand_shared_kernel(ExpArgs a) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n * a.kp) return;
+  const long long k = i / a.kp;
+  const int b = (int)(i % a.kp);
+  const float v = b < a.kb ? shared_value(a, k, b) : 0.0f;
+  const long long o = k * a.kp + b;
+  if (a.precision == GAME_FP32) {
+    const __half h = __float2half_rn(v);
+    ((__half*)a.p0)[o] = h;
+    ((__half*)a.p1)[o] = __float2half_rn(__fsub_rn(v, __half2float(h)));
+  } else if (a.precision == GAME_BF16) {
+    ((__nv_bfloat16*)a.p0)[o] = __float2bfloat16_rn(b < a.kb ? v / a.colscale[b] : 0.0f);
+  } else {
+    ((__nv_fp8_e4m3*)a.p0)[o] = __nv_fp8_e4m3(b < a.kb ? v / a.colscale[b] : 0.0f);
+  }
+}
+
 __global__ void target_coef_kernel(const float* t, float* c, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) c[i] = 2.8853900817779268f * t[i];   // 2 log2(e) t
@@ -172,7 +210,24 @@ cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax
   a.p1 = e.p1;
   a.colscale = e.colscale;
   a.colmax_bits = reinterpret_cast<unsigned int*>(qmax_scratch);
+  a.shared = s.shared;
   const int threads = 256;
+  if (s.shared) {
+    // one thread per (pattern, column); F * d basis evaluations each (small in this form)
+    if (s.precision == GAME_FP32) {
+      fill_ones_kernel<<<(s.kp + 255) / 256, 256, 0, st>>>(e.colscale, s.kp);
+    } else {
+      cudaError_t err = cudaMemsetAsync(qmax_scratch, 0, sizeof(float) * s.kp, st);
+      if (err != cudaSuccess) return err;
+      const long long nc = s.n_patterns * s.kb;
+      expand_shared_colmax_kernel<<<(unsigned)((nc + threads - 1) / threads), threads, 0, st>>>(a);
+      expand_scale_kernel<<<(s.kp + 255) / 256, 256, 0, st>>>(
+          a.colmax_bits, e.colscale, s.kb, s.kp, s.precision == GAME_BF16 ? 1.0f : 448.0f);
+    }
+    const long long ns = s.n_patterns * s.kp;
+    expand_shared_kernel<<<(unsigned)((ns + threads - 1) / threads), threads, 0, st>>>(a);
+    return cudaGetLastError();
+  }
   const long long n = s.n_patterns * s.n_features;
   const unsigned blocks = (unsigned)((n + threads - 1) / threads);
   if (s.precision == GAME_FP32) {
@@ -220,13 +275,14 @@ cudaError_t launch_expand_get(const Shape& s, const ExpDev& e, long long row0, l
 // ---------------------------------------------------------------------------
 // Prediction on new patterns (the paper's test / run use of a trained
 // chromosome): Out(x) = a_0 + sum_f sum_b g[1 + f B d + b] g_b(x_f) (eq.2, eq.8,
-// eq.9 with per-feature coefficients), then the activation.  One thread per
+// eq.9 with per-feature coefficients; g[1 + b] for every f when shared), then the
+// activation.  One thread per
 // pattern; the expansion is computed on the fly in float64 (Chebyshev
 // recurrence; cos / sin of (b+1) x by angle addition from one sincos).
 // ---------------------------------------------------------------------------
 __global__ void predict_kernel(const float* __restrict__ X, long long n, int F,
                                const float* __restrict__ genes, int K, int basis, int degree,
-                               int activation, float* __restrict__ out) {
+                               int shared, int activation, float* __restrict__ out) {
   extern __shared__ float gs[];
   for (int i = threadIdx.x; i < K; i += blockDim.x) gs[i] = genes[i];
   __syncthreads();
@@ -237,7 +293,7 @@ __global__ void predict_kernel(const float* __restrict__ X, long long n, int F,
   if (basis == GAME_CHEBYSHEV) {
     for (int f = 0; f < F; ++f) {
       const double v = (double)x[f];
-      const float* g = gs + 1 + f * degree;
+      const float* g = gs + 1 + (shared ? 0 : f * degree);
       double tm = 1.0, t = v;                     // T_0, T_1
       for (int b = 0; b < degree; ++b) {
         s = fma((double)g[b], t, s);
@@ -249,7 +305,7 @@ __global__ void predict_kernel(const float* __restrict__ X, long long n, int F,
   } else {
     for (int f = 0; f < F; ++f) {
       const double v = (double)x[f];
-      const float* g = gs + 1 + f * 2 * degree;
+      const float* g = gs + 1 + (shared ? 0 : f * 2 * degree);
       double s1, c1;
       sincos(v, &s1, &c1);
       double c = c1, sn = s1;                     // cos((b+1) v), sin((b+1) v)
@@ -266,11 +322,12 @@ __global__ void predict_kernel(const float* __restrict__ X, long long n, int F,
 }
 
 cudaError_t launch_predict(const float* X, long long n, int F, const float* genes, int K,
-                           int basis, int degree, int activation, float* out, cudaStream_t st) {
+                           int basis, int degree, int shared, int activation, float* out,
+                           cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int threads = 256;
   predict_kernel<<<(unsigned)((n + threads - 1) / threads), threads, sizeof(float) * K, st>>>(
-      X, n, F, genes, K, basis, degree, activation, out);
+      X, n, F, genes, K, basis, degree, shared, activation, out);
   return cudaGetLastError();
 }
 

@@ -91,6 +91,7 @@ struct BreedArgs {
   float* out_1;
   const double* fit;
   const int* rank;
+  const unsigned long long* cum;   // roulette / ranking cumulative weights, or nullptr
   DevState* state;
   Key key;
   int pop, n_genes, kstride;
@@ -117,8 +118,8 @@ __global__ void breed_kernel(BreedArgs a) {
 
   if (warp < n_pairs) {
     const int slot_a = e + 2 * warp, slot_b = slot_a + 1;
-    breed_pair(G, a.kstride, K, a.pop, a.fit, a.key, gen, (uint64_t)warp, a.tournament_k, a.p_c,
-               a.p_m, a.sigma, a.clamp, out + (long long)slot_a * a.kstride,
+    breed_pair(G, a.kstride, K, a.pop, a.fit, a.cum, a.key, gen, (uint64_t)warp, a.tournament_k,
+               a.p_c, a.p_m, a.sigma, a.clamp, out + (long long)slot_a * a.kstride,
                out + (long long)slot_b * a.kstride, slot_b < a.pop, lane);
   } else if (warp < n_pairs + e) {
     const int slot = warp - n_pairs;
@@ -129,10 +130,82 @@ __global__ void breed_kernel(BreedArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Roulette and ranking selection (Section 2): integer weights (so that the
+// cumulative sums are exact in any order of addition) and their inclusive
+// prefix sums, one CTA.
+//   roulette: w_c = 1 / (1e-12 + f_c) (float64, correctly rounded), NaN -> 0,
+//             q_c = floor(2^24 w_c / max w);
+//   ranking:  q = 9 (N - 1) + 2 (N - 1 - r) at rank position r (linear ranking,
+//             expected values 1.1 best to 0.9 worst).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) selection_weights_kernel(const double* fit,
+                                                                 const int* rank, int pop,
+                                                                 int mode,
+                                                                 unsigned long long* cum) {
+  __shared__ double wred[1024];
+  __shared__ unsigned long long part[1024];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (mode == GAME_SEL_RANKING) {
+    for (int r = tid; r < pop; r += nt)
+      cum[rank[r]] = 9ull * (unsigned long long)(pop - 1) + 2ull * (unsigned long long)(pop - 1 - r);
+  } else {
+    double m = 0.0;
+    for (int c = tid; c < pop; c += nt) {
+      const double f = fit[c];
+      const double w = isnan(f) ? 0.0 : 1.0 / (1e-12 + f);
+      if (w > m) m = w;
+    }
+    wred[tid] = m;
+    __syncthreads();
+    for (int o = nt >> 1; o > 0; o >>= 1) {
+      if (tid < o && wred[tid + o] > wred[tid]) wred[tid] = wred[tid + o];
+      __syncthreads();
+    }
+    const double wmax = wred[0];
+    for (int c = tid; c < pop; c += nt) {
+      const double f = fit[c];
+      const double w = isnan(f) ? 0.0 : 1.0 / (1e-12 + f);
+      cum[c] = wmax > 0.0 ? (unsigned long long)floor(w / wmax * 16777216.0) : 0ull;
+    }
+  }
+  __syncthreads();
+  // inclusive prefix sums: each thread a contiguous chunk, then a scan of the chunk totals
+  const int chunk = (pop + nt - 1) / nt;
+  const int b0 = min(pop, tid * chunk), b1 = min(pop, b0 + chunk);
+  unsigned long long sum = 0;
+  for (int i = b0; i < b1; ++i) sum += cum[i];
+  part[tid] = sum;
+  __syncthreads();
+  for (int o = 1; o < nt; o <<= 1) {
+    const unsigned long long v = tid >= o ? part[tid - o] : 0ull;
+    __syncthreads();
+    part[tid] += v;
+    __syncthreads();
+  }
+  unsigned long long run = part[tid] - sum;
+  for (int i = b0; i < b1; ++i) {
+    run += cum[i];
+    cum[i] = run;
+  }
+}
+
+cudaError_t launch_selection_weights(const game_config& cfg, const Shape& s, const double* fit,
+                                     const int* rank, unsigned long long* cum, cudaStream_t st) {
+  if (cfg.selection == GAME_SEL_TOURNAMENT) return cudaSuccess;
+  selection_weights_kernel<<<1, 1024, 0, st>>>(fit, rank, s.pop, cfg.selection, cum);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_breed(const Shape& s, const game_config& cfg, const PopDev& p,
                          const double* fit, const int* rank, DevState* state, int allow,
-                         cudaStream_t st) {
+                         cudaStream_t st, unsigned long long* cum) {
+  if ((allow & 1) && cfg.selection != GAME_SEL_TOURNAMENT) {
+    cudaError_t e = launch_selection_weights(cfg, s, fit, rank, cum, st);
+    if (e != cudaSuccess) return e;
+  }
   BreedArgs a;
+  a.cum = cfg.selection != GAME_SEL_TOURNAMENT ? cum : nullptr;
   a.g32_0 = p.g32[0];
   a.g32_1 = p.g32[1];
   a.out_0 = p.g32[0];

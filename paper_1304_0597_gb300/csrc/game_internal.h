@@ -48,7 +48,8 @@ struct Shape {
   int degree;             // d
   int basis;              // GAME_CHEBYSHEV | GAME_TRIG
   int bd;                 // basis columns per feature: B*d
-  int kb;                 // basis columns in total: F*B*d  (= n_genes - 1)
+  int shared;             // coefficients shared by all features (expansion summed over f)
+  int kb;                 // basis columns in total: F*B*d, or B*d when shared (= n_genes - 1)
   int kp;                 // stored columns of P / of the gene planes (kb padded)
   int n_genes;            // kb + 1
   int kstride;            // row stride of the float32 gene buffers (n_genes padded to 4)
@@ -90,7 +91,8 @@ cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax
                           cudaStream_t st);
 // Outputs of one chromosome on n new patterns X [n x F] (device buffers).
 cudaError_t launch_predict(const float* X, long long n, int F, const float* genes, int K,
-                           int basis, int degree, int activation, float* out, cudaStream_t st);
+                           int basis, int degree, int shared, int activation, float* out,
+                           cudaStream_t st);
 cudaError_t launch_expand_get(const Shape& s, const ExpDev& e, long long row0, long long nrows,
                               float* out, cudaStream_t st);
 cudaError_t launch_target_coef(const float* t, float* c, long long n, cudaStream_t st);
@@ -99,7 +101,11 @@ cudaError_t launch_init_population(const Shape& s, int init_mode, uint64_t seed,
                                    float* g32, cudaStream_t st);
 cudaError_t launch_breed(const Shape& s, const game_config& cfg, const PopDev& p,
                          const double* fit, const int* rank, DevState* state, int allow,
-                         cudaStream_t st);
+                         cudaStream_t st, unsigned long long* cum);
+// Roulette / ranking: cumulative integer weights of the current fitness (no-op
+// for tournament selection).
+cudaError_t launch_selection_weights(const game_config& cfg, const Shape& s, const double* fit,
+                                     const int* rank, unsigned long long* cum, cudaStream_t st);
 // use_bred_flag: bit 0 = read the bred buffer when this generation bred, bit 1 =
 // inside game_evolve (skip when stopped).  rows (optional): row i of the planes
 // takes chromosome rows[i] of src (default: p's own population buffers).

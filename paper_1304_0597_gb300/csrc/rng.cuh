@@ -187,33 +187,64 @@ __device__ __forceinline__ void shift_words(uint32_t w[16], int o) {
   }
 }
 
-// One child pair j (one warp): two tournaments of k draws with replacement
-// (winner = min (fitness, index)), single-point crossover with probability p_c
+// One child pair j (one warp): two parents by tournaments of k draws with
+// replacement (winner = min (fitness, index)), or by roulette / ranking draws on
+// cum when given; single-point crossover with probability p_c
 // (cut in [1, K-1]), per-gene Gaussian mutation with probability p_m, clamp.
 // Child a goes to oa, child b to ob (when has_b).
-__device__ __forceinline__ void breed_pair(const float* __restrict__ G, int kstride, int K, int pop,
-                                           const double* fit, Key key, uint64_t gen, uint64_t j,
-                                           int tk, float p_c, float p_m, float sigma, int clamp,
-                                           float* oa, float* ob, bool has_b, int lane) {
-  double bf0 = CUDART_INF, bf1 = CUDART_INF;
-  int bi0 = 0x7fffffff, bi1 = 0x7fffffff;
-  for (int i = lane; i < 2 * tk; i += 32) {
-    const int idx = index_draw(philox_word(key, gen, j, kStreamTournament, (uint64_t)i), pop);
-    const double f = fit_key(fit, idx);
-    if (i < tk) {
-      if (better(f, idx, bf0, bi0)) { bf0 = f; bi0 = idx; }
-    } else {
-      if (better(f, idx, bf1, bi1)) { bf1 = f; bi1 = idx; }
-    }
+// Roulette / ranking draw on inclusive cumulative integer weights cum[0..pop):
+// t = (u24 Q) >> 24 with u24 the word's top 24 bits and Q = cum[pop-1]; the first
+// index whose cumulative weight exceeds t.  A zero total draws uniformly.
+__device__ __forceinline__ int wheel_draw(const unsigned long long* __restrict__ cum, int pop,
+                                          uint32_t w) {
+  const unsigned long long total = cum[pop - 1];
+  if (total == 0ull) return index_draw(w, pop);
+  const unsigned long long t = ((unsigned long long)(w >> 8) * total) >> 24;
+  int lo = 0, hi = pop - 1;   // cum[hi] = total > t
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cum[mid] > t)
+      hi = mid;
+    else
+      lo = mid + 1;
   }
+  return lo;
+}
+
+__device__ __forceinline__ void breed_pair(const float* __restrict__ G, int kstride, int K, int pop,
+                                           const double* fit, const unsigned long long* cum,
+                                           Key key, uint64_t gen, uint64_t j, int tk, float p_c,
+                                           float p_m, float sigma, int clamp, float* oa, float* ob,
+                                           bool has_b, int lane) {
+  int bi0, bi1;
+  if (cum) {
+    // roulette / ranking: lane 0 draws the first parent, lane 1 the second
+    int mine = 0;
+    if (lane < 2) mine = wheel_draw(cum, pop, philox_word(key, gen, j, kStreamTournament, lane));
+    bi0 = __shfl_sync(0xffffffffu, mine, 0);
+    bi1 = __shfl_sync(0xffffffffu, mine, 1);
+  } else {
+    double bf0 = CUDART_INF, bf1 = CUDART_INF;
+    bi0 = 0x7fffffff;
+    bi1 = 0x7fffffff;
+    for (int i = lane; i < 2 * tk; i += 32) {
+      const int idx = index_draw(philox_word(key, gen, j, kStreamTournament, (uint64_t)i), pop);
+      const double f = fit_key(fit, idx);
+      if (i < tk) {
+        if (better(f, idx, bf0, bi0)) { bf0 = f; bi0 = idx; }
+      } else {
+        if (better(f, idx, bf1, bi1)) { bf1 = f; bi1 = idx; }
+      }
+    }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double f0 = __shfl_xor_sync(0xffffffffu, bf0, o);
-    const int i0 = __shfl_xor_sync(0xffffffffu, bi0, o);
-    const double f1 = __shfl_xor_sync(0xffffffffu, bf1, o);
-    const int i1 = __shfl_xor_sync(0xffffffffu, bi1, o);
-    if (better(f0, i0, bf0, bi0)) { bf0 = f0; bi0 = i0; }
-    if (better(f1, i1, bf1, bi1)) { bf1 = f1; bi1 = i1; }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double f0 = __shfl_xor_sync(0xffffffffu, bf0, o);
+      const int i0 = __shfl_xor_sync(0xffffffffu, bi0, o);
+      const double f1 = __shfl_xor_sync(0xffffffffu, bf1, o);
+      const int i1 = __shfl_xor_sync(0xffffffffu, bi1, o);
+      if (better(f0, i0, bf0, bi0)) { bf0 = f0; bi0 = i0; }
+      if (better(f1, i1, bf1, bi1)) { bf1 = f1; bi1 = i1; }
+    }
   }
   uint32_t wc, wk;   // crossover decision and cut: words 0 and 1 of one block
   philox_word_pair(key, gen, j, kStreamCrossover, 0, &wc, &wk);

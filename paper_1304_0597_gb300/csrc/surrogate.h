@@ -92,6 +92,7 @@ struct PoolArgs {
   float* pool;              // [n_pool x kstride] children
   const double* fit;
   const int* rank;
+  const unsigned long long* cum;   // roulette / ranking cumulative weights, or nullptr
   DevState* state;
   uint64_t k0, k1;
   int pop, n_genes, kstride, n_pool, tournament_k, clamp;

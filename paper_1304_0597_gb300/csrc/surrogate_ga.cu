@@ -29,7 +29,7 @@ __global__ void pool_breed_kernel(PoolArgs a) {
   if (warp >= n_pairs) return;
   const float* G = st->cur ? a.g32_1 : a.g32_0;
   const int sa = 2 * warp, sb = sa + 1;
-  breed_pair(G, a.kstride, a.n_genes, a.pop, a.fit, Key{a.k0, a.k1}, (uint64_t)st->gen,
+  breed_pair(G, a.kstride, a.n_genes, a.pop, a.fit, a.cum, Key{a.k0, a.k1}, (uint64_t)st->gen,
              (uint64_t)warp, a.tournament_k, a.p_c, a.p_m, a.sigma, a.clamp,
              a.pool + (long long)sa * a.kstride, a.pool + (long long)sb * a.kstride, sb < a.n_pool,
              lane);

@@ -26,13 +26,16 @@ TANH, LINEAR = 0, 1
 INIT_UNIFORM_PM1, INIT_NORMAL_PM1, INIT_UNIFORM_01 = 0, 1, 2
 ELITE_TOP, ELITE_COPIES = 0, 1
 FP32, BF16, FP8 = 0, 1, 2
+COEF_PER_FEATURE, COEF_SHARED = 0, 1
+SEL_TOURNAMENT, SEL_ROULETTE, SEL_RANKING = 0, 1, 2
 ENGINE_AUTO, ENGINE_TCGEN05, ENGINE_SIMT = 0, 1, 2
 
 
 class GameConfig(C.Structure):
     _fields_ = [
-        ("basis", C.c_int32), ("degree", C.c_int32), ("pop", C.c_int32),
-        ("tournament_k", C.c_int32), ("p_crossover", C.c_float), ("p_mutation", C.c_float),
+        ("basis", C.c_int32), ("degree", C.c_int32), ("coefficients", C.c_int32),
+        ("pop", C.c_int32), ("tournament_k", C.c_int32), ("selection", C.c_int32),
+        ("p_crossover", C.c_float), ("p_mutation", C.c_float),
         ("sigma_mutation", C.c_float), ("elitism", C.c_int32), ("elite_mode", C.c_int32),
         ("error", C.c_int32), ("tmse_R", C.c_float), ("activation", C.c_int32),
         ("init", C.c_int32), ("clamp_genes", C.c_int32), ("immigrants", C.c_int32),

@@ -30,7 +30,10 @@ def game_config(ocfg: o.Config, **kw):
         error=_ERR[ocfg.error], tmse_R=ocfg.tmse_R,
         activation=game.TANH if ocfg.activation == "tanh" else game.LINEAR,
         init=_INIT[ocfg.init], clamp_genes=int(ocfg.clamp_genes), stop_error=ocfg.stop_error,
-        seed=ocfg.seed, run=ocfg.run, immigrants=ocfg.immigrants)
+        seed=ocfg.seed, run=ocfg.run, immigrants=ocfg.immigrants,
+        coefficients=game.COEF_SHARED if ocfg.coefficients == "shared" else game.COEF_PER_FEATURE,
+        selection={"tournament": game.SEL_TOURNAMENT, "roulette": game.SEL_ROULETTE,
+                   "ranking": game.SEL_RANKING}[ocfg.selection])
     for k, v in kw.items():
         setattr(cfg, k, v)
     return cfg

@@ -133,6 +133,8 @@ def test_initial_population_bit_exact(init):
     dict(pop=600, degree=3, elitism=5),                       # counting rank, ragged blocks
     dict(pop=64, immigrants=20),                              # random immigrants
     dict(pop=50, immigrants=48, init="normal_pm1"),           # all non-elite slots immigrate
+    dict(pop=80, selection="roulette"),                       # Section 2 selection criteria
+    dict(pop=600, degree=3, selection="ranking"),             # ranking on the counting path
 ])
 def test_operators_bit_exact_given_fitness(kw):
     ds = synth.make_dataset(500, 5, kw.get("degree", 4), seed=2)
@@ -204,6 +206,71 @@ def test_evolve_is_resumable():
     assert b.evolve(4) == 4 and b.evolve(5) == 5
     np.testing.assert_array_equal(a.population(), b.population())
     assert a.state() == b.state() == (8, 0)
+
+
+# ------------------------------------------------ shared coefficients (eq.9)
+
+@pytest.mark.parametrize("basis", ["trig", "chebyshev"])
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("engine", ["tcgen05", "simt"])
+def test_shared_coefficients_fitness(basis, prec, engine):
+    """The paper's eq.2 / eq.9 form: B*d + 1 genes shared by all features; the stored
+    expansion sums every basis member over the features."""
+    game = lib()
+    ds = synth.make_dataset(4001, 11, 4, basis, seed=63)
+    ocfg = _cfg(basis=basis, degree=4, pop=160, coefficients="shared", seed=2)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=prec, elite_rescore=0,
+                  engine=game.ENGINE_TCGEN05 if engine == "tcgen05" else game.ENGINE_SIMT)
+    K = o.n_genes(basis, 11, 4, shared=True)
+    assert g.n_genes == K
+    P = o.expand(ds.X, basis, 4, shared=True)
+    got = g.expansion(0, ds.n_patterns)
+    if prec == 0:
+        np.testing.assert_allclose(got, P[:, 1:], rtol=0, atol=11 * 6e-7)
+        fit, _ = g.evaluate()
+        np.testing.assert_allclose(fit, o.fitness(P[:ds.n_train], ds.t[:ds.n_train],
+                                                  g.population(), ocfg), rtol=FIT_RTOL)
+    else:
+        Q, sc = o.quantize_columns(P[:, 1:], "bf16")
+        np.testing.assert_allclose(got, o.dequantize_columns(Q, sc), rtol=0,
+                                   atol=np.abs(P[:, 1:]).max() * 2.0 ** -8)
+        fit, _ = g.evaluate()
+        Pq = np.concatenate([np.ones((ds.n_train, 1)),
+                             o.dequantize_columns(Q[:ds.n_train], sc)], axis=1)
+        Gq = o.quantize_genes(g.population(), sc, "bf16", 2) if engine == "tcgen05" \
+            else g.population()
+        np.testing.assert_allclose(fit, o.fitness(Pq, ds.t[:ds.n_train], Gq, ocfg), rtol=1e-5)
+    genes = g.population()[0]
+    np.testing.assert_allclose(g.predict(genes, ds.X[:500]),
+                               o.activate(o.outputs(P[:500], genes[None, :]), "tanh")[0],
+                               rtol=1e-6, atol=1e-6)
+
+
+def test_paper_configuration_trajectory():
+    """Section 5's setting on a KB-shaped set (11 features, 0/1 targets): polytrigo with
+    shared coefficients, linear Out, TMSE with R = 0.49, roulette selection, normal init,
+    p_c 0.9, p_m 0.2, elitism 2, random immigrants: fitness against the oracle, and the
+    oracle's operators fed the GPU's fitness reproduce the GPU population bit for bit."""
+    ds = synth.make_dataset(2100, 11, 4, "trig", seed=64)
+    t01 = ((ds.t + 1) / 2).astype(np.float32)
+    ocfg = _cfg(basis="trig", degree=4, pop=23, coefficients="shared", activation="linear",
+                error="tmse", tmse_R=0.49, selection="roulette", init="normal_pm1",
+                p_mutation=0.2, tournament_k=4, immigrants=3, seed=11)
+    g = make_game(ocfg, ds.X, t01, ds.n_train)
+    P = o.expand(ds.X[:ds.n_train], "trig", 4, shared=True)
+    G = g.population()
+    np.testing.assert_array_equal(G, o.init_population(ocfg, g.n_genes))
+    for gen in range(8):
+        fit, _ = g.evaluate()
+        want_fit = o.fitness(P, t01[:ds.n_train], G, ocfg)
+        # TMSE drops patterns with |t - Out| <= R: a pattern within float32 rounding of R
+        # can fall on either side (one flip moves the fitness by ~1.6e-4 here)
+        rel = np.abs(fit - want_fit) / np.maximum(want_fit, 1e-300)
+        assert np.mean(rel <= FIT_RTOL) >= 0.95 and rel.max() <= 2e-3
+        g.breed(None)
+        want = o.breed(G, fit, ocfg, gen)
+        G = g.population()
+        np.testing.assert_array_equal(G, want)
 
 
 # ------------------------------------------------------- predict / checkpoint

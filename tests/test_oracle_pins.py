@@ -159,6 +159,15 @@ def test_tied_genes_equal_paper_shared_polytrigo():
     tied = np.concatenate([[v[0]], np.tile(v[1:], F)])
     np.testing.assert_allclose(o.outputs(o.expand(X, "trig", d), tied[None, :])[0], want,
                                atol=1e-13)
+    # the shared-coefficient expansion carries the paper's form with 2d + 1 genes
+    assert o.n_genes("trig", F, d, shared=True) == 2 * d + 1
+    np.testing.assert_allclose(o.outputs(o.expand(X, "trig", d, shared=True), v[None, :])[0],
+                               want, atol=1e-13)
+    cheb = rng.uniform(-1, 1, size=d + 1)
+    tied_c = np.concatenate([[cheb[0]], np.tile(cheb[1:], F)])
+    np.testing.assert_allclose(
+        o.outputs(o.expand(X, "chebyshev", d, shared=True), cheb[None, :])[0],
+        o.outputs(o.expand(X, "chebyshev", d), tied_c[None, :])[0], atol=1e-13)
 
 
 # ------------------------------------------------------------------ errors
@@ -420,6 +429,39 @@ def test_immigrants_replace_the_last_children_with_fresh_draws():
     from scipy import stats
     sd = 0.5 * np.sqrt(1 - 4 * stats.norm.pdf(2) / (2 * stats.norm.cdf(2) - 1))
     assert np.abs(v).max() <= 1 and abs(v.mean()) < 0.02 and abs(v.std() - sd) < 0.01
+
+
+def test_wheel_draw_exact_boundaries_and_frequencies():
+    """Roulette / ranking draw on integer weights: weights 1 and 3 give index 0 exactly
+    for the top 24 bits u with (4 u) >> 24 == 0, i.e. u < 2^22; frequencies of a
+    roulette on 1 / (1e-12 + f) match w / sum(w) (chi^2); NaN never drawn; a zero total
+    draws uniformly."""
+    from scipy import stats
+    cum = np.cumsum(np.array([1, 3], dtype=np.uint64), dtype=np.uint64)
+    words = np.array([0, (1 << 30) - 1, 1 << 30, (1 << 32) - 1], dtype=np.uint64)
+    np.testing.assert_array_equal(o.wheel_draw(cum, words), [0, 0, 1, 1])
+    fit = np.array([0.5, 0.25, 1.0, np.nan, 0.125])
+    cfg = o.Config(pop=5, selection="roulette")
+    q = o.selection_weights(fit, cfg)
+    assert q[3] == 0 and q[4] == 1 << 24 and q[1] == 1 << 23
+    w = np.where(np.isnan(fit), 0, 1 / fit)
+    words = o.philox_words((3, 0), 0, np.arange(200000, dtype=np.uint64), 0, 0)
+    idx = o.wheel_draw(np.cumsum(q, dtype=np.uint64), words)
+    assert not np.any(idx == 3)
+    counts = np.bincount(idx, minlength=5)[[0, 1, 2, 4]]
+    expect = (w / w.sum())[[0, 1, 2, 4]] * len(idx)
+    assert stats.chisquare(counts, expect).pvalue > 1e-3
+    z = o.wheel_draw(np.zeros(5, dtype=np.uint64), words[:10])
+    np.testing.assert_array_equal(z, o.index_draw(words[:10], 5))
+
+
+def test_ranking_weights_are_linear_in_rank():
+    """Linear ranking: expected values 1.1 (best) to 0.9 (worst), ties by index."""
+    fit = np.array([0.3, 0.1, 0.3, 0.2])
+    q = o.selection_weights(fit, o.Config(pop=4, selection="ranking"))
+    # order: 1 (0.1), 3 (0.2), 0 (0.3, lower index), 2 (0.3)
+    np.testing.assert_array_equal(q[[1, 3, 0, 2]], [33, 31, 29, 27])
+    assert q[1] / q[2] == pytest.approx(1.1 / 0.9)
 
 
 def test_clamp_keeps_genes_in_range():

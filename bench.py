@@ -61,6 +61,10 @@ def parse():
                     help="learned-surrogate form: time to the plain FP32 GA's final train RMSE")
     ap.add_argument("--seeds", type=int, default=5)
     ap.add_argument("--budget", type=int, default=200, help="plain GA generations (target run)")
+    ap.add_argument("--paper", action="store_true",
+                    help="the paper's experiment shape: Section 5 settings on the knowledge-base "
+                         "stand-in replicated to 0.15 / 16 / 128 / 512 MB, degrees 1 / 2 / 4 / 8")
+    ap.add_argument("--paper-iterations", type=int, default=4000)
     ap.add_argument("--precision-table", action="store_true",
                     help="print the per-precision fitness error / accuracy table and exit")
     return ap.parse_args()
@@ -568,6 +572,54 @@ def surrogate_ttt(args):
                    "inputs": "genes standardised by running per-gene statistics"}}), flush=True)
 
 
+# The paper's Table benchgpu (GT540M, float64 Thrust): total training time of 4000
+# iterations, polytrigo degree d, the 0.15 MB knowledge base replicated to 16 / 128 /
+# 512 MB.  Context for the table below, not a target (another machine, a 2011 GPU).
+PAPER_TOT_S = {1: (15.00, 240.00, 1870.50, 7680.00), 2: (16.00, 256.00, 1993.55, 8192.00),
+               4: (19.00, 304.00, 2372.11, 9728.00), 8: (24.00, 384.00, 3006.12, 12288.00)}
+PAPER_MB = (0.15, 16, 128, 512)
+
+
+def paper_table(args):
+    """The paper's experiment shape (Section 5): shared-coefficient polytrigo (eq.9),
+    degrees 1 / 2 / 4 / 8, TMSE with R = 0.49, linear Out, 0/1 targets, roulette
+    selection, normal init in [-1, 1], p_c 0.9, p_m 0.2, elitism 2, stop 0.001,
+    population 23 (eq.6: 2 N + 1 for N = 11 features), on the knowledge-base
+    stand-in replicated to the paper's sizes; 4000 iterations each, wall time of
+    set_data (host arrays) + evolve + get_best."""
+    import torch
+    from paper_1304_0597_gb300 import game, synth
+    rows = []
+    for mb in PAPER_MB:
+        reps = max(1, int(round(mb / PAPER_MB[0])))
+        ds = synth.paper_kb(replicas=reps)
+        for d in (1, 2, 4, 8):
+            cfg = game.default_config(basis=game.TRIG, degree=d, coefficients=game.COEF_SHARED,
+                                      pop=23, error=game.TMSE, tmse_R=0.49,
+                                      activation=game.LINEAR, selection=game.SEL_ROULETTE,
+                                      init=game.INIT_NORMAL_PM1, p_crossover=0.9,
+                                      p_mutation=0.2, elitism=2, tournament_k=4,
+                                      stop_error=0.001, seed=0)
+            g = game.Game(cfg)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.set_data(ds.X, ds.t, ds.n_train)
+            ran = g.evolve(args.paper_iterations)
+            _, fit_best, test_err, acc = g.best()
+            tot = time.perf_counter() - t0
+            ms_gen = g.timing()["ms_total"] / max(ran, 1)
+            g.close()
+            paper_s = PAPER_TOT_S[d][PAPER_MB.index(mb)] * args.paper_iterations / 4000.0
+            rows.append({"mb": mb, "patterns": int(ds.X.shape[0]), "degree": d,
+                         "iterations": ran, "tot_s": tot, "ms_per_iteration": ms_gen,
+                         "train_tmse": fit_best, "test_accuracy": acc,
+                         "paper_tot_s_gt540m": paper_s, "ratio_vs_paper": paper_s / tot})
+            print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"table": "paper experiment shape (Section 5, Table benchgpu sizes)",
+                      "rows": len(rows), "engine": "SIMT (population 23)",
+                      "note": "paper numbers are a GT540M laptop GPU in float64: context only"}))
+
+
 def main():
     args = parse()
     if args.surrogate:
@@ -578,6 +630,9 @@ def main():
         return
     if args.precision_table:
         precision_table(args)
+        return
+    if args.paper:
+        paper_table(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -97,6 +97,23 @@ def planted_targets(P: np.ndarray, h: np.ndarray) -> np.ndarray:
 
 # --- the workloads -------------------------------------------------------------------
 
+def paper_kb(replicas: int = 1, seed: int = DATA_SEED) -> Dataset:
+    """Stand-in for the paper's knowledge base (Section 3 / Section 5: 2,100 patterns,
+    11 input features, 0/1 class target), replicated `replicas` times the way the
+    paper grows it to 16 / 128 / 512 MB.  Features uniform in [-1, 1]; labels from a
+    seeded hidden degree-4 polytrigo function with 5% flips, mapped to 0/1.  The
+    first 70% of the base rows train; every replica keeps that split (train rows of
+    all replicas first)."""
+    base = make_dataset(2100, 11, 4, "trig", seed=seed)
+    t01 = ((base.t + 1.0) / 2.0).astype(np.float32)
+    n_tr = base.n_train
+    X = np.concatenate([np.tile(base.X[:n_tr], (replicas, 1)),
+                        np.tile(base.X[n_tr:], (replicas, 1))])
+    t = np.concatenate([np.tile(t01[:n_tr], replicas), np.tile(t01[n_tr:], replicas)])
+    return Dataset(X=np.ascontiguousarray(X), t=np.ascontiguousarray(t),
+                   n_train=n_tr * replicas, basis="trig", degree=4)
+
+
 def plain_small(seed: int = DATA_SEED) -> Dataset:
     """2,000 patterns x 7 uniform features, Chebyshev degree 4 (29 genes)."""
     return make_dataset(2000, 7, 4, "chebyshev", seed=seed)

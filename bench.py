@@ -65,6 +65,10 @@ def parse():
                     help="the paper's experiment shape: Section 5 settings on the knowledge-base "
                          "stand-in replicated to 0.15 / 16 / 128 / 512 MB, degrees 1 / 2 / 4 / 8")
     ap.add_argument("--paper-iterations", type=int, default=4000)
+    ap.add_argument("--paper-mb", type=float, nargs="+", default=None,
+                    help="subset of the paper's sizes (0.15 16 128 512)")
+    ap.add_argument("--paper-degrees", type=int, nargs="+", default=None,
+                    help="subset of the paper's degrees (1 2 4 8)")
     ap.add_argument("--precision-table", action="store_true",
                     help="print the per-precision fitness error / accuracy table and exit")
     return ap.parse_args()
@@ -381,7 +385,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "step": f"one training run: set_data + "
                 f"{GENS_PER_RUN} generations + get_best", "runs": len(e2e_t)},
-        "gpu_launches": 4 * K + 1,
+        "gpu_launches": tm["launches"],
         "clocks": clk.summary(),
         "best": {"train_rmse": fit_best, "test_rmse": test_rmse, "test_accuracy": test_acc},
     }
@@ -590,10 +594,14 @@ def paper_table(args):
     import torch
     from paper_1304_0597_gb300 import game, synth
     rows = []
-    for mb in PAPER_MB:
+    for mb in (args.paper_mb or PAPER_MB):
+        if mb not in PAPER_MB:
+            raise SystemExit(f"--paper-mb: {mb} is not one of {PAPER_MB}")
         reps = max(1, int(round(mb / PAPER_MB[0])))
         ds = synth.paper_kb(replicas=reps)
-        for d in (1, 2, 4, 8):
+        for d in (args.paper_degrees or (1, 2, 4, 8)):
+            if d not in PAPER_TOT_S:
+                raise SystemExit(f"--paper-degrees: {d} is not one of {tuple(PAPER_TOT_S)}")
             cfg = game.default_config(basis=game.TRIG, degree=d, coefficients=game.COEF_SHARED,
                                       pop=23, error=game.TMSE, tmse_R=0.49,
                                       activation=game.LINEAR, selection=game.SEL_ROULETTE,
@@ -607,16 +615,19 @@ def paper_table(args):
             ran = g.evolve(args.paper_iterations)
             _, fit_best, test_err, acc = g.best()
             tot = time.perf_counter() - t0
-            ms_gen = g.timing()["ms_total"] / max(ran, 1)
+            tm = g.timing()
+            ms_gen = tm["ms_total"] / max(ran, 1)
+            engine = {1: "tcgen05", 2: "simt"}.get(tm["engine"], "?")
             g.close()
             paper_s = PAPER_TOT_S[d][PAPER_MB.index(mb)] * args.paper_iterations / 4000.0
             rows.append({"mb": mb, "patterns": int(ds.X.shape[0]), "degree": d,
                          "iterations": ran, "tot_s": tot, "ms_per_iteration": ms_gen,
+                         "engine": engine,
                          "train_tmse": fit_best, "test_accuracy": acc,
                          "paper_tot_s_gt540m": paper_s, "ratio_vs_paper": paper_s / tot})
             print(json.dumps(rows[-1]), flush=True)
     print(json.dumps({"table": "paper experiment shape (Section 5, Table benchgpu sizes)",
-                      "rows": len(rows), "engine": "SIMT (population 23)",
+                      "rows": len(rows), "engines": sorted({r["engine"] for r in rows}),
                       "note": "paper numbers are a GT540M laptop GPU in float64: context only"}))
 
 

@@ -204,11 +204,15 @@ game_status game_get_state(game_ctx* ctx, int64_t* generation, int32_t* stopped)
 
 /* Device time of the last game_evolve call split by stage, in milliseconds
  * (CUDA events): breed, fitness (contraction + epilogue), rank (reduce +
- * sort).  Also the engine actually used (GAME_ENGINE_*). */
+ * sort).  Also the engine actually used (GAME_ENGINE_*) and the number of
+ * kernels the call launched: the state reset plus, per requested generation,
+ * the kernel nodes of the captured generation graph (a generation skipped
+ * after a stop still launches them and they return at once). */
 typedef struct game_timing {
   double ms_breed, ms_fitness, ms_rank, ms_total;
   int32_t generations;
   int32_t engine;
+  int32_t launches;
 } game_timing;
 game_status game_get_timing(game_ctx* ctx, game_timing* out);
 

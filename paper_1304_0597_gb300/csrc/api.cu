@@ -87,6 +87,7 @@ struct game_ctx {
   float* d_bx = nullptr;        // [batch x kstride] training rows
   float* d_bt = nullptr;        // [batch] standardised targets
   cudaGraphExec_t graph = nullptr;     // one generation
+  int gen_kernels = 0;                 // kernel nodes of one captured generation
   cudaGraph_t graph_t_tmpl = nullptr;  // one generation with stage events (template kept alive)
   cudaGraphExec_t graph_t = nullptr;
   cudaGraphNode_t ev_node[4] = {};     // event-record nodes of graph_t, stage order
@@ -347,7 +348,8 @@ static void tune_cache_store(const Shape& s, const game_tile& t) {
 static game_status choose_engine(game_ctx* c, const Shape& s, const ExpDev& e, const PopDev& p,
                                  int* engine, TcPlan* plan, int* n_part) {
   int want = c->cfg.engine;
-  if (want == GAME_ENGINE_AUTO) want = tc_supported(s) ? GAME_ENGINE_TCGEN05 : GAME_ENGINE_SIMT;
+  if (want == GAME_ENGINE_AUTO)
+    want = !simt_narrow(s) && tc_supported(s) ? GAME_ENGINE_TCGEN05 : GAME_ENGINE_SIMT;
   if (want == GAME_ENGINE_TCGEN05) {
     if (!tc_supported(s))
       return fail(c, GAME_ERR_UNSUPPORTED, "tcgen05 engine does not support this shape");
@@ -738,6 +740,20 @@ static game_status enqueue_generation(game_ctx* c, const cudaEvent_t* ev) {
   return GAME_OK;
 }
 
+// Kernel nodes of a captured generation: the kernels one replay launches.
+static int count_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return -1;
+  int k = 0;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
 static game_status ensure_events(game_ctx* c, size_t n) {
   while (c->ev_pool.size() < n) {
     cudaEvent_t e;
@@ -775,6 +791,7 @@ static game_status build_graph(game_ctx* c, bool timed) {
     return r;
   }
   if (e != cudaSuccess) return fail(c, GAME_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  c->gen_kernels = count_kernel_nodes(g);
   if (!timed) {
     e = cudaGraphInstantiate(&c->graph, g, 0);
     cudaGraphDestroy(g);
@@ -861,6 +878,7 @@ extern "C" game_status game_evolve(game_ctx* c, int32_t max_generations, int32_t
   c->timing.ms_total = ms;
   c->timing.generations = hs.gens_run;
   c->timing.engine = c->engine;
+  c->timing.launches = 1 + c->gen_kernels * max_generations;
   if (hs.status != 0) return fail(c, GAME_ERR_TIMEOUT, "device-side wait timed out (status %d)", hs.status);
   if (generations_run) *generations_run = hs.gens_run;
   return GAME_OK;
@@ -1443,6 +1461,7 @@ struct game_batch {
   int* d_item_off = nullptr;
   int n_items = 0;
   cudaGraphExec_t graph = nullptr;
+  int gen_kernels = 0;  // kernel nodes of one captured generation (all runs)
   game_timing timing{};
   std::vector<cudaStream_t> side;      // capture-time branches for the per-run kernels
   std::vector<cudaEvent_t> ev;         // fork / join events of those branches
@@ -1646,6 +1665,7 @@ static game_status batch_build_graph(game_batch* b) {
     return r;
   }
   if (e != cudaSuccess) return bfail(b, GAME_ERR_CUDA, cudaGetErrorString(e));
+  b->gen_kernels = count_kernel_nodes(g);
   e = cudaGraphInstantiate(&b->graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return bfail(b, GAME_ERR_CUDA, cudaGetErrorString(e));
@@ -1678,6 +1698,7 @@ extern "C" game_status game_batch_evolve(game_batch* b, int32_t max_generations,
   b->timing = game_timing{};
   b->timing.ms_total = ms;
   b->timing.engine = GAME_ENGINE_TCGEN05;
+  b->timing.launches = (int32_t)b->runs.size() + b->gen_kernels * max_generations;
   int status = 0;
   for (size_t i = 0; i < b->runs.size(); ++i) {
     DevState hs;

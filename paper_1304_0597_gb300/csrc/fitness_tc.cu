@@ -259,9 +259,15 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
       bias[sp] = p.bias[c];
       rs[sp] = p.rscale[c];
     }
+    constexpr int kCols = BN / kColGroups;
     for (int it = 0; it < my_tiles; ++it) {
       const int buf = it & 1;
       const uint32_t ap = (uint32_t)((it >> 1) & 1);
+      const long long tile = member + (long long)it * p.cps;
+      // The low-precision forms are bound by the epilogue: the per-pattern
+      // coefficients of this tile (one 128-byte line per lane) are brought into
+      // L1 while the MMAs run, so that the loads after the wait hit.
+      if (PREC != GAME_FP32 && lane < kCols / 32) prefetch_l1(pk + tile * BN + h * kCols + lane * 32);
       // FP32 (three products per term) is MMA-bound: the accumulator wait sleeps
       // between polls so that the issue slots go to the MMA warp on the same
       // sub-partition.  The low-precision forms are epilogue-bound and poll.
@@ -269,8 +275,6 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
                                          : warp_wait(acc_full + buf, ap, err, p.state, lane);
       if (!got) break;
       fence_after();
-      const long long tile = member + (long long)it * p.cps;
-      constexpr int kCols = BN / kColGroups;
 #pragma unroll
       for (int sp = 0; sp < SP; ++sp) {
         const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) +

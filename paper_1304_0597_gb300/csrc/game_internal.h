@@ -146,6 +146,9 @@ enum : int {
 };
 
 // SIMT fitness (FFMA) over the training rows: partial sums [n_part x pop_pad].
+// simt_narrow: the shape takes the one-pattern-per-thread kernel (pop <= 32,
+// kp 16 or 32), which the automatic engine choice prefers to the tensor cores.
+bool simt_narrow(const Shape& s);
 int simt_partials(const Shape& s, int n_sm);
 cudaError_t launch_fitness_simt(const Shape& s, const Fitness& f, const PopDev& p,
                                 const ExpDev& e, double* partial, int n_part,

@@ -15,6 +15,13 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
          z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
+// Both at once with one erf: g = z Phi(z), d = Phi(z) + z phi(z) (the same
+// roundings as gelu_f and gelu_grad_f, since halving is exact).
+__device__ __forceinline__ void gelu_and_grad_f(float z, float& g, float& d) {
+  const float c = 0.5f * (1.0f + erff(z * 0.70710678118654752f));
+  g = z * c;
+  d = c + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
 
 struct Surrogate {
   int D = 0;                 // input width (genes per chromosome)

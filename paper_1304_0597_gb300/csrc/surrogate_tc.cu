@@ -8,7 +8,11 @@
 // N = BN columns, K in 64-element blocks).  Sixteen epilogue warps read the
 // accumulator with tcgen05.ld: warp w takes TMEM lanes 32 (w % 4) (one output
 // row per thread) and a quarter of the columns, and applies one of four fused
-// epilogues:
+// epilogues.  These GEMMs are small (K <= 320) and their epilogues cost more
+// than the MMAs, so a small batch takes 64- or 128-column tiles to spread over
+// more CTAs; the output layer then needs the partial sums of the other column
+// tiles, which the CTAs of a thread-block cluster swap through distributed
+// shared memory.  The epilogues:
 //   L1    z = acc + b1; H1 = gelu(z) (bf16, the next layer's operand); when
 //         training also gelu'(z) and the transposed H1 for the weight gradient;
 //   L2    z = acc + b2; y = w3 . gelu(z) + b3; when training, from the same
@@ -37,7 +41,7 @@ constexpr int kEpiWarpsTc = 16;
 constexpr int kThreadsTc = 64 + 32 * kEpiWarpsTc;   // warp 0 TMA, warp 1 MMA, then the epilogue
 constexpr int kStagesTc = 4;
 constexpr int kTileA = 128 * 128;    // 128 rows x 64 bf16
-constexpr int kGradSplits = 4;       // K slices of the weight-gradient GEMMs
+constexpr int kGradSplits = 8;       // K slices of the weight-gradient GEMMs
 
 struct MlpParams {
   CUtensorMap a, b;
@@ -62,12 +66,14 @@ struct MlpParams {
   int kbps;                    // k-blocks per split (blockIdx.z); kblocks when unsplit
   long long zstride;           // GRAD: floats between the partial planes of the splits
   DevState* state;
+  int a_box, b_box;            // host check: rows of the A / B boxes (128 / BN)
 };
 
-__device__ __forceinline__ void store_bf16x32(__nv_bfloat16* dst, const float v[32]) {
+template <int W>
+__device__ __forceinline__ void store_bf16xw(__nv_bfloat16* dst, const float* v) {
   uint4* d4 = reinterpret_cast<uint4*>(dst);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < W / 8; ++q) {
     uint32_t w[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -78,11 +84,18 @@ __device__ __forceinline__ void store_bf16x32(__nv_bfloat16* dst, const float v[
   }
 }
 
-__device__ __forceinline__ void store_f32x32(float* dst, const float v[32]) {
+template <int W>
+__device__ __forceinline__ void store_f32xw(float* dst, const float* v) {
   float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  for (int q = 0; q < W / 4; ++q)
+    d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
+
+// Shared memory: the ring of stages, then the cross-CTA partial outputs of L2
+// (kExchBytes, outside the ring because peers write them while this CTA's MMAs
+// may still run), then the barriers.
+constexpr int kExchBytes = 4 * 128 * 4;
 
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_constant__ MlpParams p) {
@@ -92,11 +105,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
   constexpr int kTileB = BN * 128;
   constexpr int kStage = kTileA + kTileB;
   constexpr uint32_t kIdesc = make_idesc(128, BN, 1u);   // bf16 x bf16 -> f32
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStagesTc * kStage);
+  // L2 needs all 256 hidden columns of a row for y: with BN < 256 the CTAs of a
+  // cluster (1, kCN, 1) split the columns and swap their partial dot products.
+  constexpr int kCN = EPI == kEpiL2 ? 256 / BN : 1;
+  float* xpart = reinterpret_cast<float*>(smem + kStagesTc * kStage);   // [kCN][128]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStagesTc * kStage + kExchBytes);
   uint64_t* empty = full + kStagesTc;
   uint64_t* acc_full = empty + kStagesTc;
   uint64_t* fin = acc_full + 1;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  uint64_t* xbar = fin + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(xbar + 1);
   volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* last_par = reinterpret_cast<int*>(tmem_slot + 2);
 
@@ -114,6 +132,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
     }
     mbar_init(acc_full, 1);
     mbar_init(fin, 1);
+    mbar_init(xbar, 128 * kCN);
     *err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -126,6 +145,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
   }
   fence_before();
   __syncthreads();
+  // peers arrive on xbar only after it is initialised in every CTA of the cluster
+  if constexpr (kCN > 1) cluster_sync_all();
   fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -195,6 +216,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
   } else {
     // ---- epilogue: thread = output row r, columns [c0, c0 + kCols) of the tile ----
     constexpr int kCols = BN / 4;
+    constexpr int kW = kCols < 32 ? kCols : 32;   // TMEM columns per load
     const int q = warp & 3;
     const int h = (warp - 2) >> 2;
     const int r = m0 + q * 32 + lane;
@@ -203,44 +225,50 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
     const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
     const bool ok = warp_wait(acc_full, 0, err, p.state, lane);
     if (ok) fence_after();
-    float v[32];
+    float v[kW];
     if (EPI == kEpiL1) {
       if (ok) {
 #pragma unroll 1
-        for (int ch = 0; ch < kCols / 32; ++ch) {
-          tmem_ld32(tb + ch * 32, v);
-          const int nb = n0 + c0 + ch * 32;
-          float gp[32];
+        for (int ch = 0; ch < kCols / kW; ++ch) {
+          tmem_ld<kW>(tb + ch * kW, v);
+          const int nb = n0 + c0 + ch * kW;
+          if (!p.train) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float z = v[j] + p.bias[nb + j];
-            if (p.train) gp[j] = gelu_grad_f(z);
-            v[j] = gelu_f(z);
+            for (int j = 0; j < kW; ++j) v[j] = gelu_f(v[j] + p.bias[nb + j]);
+            if (rv) store_bf16xw<kW>(p.out_b + (long long)r * 256 + nb, v);
+            continue;
           }
-          if (rv) {
-            store_bf16x32(p.out_b + (long long)r * 256 + nb, v);
-            if (p.train) {
-              store_f32x32(p.gp + (long long)r * 256 + nb, gp);
+          // 16 columns at a time keep gelu' within the register budget
 #pragma unroll
-              for (int j = 0; j < 32; ++j)
-                p.out_t[(long long)(nb + j) * p.ldt + r] = __float2bfloat16_rn(v[j]);
+          for (int hh = 0; hh < kW; hh += 16) {
+            float gp[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              gelu_and_grad_f(v[hh + j] + p.bias[nb + hh + j], v[hh + j], gp[j]);
+            if (rv) {
+              store_bf16xw<16>(p.out_b + (long long)r * 256 + nb + hh, v + hh);
+              store_f32xw<16>(p.gp + (long long)r * 256 + nb + hh, gp);
+#pragma unroll
+              for (int j = 0; j < 16; ++j)
+                p.out_t[(long long)(nb + hh + j) * p.ldt + r] = __float2bfloat16_rn(v[hh + j]);
             }
           }
         }
       }
     } else if (EPI == kEpiL2) {
       // y needs all 256 columns: partial dots of the four column groups meet in
-      // shared memory (the ring is idle once the accumulator is complete).  Every
-      // epilogue warp reaches the named barrier, also after a failed wait.
+      // shared memory (the ring is idle once the accumulator is complete), then
+      // the kCN CTAs of the cluster swap their sums.  Every epilogue thread
+      // reaches the named barrier and the exchange, also after a failed wait.
       float* part = reinterpret_cast<float*>(smem);   // [4][128]
       float yp = 0.0f;
       if (ok) {
 #pragma unroll 1
-        for (int ch = 0; ch < kCols / 32; ++ch) {
-          tmem_ld32(tb + ch * 32, v);
+        for (int ch = 0; ch < kCols / kW; ++ch) {
+          tmem_ld<kW>(tb + ch * kW, v);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = c0 + ch * 32 + j;
+          for (int j = 0; j < kW; ++j) {
+            const int n = n0 + c0 + ch * kW + j;
             yp = fmaf(gelu_f(v[j] + p.bias[n]), __bfloat162float(p.w3[n]), yp);
           }
         }
@@ -248,31 +276,53 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
       part[h * 128 + q * 32 + lane] = yp;
       asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarpsTc) : "memory");
       const int rl = q * 32 + lane;
-      const float y = p.b3[0] + ((part[rl] + part[128 + rl]) + (part[256 + rl] + part[384 + rl]));
-      if (ok && h == 0 && rv) p.y[r] = y;
-      if (ok && p.train) {
+      float y;
+      bool xok = true;
+      if constexpr (kCN == 1) {
+        y = p.b3[0] + ((part[rl] + part[128 + rl]) + (part[256 + rl] + part[384 + rl]));
+      } else {
+        const uint32_t rank = cluster_rank();
+        if (h == 0) {
+          const float own = (part[rl] + part[128 + rl]) + (part[256 + rl] + part[384 + rl]);
+          const uint32_t slot = smem_u32(xpart + rank * 128 + rl);
+#pragma unroll
+          for (int c = 0; c < kCN; ++c) {
+            st_cluster_f32(mapa_shared(slot, (uint32_t)c), own);
+            mbar_arrive_cluster(mapa_shared(smem_u32(xbar), (uint32_t)c));
+          }
+        }
+        xok = mbar_wait_cluster(xbar, 0, err, p.state);
+        float sum = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kCN; ++c) sum += xpart[c * 128 + rl];
+        y = p.b3[0] + sum;
+      }
+      const bool lead = h == 0 && blockIdx.y == 0;   // one writer per row
+      if (ok && xok && lead && rv) p.y[r] = y;
+      if (ok && xok && p.train) {
         const float e = y - (rv ? p.t[r] : 0.0f);
         const float d = e * p.two_over_b;
-        if (h == 0 && rv) {
+        if (lead && rv) {
           p.dy[r] = d;
           p.sq[r] = e * e;
         }
 #pragma unroll 1
-        for (int ch = 0; ch < kCols / 32; ++ch) {
-          tmem_ld32(tb + ch * 32, v);
-          const int nb = c0 + ch * 32;
-          float dh[32];
+        for (int ch = 0; ch < kCols / kW; ++ch) {
+          tmem_ld<kW>(tb + ch * kW, v);
+          const int nb = n0 + c0 + ch * kW;
+          float dh[kW];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const float z = v[j] + p.bias[nb + j];
-            dh[j] = d * gelu_f(z);
-            v[j] = d * __bfloat162float(p.w3[nb + j]) * gelu_grad_f(z);
+          for (int j = 0; j < kW; ++j) {
+            float g, gd;
+            gelu_and_grad_f(v[j] + p.bias[nb + j], g, gd);
+            dh[j] = d * g;
+            v[j] = d * __bfloat162float(p.w3[nb + j]) * gd;
           }
           if (rv) {
-            store_bf16x32(p.out_b + (long long)r * 256 + nb, v);
-            store_f32x32(p.dyh2 + (long long)r * 256 + nb, dh);
+            store_bf16xw<kW>(p.out_b + (long long)r * 256 + nb, v);
+            store_f32xw<kW>(p.dyh2 + (long long)r * 256 + nb, dh);
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
+            for (int j = 0; j < kW; ++j)
               p.out_t[(long long)(nb + j) * p.ldt + r] = __float2bfloat16_rn(v[j]);
           }
         }
@@ -280,13 +330,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
     } else if (EPI == kEpiB1) {
       if (ok) {
 #pragma unroll 1
-        for (int ch = 0; ch < kCols / 32; ++ch) {
-          tmem_ld32(tb + ch * 32, v);
-          const int nb = n0 + c0 + ch * 32;
+        for (int ch = 0; ch < kCols / kW; ++ch) {
+          tmem_ld<kW>(tb + ch * kW, v);
+          const int nb = n0 + c0 + ch * kW;
           if (rv) {
             const float4* g4 = reinterpret_cast<const float4*>(p.gp + (long long)r * 256 + nb);
 #pragma unroll
-            for (int j4 = 0; j4 < 8; ++j4) {
+            for (int j4 = 0; j4 < kW / 4; ++j4) {
               const float4 gg = g4[j4];
               v[4 * j4] *= gg.x;
               v[4 * j4 + 1] *= gg.y;
@@ -294,35 +344,36 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
               v[4 * j4 + 3] *= gg.w;
             }
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
+            for (int j = 0; j < kW; ++j)
               p.out_t[(long long)(nb + j) * p.ldt + r] = __float2bfloat16_rn(v[j]);
           }
         }
       }
     } else {
-      // weight-gradient rows: each warp turns its 32 x 32 block around in shared
+      // weight-gradient rows: each warp turns its 32 x kW block around in shared
       // memory (the idle ring) so that the global stores run along a row
       float* tile = reinterpret_cast<float*>(smem) + (warp - 2) * (32 * 33);
       float* gm = p.g_main + blockIdx.z * p.zstride;
       float* gb = p.g_bias + blockIdx.z * p.zstride;
       if (ok) {
 #pragma unroll 1
-        for (int ch = 0; ch < kCols / 32; ++ch) {
-          tmem_ld32(tb + ch * 32, v);
+        for (int ch = 0; ch < kCols / kW; ++ch) {
+          tmem_ld<kW>(tb + ch * kW, v);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = v[j];
+          for (int j = 0; j < kW; ++j) tile[lane * 33 + j] = v[j];
           __syncwarp();
-          const int n = n0 + c0 + ch * 32 + lane;
-          for (int i = 0; i < 32; ++i) {
-            const int rr = m0 + q * 32 + i;
-            if (rr < p.M) {
-              const float w = tile[i * 33 + lane];
-              if (n < p.n_main)
-                gm[(long long)rr * p.ld_main + n] = w;
-              else if (n == p.n_main)
-                gb[rr] = w;
+          const int n = n0 + c0 + ch * kW + lane;
+          if (lane < kW)
+            for (int i = 0; i < 32; ++i) {
+              const int rr = m0 + q * 32 + i;
+              if (rr < p.M) {
+                const float w = tile[i * 33 + lane];
+                if (n < p.n_main)
+                  gm[(long long)rr * p.ld_main + n] = w;
+                else if (n == p.n_main)
+                  gb[rr] = w;
+              }
             }
-          }
           __syncwarp();
         }
       }
@@ -334,11 +385,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1) mlp_tc_kernel(const __grid_cons
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"((uint32_t)BN));
+  // No CTA leaves while a peer may still write its partial sums here.
+  if constexpr (kCN > 1) cluster_sync_all();
 }
 
 template <int BN>
 constexpr size_t smem_bytes() {
-  return (size_t)kStagesTc * (kTileA + BN * 128) + 1024 + 256;
+  return (size_t)kStagesTc * (kTileA + BN * 128) + kExchBytes + 1024 + 256;
 }
 
 // X (float32, row stride ldx, first D columns) -> Xb (bf16, row stride Dp) and,
@@ -510,13 +563,46 @@ cudaError_t bf16_map(CUtensorMap* m, const void* base, long long rows, long long
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// The operand maps of one GEMM: A boxes are 128 rows (the MMA's M), B boxes
+// one column tile of BN rows; a stage expects exactly these bytes.
+cudaError_t map_a(MlpParams& p, const void* base, long long rows, long long cols, long long ld) {
+  p.a_box = 128;
+  return bf16_map(&p.a, base, rows, cols, ld, 128);
+}
+cudaError_t map_b(MlpParams& p, const void* base, long long rows, long long cols, long long ld,
+                  int box) {
+  p.b_box = box;
+  return bf16_map(&p.b, base, rows, cols, ld, box);
+}
+
 template <int BN, int EPI>
 cudaError_t launch_mlp(MlpParams& p, int grid_m, int grid_n, cudaStream_t st, int splits = 1) {
+  if (p.a_box != 128 || p.b_box != BN) return cudaErrorInvalidValue;
   if (splits <= 1) p.kbps = p.kblocks;
-  void* args[] = {&p};
-  return cudaLaunchKernel(reinterpret_cast<void*>(&mlp_tc_kernel<BN, EPI>),
-                          dim3(grid_m, grid_n, splits), dim3(kThreadsTc), args, smem_bytes<BN>(),
-                          st);
+  constexpr int kCN = EPI == kEpiL2 ? 256 / BN : 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid_m, grid_n, splits);
+  cfg.blockDim = dim3(kThreadsTc);
+  cfg.dynamicSmemBytes = smem_bytes<BN>();
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  if (kCN > 1) {
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 1;
+    at[0].val.clusterDim.y = kCN;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, mlp_tc_kernel<BN, EPI>, p);
+}
+
+// Column-tile width of the hidden-layer GEMMs by the number of 128-row tiles:
+// the epilogue, not the MMA, bounds them, so a small batch (a training step)
+// takes narrow tiles and more CTAs, a large one (the candidate pool) wide ones.
+int hidden_bn(int grid_m, bool l2) {
+  if (l2 && grid_m >= 128) return 256;
+  return grid_m >= 32 ? 128 : 64;
 }
 
 // g[i] = sum over the splits z of ws[z * n + i], in order (deterministic).
@@ -540,8 +626,12 @@ cudaError_t surrogate_tc_init_attributes() {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize,                   \
                                 (int)smem_bytes<BN>())) != cudaSuccess)                        \
     return e;
+  GAME_MLP_ATTR(64, kEpiL1)
   GAME_MLP_ATTR(128, kEpiL1)
+  GAME_MLP_ATTR(64, kEpiL2)
+  GAME_MLP_ATTR(128, kEpiL2)
   GAME_MLP_ATTR(256, kEpiL2)
+  GAME_MLP_ATTR(64, kEpiB1)
   GAME_MLP_ATTR(128, kEpiB1)
   GAME_MLP_ATTR(128, kEpiGrad)
 #undef GAME_MLP_ATTR
@@ -643,8 +733,11 @@ cudaError_t Surrogate::tc_layers(int M, float* y, const float* t, cudaStream_t s
   a.train = train ? 1 : 0;
   a.ldt = ldt;
   // layer 1: Z1 = Xb W1b^T
-  if ((e = bf16_map(&a.a, Xb, M, D, Dp, 128)) != cudaSuccess) return e;
-  if ((e = bf16_map(&a.b, W1b, H, D, Dp, 128)) != cudaSuccess) return e;
+  // the B operand's box is one column tile: BN rows (the expected bytes of a stage)
+  const int gm = ceil_div(M, 128);
+  const int bn1 = hidden_bn(gm, false), bn2 = hidden_bn(gm, true);
+  if ((e = map_a(a, Xb, M, D, Dp)) != cudaSuccess) return e;
+  if ((e = map_b(a, W1b, H, D, Dp, bn1)) != cudaSuccess) return e;
   a.M = M;
   a.N = H;
   a.kblocks = ceil_div(D, 64);
@@ -652,11 +745,13 @@ cudaError_t Surrogate::tc_layers(int M, float* y, const float* t, cudaStream_t s
   a.out_b = H1b;
   a.out_t = H1Tb;
   a.gp = gp1;
-  if ((e = launch_mlp<128, kEpiL1>(a, ceil_div(M, 128), H / 128, st)) != cudaSuccess) return e;
+  e = bn1 == 128 ? launch_mlp<128, kEpiL1>(a, gm, H / 128, st)
+                 : launch_mlp<64, kEpiL1>(a, gm, H / 64, st);
+  if (e != cudaSuccess) return e;
   // layer 2 and the output: Z2 = H1b W2b^T
   MlpParams b = a;
-  if ((e = bf16_map(&b.a, H1b, M, H, H, 128)) != cudaSuccess) return e;
-  if ((e = bf16_map(&b.b, W2b, H, H, H, 256)) != cudaSuccess) return e;
+  if ((e = map_a(b, H1b, M, H, H)) != cudaSuccess) return e;
+  if ((e = map_b(b, W2b, H, H, H, bn2)) != cudaSuccess) return e;
   b.kblocks = H / 64;
   b.bias = b2;
   b.w3 = w3b;
@@ -669,7 +764,11 @@ cudaError_t Surrogate::tc_layers(int M, float* y, const float* t, cudaStream_t s
   b.dyh2 = dyh2;
   b.out_b = dZ2b;
   b.out_t = dZ2Tb;
-  return launch_mlp<256, kEpiL2>(b, ceil_div(M, 128), 1, st);
+  switch (bn2) {
+    case 256: return launch_mlp<256, kEpiL2>(b, gm, 1, st);
+    case 128: return launch_mlp<128, kEpiL2>(b, gm, 2, st);
+    default: return launch_mlp<64, kEpiL2>(b, gm, 4, st);
+  }
 }
 
 cudaError_t Surrogate::tc_out_grads(int B, cudaStream_t st) {
@@ -692,14 +791,18 @@ cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st) {
   a.state = state;
   a.ldt = ldt;
   // dZ1^T = ((dZ2 W2) * gelu'(Z1))^T : A = dZ2 [B x H], B operand = W2^T
-  if ((e = bf16_map(&a.a, dZ2b, B, H, H, 128)) != cudaSuccess) return e;
-  if ((e = bf16_map(&a.b, W2Tb, H, H, H, 128)) != cudaSuccess) return e;
+  const int gm = ceil_div(B, 128);
+  const int bn = hidden_bn(gm, false);
+  if ((e = map_a(a, dZ2b, B, H, H)) != cudaSuccess) return e;
+  if ((e = map_b(a, W2Tb, H, H, H, bn)) != cudaSuccess) return e;
   a.M = B;
   a.N = H;
   a.kblocks = H / 64;
   a.out_t = dZ1Tb;
   a.gp = gp1;
-  if ((e = launch_mlp<128, kEpiB1>(a, ceil_div(B, 128), H / 128, st)) != cudaSuccess) return e;
+  e = bn == 128 ? launch_mlp<128, kEpiB1>(a, gm, H / 128, st)
+                : launch_mlp<64, kEpiB1>(a, gm, H / 64, st);
+  if (e != cudaSuccess) return e;
   // The weight gradients reduce over the batch (K = B): split K into up to
   // kGradSplits slices, each writing a partial plane laid out like the flat
   // parameters [W1 | b1 | W2 | b2] (workspace gws), then add the planes in order.
@@ -712,8 +815,8 @@ cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st) {
   // [gW2 | gb2] = dZ2^T [H1 | 1] : A = dZ2^T [H x B], B operand = [H1^T ; 1] [(H + 1) x B]
   MlpParams w = {};
   w.state = state;
-  if ((e = bf16_map(&w.a, dZ2Tb, H, B, ldt, 128)) != cudaSuccess) return e;
-  if ((e = bf16_map(&w.b, H1Tb, H + 1, B, ldt, 128)) != cudaSuccess) return e;
+  if ((e = map_a(w, dZ2Tb, H, B, ldt)) != cudaSuccess) return e;
+  if ((e = map_b(w, H1Tb, H + 1, B, ldt, 128)) != cudaSuccess) return e;
   w.M = H;
   w.N = H + 1;
   w.kblocks = kblocks;
@@ -728,8 +831,8 @@ cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st) {
     return e;
   // [gW1 | gb1] = dZ1^T [X | 1] : A = dZ1^T [H x B], B operand = [X^T ; 1] [(D + 1) x B]
   MlpParams v = w;
-  if ((e = bf16_map(&v.a, dZ1Tb, H, B, ldt, 128)) != cudaSuccess) return e;
-  if ((e = bf16_map(&v.b, XTb, D + 1, B, ldt, 128)) != cudaSuccess) return e;
+  if ((e = map_a(v, dZ1Tb, H, B, ldt)) != cudaSuccess) return e;
+  if ((e = map_b(v, XTb, D + 1, B, ldt, 128)) != cudaSuccess) return e;
   v.N = D + 1;
   v.g_main = wW1;
   v.g_bias = wb1;

@@ -51,7 +51,8 @@ class GameConfig(C.Structure):
 
 class GameTiming(C.Structure):
     _fields_ = [("ms_breed", C.c_double), ("ms_fitness", C.c_double), ("ms_rank", C.c_double),
-                ("ms_total", C.c_double), ("generations", C.c_int32), ("engine", C.c_int32)]
+                ("ms_total", C.c_double), ("generations", C.c_int32), ("engine", C.c_int32),
+                ("launches", C.c_int32)]
 
 
 class GameTile(C.Structure):

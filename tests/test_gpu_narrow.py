@@ -1,0 +1,111 @@
+"""The narrow SIMT fitness kernel (at most 32 chromosomes, 16 or 32 stored basis
+columns: the paper's own Section 5 settings, population 2N + 1) against the oracle.
+
+Bars: FP32 fitness within 1e-5 relative (the stated FP32 tolerance); BF16 / FP8
+within 1e-5 of the oracle on the dequantised expansion (the kernel rounds only in
+float32); the threshold errors (eq.10) allow a pattern within float32 rounding of R
+to fall on either side.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import game_oracle as o
+from paper_1304_0597_gb300 import synth
+from tests.gpu_helpers import lib, make_game, oracle_fitness_chunked
+
+pytestmark = pytest.mark.gpu
+
+FIT_RTOL = 1e-5
+
+
+def _cfg(**kw):
+    base = dict(basis="chebyshev", degree=4, pop=23, tournament_k=3, p_crossover=0.9,
+                p_mutation=0.05, sigma_mutation=0.1, elitism=2, seed=3)
+    base.update(kw)
+    return o.Config(**base)
+
+
+@pytest.mark.parametrize("shape", [
+    dict(n=5003, F=5, d=3, pop=23, basis="chebyshev"),   # 15 columns -> 16 stored, ragged rows
+    dict(n=4099, F=8, d=4, pop=32, basis="chebyshev"),   # 32 columns, a full warp of chromosomes
+    dict(n=3001, F=7, d=4, pop=2, basis="chebyshev"),    # the smallest population
+    dict(n=777, F=3, d=5, pop=9, basis="trig"),          # 30 columns, fewer rows than one CTA
+    dict(n=40, F=2, d=8, pop=5, basis="chebyshev"),      # fewer rows than one warp
+])
+@pytest.mark.parametrize("engine", ["auto", "simt"])
+def test_narrow_fitness_matches_oracle(shape, engine):
+    game = lib()
+    ds = synth.make_dataset(shape["n"], shape["F"], shape["d"], shape["basis"], seed=17)
+    ocfg = _cfg(basis=shape["basis"], degree=shape["d"], pop=shape["pop"],
+                elitism=min(2, shape["pop"]))
+    eng = game.ENGINE_AUTO if engine == "auto" else game.ENGINE_SIMT
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=eng)
+    assert g.timing()["engine"] == game.ENGINE_SIMT
+    G = g.population()
+    fit, rank = g.evaluate()
+    P = o.expand(ds.X[:ds.n_train], shape["basis"], shape["d"])
+    want = o.fitness(P, ds.t[:ds.n_train], G, ocfg)
+    np.testing.assert_allclose(fit, want, rtol=FIT_RTOL)
+    assert list(rank) == list(o.rank(fit))
+
+
+@pytest.mark.parametrize("err,act", [("mse", "tanh"), ("tmse", "tanh"), ("tmse_sq", "tanh"),
+                                     ("rmse", "linear"), ("tmse", "linear")])
+def test_narrow_error_kinds(err, act):
+    """Section 5 form: shared polytrigo coefficients (eq.9), 11 features, d = 8 (16
+    stored columns), 23 chromosomes; linear Out with 0/1 labels or tanh with +-1."""
+    ds = synth.make_dataset(6007, 11, 8, "trig", seed=19)
+    t = ds.t if act == "tanh" else (ds.t > 0).astype(np.float32)
+    ocfg = _cfg(basis="trig", degree=8, coefficients="shared", error=err, activation=act,
+                tmse_R=0.49)
+    g = make_game(ocfg, ds.X, t, ds.n_train)
+    assert g.timing()["engine"] == lib().ENGINE_SIMT
+    fit, _ = g.evaluate()
+    P = o.expand(ds.X[:ds.n_train], "trig", 8, shared=True)
+    want = o.fitness(P, t[:ds.n_train], g.population(), ocfg)
+    if err.startswith("tmse"):
+        np.testing.assert_allclose(fit, want, rtol=1e-4, atol=1e-6)
+    else:
+        np.testing.assert_allclose(fit, want, rtol=FIT_RTOL)
+
+
+@pytest.mark.parametrize("fmt,F,d", [("bf16", 5, 3), ("bf16", 8, 4), ("fp8", 7, 4)])
+def test_narrow_low_precision(fmt, F, d):
+    game = lib()
+    ds = synth.make_dataset(4001, F, d, seed=23)
+    ocfg = _cfg(degree=d, pop=19)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=game.BF16 if fmt == "bf16" else game.FP8,
+                  elite_rescore=0)
+    assert g.timing()["engine"] == game.ENGINE_SIMT
+    fit, _ = g.evaluate()
+    Q, sc = o.quantize_columns(o.expand(ds.X[:ds.n_train], "chebyshev", d)[:, 1:], fmt)
+    Pq = np.concatenate([np.ones((ds.n_train, 1)), o.dequantize_columns(Q, sc)], axis=1)
+    np.testing.assert_allclose(fit, o.fitness(Pq, ds.t[:ds.n_train], g.population(), ocfg),
+                               rtol=FIT_RTOL)
+
+
+def test_narrow_many_blocks_per_thread():
+    """Enough rows that every thread folds several 32-pattern blocks into its float64
+    sum (2 x 152 CTAs x 256 threads x 32 patterns = 2.49M rows per round)."""
+    ds = synth.make_dataset(4_000_000, 3, 4, seed=29)
+    ocfg = _cfg(degree=4, pop=7)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train)
+    assert g.timing()["engine"] == lib().ENGINE_SIMT
+    fit, _ = g.evaluate()
+    want = oracle_fitness_chunked(ds.X[:ds.n_train], ds.t[:ds.n_train], g.population(), ocfg,
+                                  chunk=1 << 19)
+    np.testing.assert_allclose(fit, want, rtol=FIT_RTOL)
+
+
+def test_narrow_and_tensor_core_engines_agree_on_a_run():
+    """Same seed, same operators: the two engines give the same fitness to 1e-5, so
+    short runs stay on the same trajectory (ties aside)."""
+    game = lib()
+    ds = synth.make_dataset(9000, 6, 4, seed=31)
+    ocfg = _cfg(degree=4, pop=24)
+    a = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=game.ENGINE_SIMT)
+    b = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=game.ENGINE_TCGEN05)
+    fa, _ = a.evaluate()
+    fb, _ = b.evaluate()
+    np.testing.assert_allclose(fa, fb, rtol=2e-5)

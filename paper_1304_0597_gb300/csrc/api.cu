@@ -345,13 +345,23 @@ static void tune_cache_store(const Shape& s, const game_tile& t) {
   fclose(f);
 }
 
-static game_status choose_engine(game_ctx* c, const Shape& s, const ExpDev& e, const PopDev& p,
+static game_status choose_engine(game_ctx* c, Shape& s, const ExpDev& e, const PopDev& p,
                                  int* engine, TcPlan* plan, int* n_part) {
   int want = c->cfg.engine;
+  // Automatic: the narrow SIMT kernel for at most 32 chromosomes on 16 or 32 stored
+  // columns (the paper's own settings); otherwise the tensor cores where a kernel
+  // keeps the genes resident, else SIMT.  Among the tensor-core kernels the swapped
+  // one (patterns on M) takes an FP32 population of at most 32 when the tensor cores
+  // are asked for by name, or when the 128-chromosome kernel cannot hold the genes;
+  // for the automatic choice (the 16-elite re-score) the 128-chromosome kernel
+  // measured faster (c2: 0.157 against 0.199 ms for re-score and rank).
+  const bool tc_ok = tc_narrow_fits(s) || tc_supported(s);
   if (want == GAME_ENGINE_AUTO)
-    want = !simt_narrow(s) && tc_supported(s) ? GAME_ENGINE_TCGEN05 : GAME_ENGINE_SIMT;
+    want = simt_narrow(s) || !tc_ok ? GAME_ENGINE_SIMT : GAME_ENGINE_TCGEN05;
+  s.tc_narrow = want == GAME_ENGINE_TCGEN05 && tc_narrow_fits(s) &&
+                (c->cfg.engine == GAME_ENGINE_TCGEN05 || !tc_supported(s));
   if (want == GAME_ENGINE_TCGEN05) {
-    if (!tc_supported(s))
+    if (!tc_ok)
       return fail(c, GAME_ERR_UNSUPPORTED, "tcgen05 engine does not support this shape");
     TileReq req{c->cfg.tile_n, c->cfg.tile_stages, c->cfg.tile_cluster, -1, c->cfg.tile_slices};
     if (!req.n && !req.stages && !req.cluster && !req.sp) tune_cache_lookup(s, &req);

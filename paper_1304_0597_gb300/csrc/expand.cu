@@ -144,38 +144,96 @@ __global__ void expand_kernel(ExpArgs a) {
 // Shared coefficients (the paper's eq.2 / eq.9 form): column b of pattern k is the
 // sum over the features of the b-th basis value, the float32 values of the
 // per-feature expansion added in float64 and rounded once.
-__device__ __forceinline__ float shared_value(const ExpArgs& a, long long k, int b) {
-  double acc = 0.0;
+constexpr int kSharedRows = 64;   // patterns (threads) per block of the shared-form kernels
+
+// Column sums of one pattern in the shared form: acc[b * kSharedRows] (this
+// thread's slot of a column-major block array in shared memory) = the float64
+// sum over the features, in feature order, of the float32 b-th basis values.
+__device__ __forceinline__ void shared_row_sums(const ExpArgs& a, long long k, double* acc) {
+  for (int b = 0; b < a.kb; ++b) acc[b * kSharedRows] = 0.0;
   const float* x = a.X + k * a.F;
   for (int f = 0; f < a.F; ++f)
-    basis_values(a.basis, a.d, x[f], [&](int bb, float v) {
-      if (bb == b) acc += (double)v;
-    });
-  return (float)acc;
+    basis_values(a.basis, a.d, x[f], [&](int b, float v) { acc[b * kSharedRows] += (double)v; });
 }
 
-__global__ void expand_shared_colmax_kernel(ExpArgs a) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n * a.kb) return;
-  const int b = (int)(i % a.kb);
-  atomicMax(a.colmax_bits + b, __float_as_uint(fabsf(shared_value(a, i / a.kb, b))));
+__global__ void __launch_bounds__(kSharedRows) expand_shared_colmax_kernel(ExpArgs a) {
+  extern __shared__ double sacc[];   // [kb][kSharedRows]
+  __shared__ unsigned int cmax[64];  // kb <= 2 * 32
+  for (int c = threadIdx.x; c < a.kb; c += blockDim.x) cmax[c] = 0u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (long long k0 = (long long)blockIdx.x * kSharedRows; k0 < a.n;
+       k0 += (long long)gridDim.x * kSharedRows) {
+    const long long k = k0 + threadIdx.x;
+    double* acc = sacc + threadIdx.x;
+    if (k < a.n) shared_row_sums(a, k, acc);
+    for (int b = 0; b < a.kb; ++b) {
+      // non-negative floats order like their bit patterns
+      const unsigned int v = k < a.n ? __float_as_uint(fabsf((float)acc[b * kSharedRows])) : 0u;
+      const unsigned int m = __reduce_max_sync(0xffffffffu, v);
+      if (lane == 0 && m) atomicMax(cmax + b, m);
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < a.kb; c += blockDim.x)
+    if (cmax[c]) atomicMax(a.colmax_bits + c, cmax[c]);
 }
 
-__global__ void expand_shared_kernel(ExpArgs a) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n * a.kp) return;
-  const long long k = i / a.kp;
-  const int b = (int)(i % a.kp);
-  const float v = b < a.kb ? shared_value(a, k, b) : 0.0f;
-  const long long o = k * a.kp + b;
+// One pattern per thread: the kb column sums, rounded once to float32, stored as
+// the run's planes 16 bytes at a time (kp is a multiple of 16, or of 32 for e4m3).
+__global__ void __launch_bounds__(kSharedRows) expand_shared_kernel(ExpArgs a) {
+  extern __shared__ double sacc[];   // [kb][kSharedRows]
+  const long long k = (long long)blockIdx.x * kSharedRows + threadIdx.x;
+  if (k >= a.n) return;
+  const double* acc = sacc + threadIdx.x;
+  shared_row_sums(a, k, sacc + threadIdx.x);
+  const long long row = k * a.kp;
+  auto val = [&](int b) { return b < a.kb ? (float)acc[b * kSharedRows] : 0.0f; };
   if (a.precision == GAME_FP32) {
-    const __half h = __float2half_rn(v);
-    ((__half*)a.p0)[o] = h;
-    ((__half*)a.p1)[o] = __float2half_rn(__fsub_rn(v, __half2float(h)));
+    for (int b0 = 0; b0 < a.kp; b0 += 8) {
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float v0 = val(b0 + 2 * i), v1 = val(b0 + 2 * i + 1);
+        const __half h0 = __float2half_rn(v0), h1 = __float2half_rn(v1);
+        const __half l0 = __float2half_rn(__fsub_rn(v0, __half2float(h0)));
+        const __half l1 = __float2half_rn(__fsub_rn(v1, __half2float(h1)));
+        const __half2 hh = __halves2half2(h0, h1), ll = __halves2half2(l0, l1);
+        hw[i] = *reinterpret_cast<const uint32_t*>(&hh);
+        lw[i] = *reinterpret_cast<const uint32_t*>(&ll);
+      }
+      *reinterpret_cast<uint4*>((__half*)a.p0 + row + b0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4*>((__half*)a.p1 + row + b0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
   } else if (a.precision == GAME_BF16) {
-    ((__nv_bfloat16*)a.p0)[o] = __float2bfloat16_rn(b < a.kb ? v / a.colscale[b] : 0.0f);
+    for (int b0 = 0; b0 < a.kp; b0 += 8) {
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int b = b0 + 2 * i;
+        const __nv_bfloat162 q =
+            __halves2bfloat162(__float2bfloat16_rn(b < a.kb ? val(b) / a.colscale[b] : 0.0f),
+                               __float2bfloat16_rn(b + 1 < a.kb ? val(b + 1) / a.colscale[b + 1] : 0.0f));
+        w[i] = *reinterpret_cast<const uint32_t*>(&q);
+      }
+      *reinterpret_cast<uint4*>((__nv_bfloat16*)a.p0 + row + b0) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
   } else {
-    ((__nv_fp8_e4m3*)a.p0)[o] = __nv_fp8_e4m3(b < a.kb ? v / a.colscale[b] : 0.0f);
+    for (int b0 = 0; b0 < a.kp; b0 += 16) {
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int b = b0 + 4 * i + j;
+          const __nv_fp8_e4m3 q(b < a.kb ? val(b) / a.colscale[b] : 0.0f);
+          word |= (uint32_t)q.__x << (8 * j);
+        }
+        w[i] = word;
+      }
+      *reinterpret_cast<uint4*>((__nv_fp8_e4m3*)a.p0 + row + b0) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
   }
 }
 
@@ -213,19 +271,21 @@ cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax
   a.shared = s.shared;
   const int threads = 256;
   if (s.shared) {
-    // one thread per (pattern, column); F * d basis evaluations each (small in this form)
+    // one thread per pattern, F basis sequences each; column sums in shared memory
+    if (s.kb > 64) return cudaErrorInvalidValue;   // B * d <= 2 * 32
+    const size_t smem = sizeof(double) * s.kb * kSharedRows;
+    const long long nblk = (s.n_patterns + kSharedRows - 1) / kSharedRows;
     if (s.precision == GAME_FP32) {
       fill_ones_kernel<<<(s.kp + 255) / 256, 256, 0, st>>>(e.colscale, s.kp);
     } else {
       cudaError_t err = cudaMemsetAsync(qmax_scratch, 0, sizeof(float) * s.kp, st);
       if (err != cudaSuccess) return err;
-      const long long nc = s.n_patterns * s.kb;
-      expand_shared_colmax_kernel<<<(unsigned)((nc + threads - 1) / threads), threads, 0, st>>>(a);
+      const unsigned cblocks = (unsigned)(nblk < 4864 ? nblk : 4864);
+      expand_shared_colmax_kernel<<<cblocks, kSharedRows, smem, st>>>(a);
       expand_scale_kernel<<<(s.kp + 255) / 256, 256, 0, st>>>(
           a.colmax_bits, e.colscale, s.kb, s.kp, s.precision == GAME_BF16 ? 1.0f : 448.0f);
     }
-    const long long ns = s.n_patterns * s.kp;
-    expand_shared_kernel<<<(unsigned)((ns + threads - 1) / threads), threads, 0, st>>>(a);
+    expand_shared_kernel<<<(unsigned)nblk, kSharedRows, smem, st>>>(a);
     return cudaGetLastError();
   }
   const long long n = s.n_patterns * s.n_features;

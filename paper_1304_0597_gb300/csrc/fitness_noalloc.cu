@@ -123,8 +123,7 @@ __global__ void noalloc_reduce_kernel(const double* partial, int n_part, int pop
                                       double inv_n, int err, double* fitness) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= pop) return;
-  double sse = 0.0;
-  for (int b = 0; b < n_part; ++b) sse += partial[(long long)b * pop_pad + c];
+  const double sse = sum_partials(partial, n_part, pop_pad, c);
   const double mse = sse * inv_n;
   fitness[c] = err == GAME_RMSE ? sqrt(mse) : mse;
 }

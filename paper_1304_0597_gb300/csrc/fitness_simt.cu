@@ -136,6 +136,14 @@ __host__ __device__ constexpr bool narrow_shape(int pop, int kp) {
   return pop >= 1 && pop <= kNarrowPop && (kp == 16 || kp == 32);
 }
 
+// Rows per thread and pass: each gene read from shared memory then feeds this
+// many patterns.  Two FP32 rows of 16 columns would need more than the 128
+// registers that two resident CTAs of 256 threads leave, and one CTA per SM
+// hides latency worse than the shared-memory reads cost (measured).
+__host__ __device__ constexpr int narrow_rows(int prec, int kp) {
+  return kp == 16 && prec != GAME_FP32 ? 2 : 1;
+}
+
 // One row of P as 16-byte words: FP32 = hi and lo fp16 planes, BF16 = one bf16
 // plane, FP8 = one e4m3 plane.
 template <int PREC, int KP>
@@ -213,28 +221,10 @@ __device__ __forceinline__ float narrow_error(float t, float s, int err, float R
   return e;
 }
 
-// acc[c] of every lane -> lane c holds the sum over the warp of acc[c]; returns
-// it and clears acc.  Five halving exchange rounds (31 shuffles), fixed order.
-__device__ __forceinline__ float narrow_flush(float acc[kNarrowPop], int lane) {
-#pragma unroll
-  for (int w = kNarrowPop / 2; w >= 1; w >>= 1) {
-    const bool upper = (lane & w) != 0;
-#pragma unroll
-    for (int i = 0; i < w; ++i) {
-      const float send = upper ? acc[i] : acc[i + w];
-      const float keep = upper ? acc[i + w] : acc[i];
-      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
-    }
-  }
-  const float r = acc[0];
-#pragma unroll
-  for (int i = 0; i < kNarrowPop; ++i) acc[i] = 0.0f;
-  return r;
-}
-
 template <int PREC, int KP, bool TANH>
 __global__ void __launch_bounds__(kNarrowThreads, 2) fitness_narrow_kernel(SimtArgs a) {
   if (a.in_evolve && a.state->stopped) return;
+  constexpr int kRows = narrow_rows(PREC, KP);
   __shared__ __align__(16) float Gt[KP][kNarrowPop];   // Gt[g][c] = G[c][g] (x s_g)
   __shared__ __align__(16) float bs[kNarrowPop];
   __shared__ double red[kNarrowThreads / 32][kNarrowPop];
@@ -257,52 +247,82 @@ __global__ void __launch_bounds__(kNarrowThreads, 2) fitness_narrow_kernel(SimtA
   for (int c = 0; c < kNarrowPop; ++c) acc[c] = 0.0f;
   double tot = 0.0;
   int nblk = 0;
-  const long long step = (long long)gridDim.x * kNarrowThreads;
-  // warp-uniform loop over groups of 32 consecutive patterns; the next row is
-  // loaded while the current one is used
-  long long k0 = (long long)blockIdx.x * kNarrowThreads + warp * 32;
-  NarrowRow<PREC, KP> nxt;
-  if (k0 + lane < a.m) narrow_load<PREC, KP>(a, k0 + lane, nxt);
-  for (; k0 < a.m; k0 += step) {
-    const long long k = k0 + lane;
-    const bool valid = k < a.m;
-    float p[KP];
-    if (valid) {
-      narrow_unpack<PREC, KP>(nxt, p);
-    } else {
+  // A warp takes 32 * kRows consecutive rows per pass (lane l: rows l, l + 32, ...);
+  // the loop is warp-uniform.  The next pass's rows are loaded into registers
+  // while this one runs.
+  const long long step = (long long)gridDim.x * kNarrowThreads * kRows;
+  long long k0 = ((long long)blockIdx.x * kNarrowThreads + warp * 32) * kRows;
+  NarrowRow<PREC, KP> nxt[kRows];
+  float tn[kRows];   // the targets travel with their rows
 #pragma unroll
-      for (int g = 0; g < KP; ++g) p[g] = 0.0f;
+  for (int r = 0; r < kRows; ++r) {
+    tn[r] = 0.0f;
+    if (k0 + lane + 32 * r < a.m) {
+      narrow_load<PREC, KP>(a, k0 + lane + 32 * r, nxt[r]);
+      tn[r] = __ldg(a.t + k0 + lane + 32 * r);
     }
-    const float t = valid ? a.t[k] : 0.0f;
-    if (k + step < a.m) narrow_load<PREC, KP>(a, k + step, nxt);
+  }
+  for (; k0 < a.m; k0 += step) {
+    float p[kRows][KP];
+    float t[kRows];
+    bool valid[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const long long k = k0 + lane + 32 * r;
+      valid[r] = k < a.m;
+      if (valid[r]) {
+        narrow_unpack<PREC, KP>(nxt[r], p[r]);
+      } else {
+#pragma unroll
+        for (int g = 0; g < KP; ++g) p[r][g] = 0.0f;
+      }
+      t[r] = tn[r];
+      if (k + step < a.m) {
+        narrow_load<PREC, KP>(a, k + step, nxt[r]);
+        tn[r] = __ldg(a.t + k + step);
+      }
+    }
 #pragma unroll
     for (int q = 0; q < kNarrowPop / 4; ++q) {
       if (q < ngroups) {
         const float4 b4 = *reinterpret_cast<const float4*>(&bs[4 * q]);
-        unsigned long long s01 = tc::pack2(b4.x, b4.y), s23 = tc::pack2(b4.z, b4.w);
+        unsigned long long s01[kRows], s23[kRows];
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+          s01[r] = tc::pack2(b4.x, b4.y);
+          s23[r] = tc::pack2(b4.z, b4.w);
+        }
 #pragma unroll
         for (int g = 0; g < KP; ++g) {
           const float4 gv = *reinterpret_cast<const float4*>(&Gt[g][4 * q]);
-          const unsigned long long pp = tc::pack2(p[g], p[g]);
-          s01 = tc::fma2(pp, tc::pack2(gv.x, gv.y), s01);
-          s23 = tc::fma2(pp, tc::pack2(gv.z, gv.w), s23);
-        }
-        float sv[4];
-        tc::unpack2(s01, sv[0], sv[1]);
-        tc::unpack2(s23, sv[2], sv[3]);
+          const unsigned long long g01 = tc::pack2(gv.x, gv.y), g23 = tc::pack2(gv.z, gv.w);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float e = narrow_error<TANH>(t, sv[j], a.err, a.R);
-          acc[4 * q + j] += valid ? e : 0.0f;
+          for (int r = 0; r < kRows; ++r) {
+            const unsigned long long pp = tc::pack2(p[r][g], p[r][g]);
+            s01[r] = tc::fma2(pp, g01, s01[r]);
+            s23[r] = tc::fma2(pp, g23, s23[r]);
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+          float sv[4];
+          tc::unpack2(s01[r], sv[0], sv[1]);
+          tc::unpack2(s23[r], sv[2], sv[3]);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float e = narrow_error<TANH>(t[r], sv[j], a.err, a.R);
+            acc[4 * q + j] += valid[r] ? e : 0.0f;
+          }
         }
       }
     }
-    if (++nblk == 32) {
-      tot += (double)narrow_flush(acc, lane);
+    nblk += kRows;
+    if (nblk == 32) {   // float32 sums over at most 32 patterns
+      tot += (double)tc::warp_column_sums32(acc, lane);
       nblk = 0;
     }
   }
-  tot += (double)narrow_flush(acc, lane);
+  tot += (double)tc::warp_column_sums32(acc, lane);
   red[warp][lane] = tot;
   __syncthreads();
   if (tid < kNarrowPop) {
@@ -325,7 +345,8 @@ bool simt_narrow(const Shape& s) { return narrow_shape(s.pop, s.kp); }
 
 int simt_partials(const Shape& s, int n_sm) {
   if (narrow_shape(s.pop, s.kp)) {
-    const long long need = (s.n_train + kNarrowThreads - 1) / kNarrowThreads;
+    const int rows = narrow_rows(s.precision, s.kp);
+    const long long need = (s.n_train + kNarrowThreads * rows - 1) / (kNarrowThreads * rows);
     const long long g = 2LL * n_sm;
     return (int)(need < 1 ? 1 : need < g ? need : g);
   }

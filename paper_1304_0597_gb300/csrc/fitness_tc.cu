@@ -425,6 +425,8 @@ cudaError_t tc_timeout_selftest(DevState* st, unsigned long long wait_ns, int* o
 }
 
 cudaError_t tc_init_attributes() {
+  cudaError_t en = tc_narrow_init_attributes();
+  if (en != cudaSuccess) return en;
   for (int bn : {128, 256})
     for (int prec : {GAME_FP32, GAME_BF16, GAME_FP8})
       for (bool fast : {false, true})
@@ -453,6 +455,10 @@ static int max_stages(const Shape& s, int bn, int sp) {
 }
 
 void tc_candidates(const Shape& s, std::vector<TileReq>* out) {
+  if (tc_narrow_shape(s)) {
+    tc_narrow_candidates(s, out);
+    return;
+  }
   const int n_slices = s.pop_pad / 128;
   for (int sp : {1, 2})
     for (int bn : {256, 128}) {
@@ -468,6 +474,7 @@ void tc_candidates(const Shape& s, std::vector<TileReq>* out) {
 
 cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, TcPlan* plan,
                     TileReq req) {
+  if (tc_narrow_shape(s)) return tc_narrow_plan(s, e, p, n_sm, plan, req);
   TcPlan& t = *plan;
   t.kblocks = kblocks_of(s);
   const int n_bplanes = s.precision == GAME_FP32 ? 2 : 1;
@@ -544,6 +551,7 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
 
 cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const PopDev& pd,
                       const ExpDev& e, double* partial, const DevState* state, cudaStream_t st) {
+  if (t.narrow) return tc_narrow_launch(t, s, f, pd, e, partial, state, st);
   TcParams p;
   p.a[0] = t.a_map[0];
   p.a[1] = t.a_map[1];

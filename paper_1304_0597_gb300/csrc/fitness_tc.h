@@ -25,6 +25,7 @@ struct TcPlan {
   int cluster;            // CTAs (one per group) sharing each B tile by TMA multicast
   int prefetch = 1;       // L2 prefetch of each CTA's next pattern tile
   size_t smem;            // dynamic shared memory bytes
+  int narrow = 0;         // 1: the swapped kernel (patterns on M, <= 32 chromosomes on N)
 };
 
 // Requested tile shape; 0 fields are chosen automatically.
@@ -41,6 +42,20 @@ void tc_candidates(const Shape& s, std::vector<TileReq>* out);
 cudaError_t tc_launch(const TcPlan& plan, const Shape& s, const Fitness& f, const PopDev& p,
                       const ExpDev& e, double* partial, const DevState* state, cudaStream_t st);
 cudaError_t tc_init_attributes();
+
+// Narrow populations in the FP32 form (at most 32 chromosomes): the swapped
+// kernel of fitness_tc_narrow.cu.  tc_narrow_fits: the kernel can take the shape;
+// tc_narrow_shape: it fits and the shape is marked for it (Shape::tc_narrow), in
+// which case tc_plan / tc_candidates / tc_launch route to it.
+bool tc_narrow_fits(const Shape& s);
+bool tc_narrow_shape(const Shape& s);
+void tc_narrow_candidates(const Shape& s, std::vector<TileReq>* out);
+cudaError_t tc_narrow_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm,
+                           TcPlan* plan, TileReq req);
+cudaError_t tc_narrow_launch(const TcPlan& t, const Shape& s, const Fitness& f, const PopDev& pd,
+                             const ExpDev& e, double* partial, const DevState* state,
+                             cudaStream_t st);
+cudaError_t tc_narrow_init_attributes();
 // Tensor map of a K-major operand plane [rows x cols] in the storage type of
 // `precision`, 128-byte rows per box, 128-byte swizzle, box of box_rows rows.
 cudaError_t tc_timeout_selftest(DevState* st, unsigned long long wait_ns, int* out, cudaStream_t s);

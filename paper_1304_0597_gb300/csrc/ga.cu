@@ -369,18 +369,35 @@ __global__ void __launch_bounds__(1024) reduce_rank_kernel(RankArgs a) {
   int* idx = reinterpret_cast<int*>(key + a.n2);
   __shared__ double best_f;
   const int tid = threadIdx.x;
+  if (a.mode == kRankEvaluate && a.n_part <= 32) {
+    // few partial rows: one thread per chromosome adds them in row order
+    for (int c = tid; c < a.pop; c += blockDim.x) {
+      const double mse = sum_partials(a.partial, a.n_part, a.pop_pad, c) * a.inv_m;
+      a.fit[c] = (a.error == GAME_RMSE) ? sqrt(mse) : mse;
+    }
+    __syncthreads();
+  } else if (a.mode == kRankEvaluate) {
+    // many (one per CTA of the narrow SIMT kernel): one warp per chromosome, lane l
+    // adds rows l, l + 32, ... in order, then a fixed butterfly adds the 32 lane
+    // sums (deterministic; the lanes' loads overlap instead of forming one chain
+    // of memory latencies)
+    const int lane = tid & 31;
+    for (int c = tid >> 5; c < a.pop; c += blockDim.x >> 5) {
+      double sse = 0.0;
+      for (int b = lane; b < a.n_part; b += 32) sse += a.partial[(long long)b * a.pop_pad + c];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, o);
+      if (lane == 0) {
+        const double mse = sse * a.inv_m;
+        a.fit[c] = (a.error == GAME_RMSE) ? sqrt(mse) : mse;
+      }
+    }
+    __syncthreads();
+  }
   for (int c = tid; c < a.n2; c += blockDim.x) {
     double f = CUDART_INF;
     if (c < a.pop) {
-      if (a.mode == kRankEvaluate) {
-        double sse = 0.0;
-        for (int b = 0; b < a.n_part; ++b) sse += a.partial[(long long)b * a.pop_pad + c];
-        const double mse = sse * a.inv_m;
-        f = (a.error == GAME_RMSE) ? sqrt(mse) : mse;
-        a.fit[c] = f;
-      } else {
-        f = a.fit[c];
-      }
+      f = a.fit[c];
       if (isnan(f)) f = CUDART_INF;
     }
     key[c] = ordered_key(f);
@@ -433,8 +450,7 @@ __global__ void fit_reduce_kernel(RankArgs a) {
   if (a.in_evolve && a.state->stopped) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= a.pop) return;
-  double sse = 0.0;
-  for (int b = 0; b < a.n_part; ++b) sse += a.partial[(long long)b * a.pop_pad + c];
+  const double sse = sum_partials(a.partial, a.n_part, a.pop_pad, c);
   const double mse = sse * a.inv_m;
   a.fit[c] = (a.error == GAME_RMSE) ? sqrt(mse) : mse;
 }
@@ -524,7 +540,10 @@ cudaError_t launch_reduce_rank(const Shape& s, const game_config& cfg, const dou
     return cudaGetLastError();
   }
   const size_t smem = (size_t)a.n2 * (sizeof(unsigned long long) + sizeof(int));
-  const int threads = a.n2 < 1024 ? (a.n2 < 32 ? 32 : a.n2) : 1024;
+  // n2 threads for the sort; with many partial rows, one warp per chromosome
+  int threads = a.n2 < 32 ? 32 : a.n2;
+  if (n_part > 32 && threads < 32 * s.pop) threads = 32 * s.pop;
+  if (threads > 1024) threads = 1024;
   reduce_rank_kernel<<<1, threads, smem, st>>>(a);
   return cudaGetLastError();
 }
@@ -537,8 +556,7 @@ __global__ void rescore_merge_kernel(const double* partial, int n_part, int pop_
   if (in_evolve && st->stopped) return;
   const int i = threadIdx.x;
   if (i >= n) return;
-  double sse = 0.0;
-  for (int b = 0; b < n_part; ++b) sse += partial[(long long)b * pop_pad + i];
+  const double sse = sum_partials(partial, n_part, pop_pad, i);
   const double mse = sse * inv_m;
   fit[rank[i]] = error == GAME_RMSE ? sqrt(mse) : mse;
 }

@@ -57,6 +57,7 @@ struct Shape {
   int pop_pad;            // pop padded to the 128-row MMA tile
   int precision;          // GAME_FP32 | GAME_BF16 | GAME_FP8
   int gene_planes;        // terms of each gene in the operand planes (FP32: always 2)
+  int tc_narrow = 0;      // tensor cores: the swapped kernel (patterns on M), see fitness_tc_narrow.cu
 };
 
 // Population double buffer plus the operand planes of the population being evaluated.
@@ -144,6 +145,24 @@ enum : int {
   kRankInEvolve = 1 << 8,
   kRankNoStop = 1 << 9,
 };
+
+// sum_{b < n_part} partial[b * stride + c], added in b order.  The loads are
+// issued eight at a time ahead of the adds: one chain of dependent global loads
+// would cost a memory latency per partial row.
+__device__ __forceinline__ double sum_partials(const double* __restrict__ partial, int n_part,
+                                               long long stride, long long c) {
+  double s = 0.0;
+  int b = 0;
+  for (; b + 8 <= n_part; b += 8) {
+    double v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = partial[(long long)(b + i) * stride + c];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += v[i];
+  }
+  for (; b < n_part; ++b) s += partial[(long long)b * stride + c];
+  return s;
+}
 
 // SIMT fitness (FFMA) over the training rows: partial sums [n_part x pop_pad].
 // simt_narrow: the shape takes the one-pattern-per-thread kernel (pop <= 32,

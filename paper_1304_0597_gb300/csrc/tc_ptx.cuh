@@ -310,6 +310,26 @@ struct F2Sum {
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
+// acc[c] of every lane of the warp -> the return value on lane c is the sum over
+// the 32 lanes of acc[c]; acc is cleared.  Five halving exchange rounds (31
+// shuffles), in a fixed order.
+__device__ __forceinline__ float warp_column_sums32(float acc[32], int lane) {
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool upper = (lane & w) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const float send = upper ? acc[i] : acc[i + w];
+      const float keep = upper ? acc[i + w] : acc[i];
+      acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  const float r = acc[0];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) acc[i] = 0.0f;
+  return r;
+}
+
 __device__ __forceinline__ float general_error(float t, float s, int act, int err, float R) {
   const float y = act == GAME_TANH ? tanhf(s) : s;
   const float d = t - y;

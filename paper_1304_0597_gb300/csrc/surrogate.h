@@ -82,12 +82,15 @@ struct Surrogate {
   cudaError_t tc_layers(int M, float* y, const float* t, cudaStream_t st);
   // one training step on the B rows in Xb / X^T with targets t: gradients, Adam
   cudaError_t tc_train_step(int B, const float* t, float lr, cudaStream_t st);
-  // dZ1^T, [gW2 | gb2] and [gW1 | gb1] of the batch just run forward with targets
-  cudaError_t tc_backward_gemms(int B, cudaStream_t st);
+  // dZ1^T, [gW2 | gb2] and [gW1 | gb1] of the batch just run forward with targets,
+  // as split-K planes in gws, added into g when sum_planes
+  cudaError_t tc_backward_gemms(int B, cudaStream_t st, bool sum_planes = true);
   // gw3, gb3 and the loss of that batch
   cudaError_t tc_out_grads(int B, cudaStream_t st);
-  // Adam step that also refreshes the bf16 GEMM copies and the step counter
-  cudaError_t tc_adam(float lr, cudaStream_t st);
+  // Adam step that also refreshes the bf16 GEMM copies and the step counter; with
+  // from_planes it adds the split-K planes of the last tc_backward_gemms itself
+  cudaError_t tc_adam(float lr, cudaStream_t st, bool from_planes = false);
+  int grad_splits = 0;       // split-K planes written by the last tc_backward_gemms
 };
 
 cudaError_t surrogate_tc_init_attributes();

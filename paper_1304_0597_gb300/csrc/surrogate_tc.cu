@@ -493,16 +493,26 @@ __global__ void out_grads_kernel(const float* __restrict__ dyh2, const float* __
 // Adam (Kingma & Ba 2015) over the flat parameters, with the bf16 copies that the
 // tensor-core GEMMs read (flat, W1 padded to Dp, W2 and W2^T).  Every block reads
 // the step count first; the last block to finish advances it.
+// With ws != nullptr the gradient of [W1 | b1 | W2 | b2] (the first n12 entries) is
+// the in-order sum of the split-K planes ws[z * n12 + i] (what grad_sum_kernel would
+// write to g first); w3 and b3 come from g.
 __global__ void adam_tc_kernel(float* __restrict__ p, const float* __restrict__ g,
                                float* __restrict__ m, float* __restrict__ v,
                                __nv_bfloat16* __restrict__ ph, long long n, int* step,
                                unsigned int* done, float lr, float beta1, float beta2, float eps,
                                int D, int Dp, int H, __nv_bfloat16* __restrict__ W1b,
-                               __nv_bfloat16* __restrict__ W2b, __nv_bfloat16* __restrict__ W2Tb) {
+                               __nv_bfloat16* __restrict__ W2b, __nv_bfloat16* __restrict__ W2Tb,
+                               const float* __restrict__ ws, int splits, long long n12) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int t = *step + 1;
   if (i < n) {
-    const float gi = g[i];
+    float gi;
+    if (ws && i < n12) {
+      gi = ws[i];
+      for (int z = 1; z < splits; ++z) gi += ws[z * n12 + i];
+    } else {
+      gi = g[i];
+    }
     const float mi = beta1 * m[i] + (1.0f - beta1) * gi;
     const float vi = beta2 * v[i] + (1.0f - beta2) * gi * gi;
     m[i] = mi;
@@ -717,8 +727,9 @@ cudaError_t Surrogate::tc_train_step(int B, const float* t, float lr, cudaStream
   cudaError_t e;
   if ((e = tc_layers(B, yb, t, st)) != cudaSuccess) return e;
   if ((e = tc_out_grads(B, st)) != cudaSuccess) return e;
-  if ((e = tc_backward_gemms(B, st)) != cudaSuccess) return e;
-  return tc_adam(lr, st);
+  // the Adam launch adds the split-K planes itself: one launch fewer per step
+  if ((e = tc_backward_gemms(B, st, false)) != cudaSuccess) return e;
+  return tc_adam(lr, st, true);
 }
 
 cudaError_t Surrogate::tc_layers(int M, float* y, const float* t, cudaStream_t st) {
@@ -778,14 +789,17 @@ cudaError_t Surrogate::tc_out_grads(int B, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t Surrogate::tc_adam(float lr, cudaStream_t st) {
+cudaError_t Surrogate::tc_adam(float lr, cudaStream_t st, bool from_planes) {
   const long long n = (long long)n_params();
-  adam_tc_kernel<<<ceil_div(n, 256), 256, 0, st>>>(p, g, m, v, ph, n, step, adam_done, lr, 0.9f,
-                                                  0.999f, 1e-8f, D, Dp, H, W1b, W2b, W2Tb);
+  const long long n12 = (long long)H * D + H + (long long)H * H + H;
+  if (from_planes && grad_splits < 1) return cudaErrorInvalidValue;
+  adam_tc_kernel<<<ceil_div(n, 256), 256, 0, st>>>(
+      p, g, m, v, ph, n, step, adam_done, lr, 0.9f, 0.999f, 1e-8f, D, Dp, H, W1b, W2b, W2Tb,
+      from_planes ? gws : nullptr, grad_splits, n12);
   return cudaGetLastError();
 }
 
-cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st) {
+cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st, bool sum_planes) {
   cudaError_t e;
   MlpParams a = {};
   a.state = state;
@@ -810,6 +824,7 @@ cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st) {
   const int kblocks = ceil_div(B, 64);
   const int kbps = ceil_div(kblocks, kGradSplits);
   const int splits = ceil_div(kblocks, kbps);
+  grad_splits = splits;
   float *wW1, *wb1, *wW2, *wb2, *ww3, *wb3;
   views(gws, &wW1, &wb1, &wW2, &wb2, &ww3, &wb3);
   // [gW2 | gb2] = dZ2^T [H1 | 1] : A = dZ2^T [H x B], B operand = [H1^T ; 1] [(H + 1) x B]
@@ -841,7 +856,7 @@ cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st) {
   if ((e = launch_mlp<128, kEpiGrad>(v, ceil_div(H, 128), ceil_div(D + 1, 128), st, splits)) !=
       cudaSuccess)
     return e;
-  grad_sum_kernel<<<ceil_div(n12, 256), 256, 0, st>>>(gws, splits, n12, g);
+  if (sum_planes) grad_sum_kernel<<<ceil_div(n12, 256), 256, 0, st>>>(gws, splits, n12, g);
   return cudaGetLastError();
 }
 

@@ -15,11 +15,16 @@
 // FP32 split as in the main kernel: P = P_hi + P_lo and G = G_hi + G_lo as fp16
 // pairs, D accumulates P_hi G_hi + P_lo G_hi + P_hi G_lo (kind::f16, float32 in
 // TMEM).  The gene planes (32 rows) stay in shared memory; pattern tiles of 128
-// rows stream through a ring of stages, one (k-block, plane) per stage.
+// rows stream through a ring of stages, one (k-block, plane) per stage.  A row of
+// P takes SWA bytes of shared memory: 32 or 64 when the whole stored row fits
+// (16 or 32 columns, 32- / 64-byte swizzle, one stage per tile and plane), else
+// 128-byte k-blocks.  With short rows a 128-byte k-block would be mostly zero
+// fill, and the ring would carry a quarter of the data it could.
 //
-// Roles (320 threads): warp 0 TMA producer, warp 1 TMEM allocator + MMA issuer,
-// warps 2..9 epilogue in two sets of four (set s takes the tiles of parity s and
-// TMEM buffer s; warp w reads lanes 32 (w % 4)).  Each epilogue thread adds its
+// Roles (448 threads): warp 0 TMA producer, warp 1 TMEM allocator + MMA issuer,
+// warps 2..13 epilogue in three sets of four (set s takes the tiles i = s mod 3;
+// tile i sits in TMEM accumulator i mod 4, so the MMAs run up to three tiles ahead
+// of the epilogue; warp w reads lanes 32 (w % 4)).  Each epilogue thread adds its
 // pattern's error per chromosome in float32 over blocks of 32 tiles; a butterfly
 // over the warp then gives lane c the block total of chromosome c, added in
 // float64.  Every mbarrier wait is bounded (2 s); on a timeout the CTA records
@@ -35,13 +40,32 @@ namespace {
 
 using namespace tc;
 
-constexpr int kNThreads = 64 + 32 * 8;
+constexpr int kNSets = 3;                        // epilogue sets of four warps
+constexpr int kNThreads = 64 + 32 * 4 * kNSets;
 constexpr int kNPop = 32;                        // chromosomes per launch (MMA N)
-constexpr int kNTileA = 128 * 128;               // one 128-pattern x 128-byte stage
 constexpr int kNTileG = kNPop * 128;             // one 32-row x 128-byte gene block
 constexpr int kNMaxKblocks = 12;
+constexpr int kNMaxStages = 32;
+constexpr int kNBuf = 8;                         // TMEM accumulators (32 columns each)
+constexpr int kNR = 2;                           // 128-pattern tiles per stage (one 256-row box)
 constexpr int kNSmemMax = 232448;
-constexpr int kNSmemMisc = 1024 + 512 + 8 * 32 * 8;   // alignment, barriers, warp totals
+constexpr int kNGuard = 1024;                    // after the ring, before the barriers
+// alignment, guard, barriers + TMEM slot + last parities, per-warp totals
+constexpr int kNSmemMisc = 1024 + kNGuard + 1024 + 4 * kNSets * 32 * 8 + kNPop * 4;
+
+// Shared-memory matrix descriptor for K-major rows of SW = 32, 64 or 128 bytes:
+// that swizzle, 8-row groups 8 * SW bytes apart, descriptor version 1.
+template <int SW>
+__device__ __forceinline__ uint64_t swz_desc(uint32_t saddr) {
+  static_assert(SW == 32 || SW == 64 || SW == 128, "swizzle span");
+  constexpr uint64_t kLayout = SW == 128 ? 2 : SW == 64 ? 4 : 6;
+  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)((8 * SW) >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= kLayout << 61;
+  return d;
+}
 
 struct NarrowParams {
   CUtensorMap a[2];       // expansion planes P_hi, P_lo (M operand, patterns x genes)
@@ -51,7 +75,7 @@ struct NarrowParams {
   double* partial;
   DevState* state;
   long long m;
-  int pop, pop_pad, n_tiles, kblocks, ksteps, stages, act, err, in_evolve;
+  int pop, pop_pad, n_tiles, per_cta, kblocks, ksteps, stages, act, err, in_evolve;
   float R;
 };
 
@@ -74,31 +98,39 @@ __device__ __forceinline__ float narrow_tc_error(float pk, float s, int act, int
   return e;
 }
 
-template <int EF>
+template <int EF, int SWA>
 __global__ void __launch_bounds__(kNThreads, 1) fitness_tc_narrow_kernel(const __grid_constant__ NarrowParams p) {
   if (p.in_evolve && p.state->stopped) return;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
   constexpr uint32_t kIdesc = make_idesc(128, kNPop, 0u);   // fp16 x fp16 -> f32
+  constexpr int kTileA = 128 * SWA;                         // one 128-pattern tile
+  constexpr int kStageA = kNR * kTileA;                     // one stage: kNR tiles
+  constexpr int kStepsA = SWA / 32;                         // 16-element K steps per A row block
+  const int a_blocks = (p.ksteps + kStepsA - 1) / kStepsA;  // A k-blocks per tile
   const int S = p.stages;
   uint8_t* sG = smem;                                      // [plane][kb] 4 KB blocks
-  uint8_t* sA = sG + 2 * p.kblocks * kNTileG;              // [stage] 16 KB
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + S * kNTileA);
+  uint8_t* sA = sG + 2 * p.kblocks * kNTileG;              // [stage] kStageA
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + S * kStageA + kNGuard);
   uint64_t* g_full = bars;
   uint64_t* a_full = bars + 1;
   uint64_t* a_empty = a_full + S;
   uint64_t* acc_full = a_empty + S;
-  uint64_t* acc_empty = acc_full + 2;
-  uint64_t* fin = acc_empty + 2;
+  uint64_t* acc_empty = acc_full + kNBuf;
+  uint64_t* fin = acc_empty + kNBuf;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* err = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* last_par = reinterpret_cast<int*>(tmem_slot + 2);   // [S]
-  double* red = reinterpret_cast<double*>(last_par + 16);  // [8][32]
+  double* red = reinterpret_cast<double*>(last_par + kNMaxStages);  // [epilogue warps][32]
+  float* bsm = reinterpret_cast<float*>(red + 4 * kNSets * 32);     // [32] gene 0 per chromosome
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int my_tiles =
-      (int)blockIdx.x < p.n_tiles ? (p.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  // This CTA's tiles are t0 .. t0 + my_tiles - 1 (contiguous, per_cta a multiple of kNR),
+  // loaded and multiplied kNR at a time; a group past the last tile reads zero fill.
+  const int t0 = (int)blockIdx.x * p.per_cta;
+  const int my_tiles = max(0, min(p.per_cta, p.n_tiles - t0));
+  const int my_groups = (my_tiles + kNR - 1) / kNR;
 
   if (threadIdx.x == 0) {
     mbar_init(g_full, 1);
@@ -107,19 +139,20 @@ __global__ void __launch_bounds__(kNThreads, 1) fitness_tc_narrow_kernel(const _
       mbar_init(a_empty + s, 1);
       last_par[s] = -1;
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kNBuf; ++b) {
       mbar_init(acc_full + b, 1);
-      mbar_init(acc_empty + b, 4);   // the four warps of the buffer's set
+      mbar_init(acc_empty + b, 4);   // the four warps of the set that reads the buffer
     }
     mbar_init(fin, 1);
     *err = 0;
+    for (int c = 0; c < kNPop; ++c) bsm[c] = c < p.pop ? p.bias[c] : 0.0f;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(2u * kNPop));
+                 "r"((uint32_t)(kNBuf * kNPop)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_before();
@@ -138,17 +171,17 @@ __global__ void __launch_bounds__(kNThreads, 1) fitness_tc_narrow_kernel(const _
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
-    for (int it = 0; it < my_tiles && ok; ++it) {
-      const int row0 = ((int)blockIdx.x + it * (int)gridDim.x) * 128;
-      for (int kb = 0; kb < p.kblocks && ok; ++kb)
+    for (int gi = 0; gi < my_groups && ok; ++gi) {
+      const int row0 = (t0 + gi * kNR) * 128;
+      for (int kb = 0; kb < a_blocks && ok; ++kb)
         for (int pl = 0; pl < 2; ++pl) {
           if (!warp_wait(a_empty + stage, phase ^ 1u, err, p.state, lane)) {
             ok = false;
             break;
           }
           if (lane == 0) {
-            mbar_expect_tx(a_full + stage, kNTileA);
-            tma_load_2d(sA + stage * kNTileA, &p.a[pl], kb * 64, row0, a_full + stage);
+            mbar_expect_tx(a_full + stage, kStageA);
+            tma_load_2d(sA + stage * kStageA, &p.a[pl], kb * (SWA / 2), row0, a_full + stage);
             last_par[stage] = (int)phase;
           }
           if (++stage == S) {
@@ -162,8 +195,8 @@ __global__ void __launch_bounds__(kNThreads, 1) fitness_tc_narrow_kernel(const _
       mbar_wait(g_full, 0, err, p.state);
       for (int s2 = 0; s2 < S; ++s2)
         if (last_par[s2] >= 0) {
-          const unsigned long long t0 = globaltimer();
-          while (!mbar_try_wait(a_full + s2, (uint32_t)last_par[s2]) && globaltimer() - t0 < kWaitNs) {
+          const unsigned long long w0 = globaltimer();
+          while (!mbar_try_wait(a_full + s2, (uint32_t)last_par[s2]) && globaltimer() - w0 < kWaitNs) {
           }
         }
     }
@@ -176,36 +209,49 @@ __global__ void __launch_bounds__(kNThreads, 1) fitness_tc_narrow_kernel(const _
       uint32_t phase = 0;
       const uint32_t a_addr = smem_u32(sA);
       const uint32_t g_addr = smem_u32(sG);
-      for (int it = 0; it < my_tiles; ++it) {
-        const int buf = it & 1;
-        const uint32_t ap = (uint32_t)((it >> 1) & 1);
-        if (!warp_wait(acc_empty + buf, ap ^ 1u, err, p.state, lane)) break;
+      bool ok = true;
+      for (int gi = 0; gi < my_groups && ok; ++gi) {
+        // the group's accumulators must be free before its first stage is multiplied
+        for (int r = 0; r < kNR && ok; ++r) {
+          const int it = gi * kNR + r;
+          ok = warp_wait(acc_empty + (it & (kNBuf - 1)), (uint32_t)((it / kNBuf) & 1) ^ 1u, err,
+                         p.state, lane);
+        }
+        if (!ok) break;
         fence_after();
-        const uint32_t d = tmem + (uint32_t)(buf * kNPop);
         uint32_t accum = 0;
-        bool ok = true;
-        for (int kb = 0; kb < p.kblocks && ok; ++kb) {
-          const int steps = min(4, p.ksteps - kb * 4);
+        for (int kb = 0; kb < a_blocks && ok; ++kb) {
+          const int steps = min(kStepsA, p.ksteps - kb * kStepsA);
           for (int pl = 0; pl < 2; ++pl) {
             if (!warp_wait(a_full + stage, phase, err, p.state, lane)) {
               ok = false;
               break;
             }
             fence_after();
-            const uint64_t adesc = sw128_desc(a_addr + (uint32_t)(stage * kNTileA));
             // P_hi meets G_hi and G_lo; P_lo meets G_hi
             const int n_g = pl == 0 ? 2 : 1;
-            for (int gi = 0; gi < n_g; ++gi) {
-              const uint64_t gdesc =
-                  sw128_desc(g_addr + (uint32_t)((gi * p.kblocks + kb) * kNTileG));
 #pragma unroll
-              for (int k = 0; k < 4; ++k) {
-                if (k < steps) {
-                  // +32 bytes along K inside the 128-byte swizzle row = +2 in the address field
-                  if (lane == 0) mma<GAME_FP32>(d, adesc + 2 * k, gdesc + 2 * k, kIdesc, accum);
-                  accum = 1;
+            for (int r = 0; r < kNR; ++r) {
+              const uint32_t d = tmem + (uint32_t)(((gi * kNR + r) & (kNBuf - 1)) * kNPop);
+              const uint64_t adesc =
+                  swz_desc<SWA>(a_addr + (uint32_t)(stage * kStageA + r * kTileA));
+              uint32_t acc_r = accum;
+              for (int g = 0; g < n_g; ++g) {
+#pragma unroll
+                for (int k = 0; k < kStepsA; ++k) {
+                  if (k < steps) {
+                    // K step ks of the row: gene block ks / 4, +32 bytes per step inside
+                    // a swizzled row = +2 in the address field (on both sides)
+                    const int ks = kb * kStepsA + k;
+                    const uint64_t gdesc = swz_desc<128>(
+                        g_addr + (uint32_t)((g * p.kblocks + (ks >> 2)) * kNTileG));
+                    if (lane == 0)
+                      mma<GAME_FP32>(d, adesc + 2 * k, gdesc + 2 * (ks & 3), kIdesc, acc_r);
+                    acc_r = 1;
+                  }
                 }
               }
+              if (r == kNR - 1) accum = acc_r;
             }
             if (lane == 0) mma_commit(a_empty + stage);
             if (++stage == S) {
@@ -215,57 +261,57 @@ __global__ void __launch_bounds__(kNThreads, 1) fitness_tc_narrow_kernel(const _
           }
         }
         if (!ok) break;
-        if (lane == 0) mma_commit(acc_full + buf);
+        if (lane == 0)
+          for (int r = 0; r < kNR; ++r) mma_commit(acc_full + ((gi * kNR + r) & (kNBuf - 1)));
       }
     }
     // Drain: all issued MMAs complete before TMEM is released.
     if (lane == 0) {
       mma_commit(fin);
-      const unsigned long long t0 = globaltimer();
-      while (!mbar_try_wait(fin, 0) && globaltimer() - t0 < kWaitNs) {
+      const unsigned long long w0 = globaltimer();
+      while (!mbar_try_wait(fin, 0) && globaltimer() - w0 < kWaitNs) {
       }
     }
     __syncwarp();
   } else {
     // ---- epilogue: thread = one pattern of the tile, all chromosomes ----
     const int ew = warp - 2;
-    const int set = ew >> 2;               // tiles of parity `set`, TMEM buffer `set`
+    const int set = ew >> 2;               // tiles it = set (mod kNSets)
     const int q = warp & 3;                // TMEM lane quadrant
-    float bias[kNPop];
-#pragma unroll
-    for (int c = 0; c < kNPop; ++c) bias[c] = c < p.pop ? p.bias[c] : 0.0f;
+
     float acc[kNPop];
 #pragma unroll
     for (int c = 0; c < kNPop; ++c) acc[c] = 0.0f;
     double tot = 0.0;
     int nblk = 0;
-    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(set * kNPop);
-    // This thread's pattern in the set's tiles it = set, set + 2, ...: k advances by
-    // 2 * grid * 128 per tile.  Its target is loaded two tiles ahead (a DRAM miss:
-    // the pattern stream evicts the targets from L2); the target arrays are padded
-    // past the last tile.
-    const long long kstep = 2LL * gridDim.x * 128;
-    long long k = ((long long)blockIdx.x + (long long)set * gridDim.x) * 128 + q * 32 + lane;
+    const uint32_t tlane = tmem + ((uint32_t)(q * 32) << 16);
+    // This thread's pattern in the set's tiles it = set, set + kNSets, ...: k advances
+    // by kNSets * 128 per tile.  Its target is loaded two tiles ahead (a DRAM miss: the
+    // pattern stream evicts the targets from L2); the target arrays are padded past the
+    // last tile.
+    const long long kstep = (long long)kNSets * 128;
+    long long k = (long long)(t0 + set) * 128 + q * 32 + lane;
     float pk0 = set < my_tiles ? p.pk[k] : 0.0f;
-    float pk1 = set + 2 < my_tiles ? p.pk[k + kstep] : 0.0f;
-    for (int it = set; it < my_tiles; it += 2, k += kstep) {
-      const uint32_t ap = (uint32_t)((it >> 1) & 1);
+    float pk1 = set + kNSets < my_tiles ? p.pk[k + kstep] : 0.0f;
+    for (int it = set; it < my_tiles; it += kNSets, k += kstep) {
+      const int buf = it & (kNBuf - 1);
+      const uint32_t ap = (uint32_t)((it / kNBuf) & 1);
       const float pk = pk0;
       pk0 = pk1;
-      pk1 = it + 4 < my_tiles ? p.pk[k + 2 * kstep] : 0.0f;
-      if (!warp_wait(acc_full + set, ap, err, p.state, lane)) break;
+      pk1 = it + 2 * kNSets < my_tiles ? p.pk[k + 2 * kstep] : 0.0f;
+      if (!warp_wait(acc_full + buf, ap, err, p.state, lane)) break;
       fence_after();
       float v[kNPop];
-      tmem_ld32(taddr, v);
+      tmem_ld32(tlane + (uint32_t)(buf * kNPop), v);
       // the accumulator is in registers: hand the buffer back to the MMA warp
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty + set);
+      if (lane == 0) mbar_arrive(acc_empty + buf);
       const bool valid = k < p.m;
       // all 32 columns, without branches: columns past the population are never read
 #pragma unroll
       for (int c = 0; c < kNPop; ++c) {
-        const float e = narrow_tc_error<EF>(pk, v[c] + bias[c], p.act, p.err, p.R);
+        const float e = narrow_tc_error<EF>(pk, v[c] + bsm[c], p.act, p.err, p.R);
         acc[c] += valid ? e : 0.0f;
       }
       if (++nblk == 32) {
@@ -281,35 +327,77 @@ __global__ void __launch_bounds__(kNThreads, 1) fitness_tc_narrow_kernel(const _
   fence_after();
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(2u * kNPop));
+                 "r"((uint32_t)(kNBuf * kNPop)));
   if (threadIdx.x < kNPop) {
     double sum = 0.0;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) sum += red[w * 32 + threadIdx.x];
+    for (int w = 0; w < 4 * kNSets; ++w) sum += red[w * 32 + threadIdx.x];
     p.partial[(long long)blockIdx.x * p.pop_pad + threadIdx.x] = sum;
   }
 }
 
-void* narrow_kernel(int ef) {
+template <int SWA>
+void* narrow_kernel_sw(int ef) {
   switch (ef) {
-    case kEfFast: return reinterpret_cast<void*>(&fitness_tc_narrow_kernel<kEfFast>);
-    case kEfMse: return reinterpret_cast<void*>(&fitness_tc_narrow_kernel<kEfMse>);
-    case kEfTmse: return reinterpret_cast<void*>(&fitness_tc_narrow_kernel<kEfTmse>);
-    case kEfTmseSq: return reinterpret_cast<void*>(&fitness_tc_narrow_kernel<kEfTmseSq>);
-    default: return reinterpret_cast<void*>(&fitness_tc_narrow_kernel<kEfGeneral>);
+    case kEfFast: return reinterpret_cast<void*>(&fitness_tc_narrow_kernel<kEfFast, SWA>);
+    case kEfMse: return reinterpret_cast<void*>(&fitness_tc_narrow_kernel<kEfMse, SWA>);
+    case kEfTmse: return reinterpret_cast<void*>(&fitness_tc_narrow_kernel<kEfTmse, SWA>);
+    case kEfTmseSq: return reinterpret_cast<void*>(&fitness_tc_narrow_kernel<kEfTmseSq, SWA>);
+    default: return reinterpret_cast<void*>(&fitness_tc_narrow_kernel<kEfGeneral, SWA>);
   }
+}
+
+void* narrow_kernel(int ef, int swa) {
+  return swa == 32 ? narrow_kernel_sw<32>(ef) : swa == 64 ? narrow_kernel_sw<64>(ef)
+                                                          : narrow_kernel_sw<128>(ef);
 }
 
 int narrow_kblocks(const Shape& s) { return (s.kp + 63) / 64; }
 
+// Tiles per CTA over `ctas` CTAs, rounded up to whole stages of kNR tiles.  For the
+// grid this gives, every CTA gets at least one tile and the ranges cover all.
+int narrow_per_cta(int n_tiles, int ctas) {
+  const int per = (n_tiles + ctas - 1) / ctas;
+  return (per + kNR - 1) / kNR * kNR;
+}
+
+// Bytes of shared memory per stored row of P: the whole row when it is 32 or 64 bytes.
+int narrow_swa(const Shape& s) { return s.kp * 2 <= 32 ? 32 : s.kp * 2 <= 64 ? 64 : 128; }
+
 size_t narrow_smem(const Shape& s, int stages) {
-  return (size_t)2 * narrow_kblocks(s) * kNTileG + (size_t)stages * kNTileA + kNSmemMisc;
+  return (size_t)2 * narrow_kblocks(s) * kNTileG + (size_t)stages * kNR * 128 * narrow_swa(s) +
+         kNSmemMisc;
 }
 
 int narrow_max_stages(const Shape& s) {
   const long long room = kNSmemMax - kNSmemMisc - 2LL * narrow_kblocks(s) * kNTileG;
-  const long long st = room / kNTileA;
-  return (int)(st > 10 ? 10 : st);
+  const long long st = room / ((long long)kNR * 128 * narrow_swa(s));
+  // 128-byte rows: up to 6 stages of 32 KB; shorter rows: up to 32 stages
+  const long long cap = narrow_swa(s) == 128 ? 10 : 32;
+  return (int)(st > cap ? cap : st);
+}
+
+cudaError_t narrow_map(CUtensorMap* m, const void* base, long long rows, int cols, int swa) {
+  if (swa == 128) return tc_make_map(m, base, GAME_FP32, rows, cols, 128 * kNR);
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* ptr = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return cudaErrorNotSupported;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  cuuint32_t box[2] = {(cuuint32_t)(swa / 2), (cuuint32_t)(128 * kNR)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  swa == 32 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace
@@ -323,7 +411,7 @@ bool tc_narrow_shape(const Shape& s) { return s.tc_narrow && tc_narrow_fits(s); 
 
 void tc_narrow_candidates(const Shape& s, std::vector<TileReq>* out) {
   const int ms = narrow_max_stages(s);
-  for (int st : {ms, 6, 4, 3})
+  for (int st : {ms, 16, 6, 4})
     if (st >= 2 && st <= ms) {
       bool dup = false;
       for (const TileReq& r : *out) dup |= r.stages == st;
@@ -343,18 +431,21 @@ cudaError_t tc_narrow_plan(const Shape& s, const ExpDev& e, const PopDev& p, int
   t.prefetch = 0;
   t.kblocks = narrow_kblocks(s);
   const int ms = narrow_max_stages(s);
-  t.stages = req.stages ? req.stages : (ms < 6 ? ms : 6);
+  const int dflt = narrow_swa(s) == 128 ? 6 : 16;
+  t.stages = req.stages ? req.stages : (ms < dflt ? ms : dflt);
   if (t.stages < 2 || t.stages > ms) return cudaErrorNotSupported;
   t.n_slices = 1;
   t.n_groups = 1;
   t.n_tiles = (int)((s.n_train + 127) / 128);
-  t.grid = t.n_tiles < n_sm ? t.n_tiles : n_sm;
+  // contiguous tile ranges, a multiple of kNR tiles each, over at most one CTA per SM
+  t.grid = (t.n_tiles + narrow_per_cta(t.n_tiles, n_sm) - 1) / narrow_per_cta(t.n_tiles, n_sm);
   t.ctas_per_slice = t.grid;
   t.n_part = t.grid;
   t.smem = narrow_smem(s, t.stages);
   cudaError_t err;
-  if ((err = tc_make_map(&t.b_map[0], e.p0, GAME_FP32, s.n_train, s.kp, 128)) != cudaSuccess) return err;
-  if ((err = tc_make_map(&t.b_map[1], e.p1, GAME_FP32, s.n_train, s.kp, 128)) != cudaSuccess) return err;
+  const int swa = narrow_swa(s);
+  if ((err = narrow_map(&t.b_map[0], e.p0, s.n_train, s.kp, swa)) != cudaSuccess) return err;
+  if ((err = narrow_map(&t.b_map[1], e.p1, s.n_train, s.kp, swa)) != cudaSuccess) return err;
   if ((err = tc_make_map(&t.a_map[0], p.ghi, GAME_FP32, s.pop_pad, s.kp, kNPop)) != cudaSuccess) return err;
   if ((err = tc_make_map(&t.a_map[1], p.glo, GAME_FP32, s.pop_pad, s.kp, kNPop)) != cudaSuccess) return err;
   return cudaSuccess;
@@ -378,6 +469,7 @@ cudaError_t tc_narrow_launch(const TcPlan& t, const Shape& s, const Fitness& f, 
   p.pop = s.pop;
   p.pop_pad = s.pop_pad;
   p.n_tiles = t.n_tiles;
+  p.per_cta = narrow_per_cta(t.n_tiles, t.grid);
   p.kblocks = t.kblocks;
   p.ksteps = s.kp / 16;
   p.stages = t.stages;
@@ -391,15 +483,17 @@ cudaError_t tc_narrow_launch(const TcPlan& t, const Shape& s, const Fitness& f, 
   else if (f.activation == GAME_LINEAR)
     ef = f.error == GAME_TMSE ? kEfTmse : f.error == GAME_TMSE_SQ ? kEfTmseSq : kEfMse;
   void* args[] = {&p};
-  return cudaLaunchKernel(narrow_kernel(ef), dim3(t.grid), dim3(kNThreads), args, t.smem, st);
+  return cudaLaunchKernel(narrow_kernel(ef, narrow_swa(s)), dim3(t.grid), dim3(kNThreads), args,
+                          t.smem, st);
 }
 
 cudaError_t tc_narrow_init_attributes() {
-  for (int ef = kEfFast; ef <= kEfGeneral; ++ef) {
-    cudaError_t e = cudaFuncSetAttribute(narrow_kernel(ef),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kNSmemMax);
-    if (e != cudaSuccess) return e;
-  }
+  for (int swa : {32, 64, 128})
+    for (int ef = kEfFast; ef <= kEfGeneral; ++ef) {
+      cudaError_t e = cudaFuncSetAttribute(narrow_kernel(ef, swa),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, kNSmemMax);
+      if (e != cudaSuccess) return e;
+    }
   return cudaSuccess;
 }
 

@@ -94,7 +94,17 @@ struct game_ctx {
   std::vector<cudaEvent_t> ev_pool;    // 4 events per generation of a timed call
   bool timing_on = false;
   game_timing timing{};
-  std::vector<void*> allocs;
+  // Device blocks of the data set, in allocation order.  A later game_set_data walks
+  // the same order and reuses every block whose size matches (same shapes: all of
+  // them), so repeated runs on equal shapes pay no cudaMalloc / cudaFree.
+  struct Block {
+    void* p;
+    size_t bytes;
+  };
+  std::vector<Block> allocs;
+  size_t alloc_next = 0;
+  cudaStream_t st_copy = nullptr;      // host-to-device copies of set_data, overlapped with the expansion
+  std::vector<cudaEvent_t> copy_ev;    // one per copied chunk
 };
 
 static std::string g_global_err;
@@ -122,15 +132,33 @@ static game_status fail(game_ctx* c, game_status code, const char* fmt, ...) {
                   "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);     \
   } while (0)
 
+// Blocks from position alloc_next on are released (the sequence changed or ended).
+static void release_tail(game_ctx* c) {
+  for (size_t i = c->alloc_next; i < c->allocs.size(); ++i) cudaFree(c->allocs[i].p);
+  c->allocs.resize(c->alloc_next);
+}
+
+// The next zero-filled device block of the data set: the block at this position of
+// the previous sequence when its size matches, else a new one.
 template <typename T>
 static game_status dalloc(game_ctx* c, T** ptr, size_t bytes) {
   *ptr = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc((void**)ptr, bytes);
-  if (e != cudaSuccess)
-    return fail(c, GAME_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
-  c->allocs.push_back(*ptr);
-  e = cudaMemsetAsync(*ptr, 0, bytes, c->st);
+  if (c->alloc_next < c->allocs.size()) {
+    if (c->allocs[c->alloc_next].bytes == bytes) {
+      *ptr = static_cast<T*>(c->allocs[c->alloc_next++].p);
+    } else {
+      release_tail(c);
+    }
+  }
+  if (!*ptr) {
+    cudaError_t e = cudaMalloc((void**)ptr, bytes);
+    if (e != cudaSuccess)
+      return fail(c, GAME_ERR_OOM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    c->allocs.push_back(game_ctx::Block{*ptr, bytes});
+    ++c->alloc_next;
+  }
+  cudaError_t e = cudaMemsetAsync(*ptr, 0, bytes, c->st);
   if (e != cudaSuccess) return fail(c, GAME_ERR_CUDA, "cudaMemset: %s", cudaGetErrorString(e));
   return GAME_OK;
 }
@@ -145,8 +173,16 @@ static void drop_graphs(game_ctx* c) {
 
 static void free_all(game_ctx* c) {
   drop_graphs(c);
-  for (void* p : c->allocs) cudaFree(p);
-  c->allocs.clear();
+  c->alloc_next = 0;
+  release_tail(c);
+  c->have_data = false;
+}
+
+// Start a new data set on the blocks of the last one (see game_ctx::allocs).
+static void reuse_blocks(game_ctx* c) {
+  cudaStreamSynchronize(c->st);   // nothing of the last data set is still in flight
+  drop_graphs(c);
+  c->alloc_next = 0;
   c->have_data = false;
 }
 
@@ -279,6 +315,8 @@ extern "C" void game_destroy(game_ctx* c) {
   cudaStreamSynchronize(c->st);
   free_all(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : c->copy_ev) cudaEventDestroy(e);
+  if (c->st_copy) cudaStreamDestroy(c->st_copy);
   delete c;
 }
 
@@ -473,7 +511,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   const long long kb = (long long)B * (shared ? 1 : n_features) * c->cfg.degree;
   if (kb > 4096)
     return fail(c, GAME_ERR_UNSUPPORTED, "%lld basis columns exceed 4096", kb);
-  free_all(c);
+  reuse_blocks(c);
   Shape& s = c->s;
   s.n_patterns = n_patterns;
   s.n_train = n_train;
@@ -501,11 +539,56 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   if ((r = dalloc(c, &dX, xbytes)) != GAME_OK) return r;
   const long long tpad = (n_patterns + 255) / 256 * 256 + 256;
   if ((r = dalloc(c, &c->e.t, sizeof(float) * tpad)) != GAME_OK) return r;
-  CUDA_OK(c, cudaMemcpyAsync(dX, X, xbytes, device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
-  CUDA_OK(c, cudaMemcpyAsync(c->e.t, t, sizeof(float) * n_patterns,
-                             device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
   unsigned int* dflags = nullptr;
   if ((r = dalloc(c, &dflags, sizeof(unsigned int))) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->e.tcoef, sizeof(float) * tpad)) != GAME_OK) return r;
+  const size_t esz = s.precision == GAME_FP32 ? 2 : (s.precision == GAME_BF16 ? 2 : 1);
+  const size_t pbytes = esz * (size_t)n_patterns * s.kp;
+  if ((r = dalloc(c, &c->e.p0, pbytes)) != GAME_OK) return r;
+  if (s.precision == GAME_FP32) {
+    if ((r = dalloc(c, &c->e.p1, pbytes)) != GAME_OK) return r;
+  }
+  if ((r = dalloc(c, &c->e.colscale, sizeof(float) * s.kp)) != GAME_OK) return r;
+  if ((r = dalloc(c, &c->d_scratch, sizeof(float) * s.kp)) != GAME_OK) return r;
+  CUDA_OK(c, cudaMemcpyAsync(c->e.t, t, sizeof(float) * n_patterns,
+                             device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+
+  // Expansion matrix (Section 4.1: computed once, reused every generation).  From
+  // host memory in the FP32 form, X comes over in chunks on a copy stream and each
+  // chunk is expanded as soon as it lands (the rows are independent); the
+  // quantised forms need the column maxima of all rows first.
+  if (!device_ptrs && s.precision == GAME_FP32) {
+    if (!c->st_copy) CUDA_OK(c, cudaStreamCreateWithFlags(&c->st_copy, cudaStreamNonBlocking));
+    const long long chunk = std::max<long long>(65536, ((long long)n_patterns + 7) / 8);
+    const int n_chunks = (int)((n_patterns + chunk - 1) / chunk);
+    while ((int)c->copy_ev.size() < n_chunks) {
+      cudaEvent_t e;
+      CUDA_OK(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      c->copy_ev.push_back(e);
+    }
+    // the copy stream starts after this call's earlier work (the block memsets)
+    CUDA_OK(c, cudaEventRecord(c->copy_ev[0], c->st));
+    CUDA_OK(c, cudaStreamWaitEvent(c->st_copy, c->copy_ev[0], 0));
+    for (int i = 0; i < n_chunks; ++i) {
+      const long long r0 = i * chunk;
+      const long long nr = std::min<long long>(chunk, (long long)n_patterns - r0);
+      CUDA_OK(c, cudaMemcpyAsync(dX + r0 * n_features, X + r0 * n_features,
+                                 sizeof(float) * (size_t)nr * n_features, cudaMemcpyHostToDevice,
+                                 c->st_copy));
+      CUDA_OK(c, cudaEventRecord(c->copy_ev[i], c->st_copy));
+      CUDA_OK(c, cudaStreamWaitEvent(c->st, c->copy_ev[i], 0));
+      Shape sc = s;
+      sc.n_patterns = nr;
+      ExpDev ec = c->e;
+      ec.p0 = static_cast<__half*>(c->e.p0) + r0 * s.kp;
+      ec.p1 = static_cast<__half*>(c->e.p1) + r0 * s.kp;
+      CUDA_OK(c, launch_expand(dX + r0 * n_features, sc, ec, c->d_scratch, c->st));
+    }
+  } else {
+    CUDA_OK(c, cudaMemcpyAsync(dX, X, xbytes,
+                               device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               c->st));
+  }
   check_data_kernel<<<4 * c->n_sm, 256, 0, c->st>>>(dX, n_patterns * n_features, c->e.t,
                                                       n_patterns, n_train, dflags);
   CUDA_OK(c, cudaGetLastError());
@@ -517,19 +600,9 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
     return fail(c, GAME_ERR_NUMERIC, "X or t holds NaN or Inf");
   }
   c->fit.pm1_targets = (flags & 2u) ? 0 : 1;
-  if ((r = dalloc(c, &c->e.tcoef, sizeof(float) * tpad)) != GAME_OK) return r;
   CUDA_OK(c, launch_target_coef(c->e.t, c->e.tcoef, n_patterns, c->st));
-
-  // Expansion matrix (Section 4.1: computed once, reused every generation).
-  const size_t esz = s.precision == GAME_FP32 ? 2 : (s.precision == GAME_BF16 ? 2 : 1);
-  const size_t pbytes = esz * (size_t)n_patterns * s.kp;
-  if ((r = dalloc(c, &c->e.p0, pbytes)) != GAME_OK) return r;
-  if (s.precision == GAME_FP32) {
-    if ((r = dalloc(c, &c->e.p1, pbytes)) != GAME_OK) return r;
-  }
-  if ((r = dalloc(c, &c->e.colscale, sizeof(float) * s.kp)) != GAME_OK) return r;
-  if ((r = dalloc(c, &c->d_scratch, sizeof(float) * s.kp)) != GAME_OK) return r;
-  CUDA_OK(c, launch_expand(dX, s, c->e, c->d_scratch, c->st));
+  if (device_ptrs || s.precision != GAME_FP32)
+    CUDA_OK(c, launch_expand(dX, s, c->e, c->d_scratch, c->st));
   c->lowp = s.precision != GAME_FP32;
   c->s32 = s;
   c->e32 = c->e;
@@ -610,13 +683,9 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   CUDA_OK(c, launch_state_op(c->d_state, kStateReset, c->st));
   CUDA_OK(c, launch_init_population(s, c->cfg.init, c->cfg.seed, c->cfg.run, c->p.g32[0], c->st));
   CUDA_OK(c, cudaStreamSynchronize(c->st));
-  // X is no longer needed once P exists.
-  for (size_t i = 0; i < c->allocs.size(); ++i)
-    if (c->allocs[i] == dX) {
-      cudaFree(dX);
-      c->allocs.erase(c->allocs.begin() + i);
-      break;
-    }
+  // The blocks of a longer earlier sequence are not needed.  X stays allocated (it
+  // is no longer read once P exists) for the next data set of the same shape.
+  release_tail(c);
   c->have_data = true;
   return GAME_OK;
 }

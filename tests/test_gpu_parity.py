@@ -39,13 +39,27 @@ def test_expansion_matches_closed_form(basis, F, d):
     np.testing.assert_allclose(got, want, rtol=0, atol=6e-7)
 
 
-def test_expansion_of_device_inputs_equals_host_inputs():
+@pytest.mark.parametrize("n", [700, 200_003])
+def test_expansion_of_device_inputs_equals_host_inputs(n):
+    """From host memory the FP32 expansion runs chunk by chunk as X arrives (200,003 rows:
+    four chunks and a ragged last one); from device memory in one launch."""
     import torch
-    ds = synth.make_dataset(700, 5, 3, seed=4)
+    ds = synth.make_dataset(n, 5, 3, seed=4)
     ocfg = _cfg(degree=3)
     a = make_game(ocfg, ds.X, ds.t, ds.n_train)
     b = make_game(ocfg, torch.from_numpy(ds.X).cuda(), torch.from_numpy(ds.t).cuda(), ds.n_train)
-    np.testing.assert_array_equal(a.expansion(0, 700), b.expansion(0, 700))
+    np.testing.assert_array_equal(a.expansion(0, n), b.expansion(0, n))
+    fa, _ = a.evaluate()
+    fb, _ = b.evaluate()
+    np.testing.assert_array_equal(fa, fb)
+    # a second data set of the same shape reuses the device blocks of the first
+    a.set_data(ds.X[::-1].copy(), ds.t[::-1].copy(), ds.n_train)
+    b.set_data(torch.from_numpy(ds.X[::-1].copy()).cuda(), torch.from_numpy(ds.t[::-1].copy()).cuda(),
+               ds.n_train)
+    np.testing.assert_array_equal(a.expansion(0, n), b.expansion(0, n))
+    m = min(n, 1000)
+    P = o.expand(ds.X[::-1][:m], "chebyshev", 3)[:, 1:]
+    np.testing.assert_allclose(a.expansion(0, m), P, rtol=0, atol=6e-7)
 
 
 # ------------------------------------------------------------------- fitness

@@ -423,8 +423,17 @@ __global__ void __launch_bounds__(256) score_kernel(const void* p0, const void* 
   double v[5] = {0, 0, 0, 0, 0};
   for (long long r = r0 + (long long)blockIdx.x * blockDim.x + threadIdx.x; r < r1;
        r += (long long)gridDim.x * blockDim.x) {
-    double s = (double)genes[0];
-    for (int c = 0; c < kb; ++c) s += (double)load_p<PREC>(p0, p1, cs, r * kp + c, c) * (double)genes[1 + c];
+    // four interleaved float64 partial sums: one dependent chain of kb float64 FMAs
+    // per row would leave the (narrow) float64 pipe waiting on its own latency
+    double part[4] = {0.0, 0.0, 0.0, 0.0};
+    int c = 0;
+    for (; c + 4 <= kb; c += 4) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        part[j] += (double)load_p<PREC>(p0, p1, cs, r * kp + c + j, c + j) * (double)genes[1 + c + j];
+    }
+    for (; c < kb; ++c) part[0] += (double)load_p<PREC>(p0, p1, cs, r * kp + c, c) * (double)genes[1 + c];
+    const double s = (double)genes[0] + ((part[0] + part[1]) + (part[2] + part[3]));
     const double y = act == GAME_TANH ? tanh(s) : s;
     const double tt = (double)t[r];
     const double d = tt - y;

@@ -571,7 +571,7 @@ def surrogate_ttt(args):
         "mean_test_accuracy_delta": {name: dacc(name) for name, _ in contenders},
         "config": {"workload": "2,000,000 patterns x 48 features, Chebyshev d=6, 289 genes, "
                                "pop 4096, 8x pool, surrogate MLP 289-256-256-1 (bf16, tcgen05)",
-                   "surrogate_steps_per_generation": 4, "surrogate_batch": 1024,
+                   "surrogate_steps_per_generation": 6, "surrogate_batch": 1024,
                    "surrogate_lr": 2e-3, "replay_ring": "latest population (4096 pairs)",
                    "inputs": "genes standardised by running per-gene statistics"}}), flush=True)
 

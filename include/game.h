@@ -97,7 +97,7 @@ typedef struct game_config {
   int32_t elite_rescore;  /* low precision: top-n re-scored with the FP32 path each gen     */
   int32_t gene_planes;    /* low precision: genes as 1 or 2 terms in P's format (0 = 2)     */
   int32_t surrogate_pool; /* 0 off; else offspring pool multiplier screened by the MLP      */
-  int32_t surrogate_steps;  /* Adam steps per generation (0 = 4)                            */
+  int32_t surrogate_steps;  /* Adam steps per generation (0 = 6)                            */
   int32_t surrogate_batch;  /* training batch rows (0 = 1024)                               */
   float surrogate_lr;       /* Adam learning rate (0 = 2e-3)                                */
   int32_t surrogate_select; /* 0: surrogate's best of the pool; 1: plain children (ablation)*/

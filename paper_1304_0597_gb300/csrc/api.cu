@@ -426,7 +426,7 @@ __global__ void fill_f32_kernel(float* p, long long n, float v) {
 // Network, pool, replay ring and training buffers of the surrogate.
 static game_status alloc_surrogate(game_ctx* c) {
   const Shape& s = c->s;
-  c->sg_steps = c->cfg.surrogate_steps > 0 ? c->cfg.surrogate_steps : 4;
+  c->sg_steps = c->cfg.surrogate_steps > 0 ? c->cfg.surrogate_steps : 6;
   c->sg_batch = c->cfg.surrogate_batch > 0 ? c->cfg.surrogate_batch : 1024;
   c->sg_lr = c->cfg.surrogate_lr > 0.0f ? c->cfg.surrogate_lr : 2e-3f;
   const int e = c->cfg.elitism < s.pop ? c->cfg.elitism : s.pop;

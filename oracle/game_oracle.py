@@ -25,8 +25,7 @@ of a chromosome are stored as float32 and the operator output is compared
 bit-for-bit with the GPU's.  Those float32 steps use only correctly rounded
 IEEE operations (+, -, *, /, sqrt, floor, frexp) in a fixed order.
 
-Readings of the paper where it is silent or ambiguous (listed again in
-DESIGN.md):
+Readings of the paper where it is silent or ambiguous:
 
 * coefficients are per feature (gene = 1 + f*B*d + b); the paper's shared
   coefficients of eq.2 / eq.9 are the special case of tied genes;

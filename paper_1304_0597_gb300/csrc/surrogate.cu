@@ -3,9 +3,9 @@
 // mapping a chromosome's genes g to its standardised log fitness.  It is
 // trained online on the (chromosome, exact fitness) pairs that each generation
 // evaluates, and pre-screens an oversized offspring pool: only the children it
-// ranks best go on to exact evaluation, which stays the judge of its error
-// (Spearman correlation per generation) and the fallback (plain selection when
-// the correlation drops).
+// ranks best go on to exact evaluation, which keeps measuring its error
+// (Spearman correlation per generation) and is the fallback (plain selection
+// when the correlation drops).
 //
 // Weights live in float32 (master, Adam moments) with bfloat16 copies that the
 // forward and backward GEMMs read (float32 accumulation); a float32-weight mode

@@ -61,6 +61,12 @@ enum { GAME_ELITE_TOP = 0, GAME_ELITE_COPIES = 1 };               /* elitism rea
 enum { GAME_COEF_PER_FEATURE = 0, GAME_COEF_SHARED = 1 };         /* eq.2 coefficients */
 enum { GAME_SEL_TOURNAMENT = 0, GAME_SEL_ROULETTE = 1, GAME_SEL_RANKING = 2 };   /* selection */
 enum { GAME_FP32 = 0, GAME_BF16 = 1, GAME_FP8 = 2 };              /* storage of P    */
+/* Fitness engine.  TCGEN05: the tensor-core contraction (128-chromosome tiles, or
+ * for at most 32 FP32 chromosomes the kernel with patterns on the MMA's M side).
+ * SIMT: CUDA-core FMAs (for at most 32 chromosomes on 16 or 32 stored columns, one
+ * pattern per thread).  AUTO: SIMT for those narrow shapes (the paper's own
+ * population of 2N + 1) and where the genes exceed what the tensor-core kernels
+ * keep in shared memory, TCGEN05 otherwise. */
 enum { GAME_ENGINE_AUTO = 0, GAME_ENGINE_TCGEN05 = 1, GAME_ENGINE_SIMT = 2 };
 
 /*
@@ -102,7 +108,7 @@ typedef struct game_config {
   float surrogate_lr;       /* Adam learning rate (0 = 2e-3)                                */
   int32_t surrogate_select; /* 0: surrogate's best of the pool; 1: plain children (ablation)*/
   int32_t surrogate_fp32;   /* 1: float32 weights in the GEMMs (checks); 0: bfloat16        */
-  int32_t engine;         /* GAME_ENGINE_* fitness kernel choice (AUTO picks tcgen05)       */
+  int32_t engine;         /* GAME_ENGINE_* fitness kernel choice (see the enum above)      */
   int32_t tile_n;         /* tcgen05 tile: patterns per tile, 128 | 256 (0 = tuned / auto)  */
   int32_t tile_stages;    /* tcgen05 tile: depth of the pattern-tile ring (0 = auto)        */
   int32_t tile_cluster;   /* tcgen05 tile: CTAs sharing a pattern tile by multicast, 1|2|4|8 (0 = auto) */

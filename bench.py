@@ -97,8 +97,8 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
-def workload_config(n_patterns):
-    return {"workload": "plain GAME at scale, FP32 fitness",
+def workload_config(n_patterns, precision="fp32"):
+    return {"workload": f"plain GAME at scale, {precision.upper()} fitness",
             "n_patterns": n_patterns, "n_features": 32, "basis": "chebyshev", "degree": 8,
             "n_genes": 257, "pop": 1024, "train_frac": 0.7, "tournament_k": 3,
             "p_crossover": 0.9, "p_mutation": 0.05, "sigma_mutation": 0.1, "elitism": 2,
@@ -258,7 +258,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * el / n, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": dict(workload_config(args.n_patterns), sample_train_patterns=n_sample),
+        "config": dict(workload_config(args.n_patterns, args.precision), sample_train_patterns=n_sample),
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{n} generations (fitness+rank+breed) of pop 1024 on "
                                    f"{n_sample} training patterns of the workload"},
@@ -364,7 +364,7 @@ def run_ours(args):
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3"}[args.precision],
         "data": "synthetic",
-        "config": dict(workload_config(args.n_patterns), n_train=n_train,
+        "config": dict(workload_config(args.n_patterns, args.precision), n_train=n_train,
                        precision=args.precision,
                        gene_planes=args.gene_planes if args.precision != "fp32" else None,
                        engine={1: "tcgen05", 2: "simt"}.get(engine_used, "?"),

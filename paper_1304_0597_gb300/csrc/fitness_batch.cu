@@ -217,7 +217,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
         for (int ch = 0; ch < kCols / 32; ++ch) {
           const long long p0 = (long long)tile * kBN + h * kCols + ch * 32;
-          if (r.fast)   // same arithmetic as the single-run kernels
+          // same arithmetic as the single-run kernels
+          if (r.fast == 2)
+            acc.add(chunk_error<true, true, true>(tb + ch * 32, r.pk, p0, r.m, rs, bias, r.act,
+                                                  r.err, r.R));
+          else if (r.fast)
             acc.add(chunk_error<true, true>(tb + ch * 32, r.pk, p0, r.m, rs, bias, r.act, r.err,
                                             r.R));
           else
@@ -262,7 +266,8 @@ cudaError_t batch_make_run(const Shape& s, const Fitness& f, const PopDev& p, co
     r.b[1] = r.b[0];
   }
   r.fast = f.pm1_targets && f.activation == GAME_TANH && (f.error == GAME_RMSE || f.error == GAME_MSE);
-  r.pk = r.fast ? e.tcoef : e.t;
+  if (r.fast && s.precision != GAME_FP32) r.fast = 2;
+  r.pk = r.fast == 1 ? e.tcoef : e.t;
   r.bias = p.bias;
   r.rscale = p.rscale;
   r.partial = partial;

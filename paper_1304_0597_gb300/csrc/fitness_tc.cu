@@ -20,6 +20,9 @@
 // G_hi.P_lo in float32 (kind::f16).  BF16 / FP8: one quantised P plane with
 // per-column scales folded into the genes, genes as a hi/lo pair with a
 // per-chromosome scale applied in the epilogue (kind::f16 bf16 / kind::f8f6f4).
+// With +-1 targets, tanh and (R)MSE the FP32 form takes E = 4 / (1 + 2^(c_k s))^2
+// (ex2 and rcp, no cancellation), the low-precision forms (t_k tanh.approx(s) - 1)^2
+// (one MUFU op); both are in chunk_error.
 //
 // Roles (576 threads): warp 0 = TMA producer, warp 1 = TMEM allocator + MMA
 // issuer, warps 2..17 = epilogue (warp w reads TMEM lanes 32*(w%4) and a
@@ -251,7 +254,10 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     // ---- epilogue ----
     const int q = warp & 3;
     const int h = (warp - 2) >> 2;                    // column group 0..kColGroups-1
-    const float* pk = FAST ? p.tcoef : p.t;
+    // FP32 keeps the exact fast form (c_k = 2 log2(e) t_k); the low-precision forms
+    // take the one-MUFU tanh form, which reads t_k.
+    constexpr bool kTanh = FAST && PREC != GAME_FP32;
+    const float* pk = FAST && !kTanh ? p.tcoef : p.t;
     float bias[SP], rs[SP];
 #pragma unroll
     for (int sp = 0; sp < SP; ++sp) {
@@ -282,8 +288,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
 #pragma unroll
         for (int ch = 0; ch < kCols / 32; ++ch) {
           const long long p0 = tile * BN + h * kCols + ch * 32;
-          acc[sp].add(chunk_error<FAST, true>(tbase + ch * 32, pk, p0, p.m, rs[sp], bias[sp],
-                                              p.act, p.err, p.R));
+          acc[sp].add(chunk_error<FAST, true, kTanh>(tbase + ch * 32, pk, p0, p.m, rs[sp],
+                                                     bias[sp], p.act, p.err, p.R));
         }
       }
       fence_before();

@@ -69,13 +69,15 @@ cudaError_t tc_make_map(CUtensorMap* m, const void* base, int precision, long lo
 struct alignas(64) BatchRunDev {
   CUtensorMap a[2];       // gene planes (hi, lo)
   CUtensorMap b[2];       // expansion planes
-  const float* pk;        // per-pattern epilogue input (2 log2(e) t, or t)
+  const float* pk;        // per-pattern epilogue input (2 log2(e) t when fast == 1, else t)
   const float* bias;
   const float* rscale;
   double* partial;        // [n_chunks * 4 x pop_pad]
   const DevState* state;
   long long m;
-  int pop_pad, kblocks, ksteps, n_bplanes, n_aplanes, prec, fast, act, err;
+  int pop_pad, kblocks, ksteps, n_bplanes, n_aplanes, prec;
+  int fast;               // 0 general error, 1 exact fast form (FP32), 2 tanh form (BF16 / FP8)
+  int act, err;
   float R;
 };
 

@@ -46,6 +46,25 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kColGroups = kEpiWarps / 4;     // epilogue warps sharing one TMEM lane quadrant
 constexpr int kTileA = 128 * 128;         // bytes of one 128-row x 128-byte A tile
 
+// Profiling build only (-DGAME_TC_TIMELINE): CTA 0 stamps clock64 at each role's
+// waits and hand-offs for its first 32 tiles, read back by game_tc_timeline().
+// Slot (event, tile, k-block) = event * 256 + tile * 8 + k-block; events: 0 producer
+// issues a B k-block, 1 MMA warp past its ring wait, 2 MMA warp past the accumulator
+// wait, 3 MMA warp committed the tile, 4 / 5 epilogue warp 2 starts / ends the tile,
+// 6 / 7 the same for warp 17.
+#ifdef GAME_TC_TIMELINE
+__device__ long long g_tc_timeline[2048];
+#define TC_STAMP(cond, ev, tile, kb)                                                   \
+  do {                                                                                 \
+    if ((cond) && blockIdx.x == 0 && (tile) < 32 && (kb) < 8)                          \
+      g_tc_timeline[(ev) * 256 + (tile) * 8 + (kb)] = clock64();                       \
+  } while (0)
+#else
+#define TC_STAMP(cond, ev, tile, kb) \
+  do {                               \
+  } while (0)
+#endif
+
 struct TcParams {
   CUtensorMap a[2];
   CUtensorMap b[2];
@@ -153,6 +172,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
             ok = false;
             break;
           }
+          TC_STAMP(lane == 0 && bp == 0, 0, it, kb);
           if (lane == 0) {
             // warm L2 with the same box of this CTA's next tile
             if (it + 1 < my_tiles && p.prefetch)
@@ -195,6 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
         const uint32_t ap = (uint32_t)((it >> 1) & 1);
         if (!warp_wait(acc_empty + buf, ap ^ 1u, err, p.state, lane)) break;
         fence_after();
+        TC_STAMP(lane == 0, 2, it, 0);
         uint32_t accum = 0;   // the first k-step of a tile starts every slice's accumulator
         bool ok = true;
         for (int kb = 0; kb < p.kblocks && ok; ++kb) {
@@ -205,6 +226,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
               break;
             }
             fence_after();
+            TC_STAMP(lane == 0 && bp == 0, 1, it, kb);
             const uint64_t bdesc = sw128_desc(b_addr + (uint32_t)(stage * kTileB));
             // FP32 split: B = P_hi meets A = G_hi and G_lo; B = P_lo meets G_hi.
             const int n_ap = (PREC == GAME_FP32 && bp == 1) ? 1 : NA;
@@ -240,6 +262,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
         }
         if (!ok) break;
         if (lane == 0) mma_commit(acc_full + buf);
+        TC_STAMP(lane == 0, 3, it, 0);
       }
     }
     // Drain: all issued MMAs complete before TMEM is released.
@@ -281,6 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
                                          : warp_wait(acc_full + buf, ap, err, p.state, lane);
       if (!got) break;
       fence_after();
+      TC_STAMP(lane == 0 && (warp == 2 || warp == 17), warp == 2 ? 4 : 6, it, 0);
 #pragma unroll
       for (int sp = 0; sp < SP; ++sp) {
         const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) +
@@ -292,6 +316,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
                                                      bias[sp], p.act, p.err, p.R));
         }
       }
+      TC_STAMP(lane == 0 && (warp == 2 || warp == 17), warp == 2 ? 5 : 7, it, 0);
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(acc_empty + buf);
@@ -604,5 +629,12 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
   cfg.numAttrs = 1;
   return cudaLaunchKernelExC(&cfg, k, args);
 }
+
+#ifdef GAME_TC_TIMELINE
+// Copies the 2048 stamps of the last launch to host memory (profiling build only).
+extern "C" int game_tc_timeline(long long* host) {
+  return (int)cudaMemcpyFromSymbol(host, g_tc_timeline, sizeof(long long) * 2048);
+}
+#endif
 
 }  // namespace game

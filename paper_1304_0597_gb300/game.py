@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libgame.so")
+# GAME_LIB_PATH selects another build of the same library (the profiling variant
+# _lib/libgame_timeline.so); unset, the in-tree libgame.so.
+LIB_PATH = os.environ.get("GAME_LIB_PATH") or os.path.join(_HERE, "_lib", "libgame.so")
 
 GAME_OK = 0
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "STATE", -3: "OOM", -4: "CUDA", -5: "NO_DEVICE",

@@ -111,7 +111,8 @@ typedef struct game_config {
   int32_t engine;         /* GAME_ENGINE_* fitness kernel choice (see the enum above)      */
   int32_t tile_n;         /* tcgen05 tile: patterns per tile, 128 | 256 (0 = tuned / auto)  */
   int32_t tile_stages;    /* tcgen05 tile: depth of the pattern-tile ring (0 = auto)        */
-  int32_t tile_cluster;   /* tcgen05 tile: CTAs sharing a pattern tile by multicast, 1|2|4|8 (0 = auto) */
+  int32_t tile_cluster;   /* tcgen05 tile: 0 or 1 (each CTA loads its own pattern tiles; other values
+                             are INVALID_ARG)                                                  */
   int32_t tile_slices;    /* tcgen05 tile: 128-chromosome slices per CTA, 1 | 2 (2 needs tile_n 128; 0 = auto) */
   int32_t device;         /* CUDA device ordinal                                            */
   void* stream;           /* cudaStream_t, or NULL for the legacy default stream           */
@@ -258,7 +259,7 @@ game_status game_selftest_timeout(game_ctx* ctx, int32_t wait_us, int32_t* waite
 typedef struct game_tile {
   int32_t n;          /* patterns per tile (MMA N)                            */
   int32_t stages;     /* pattern-tile ring depth                              */
-  int32_t cluster;    /* CTAs sharing each pattern tile (TMA multicast)       */
+  int32_t cluster;    /* always 1 (no thread-block clusters)                  */
   int32_t prefetch;   /* 1: L2 prefetch of each CTA's next pattern tile       */
   int32_t slices;     /* 128-chromosome slices per CTA fed by each pattern tile */
   double ms;          /* median fitness time of this shape, milliseconds      */
@@ -350,10 +351,11 @@ void game_batch_destroy(game_batch* b);
 /* Population fitness for callers that cannot allocate device memory.  The
  * paper has no counterpart: this is a packaging of the fitness step (the same
  * float32 CUDA-core kernel as GAME_ENGINE_SIMT) for code that must not call
- * cudaMalloc -- work captured into a CUDA graph, a service whose device memory
- * is a fixed arena owned by another allocator, or a latency-critical path that
- * cannot afford cudaMalloc's device-wide synchronisation.  It calls no
- * cudaMalloc, cudaFree or allocating library routine.
+ * cudaMalloc -- a service whose device memory is a fixed arena owned by another
+ * allocator, a plugin inside a program that owns every device allocation, or a
+ * latency-critical path that cannot afford cudaMalloc's device-wide
+ * synchronisation.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine.
  *   P: device, n_patterns x (n_genes-1) float32 row-major: the basis columns
  *      of the expansion (the bias column of ones is implicit), e.g. as
  *      returned by game_get_expansion.

@@ -3,13 +3,12 @@
 // per-block partial sums kept in one fixed, file-scope device array instead of
 // a buffer from cudaMalloc; the caller passes every input and the output.
 //
-// Who needs it: code that runs where cudaMalloc is not allowed or not wanted --
-// inside a region being captured into a CUDA graph, in a service whose device
+// Who needs it: code that must not call cudaMalloc -- a service whose device
 // memory is a fixed arena owned by another allocator (a framework's caching
-// allocator, a memory budget set at start-up), or on a latency-critical path
-// where cudaMalloc's implicit device-wide synchronisation would stall other
-// streams.  This path calls no cudaMalloc, cudaFree or allocating library
-// routine.
+// allocator, a memory budget set at start-up), a plugin inside a host program
+// that owns every device allocation, or a latency-critical path where
+// cudaMalloc's implicit device-wide synchronisation would stall other streams.
+// This path calls no cudaMalloc, cudaFree or allocating library routine.
 //
 // Limits and sharing: pop <= 4096 chromosomes; the partial sums use at most
 // 32 x 4096 doubles (1 MiB), resident on every device that loads the library

@@ -79,7 +79,6 @@ struct TcParams {
   int n_bplanes;          // FP32: 2 (P_hi, P_lo); else 1
   int act, err, in_evolve;
   float R;
-  int cl;                 // CTAs per cluster sharing each B tile by multicast (1 = none)
   int prefetch;           // L2 prefetch of the next tile's boxes
 };
 
@@ -120,7 +119,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     mbar_init(a_full, 1);
     for (int s = 0; s < S; ++s) {
       mbar_init(b_full + s, 1);
-      mbar_init(b_empty + s, p.cl);     // one MMA commit from every CTA that reads the tile
+      mbar_init(b_empty + s, 1);        // the MMA commit that frees the stage
       last_par[s] = -1;
     }
     for (int b = 0; b < 2; ++b) {
@@ -141,12 +140,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   fence_before();
   __syncthreads();
   fence_after();
-  // Peers multicast into this CTA's ring: every barrier of the cluster exists first.
-  if (p.cl > 1) cluster_sync_all();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t crank = p.cl > 1 ? cluster_rank() : 0u;
-  const uint16_t cmask = (uint16_t)((1u << p.cl) - 1u);
-  const int sub_rows = BN / p.cl;                     // rows of the B tile this CTA fetches
   const int a_steps_total = p.kp / kKStep;
   F2Sum acc[SP];   // epilogue threads: each slice's chromosome error sum over its columns
 
@@ -176,13 +170,9 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
           if (lane == 0) {
             // warm L2 with the same box of this CTA's next tile
             if (it + 1 < my_tiles && p.prefetch)
-              tma_prefetch_2d(&p.b[bp], kb * kKB, row0 + p.cps * BN + (int)crank * sub_rows);
-            mbar_expect_tx(b_full + stage, kTileB);     // the whole tile lands here
-            if (p.cl > 1)
-              tma_load_2d_mc(sB + stage * kTileB + crank * sub_rows * 128, &p.b[bp], kb * kKB,
-                             row0 + (int)crank * sub_rows, b_full + stage, cmask);
-            else
-              tma_load_2d(sB + stage * kTileB, &p.b[bp], kb * kKB, row0, b_full + stage);
+              tma_prefetch_2d(&p.b[bp], kb * kKB, row0 + p.cps * BN);
+            mbar_expect_tx(b_full + stage, kTileB);
+            tma_load_2d(sB + stage * kTileB, &p.b[bp], kb * kKB, row0, b_full + stage);
             last_par[stage] = (int)phase;
           }
           if (++stage == S) {
@@ -248,12 +238,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
               }
               if (sp == SP - 1) accum = acc_sp;
             }
-            if (lane == 0) {
-              if (p.cl > 1)
-                mma_commit_mc(b_empty + stage, cmask);
-              else
-                mma_commit(b_empty + stage);
-            }
+            if (lane == 0) mma_commit(b_empty + stage);
             if (++stage == S) {
               stage = 0;
               phase ^= 1u;
@@ -343,8 +328,6 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     for (int g = 0; g < kColGroups; ++g) tot += red[(sp * kColGroups + g) * 128 + r];
     p.partial[(long long)member * p.pop_pad + (group * SP + sp) * 128 + r] = tot;
   }
-  // No CTA leaves while a peer may still signal its barriers.
-  if (p.cl > 1) cluster_sync_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -497,9 +480,7 @@ void tc_candidates(const Shape& s, std::vector<TileReq>* out) {
       const int n_groups = n_slices / sp;
       const int ms = max_stages(s, bn, sp);
       for (int st = ms; st >= 2 && st >= ms - 1; --st)
-        for (int cl : {1, 2, 4, 8})
-          if (n_groups % cl == 0 && bn / cl >= 16)
-            for (int pf : {1, 0}) out->push_back(TileReq{bn, st, cl, pf, sp});
+        for (int pf : {1, 0}) out->push_back(TileReq{bn, st, 1, pf, sp});
     }
 }
 
@@ -515,52 +496,20 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
   if (t.sp == 2 && (t.n_slices % 2 != 0 || (req.n && req.n != 128))) return cudaErrorInvalidValue;
   t.n_groups = t.n_slices / t.sp;
   const int a_bytes = t.sp * s.gene_planes * t.kblocks * kTileA;
-  // Default shape: 256-pattern tiles when two stages fit, else 128; multicast
-  // across the largest power-of-two group of slices up to 4.
-  // (128-pattern tiles cost as much per MMA instruction as 256-pattern ones)
+  // Default shape: 256-pattern tiles when two stages fit, else 128
+  // (128-pattern tiles cost as much per MMA instruction as 256-pattern ones).
   t.bn = t.sp == 2 ? 128 : (req.n ? req.n : (max_stages(s, 256, 1) >= 2 ? 256 : 128));
   if (t.bn != 128 && t.bn != 256) return cudaErrorInvalidValue;
   const int ms = max_stages(s, t.bn, t.sp);
   t.stages = req.stages ? req.stages : ms;
   if (t.stages < 2 || t.stages > ms) return cudaErrorNotSupported;
-  int cl = req.cluster;
-  if (!cl) {
-    cl = 1;
-    for (int c : {4, 2})
-      if (t.n_groups % c == 0) {
-        cl = c;
-        break;
-      }
-  }
-  if (t.n_groups % cl != 0 || t.bn / cl < 16 || cl > 8) return cudaErrorInvalidValue;
-  t.cluster = cl;
+  // Every CTA loads its own pattern tiles (no thread-block clusters).
+  if (req.cluster > 1) return cudaErrorInvalidValue;
+  t.cluster = 1;
   t.prefetch = req.prefetch == 0 ? 0 : 1;
   t.n_tiles = (int)((s.n_train + t.bn - 1) / t.bn);
   t.smem = (size_t)a_bytes + (size_t)t.stages * t.bn * 128 + kSmemMisc;
-  // Co-resident CTAs under this cluster shape (clusters must fit in one GPC).
-  int resident = n_sm;
-  if (cl > 1) {
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = cl;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.gridDim = dim3(cl * 64);
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = t.smem;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    int n_clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&n_clusters,
-                                       pick_kernel(t.bn, s.precision, true, s.gene_planes, t.sp),
-                                       &cfg) ==
-            cudaSuccess &&
-        n_clusters > 0)
-      resident = n_clusters * cl;
-    else
-      cudaGetLastError();
-  }
+  const int resident = n_sm;   // one CTA per SM (the shared memory of one fills it)
   int cps = resident / t.n_groups;
   if (cps < 1) cps = 1;
   if (cps > t.n_tiles) cps = t.n_tiles;
@@ -570,10 +519,9 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
   cudaError_t err;
   if ((err = make_map(&t.a_map[0], p.ghi, s.precision, s.pop_pad, s.kp, 128)) != cudaSuccess) return err;
   if ((err = make_map(&t.a_map[1], p.glo, s.precision, s.pop_pad, s.kp, 128)) != cudaSuccess) return err;
-  const int box = t.bn / cl;
-  if ((err = make_map(&t.b_map[0], e.p0, s.precision, s.n_train, s.kp, box)) != cudaSuccess) return err;
+  if ((err = make_map(&t.b_map[0], e.p0, s.precision, s.n_train, s.kp, t.bn)) != cudaSuccess) return err;
   if (n_bplanes == 2) {
-    if ((err = make_map(&t.b_map[1], e.p1, s.precision, s.n_train, s.kp, box)) != cudaSuccess) return err;
+    if ((err = make_map(&t.b_map[1], e.p1, s.precision, s.n_train, s.kp, t.bn)) != cudaSuccess) return err;
   } else {
     t.b_map[1] = t.b_map[0];
   }
@@ -607,27 +555,13 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
   p.err = f.error;
   p.R = f.tmse_R;
   p.in_evolve = state != nullptr;
-  p.cl = t.cluster;
   p.prefetch = t.prefetch;
   const bool fast = f.pm1_targets && f.activation == GAME_TANH &&
                     (f.error == GAME_RMSE || f.error == GAME_MSE);
   void* k = pick_kernel(t.bn, s.precision, fast, s.gene_planes, t.sp);
   if (!k) return cudaErrorNotSupported;
   void* args[] = {&p};
-  if (t.cluster <= 1) return cudaLaunchKernel(k, dim3(t.grid), dim3(kThreads), args, t.smem, st);
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr;
-  attr.id = cudaLaunchAttributeClusterDimension;
-  attr.val.clusterDim.x = t.cluster;
-  attr.val.clusterDim.y = 1;
-  attr.val.clusterDim.z = 1;
-  cfg.gridDim = dim3(t.grid);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = t.smem;
-  cfg.stream = st;
-  cfg.attrs = &attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, k, args);
+  return cudaLaunchKernel(k, dim3(t.grid), dim3(kThreads), args, t.smem, st);
 }
 
 #ifdef GAME_TC_TIMELINE

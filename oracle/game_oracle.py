@@ -641,16 +641,21 @@ def round_e4m3(x: np.ndarray) -> np.ndarray:
 QMAX = {"bf16": 1.0, "fp8": 448.0}
 
 
-def quantize_columns(P: np.ndarray, fmt: str):
+def quantize_columns(P: np.ndarray, fmt: str, s: np.ndarray | None = None):
     """P held in a low-precision format with a per-column scale: P ~ Q * s.
 
     P is first rounded to float32 (the working precision of the expansion);
     s_g = max_k |P[k,g]| / qmax (1 where the column is zero); Q = round(P / s)
-    in the format.  Returns (Q, s) as float32 arrays.
+    in the format.  Returns (Q, s) as float32 arrays.  A caller that walks a
+    large P in row blocks passes the scales of the whole matrix as ``s`` (for
+    instance those this function returns for the stacked per-block column
+    maxima of |P|).
     """
     P32 = np.asarray(P, dtype=np.float32)
-    m = np.max(np.abs(P32), axis=0) if P32.shape[0] else np.zeros(P32.shape[1], np.float32)
-    s = np.where(m > 0, m / np.float32(QMAX[fmt]), np.float32(1.0)).astype(np.float32)
+    if s is None:
+        m = np.max(np.abs(P32), axis=0) if P32.shape[0] else np.zeros(P32.shape[1], np.float32)
+        s = np.where(m > 0, m / np.float32(QMAX[fmt]), np.float32(1.0)).astype(np.float32)
+    s = np.asarray(s, dtype=np.float32)
     R = (P32 / s[None, :]).astype(np.float32)
     Q = round_bf16(R) if fmt == "bf16" else round_e4m3(R)
     return Q, s

@@ -90,9 +90,29 @@ def make_dataset(n_patterns: int, n_features: int, degree: int, basis: str = "ch
                    n_train=n_train, basis=basis, degree=degree)
 
 
-def planted_targets(P: np.ndarray, h: np.ndarray) -> np.ndarray:
-    """Regression targets tanh(P h) for a planted chromosome h (P given by the caller)."""
-    return np.tanh(np.asarray(P, dtype=np.float64) @ np.asarray(h, dtype=np.float64))
+def planted_targets(X: np.ndarray, h: np.ndarray, basis: str, degree: int) -> np.ndarray:
+    """Regression targets tanh(f_h(x)) of a planted chromosome h, float64.
+
+    f_h is the function whose coefficients h holds in the gene layout (h[0] the
+    constant; h[1 + f*B*d + b] the b-th basis member of feature f: Chebyshev T_{b+1},
+    or for the trig basis cos((b+1)x) for b < d and sin((b-d+1)x) after), evaluated
+    feature by feature with numpy's Chebyshev series routine or with np.cos / np.sin,
+    never through an expansion matrix.
+    """
+    X = np.asarray(X, dtype=np.float64)
+    h = np.asarray(h, dtype=np.float64)
+    n, F = X.shape
+    Bd = (2 if basis == "trig" else 1) * degree
+    assert h.shape == (1 + F * Bd,)
+    v = np.full(n, h[0])
+    for f in range(F):
+        c = h[1 + f * Bd: 1 + (f + 1) * Bd]
+        if basis == "chebyshev":
+            v += _cheb.chebval(X[:, f], np.concatenate([[0.0], c]))
+        else:
+            for k in range(1, degree + 1):
+                v += c[k - 1] * np.cos(k * X[:, f]) + c[degree + k - 1] * np.sin(k * X[:, f])
+    return np.tanh(v)
 
 
 # --- the workloads -------------------------------------------------------------------

@@ -110,9 +110,8 @@ def test_planted_chromosome_fits_exactly():
     rng = np.random.default_rng(9)
     X = rng.uniform(-1, 1, size=(4000, 6)).astype(np.float32)
     ocfg = _cfg(degree=3, pop=33, stop_error=1e-5)
-    P = o.expand(X, "chebyshev", 3)
-    h = o.init_population(o.Config(pop=1, seed=99), P.shape[1])[0]
-    t = synth.planted_targets(P, h).astype(np.float32)
+    h = o.init_population(o.Config(pop=1, seed=99), o.n_genes("chebyshev", 6, 3))[0]
+    t = synth.planted_targets(X, h, "chebyshev", 3).astype(np.float32)
     g = make_game(ocfg, X, t, 3000)
     G = g.population()
     G[5] = h

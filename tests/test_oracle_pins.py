@@ -208,17 +208,26 @@ def test_rmse_squared_is_mse_and_permutation_invariance():
     np.testing.assert_allclose(o.fitness(P[perm], t[perm], G, o.Config()), rm, rtol=1e-13)
 
 
-def test_planted_chromosome_has_zero_error():
+@pytest.mark.parametrize("basis", ["chebyshev", "trig"])
+def test_planted_chromosome_has_zero_error(basis):
+    """Targets made by numpy's own Chebyshev series routine (or np.cos / np.sin) from the
+    planted genes, not by the oracle's expansion: the oracle's output path (eq.2 through
+    expand + outputs, the activation, the error and its reduction) must give the planted
+    chromosome zero error, and a perturbed copy a positive one."""
     from paper_1304_0597_gb300 import synth
     rng = np.random.default_rng(6)
     X = rng.uniform(-1, 1, size=(500, 6))
-    P = o.expand(X, "chebyshev", 4)
+    P = o.expand(X, basis, 4)
     h = rng.uniform(-1, 1, size=P.shape[1])
-    t = synth.planted_targets(P, h)
-    G = np.stack([h, rng.uniform(-1, 1, size=h.shape)])
-    fit = o.fitness(P, t, G, o.Config())
-    assert fit[0] <= 1e-15
-    assert fit[1] > 1e-2
+    t = synth.planted_targets(X, h, basis, 4)
+    h2 = h.copy()
+    h2[-1] += 1e-3                      # the last basis member of the last feature
+    G = np.stack([h, rng.uniform(-1, 1, size=h.shape), h2])
+    for err in ("rmse", "mse", "tmse"):
+        fit = o.fitness(P, t, G, o.Config(basis=basis, degree=4, error=err))
+        assert fit[0] <= 1e-15
+        assert fit[1] > 1e-4
+        assert err == "tmse" or fit[2] > 0.0
 
 
 def test_rank_orders_by_fitness_then_index_nan_last():
@@ -498,7 +507,7 @@ def test_stop_criterion_on_planted_solution():
     X = rng.uniform(-1, 1, size=(300, 3))
     P = o.expand(X, "chebyshev", 2)
     h = o.init_population(_cfg(pop=1), P.shape[1])[0].astype(np.float64)
-    t = synth.planted_targets(P, h)
+    t = synth.planted_targets(X, h, "chebyshev", 2)
     cfg = _cfg(pop=10, stop_error=1e-9)
     G0 = o.init_population(cfg, P.shape[1])
     G0[3] = h
@@ -542,6 +551,92 @@ def test_quantize_columns_bounds():
         # relative rounding bound of the format for normal values, plus the subnormal floor
         floor = s[None, :] * (2.0 ** -9 if fmt == "fp8" else 0.0)
         assert np.all(np.abs(D - P) <= rel * np.abs(P) + floor + 1e-7)
+
+
+def _gene_case(seed=16, pop=40, K=33):
+    """Genes in [-1, 1] (a few chromosomes with one dominant gene) and column scales spread
+    over six decades, so that a scale applied on the wrong side or over the wrong axis
+    moves genes by orders of magnitude."""
+    rng = np.random.default_rng(seed)
+    G = rng.uniform(-1, 1, size=(pop, K)).astype(np.float32)
+    G[3, 1:] *= 1e-3
+    G[3, 7] = 0.9
+    G[5, 1:] = 0.0                                           # an all-zero chromosome
+    s = (10.0 ** rng.uniform(-3, 3, size=K - 1)).astype(np.float32)
+    return G, s
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+def test_quantize_genes_one_plane_error_bound(fmt):
+    """One term: gene g meets the stored Q through w = g s_g / r_c rounded to the format, so
+    |Gq - G| <= u |G| + (subnormal half-step) r_c / s_g, with u the format's unit roundoff
+    (2^-8 bf16, 2^-4 e4m3; e4m3 half-step below its smallest normal 2^-10) and a float32
+    allowance; r_c = max_g |G s_g| / qmax."""
+    G, s = _gene_case()
+    Gq = o.quantize_genes(G, s, fmt, 1)
+    u = 2.0 ** -8 if fmt == "bf16" else 2.0 ** -4
+    half_sub = 0.0 if fmt == "bf16" else 2.0 ** -10
+    r = np.abs(G[:, 1:].astype(np.float64) * s).max(axis=1) / o.QMAX[fmt]
+    r = np.where(r > 0, r, 1.0)
+    bound = (u + 2.0 ** -21) * np.abs(G[:, 1:]) + half_sub * r[:, None] / s[None, :]
+    assert np.all(np.abs(Gq[:, 1:] - G[:, 1:]) <= bound)
+    # the bound is not loose: typical genes do move by a sizeable share of it
+    assert np.median(np.abs(Gq[:, 1:] - G[:, 1:]) / np.maximum(bound, 1e-300)) > 0.05
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+def test_quantize_genes_two_planes_error_bound(fmt):
+    """Two terms hi + lo with lo = q(w - hi): the error is the rounding of the remainder,
+    |Gq - G| <= (u^2 + 2^-21) |G| + (subnormal half-step) r_c / s_g -- second order in u."""
+    G, s = _gene_case()
+    Gq = o.quantize_genes(G, s, fmt, 2)
+    u = 2.0 ** -8 if fmt == "bf16" else 2.0 ** -4
+    half_sub = 0.0 if fmt == "bf16" else 2.0 ** -10
+    r = np.abs(G[:, 1:].astype(np.float64) * s).max(axis=1) / o.QMAX[fmt]
+    r = np.where(r > 0, r, 1.0)
+    bound = (u * u + 2.0 ** -21) * np.abs(G[:, 1:]) + half_sub * r[:, None] / s[None, :]
+    assert np.all(np.abs(Gq[:, 1:] - G[:, 1:]) <= bound)
+    # where the format's normal range holds the remainder, the second term helps
+    normal = half_sub * r[:, None] / s[None, :] <= 0.1 * u * u * np.abs(G[:, 1:])
+    assert normal.sum() > 100
+    one = np.abs(o.quantize_genes(G, s, fmt, 1)[:, 1:] - G[:, 1:])[normal].sum()
+    assert np.abs(Gq[:, 1:] - G[:, 1:])[normal].sum() < 0.25 * one
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+def test_quantize_genes_largest_scaled_gene_is_exact_and_bias_untouched(fmt):
+    """The largest |g s_g| of a chromosome maps to +-qmax, a value of both formats, so that
+    gene comes back unchanged (to float32 rounding); gene 0 (the bias, which meets the
+    implicit column of ones) is never quantised; a zero chromosome stays zero."""
+    G, s = _gene_case()
+    for planes in (1, 2):
+        Gq = o.quantize_genes(G, s, fmt, planes)
+        np.testing.assert_array_equal(Gq[:, 0], G[:, 0].astype(np.float64))
+        j = np.argmax(np.abs(G[:, 1:].astype(np.float64) * s), axis=1)
+        rows = np.arange(G.shape[0])
+        keep = np.abs(G[rows, 1 + j]) > 0
+        np.testing.assert_allclose(Gq[rows, 1 + j][keep], G[rows, 1 + j][keep], rtol=3e-7)
+        assert np.all(Gq[5, 1:] == 0.0)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+def test_quantize_genes_matches_torch_cast_construction(fmt):
+    """The same operand built with torch's own format casts (float32 arithmetic, torch
+    bfloat16 / float8_e4m3fn conversion)."""
+    import torch
+    G, s = _gene_case(seed=17)
+    dt = torch.bfloat16 if fmt == "bf16" else torch.float8_e4m3fn
+    g = torch.from_numpy(G[:, 1:]) * torch.from_numpy(s)[None, :]
+    r = g.abs().amax(dim=1) / o.QMAX[fmt]
+    r = torch.where(r > 0, r, torch.ones_like(r))
+    w = g / r[:, None]
+    for planes in (1, 2):
+        hi = w.to(dt).to(torch.float32)
+        val = hi.double()
+        if planes == 2:
+            val = val + (w - hi).to(dt).to(torch.float32).double()
+        want = val * r.double()[:, None] / torch.from_numpy(s).double()[None, :]
+        np.testing.assert_array_equal(o.quantize_genes(G, s, fmt, planes)[:, 1:], want.numpy())
 
 
 # --------------------------------------------------------------- surrogate

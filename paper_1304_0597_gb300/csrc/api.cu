@@ -23,6 +23,7 @@
 #include <sys/stat.h>
 
 #include <algorithm>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -58,6 +59,7 @@ struct game_ctx {
   int part_rows_r = 0;          // rows of d_partial_r
   Shape s32{};                  // FP32 shape of P (report, re-score)
   ExpDev e32{};                 // FP32 planes of P (== e when precision is FP32)
+  std::vector<float> scale32;   // power-of-two column scales of the FP32 planes (host copy)
   Shape sr{};                   // shape of the re-score population (pop = n_rescore)
   PopDev pr{};                  // gene planes of the gathered elites
   int engine_r = GAME_ENGINE_SIMT;
@@ -541,6 +543,8 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   if ((r = dalloc(c, &c->e.t, sizeof(float) * tpad)) != GAME_OK) return r;
   unsigned int* dflags = nullptr;
   if ((r = dalloc(c, &dflags, sizeof(unsigned int))) != GAME_OK) return r;
+  unsigned int* dfmax = nullptr;   // per-feature max |x| (float bits)
+  if ((r = dalloc(c, &dfmax, sizeof(unsigned int) * n_features)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->e.tcoef, sizeof(float) * tpad)) != GAME_OK) return r;
   const size_t esz = s.precision == GAME_FP32 ? 2 : (s.precision == GAME_BF16 ? 2 : 1);
   const size_t pbytes = esz * (size_t)n_patterns * s.kp;
@@ -550,6 +554,8 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   }
   if ((r = dalloc(c, &c->e.colscale, sizeof(float) * s.kp)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_scratch, sizeof(float) * s.kp)) != GAME_OK) return r;
+  // FP32 planes start unscaled; out-of-range Chebyshev columns get scales below.
+  if (s.precision == GAME_FP32) CUDA_OK(c, launch_fill_ones(c->e.colscale, s.kp, c->st));
   CUDA_OK(c, cudaMemcpyAsync(c->e.t, t, sizeof(float) * n_patterns,
                              device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
 
@@ -592,6 +598,13 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   check_data_kernel<<<4 * c->n_sm, 256, 0, c->st>>>(dX, n_patterns * n_features, c->e.t,
                                                       n_patterns, n_train, dflags);
   CUDA_OK(c, cudaGetLastError());
+  const bool cheb = s.basis == GAME_CHEBYSHEV;
+  std::vector<float> fmax(cheb ? n_features : 0);
+  if (cheb) {
+    CUDA_OK(c, launch_feature_absmax(dX, n_patterns, n_features, dfmax, c->n_sm, c->st));
+    CUDA_OK(c, cudaMemcpyAsync(fmax.data(), dfmax, sizeof(float) * n_features,
+                               cudaMemcpyDeviceToHost, c->st));
+  }
   unsigned int flags = 0;
   CUDA_OK(c, cudaMemcpyAsync(&flags, dflags, sizeof(flags), cudaMemcpyDeviceToHost, c->st));
   CUDA_OK(c, cudaStreamSynchronize(c->st));
@@ -599,9 +612,43 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
     free_all(c);
     return fail(c, GAME_ERR_NUMERIC, "X or t holds NaN or Inf");
   }
+  // Chebyshev values grow without bound outside [-1, 1] (eq.1 bounds no feature):
+  // |T_j(x)| <= T_j(max(1, |x|)) = cosh(j acosh max(1, |x|)).  Columns whose bound
+  // passes 2^15 get a power-of-two scale in the FP32 planes (fp16 tops out at 65504);
+  // values beyond float32 are refused.
+  c->scale32.assign(s.kp, 1.0f);
+  bool scaled = false;
+  if (cheb) {
+    std::vector<double> bound(s.kb, 0.0);
+    for (int f = 0; f < n_features; ++f) {
+      const double a = std::max(1.0, (double)fmax[f]);
+      for (int b = 0; b < s.degree; ++b) {
+        const double v = a == 1.0 ? 1.0 : std::cosh((b + 1) * std::acosh(a));
+        if (!(v < 0x1p100)) {
+          free_all(c);
+          return fail(c, GAME_ERR_UNSUPPORTED,
+                      "feature %d reaches |x| = %g: T_%d there exceeds 2^100 (rescale the feature)",
+                      f, (double)fmax[f], b + 1);
+        }
+        bound[shared ? b : f * s.degree + b] += v;
+      }
+    }
+    for (int col = 0; col < s.kb; ++col) {
+      int ex = 0;
+      std::frexp(bound[col], &ex);                   // bound < 2^ex
+      if (ex > 15) {
+        c->scale32[col] = std::ldexp(1.0f, ex - 15);
+        scaled = true;
+      }
+    }
+  }
   c->fit.pm1_targets = (flags & 2u) ? 0 : 1;
   CUDA_OK(c, launch_target_coef(c->e.t, c->e.tcoef, n_patterns, c->st));
-  if (device_ptrs || s.precision != GAME_FP32)
+  if (scaled && s.precision == GAME_FP32)
+    CUDA_OK(c, cudaMemcpyAsync(c->e.colscale, c->scale32.data(), sizeof(float) * s.kp,
+                               cudaMemcpyHostToDevice, c->st));
+  // (the host chunks of the FP32 form were expanded unscaled as they landed)
+  if (device_ptrs || s.precision != GAME_FP32 || scaled)
     CUDA_OK(c, launch_expand(dX, s, c->e, c->d_scratch, c->st));
   c->lowp = s.precision != GAME_FP32;
   c->s32 = s;
@@ -618,6 +665,9 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
     if ((r = dalloc(c, &c->e32.p0, b32)) != GAME_OK) return r;
     if ((r = dalloc(c, &c->e32.p1, b32)) != GAME_OK) return r;
     if ((r = dalloc(c, &c->e32.colscale, sizeof(float) * c->s32.kp)) != GAME_OK) return r;
+    c->scale32.resize(c->s32.kp, 1.0f);
+    CUDA_OK(c, cudaMemcpyAsync(c->e32.colscale, c->scale32.data(), sizeof(float) * c->s32.kp,
+                               cudaMemcpyHostToDevice, c->st));
     CUDA_OK(c, launch_expand(dX, c->s32, c->e32, c->d_scratch, c->st));
   }
 

@@ -12,10 +12,14 @@
 // (Chebyshev: T_{k+1} = 2x T_k - T_{k-1} in float-float; trig: angle addition
 // from one float64 sincos(x)), rounded once to float32, then stored in the
 // precision of the run:
-//   FP32: two fp16 planes, hi = fp16(v), lo = fp16(v - hi)  (v = hi + lo to ~22 bits)
+//   FP32: two fp16 planes of v' = v / s_g, hi = fp16(v'), lo = fp16(v' - hi) (v' = hi + lo
+//         to ~22 bits); s_g is a power of two, 1 unless the column's values could pass
+//         2^15 (Chebyshev features beyond [-1, 1]), so that hi never overflows fp16
 //   BF16: bf16(v / s_g), s_g = max_k |P[k,g]|          (per-column scale)
 //   FP8 : e4m3(v / s_g), s_g = max_k |P[k,g]| / 448
 #include "game_internal.h"
+
+#include <algorithm>
 
 namespace game {
 
@@ -116,7 +120,9 @@ __global__ void expand_kernel(ExpArgs a) {
   if (a.precision == GAME_FP32) {
     __half* hi = (__half*)a.p0 + row + col0;
     __half* lo = (__half*)a.p1 + row + col0;
+    const float* sc = a.colscale + col0;
     basis_values(a.basis, a.d, x, [&](int b, float v) {
+      v = v * (1.0f / sc[b]);                     // a power of two: exact
       const __half h = __float2half_rn(v);
       hi[b] = h;
       lo[b] = __float2half_rn(__fsub_rn(v, __half2float(h)));
@@ -190,11 +196,13 @@ __global__ void __launch_bounds__(kSharedRows) expand_shared_kernel(ExpArgs a) {
   const long long row = k * a.kp;
   auto val = [&](int b) { return b < a.kb ? (float)acc[b * kSharedRows] : 0.0f; };
   if (a.precision == GAME_FP32) {
+    // the power-of-two column scale divides exactly
+    auto vs = [&](int b) { return b < a.kb ? val(b) * (1.0f / a.colscale[b]) : 0.0f; };
     for (int b0 = 0; b0 < a.kp; b0 += 8) {
       uint32_t hw[4], lw[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const float v0 = val(b0 + 2 * i), v1 = val(b0 + 2 * i + 1);
+        const float v0 = vs(b0 + 2 * i), v1 = vs(b0 + 2 * i + 1);
         const __half h0 = __float2half_rn(v0), h1 = __float2half_rn(v1);
         const __half l0 = __float2half_rn(__fsub_rn(v0, __half2float(h0)));
         const __half l1 = __float2half_rn(__fsub_rn(v1, __half2float(h1)));
@@ -252,6 +260,37 @@ __global__ void fill_ones_kernel(float* v, int n) {
   if (i < n) v[i] = 1.0f;
 }
 
+cudaError_t launch_fill_ones(float* v, int n, cudaStream_t st) {
+  fill_ones_kernel<<<(n + 255) / 256, 256, 0, st>>>(v, n);
+  return cudaGetLastError();
+}
+
+// Largest |x| of every feature over all patterns (bits of non-negative floats order
+// like the floats): block maxima in shared memory, one global atomic per block and
+// feature.  absmax_bits [F] must be zero on entry.
+__global__ void feature_absmax_kernel(const float* X, long long n_elems, int F,
+                                      unsigned int* absmax_bits) {
+  extern __shared__ unsigned int fm[];
+  for (int f = threadIdx.x; f < F; f += blockDim.x) fm[f] = 0u;
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_elems;
+       i += (long long)gridDim.x * blockDim.x)
+    atomicMax(fm + (int)(i % F), __float_as_uint(fabsf(X[i])));
+  __syncthreads();
+  for (int f = threadIdx.x; f < F; f += blockDim.x)
+    if (fm[f]) atomicMax(absmax_bits + f, fm[f]);
+}
+
+cudaError_t launch_feature_absmax(const float* X, long long n, int F, unsigned int* absmax_bits,
+                                  int n_sm, cudaStream_t st) {
+  cudaError_t err = cudaMemsetAsync(absmax_bits, 0, sizeof(unsigned int) * F, st);
+  if (err != cudaSuccess) return err;
+  const long long blocks = std::min<long long>((n * F + 255) / 256, 2LL * n_sm);
+  feature_absmax_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256,
+                          sizeof(unsigned int) * F, st>>>(X, n * F, F, absmax_bits);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax_scratch,
                           cudaStream_t st) {
   ExpArgs a;
@@ -275,9 +314,7 @@ cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax
     if (s.kb > 64) return cudaErrorInvalidValue;   // B * d <= 2 * 32
     const size_t smem = sizeof(double) * s.kb * kSharedRows;
     const long long nblk = (s.n_patterns + kSharedRows - 1) / kSharedRows;
-    if (s.precision == GAME_FP32) {
-      fill_ones_kernel<<<(s.kp + 255) / 256, 256, 0, st>>>(e.colscale, s.kp);
-    } else {
+    if (s.precision != GAME_FP32) {   // FP32: the caller has set the power-of-two scales
       cudaError_t err = cudaMemsetAsync(qmax_scratch, 0, sizeof(float) * s.kp, st);
       if (err != cudaSuccess) return err;
       const unsigned cblocks = (unsigned)(nblk < 4864 ? nblk : 4864);
@@ -290,9 +327,7 @@ cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax
   }
   const long long n = s.n_patterns * s.n_features;
   const unsigned blocks = (unsigned)((n + threads - 1) / threads);
-  if (s.precision == GAME_FP32) {
-    fill_ones_kernel<<<(s.kp + 255) / 256, 256, 0, st>>>(e.colscale, s.kp);
-  } else {
+  if (s.precision != GAME_FP32) {   // FP32: the caller has set the power-of-two scales
     cudaError_t err = cudaMemsetAsync(qmax_scratch, 0, sizeof(float) * s.kp, st);
     if (err != cudaSuccess) return err;
     const unsigned cblocks = blocks < 1216u ? blocks : 1216u;
@@ -315,7 +350,7 @@ __global__ void expand_get_kernel(const void* p0, const void* p1, const float* c
   const long long o = r * kp + c;
   float v;
   if (precision == GAME_FP32)
-    v = __half2float(((const __half*)p0)[o]) + __half2float(((const __half*)p1)[o]);
+    v = (__half2float(((const __half*)p0)[o]) + __half2float(((const __half*)p1)[o])) * colscale[c];
   else if (precision == GAME_BF16)
     v = __bfloat162float(((const __nv_bfloat16*)p0)[o]) * colscale[c];
   else

@@ -30,8 +30,8 @@ __device__ __forceinline__ float pattern_error(float t, float s, int act, int er
 template <int PREC>
 __device__ __forceinline__ float load_p(const void* p0, const void* p1, const float* cs,
                                         long long o, int c) {
-  if (PREC == GAME_FP32)
-    return __half2float(((const __half*)p0)[o]) + __half2float(((const __half*)p1)[o]);
+  if (PREC == GAME_FP32)   // hi + lo, times the column's power-of-two scale (1 in range)
+    return (__half2float(((const __half*)p0)[o]) + __half2float(((const __half*)p1)[o])) * cs[c];
   if (PREC == GAME_BF16) return __bfloat162float(((const __nv_bfloat16*)p0)[o]) * cs[c];
   return (float)(((const __nv_fp8_e4m3*)p0)[o]) * cs[c];
 }
@@ -233,8 +233,7 @@ __global__ void __launch_bounds__(kNarrowThreads, 2) fitness_narrow_kernel(SimtA
     const int g = i / kNarrowPop, c = i % kNarrowPop;
     float v = 0.0f;
     if (c < a.pop && g < a.kb) {
-      v = a.geval[(long long)c * a.kp + g];
-      if (PREC != GAME_FP32) v *= a.colscale[g];
+      v = a.geval[(long long)c * a.kp + g] * a.colscale[g];
     }
     Gt[g][c] = v;
   }

@@ -51,7 +51,7 @@ constexpr int kNR = 2;                           // 128-pattern tiles per stage 
 constexpr int kNSmemMax = 232448;
 constexpr int kNGuard = 1024;                    // after the ring, before the barriers
 // alignment, guard, barriers + TMEM slot + last parities, per-warp totals
-constexpr int kNSmemMisc = 1024 + kNGuard + 1024 + 4 * kNSets * 32 * 8 + kNPop * 4;
+constexpr int kNSmemMisc = 1024 + kNGuard + 1024 + 4 * kNSets * 32 * 8 + 2 * kNPop * 4;
 
 // Shared-memory matrix descriptor for K-major rows of SW = 32, 64 or 128 bytes:
 // that swizzle, 8-row groups 8 * SW bytes apart, descriptor version 1.
@@ -72,6 +72,7 @@ struct NarrowParams {
   CUtensorMap g[2];       // gene planes G_hi, G_lo (N operand, chromosomes x genes)
   const float* pk;        // 2 log2(e) t_k (fused +-1 / tanh form) or t_k
   const float* bias;
+  const float* rscale;    // per-chromosome scale of the gene planes (a power of two)
   double* partial;
   DevState* state;
   long long m;
@@ -124,6 +125,7 @@ __global__ void __launch_bounds__(kNThreads, 1) fitness_tc_narrow_kernel(const _
   int* last_par = reinterpret_cast<int*>(tmem_slot + 2);   // [S]
   double* red = reinterpret_cast<double*>(last_par + kNMaxStages);  // [epilogue warps][32]
   float* bsm = reinterpret_cast<float*>(red + 4 * kNSets * 32);     // [32] gene 0 per chromosome
+  float* rsm = bsm + kNPop;                                           // [32] plane scale per chromosome
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // This CTA's tiles are t0 .. t0 + my_tiles - 1 (contiguous, per_cta a multiple of kNR),
@@ -145,7 +147,10 @@ __global__ void __launch_bounds__(kNThreads, 1) fitness_tc_narrow_kernel(const _
     }
     mbar_init(fin, 1);
     *err = 0;
-    for (int c = 0; c < kNPop; ++c) bsm[c] = c < p.pop ? p.bias[c] : 0.0f;
+    for (int c = 0; c < kNPop; ++c) {
+      bsm[c] = c < p.pop ? p.bias[c] : 0.0f;
+      rsm[c] = c < p.pop ? p.rscale[c] : 1.0f;
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -311,7 +316,7 @@ __global__ void __launch_bounds__(kNThreads, 1) fitness_tc_narrow_kernel(const _
       // all 32 columns, without branches: columns past the population are never read
 #pragma unroll
       for (int c = 0; c < kNPop; ++c) {
-        const float e = narrow_tc_error<EF>(pk, v[c] + bsm[c], p.act, p.err, p.R);
+        const float e = narrow_tc_error<EF>(pk, fmaf(v[c], rsm[c], bsm[c]), p.act, p.err, p.R);
         acc[c] += valid ? e : 0.0f;
       }
       if (++nblk == 32) {
@@ -463,6 +468,7 @@ cudaError_t tc_narrow_launch(const TcPlan& t, const Shape& s, const Fitness& f, 
                     (f.error == GAME_RMSE || f.error == GAME_MSE);
   p.pk = fast ? e.tcoef : e.t;
   p.bias = pd.bias;
+  p.rscale = pd.rscale;
   p.partial = partial;
   p.state = const_cast<DevState*>(state);
   p.m = s.n_train;

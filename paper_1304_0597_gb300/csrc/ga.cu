@@ -239,7 +239,10 @@ cudaError_t launch_breed(const Shape& s, const game_config& cfg, const PopDev& p
 // Operand preparation: basis genes of the population under evaluation, in the
 // float32 layout of the SIMT path and in the tensor-core planes of the chosen
 // precision.  One warp per chromosome row (rows >= pop are zero).
-//   FP32: plane hi = fp16(g), lo = fp16(g - hi): g = hi + lo to ~22 bits.
+//   FP32: g' = g * s_col / r_c with s_col the power-of-two column scale of P and r_c
+//   the smallest power of two >= 1 that keeps max_col |g * s_col| / r_c <= 2^15 (so both
+//   are 1 for features in range and genes in [-1, 1]); plane hi = fp16(g'),
+//   lo = fp16(g' - hi): g' = hi + lo to ~22 bits.  The epilogue multiplies by r_c.
 //   BF16 / FP8: g' = g * s_col / r_c with r_c = max_col |g * s_col| / qmax;
 //   hi = q(g'), lo = q(g' - hi); the contraction result is scaled back by r_c.
 // ---------------------------------------------------------------------------
@@ -273,14 +276,24 @@ __global__ void prepare_kernel(PrepArgs a) {
   if (a.precision == GAME_FP32) {
     __half* hi = (__half*)a.ghi + (long long)row * a.kp;
     __half* lo = (__half*)a.glo + (long long)row * a.kp;
+    float m = 0.0f;
+    for (int c = lane; c < a.kb; c += 32)
+      if (live) m = fmaxf(m, fabsf(G[1 + c] * a.colscale[c]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int ex = 0;
+    frexpf(m, &ex);                                  // m < 2^ex
+    const float r = ex > 15 ? ldexpf(1.0f, ex - 15) : 1.0f;
+    const float inv_r = 1.0f / r;                    // powers of two: exact
     for (int c = lane; c < a.kp; c += 32) {
       const float v = (live && c < a.kb) ? G[1 + c] : 0.0f;
       ge[c] = v;
-      const __half h = __float2half_rn(v);
+      const float w = c < a.kb ? (v * a.colscale[c]) * inv_r : 0.0f;
+      const __half h = __float2half_rn(w);
       hi[c] = h;
-      lo[c] = __float2half_rn(__fsub_rn(v, __half2float(h)));
+      lo[c] = __float2half_rn(__fsub_rn(w, __half2float(h)));
     }
-    if (lane == 0) a.rscale[row] = 1.0f;
+    if (lane == 0) a.rscale[row] = r;
     return;
   }
   const float qmax = a.precision == GAME_BF16 ? 1.0f : 448.0f;

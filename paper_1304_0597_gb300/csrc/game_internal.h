@@ -67,14 +67,16 @@ struct PopDev {
   float* bias;            // [pop_pad] gene 0 of the population under evaluation
   void* ghi;              // [pop_pad x kp] MMA operand plane (hi part)
   void* glo;              // [pop_pad x kp] MMA operand plane (lo part)
-  float* rscale;          // [pop_pad] per-chromosome scale of the planes (1 for FP32)
+  float* rscale;          // [pop_pad] per-chromosome scale of the planes (FP32: a power of
+                          // two, 1 unless a gene times its column scale passes 2^15)
 };
 
 // Expansion matrix P (basis columns only; the bias column of ones is implicit).
 struct ExpDev {
   void* p0;               // FP32: fp16 hi plane; BF16: bf16 values; FP8: e4m3 values
   void* p1;               // FP32: fp16 lo plane; otherwise unused
-  float* colscale;        // [kp] per-column scale s_g of quantised P (1 for FP32)
+  float* colscale;        // [kp] per-column scale s_g: quantised P, or for FP32 a power of two
+                          // (1 unless a column's values could pass 2^15)
   float* t;               // [n_patterns padded to 256] targets
   float* tcoef;           // [same] 2 log2(e) t_k, read by the fused +-1 / tanh epilogue
 };
@@ -88,8 +90,14 @@ struct Fitness {
 
 // ---- launchers (each returns cudaGetLastError of its launch) ----------------
 
+// FP32 planes hold P / s_g with the power-of-two scales the caller has written to
+// e.colscale (launch_fill_ones for none); the quantised forms compute theirs.
 cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax_scratch,
                           cudaStream_t st);
+cudaError_t launch_fill_ones(float* v, int n, cudaStream_t st);
+// absmax_bits[f] = float bits of max_k |X[k][f]| (F <= 12288).
+cudaError_t launch_feature_absmax(const float* X, long long n, int F, unsigned int* absmax_bits,
+                                  int n_sm, cudaStream_t st);
 // Outputs of one chromosome on n new patterns X [n x F] (device buffers).
 cudaError_t launch_predict(const float* X, long long n, int F, const float* genes, int K,
                            int basis, int degree, int shared, int activation, float* out,

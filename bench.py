@@ -71,6 +71,11 @@ def parse():
                     help="subset of the paper's degrees (1 2 4 8)")
     ap.add_argument("--precision-table", action="store_true",
                     help="print the per-precision fitness error / accuracy table and exit")
+    ap.add_argument("--timeline", action="store_true",
+                    help="CTA-0 clock64 timeline of one tensor-core fitness launch per precision "
+                         "(builds the -DGAME_TC_TIMELINE variant of the library)")
+    ap.add_argument("--timeline-tiles", type=int, default=16)
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -197,15 +202,51 @@ def kernel_traffic(kernel_file: str, variant: str):
     return rec.get("bytes_per_launch")
 
 
-def blas_threads():
+def host_cores() -> int:
+    """Cores this process may run on (nproc)."""
     try:
-        from threadpoolctl import threadpool_info
-        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
-        if n:
-            return max(n)
-    except Exception:
-        pass
-    return os.cpu_count()
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                "BLIS_NUM_THREADS", "NUMEXPR_NUM_THREADS")
+
+
+def oracle_sample_subprocess(threads: int, seconds: float, n_sample: int = 10_000):
+    """The oracle's generation rate on a bounded sample, in a fresh interpreter whose BLAS
+    is limited to `threads` threads (the environment is read when numpy loads)."""
+    env = dict(os.environ, **{v: str(threads) for v in _THREAD_VARS})
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample",
+                        "--cpu-seconds", str(seconds)], env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle sample failed: {r.stderr[-400:]}")
+    rec = json.loads(r.stdout.strip().splitlines()[-1])
+    rec["threads"] = threads
+    return rec
+
+
+def oracle_sample_main(args):
+    from paper_1304_0597_gb300 import synth
+    n_sample = 10_000
+    ds = synth.make_dataset(max(n_sample * 2, 20_000), 32, 8, "chebyshev", correlated=True)
+    rate, n, el = oracle_generation_rate(ds, n_sample, 1024, args.cpu_seconds)
+    print(json.dumps({"rate": rate, "generations": n, "seconds": el, "n_sample": n_sample}))
+
+
+def cpu_baseline_record(seconds: float):
+    """cpu_baseline of the bench line: the oracle as it stands on all host cores, plus the
+    same sample on one thread."""
+    cores = host_cores()
+    allc = oracle_sample_subprocess(cores, seconds)
+    one = oracle_sample_subprocess(1, seconds)
+    sample = lambda r: (f"{r['generations']} generations (fitness+rank+breed, float64) of pop "
+                        f"1024 on {r['n_sample']:,} training patterns, {r['seconds']:.1f} s")
+    return {"value": allc["rate"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": sample(allc),
+            "single_thread": {"value": one["rate"], "unit": UNIT, "cores": 1,
+                              "sample": sample(one)}}
 
 
 def oracle_generation_rate(ds, n_sample: int, pop: int, seconds: float, min_steps: int = 1,
@@ -252,7 +293,7 @@ def run_reference(args):
     ds = synth.make_dataset(max(n_sample * 2, 20_000), 32, 8, "chebyshev", correlated=True)
     rate, n, el = oracle_generation_rate(ds, n_sample, 1024, 0.0, steps=args.steps,
                                          warmup=args.warmup)
-    cores = blas_threads()
+    cores = host_cores()
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -390,11 +431,7 @@ def run_ours(args):
         "best": {"train_rmse": fit_best, "test_rmse": test_rmse, "test_accuracy": test_acc},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, n, el = oracle_generation_rate(ds, 10_000, pop, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": blas_threads(),
-                                "kind": "oracle",
-                                "sample": f"{n} generations (fitness+rank+breed, float64) of pop "
-                                          f"1024 on 10,000 training patterns, {el:.1f} s"}
+        line["cpu_baseline"] = cpu_baseline_record(args.cpu_seconds)
     g.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -624,11 +661,62 @@ def paper_table(args):
                          "iterations": ran, "tot_s": tot, "ms_per_iteration": ms_gen,
                          "engine": engine,
                          "train_tmse": fit_best, "test_accuracy": acc,
-                         "paper_tot_s_gt540m": paper_s, "ratio_vs_paper": paper_s / tot})
+                         "paper_tot_s_gt540m_context": paper_s})
             print(json.dumps(rows[-1]), flush=True)
     print(json.dumps({"table": "paper experiment shape (Section 5, Table benchgpu sizes)",
                       "rows": len(rows), "engines": sorted({r["engine"] for r in rows}),
                       "note": "paper numbers are a GT540M laptop GPU in float64: context only"}))
+
+
+def timeline(args):
+    """Per-tile clock64 timeline of CTA 0 of the tensor-core fitness kernel, one launch per
+    precision (FP32; BF16 and FP8 with one gene plane), on the bench workload with the
+    autotuned tile and no elite re-score.  Builds the -DGAME_TC_TIMELINE variant of the
+    library (stamps: the producer issuing each pattern k-block, the MMA warp passing each
+    ring wait and the accumulator wait and committing the tile, epilogue warps 2 and 17
+    starting and ending the tile) and prints them in cycles from the first tile start."""
+    import ctypes as C
+    from paper_1304_0597_gb300 import build as _build
+    os.environ["GAME_LIB_PATH"] = _build.build(timeline=True)
+    from paper_1304_0597_gb300 import game, synth
+    read, clear = game.lib.game_tc_timeline, game.lib.game_tc_timeline_clear
+    read.argtypes, read.restype, clear.restype = [C.c_void_p], C.c_int, C.c_int
+    ds = synth.plain_at_scale(n_patterns=args.n_patterns)
+    buf = np.zeros(2048, dtype=np.int64)
+    for name, prec in (("fp32", game.FP32), ("bf16", game.BF16), ("fp8", game.FP8)):
+        kw = {} if prec == game.FP32 else {"gene_planes": 1}
+        cfg = game.default_config(degree=8, pop=1024, seed=0, engine=game.ENGINE_TCGEN05,
+                                  precision=prec, elite_rescore=0, **kw)
+        with game.Game(cfg) as g:
+            g.set_data(ds.X, ds.t, ds.n_train)
+            tile, _ = g.autotune(reps=3)
+            g.evolve(3)
+            if clear() != 0:
+                raise RuntimeError("clearing the timeline failed")
+            g.evolve(1)                      # one fitness launch
+            if read(buf.ctypes.data) != 0:
+                raise RuntimeError("reading the timeline failed")
+        T = buf.reshape(8, 32, 8)
+        nkb = {"fp32": 4, "bf16": 4, "fp8": 2}[name]
+        ran = [it for it in range(32) if T[2, it, 0] != 0]      # tiles CTA 0 ran
+        n = min(args.timeline_tiles, len(ran))
+        t0 = T[2, 0, 0]
+        print(f"{name}: tile {tile}, CTA 0 ran {len(ran)} stamped tiles")
+        print("tile | producer issues k-block 0..   | MMA past ring wait k-block 0..  "
+              "| MMA start  commit | epi w2 start end | epi w17 start end")
+        for it in range(n):
+            rel = lambda e, k=0: int(T[e, it, k] - t0)
+            print("%4d | %s | %s | %6d %6d | %6d %6d | %6d %6d" % (
+                it, " ".join("%6d" % rel(0, k) for k in range(nkb)),
+                " ".join("%6d" % rel(1, k) for k in range(nkb)),
+                rel(2), rel(3), rel(4), rel(5), rel(6), rel(7)), flush=True)
+        if n > 3:
+            period = np.diff(T[2, 2:n, 0]).mean()
+            gaps = np.diff(T[1, 2:n, :nkb], axis=1).mean()
+            epi = (T[5, 2:n, 0] - T[4, 2:n, 0]).mean()
+            print(f"{name}: tile period {period:.0f} cycles, MMA ring waits {gaps:.0f} cycles "
+                  f"apart within a tile, epilogue warp 2 busy {epi:.0f} cycles per tile\n",
+                  flush=True)
 
 
 def main():
@@ -644,6 +732,12 @@ def main():
         return
     if args.paper:
         paper_table(args)
+        return
+    if args.timeline:
+        timeline(args)
+        return
+    if args.oracle_sample:
+        oracle_sample_main(args)
         return
     if args.impl == "reference":
         run_reference(args)

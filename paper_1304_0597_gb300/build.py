@@ -3,7 +3,7 @@
 Usage: ``python -m paper_1304_0597_gb300.build`` (or ``__graft_entry__.build()``).
 The library lands in ``paper_1304_0597_gb300/_lib/libgame.so``.  ``build(timeline=True)``
 makes the profiling variant ``_lib/libgame_timeline.so`` (-DGAME_TC_TIMELINE: CTA 0 of the
-tensor-core fitness kernel stamps its per-tile timeline; see ``tc_timeline.py``).
+tensor-core fitness kernel stamps its per-tile timeline; ``bench.py --timeline`` reads it).
 """
 
 from __future__ import annotations

@@ -565,9 +565,14 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
 }
 
 #ifdef GAME_TC_TIMELINE
-// Copies the 2048 stamps of the last launch to host memory (profiling build only).
+// Copies the 2048 stamps to host memory (profiling build only).
 extern "C" int game_tc_timeline(long long* host) {
   return (int)cudaMemcpyFromSymbol(host, g_tc_timeline, sizeof(long long) * 2048);
+}
+// Zeroes the stamps, so that a read after one launch shows that launch alone.
+extern "C" int game_tc_timeline_clear() {
+  static const long long zeros[2048] = {};
+  return (int)cudaMemcpyToSymbol(g_tc_timeline, zeros, sizeof(zeros));
 }
 #endif
 

@@ -555,6 +555,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   if ((r = dalloc(c, &c->e.colscale, sizeof(float) * s.kp)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_scratch, sizeof(float) * s.kp)) != GAME_OK) return r;
   // FP32 planes start unscaled; out-of-range Chebyshev columns get scales below.
+  c->e.unit_scale32 = 1;
   if (s.precision == GAME_FP32) CUDA_OK(c, launch_fill_ones(c->e.colscale, s.kp, c->st));
   CUDA_OK(c, cudaMemcpyAsync(c->e.t, t, sizeof(float) * n_patterns,
                              device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
@@ -644,9 +645,11 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   }
   c->fit.pm1_targets = (flags & 2u) ? 0 : 1;
   CUDA_OK(c, launch_target_coef(c->e.t, c->e.tcoef, n_patterns, c->st));
-  if (scaled && s.precision == GAME_FP32)
+  if (scaled && s.precision == GAME_FP32) {
     CUDA_OK(c, cudaMemcpyAsync(c->e.colscale, c->scale32.data(), sizeof(float) * s.kp,
                                cudaMemcpyHostToDevice, c->st));
+    c->e.unit_scale32 = 0;
+  }
   // (the host chunks of the FP32 form were expanded unscaled as they landed)
   if (device_ptrs || s.precision != GAME_FP32 || scaled)
     CUDA_OK(c, launch_expand(dX, s, c->e, c->d_scratch, c->st));
@@ -666,6 +669,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
     if ((r = dalloc(c, &c->e32.p1, b32)) != GAME_OK) return r;
     if ((r = dalloc(c, &c->e32.colscale, sizeof(float) * c->s32.kp)) != GAME_OK) return r;
     c->scale32.resize(c->s32.kp, 1.0f);
+    c->e32.unit_scale32 = scaled ? 0 : 1;
     CUDA_OK(c, cudaMemcpyAsync(c->e32.colscale, c->scale32.data(), sizeof(float) * c->s32.kp,
                                cudaMemcpyHostToDevice, c->st));
     CUDA_OK(c, launch_expand(dX, c->s32, c->e32, c->d_scratch, c->st));

@@ -73,6 +73,45 @@ __device__ __forceinline__ void basis_values(int basis, int d, float x, Emit emi
   }
 }
 
+// Calls emit(v) with the float32 basis values of x for b = b_lo .. b_hi - 1 in order
+// (0 <= b_lo < b_hi <= B*d): the same arithmetic as basis_values, stopped at b_hi.
+template <typename Emit>
+__device__ __forceinline__ void basis_range(int basis, int d, float x, int b_lo, int b_hi,
+                                            Emit emit) {
+  if (basis == GAME_CHEBYSHEV) {
+    const float y = __fmul_rn(2.0f, x);
+    float mh = 1.0f, ml = 0.0f, th = x, tl = 0.0f;
+    for (int b = 0; b < b_hi; ++b) {
+      if (b >= b_lo) emit(__fadd_rn(th, tl));
+      float p, pe, s2, se;
+      two_prod(y, th, p, pe);
+      two_sum(p, -mh, s2, se);
+      const float low = __fsub_rn(__fadd_rn(__fadd_rn(se, pe), __fmul_rn(y, tl)), ml);
+      const float nh = __fadd_rn(s2, low);
+      const float nl = __fsub_rn(low, __fsub_rn(nh, s2));
+      mh = th;
+      ml = tl;
+      th = nh;
+      tl = nl;
+    }
+  } else {
+    double s1, c1;
+    sincos((double)x, &s1, &c1);
+    // cos((k+1) x) for the columns below d, then sin((k+1) x) for those from d
+    for (int half = 0; half < 2; ++half) {
+      const int lo = half ? max(b_lo, d) - d : b_lo;
+      const int hi = half ? b_hi - d : min(b_hi, d);
+      double c = c1, sn = s1;
+      for (int k = 0; k < hi; ++k) {
+        if (k >= lo) emit((float)(half ? sn : c));
+        const double cn = c * c1 - sn * s1;
+        sn = sn * c1 + c * s1;
+        c = cn;
+      }
+    }
+  }
+}
+
 struct ExpArgs {
   const float* X;
   long long n;
@@ -81,6 +120,7 @@ struct ExpArgs {
   void* p1;
   const float* colscale;
   unsigned int* colmax_bits;
+  int unit_scale;         // FP32: every column scale is 1 (no multiply)
 };
 
 // Column maxima of |P|: block-local maxima in shared memory (non-negative floats
@@ -109,42 +149,134 @@ __global__ void expand_scale_kernel(const unsigned int* colmax_bits, float* cols
   colscale[c] = m > 0.0f ? m / qmax : 1.0f;
 }
 
-__global__ void expand_kernel(ExpArgs a) {
+// Vectorised expansion: one thread per (pattern row, 16-byte chunk of the stored row),
+// consecutive threads on consecutive chunks of a row, so that every store is a full
+// coalesced 16-byte vector.  A chunk holds EPC = 16 / element-size columns; the thread
+// runs the recurrence of each feature its columns belong to (from T_1 / m = 1, stopping
+// at the chunk's last column) and shifts every value into packed registers in column
+// order.  Columns past kb are zero.
+template <int PREC>
+__global__ void __launch_bounds__(256) expand_chunk_kernel(ExpArgs a) {
+  constexpr int kEsz = PREC == GAME_FP8 ? 1 : 2;
+  constexpr int kEpc = 16 / kEsz;
+  constexpr int kBits = 8 * kEsz;
+  const int n_chunks = a.kp / kEpc;
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n * a.F) return;
-  const long long k = i / a.F;
-  const int f = (int)(i % a.F);
-  const float x = a.X[i];
-  const long long row = k * a.kp;
-  const int col0 = f * a.bd;
-  if (a.precision == GAME_FP32) {
-    __half* hi = (__half*)a.p0 + row + col0;
-    __half* lo = (__half*)a.p1 + row + col0;
-    const float* sc = a.colscale + col0;
-    basis_values(a.basis, a.d, x, [&](int b, float v) {
-      v = v * (1.0f / sc[b]);                     // a power of two: exact
+  if (i >= a.n * n_chunks) return;
+  const long long row = i / n_chunks;
+  const int col0 = (int)(i % n_chunks) * kEpc;
+  uint32_t w0[4] = {0u, 0u, 0u, 0u}, w1[4] = {0u, 0u, 0u, 0u};   // plane 0 / plane 1 words
+  // shift the 128-bit chunk right by one element and put e (its low kBits) on top
+  auto push = [&](uint32_t* w, uint32_t e) {
+    w[0] = __funnelshift_r(w[0], w[1], kBits);
+    w[1] = __funnelshift_r(w[1], w[2], kBits);
+    w[2] = __funnelshift_r(w[2], w[3], kBits);
+    w[3] = __funnelshift_r(w[3], e, kBits);
+  };
+  int col = col0;
+  auto emit = [&](float v) {
+    if (PREC == GAME_FP32) {
+      v = v * (1.0f / a.colscale[col]);                  // a power of two: exact
       const __half h = __float2half_rn(v);
-      hi[b] = h;
-      lo[b] = __float2half_rn(__fsub_rn(v, __half2float(h)));
-    });
-    if (f == a.F - 1)
-      for (int c = a.kb; c < a.kp; ++c) {
-        ((__half*)a.p0)[row + c] = __float2half_rn(0.0f);
-        ((__half*)a.p1)[row + c] = __float2half_rn(0.0f);
-      }
-  } else if (a.precision == GAME_BF16) {
-    __nv_bfloat16* q = (__nv_bfloat16*)a.p0 + row + col0;
-    const float* sc = a.colscale + col0;
-    basis_values(a.basis, a.d, x, [&](int b, float v) { q[b] = __float2bfloat16_rn(v / sc[b]); });
-    if (f == a.F - 1)
-      for (int c = a.kb; c < a.kp; ++c) ((__nv_bfloat16*)a.p0)[row + c] = __float2bfloat16_rn(0.0f);
-  } else {
-    __nv_fp8_e4m3* q = (__nv_fp8_e4m3*)a.p0 + row + col0;
-    const float* sc = a.colscale + col0;
-    basis_values(a.basis, a.d, x, [&](int b, float v) { q[b] = __nv_fp8_e4m3(v / sc[b]); });
-    if (f == a.F - 1)
-      for (int c = a.kb; c < a.kp; ++c) ((__nv_fp8_e4m3*)a.p0)[row + c] = __nv_fp8_e4m3(0.0f);
+      const __half l = __float2half_rn(__fsub_rn(v, __half2float(h)));
+      push(w0, (uint32_t)__half_as_ushort(h));
+      push(w1, (uint32_t)__half_as_ushort(l));
+    } else if (PREC == GAME_BF16) {
+      push(w0, (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v / a.colscale[col])));
+    } else {
+      push(w0, (uint32_t)__nv_fp8_e4m3(v / a.colscale[col]).__x);
+    }
+    ++col;
+  };
+  const int c_end = min(col0 + kEpc, a.kb);
+  const float* x = a.X + row * a.F;
+  while (col < c_end) {
+    const int f = col / a.bd;
+    const int b_lo = col - f * a.bd;
+    const int b_hi = min(a.bd, c_end - f * a.bd);
+    basis_range(a.basis, a.d, __ldg(x + f), b_lo, b_hi, emit);
   }
+  for (; col < col0 + kEpc; ++col) {   // zero padding (shifted in like values)
+    push(w0, 0u);
+    if (PREC == GAME_FP32) push(w1, 0u);
+  }
+  const long long o = (row * a.kp + col0) * kEsz;   // byte offset, a multiple of 16
+  *reinterpret_cast<uint4*>((uint8_t*)a.p0 + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+  if (PREC == GAME_FP32)
+    *reinterpret_cast<uint4*>((uint8_t*)a.p1 + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+}
+
+// The same for Chebyshev bases whose kb columns per feature are a whole number of
+// chunks (B d a multiple of EPC, e.g. d = 8 with 16-bit storage): a chunk lies inside
+// one feature, starts at a multiple of EPC and is wholly values or wholly padding, so
+// the EPC values are computed in an unrolled loop and packed at fixed positions.
+template <int PREC>
+__global__ void __launch_bounds__(256) expand_cheb_aligned_kernel(ExpArgs a) {
+  constexpr int kEsz = PREC == GAME_FP8 ? 1 : 2;
+  constexpr int kEpc = 16 / kEsz;
+  const int n_chunks = a.kp / kEpc;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n * n_chunks) return;
+  const long long row = i / n_chunks;
+  const int col0 = (int)(i % n_chunks) * kEpc;
+  float v[kEpc];
+  if (col0 < a.kb) {
+    const int f = col0 / a.bd;
+    const int b0 = col0 - f * a.bd;
+    const float x = __ldg(a.X + row * a.F + f);
+    const float y = __fmul_rn(2.0f, x);
+    float mh = 1.0f, ml = 0.0f, th = x, tl = 0.0f;
+    auto step = [&]() {
+      float p, pe, s2, se;
+      two_prod(y, th, p, pe);
+      two_sum(p, -mh, s2, se);
+      const float low = __fsub_rn(__fadd_rn(__fadd_rn(se, pe), __fmul_rn(y, tl)), ml);
+      const float nh = __fadd_rn(s2, low);
+      const float nl = __fsub_rn(low, __fsub_rn(nh, s2));
+      mh = th;
+      ml = tl;
+      th = nh;
+      tl = nl;
+    };
+    for (int b = 0; b < b0; ++b) step();
+#pragma unroll
+    for (int j = 0; j < kEpc; ++j) {
+      v[j] = __fadd_rn(th, tl);
+      if (j + 1 < kEpc) step();
+    }
+    if (PREC != GAME_FP32 || !a.unit_scale) {
+#pragma unroll
+      for (int j = 0; j < kEpc; ++j)
+        v[j] = PREC == GAME_FP32 ? v[j] * (1.0f / __ldg(a.colscale + col0 + j))
+                                 : v[j] / __ldg(a.colscale + col0 + j);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < kEpc; ++j) v[j] = 0.0f;
+  }
+  uint32_t w0[4], w1[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (PREC == GAME_FP32) {
+      const __half h0 = __float2half_rn(v[2 * q]), h1 = __float2half_rn(v[2 * q + 1]);
+      const __half l0 = __float2half_rn(__fsub_rn(v[2 * q], __half2float(h0)));
+      const __half l1 = __float2half_rn(__fsub_rn(v[2 * q + 1], __half2float(h1)));
+      w0[q] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+      w1[q] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+    } else if (PREC == GAME_BF16) {
+      w0[q] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[2 * q])) |
+              ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[2 * q + 1])) << 16);
+    } else {
+      uint32_t w = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w |= (uint32_t)__nv_fp8_e4m3(v[4 * q + j]).__x << (8 * j);
+      w0[q] = w;
+    }
+  }
+  const long long o = (row * a.kp + col0) * kEsz;
+  *reinterpret_cast<uint4*>((uint8_t*)a.p0 + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+  if (PREC == GAME_FP32)
+    *reinterpret_cast<uint4*>((uint8_t*)a.p1 + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
 }
 
 // Shared coefficients (the paper's eq.2 / eq.9 form): column b of pattern k is the
@@ -266,16 +398,26 @@ cudaError_t launch_fill_ones(float* v, int n, cudaStream_t st) {
 }
 
 // Largest |x| of every feature over all patterns (bits of non-negative floats order
-// like the floats): block maxima in shared memory, one global atomic per block and
+// like the floats).  Lane l of a warp owns feature fc + l of each 32-feature group and
+// keeps a running maximum over the warp's rows (row r reads 32 consecutive floats);
+// the block's warps meet in shared memory, then one global atomic per block and
 // feature.  absmax_bits [F] must be zero on entry.
-__global__ void feature_absmax_kernel(const float* X, long long n_elems, int F,
+__global__ void feature_absmax_kernel(const float* __restrict__ X, long long n, int F,
                                       unsigned int* absmax_bits) {
   extern __shared__ unsigned int fm[];
   for (int f = threadIdx.x; f < F; f += blockDim.x) fm[f] = 0u;
   __syncthreads();
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_elems;
-       i += (long long)gridDim.x * blockDim.x)
-    atomicMax(fm + (int)(i % F), __float_as_uint(fabsf(X[i])));
+  const int lane = threadIdx.x & 31;
+  const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (int fc = 0; fc < F; fc += 32) {
+    const int f = fc + lane;
+    if (f >= F) continue;
+    float m = 0.0f;
+#pragma unroll 4
+    for (long long r = wg; r < n; r += nw) m = fmaxf(m, fabsf(__ldg(X + r * F + f)));
+    atomicMax(fm + f, __float_as_uint(m));
+  }
   __syncthreads();
   for (int f = threadIdx.x; f < F; f += blockDim.x)
     if (fm[f]) atomicMax(absmax_bits + f, fm[f]);
@@ -285,9 +427,9 @@ cudaError_t launch_feature_absmax(const float* X, long long n, int F, unsigned i
                                   int n_sm, cudaStream_t st) {
   cudaError_t err = cudaMemsetAsync(absmax_bits, 0, sizeof(unsigned int) * F, st);
   if (err != cudaSuccess) return err;
-  const long long blocks = std::min<long long>((n * F + 255) / 256, 2LL * n_sm);
+  const long long blocks = std::min<long long>((n + 7) / 8, 4LL * n_sm);   // 8 warps a block
   feature_absmax_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256,
-                          sizeof(unsigned int) * F, st>>>(X, n * F, F, absmax_bits);
+                          sizeof(unsigned int) * F, st>>>(X, n, F, absmax_bits);
   return cudaGetLastError();
 }
 
@@ -335,7 +477,25 @@ cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax
     expand_scale_kernel<<<(s.kp + 255) / 256, 256, 0, st>>>(
         a.colmax_bits, e.colscale, s.kb, s.kp, s.precision == GAME_BF16 ? 1.0f : 448.0f);
   }
-  expand_kernel<<<blocks, threads, 0, st>>>(a);
+  const int epc = s.precision == GAME_FP8 ? 16 : 8;
+  const long long items = s.n_patterns * (s.kp / epc);
+  const unsigned cb = (unsigned)((items + threads - 1) / threads);
+  a.unit_scale = e.unit_scale32;
+  if (s.basis == GAME_CHEBYSHEV && s.bd % epc == 0) {
+    if (s.precision == GAME_FP32)
+      expand_cheb_aligned_kernel<GAME_FP32><<<cb, threads, 0, st>>>(a);
+    else if (s.precision == GAME_BF16)
+      expand_cheb_aligned_kernel<GAME_BF16><<<cb, threads, 0, st>>>(a);
+    else
+      expand_cheb_aligned_kernel<GAME_FP8><<<cb, threads, 0, st>>>(a);
+    return cudaGetLastError();
+  }
+  if (s.precision == GAME_FP32)
+    expand_chunk_kernel<GAME_FP32><<<cb, threads, 0, st>>>(a);
+  else if (s.precision == GAME_BF16)
+    expand_chunk_kernel<GAME_BF16><<<cb, threads, 0, st>>>(a);
+  else
+    expand_chunk_kernel<GAME_FP8><<<cb, threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

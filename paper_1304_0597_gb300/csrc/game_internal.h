@@ -79,6 +79,7 @@ struct ExpDev {
                           // (1 unless a column's values could pass 2^15)
   float* t;               // [n_patterns padded to 256] targets
   float* tcoef;           // [same] 2 log2(e) t_k, read by the fused +-1 / tanh epilogue
+  int unit_scale32 = 1;   // FP32: colscale holds only ones (the expansion skips the multiply)
 };
 
 struct Fitness {

@@ -111,8 +111,10 @@ typedef struct game_config {
   int32_t engine;         /* GAME_ENGINE_* fitness kernel choice (see the enum above)      */
   int32_t tile_n;         /* tcgen05 tile: patterns per tile, 128 | 256 (0 = tuned / auto)  */
   int32_t tile_stages;    /* tcgen05 tile: depth of the pattern-tile ring (0 = auto)        */
-  int32_t tile_cluster;   /* tcgen05 tile: 0 or 1 (each CTA loads its own pattern tiles; other values
-                             are INVALID_ARG)                                                  */
+  int32_t tile_cluster;   /* tcgen05 tile: 1 = each CTA alone; 2 = CTA pairs sharing every MMA
+                             (tcgen05 cta_group::2, M = 256 chromosomes: each CTA stages half of
+                             each pattern tile; needs an even number of 128-chromosome slices);
+                             0 = tuned / 1.  Other values are INVALID_ARG.  No TMA multicast. */
   int32_t tile_slices;    /* tcgen05 tile: 128-chromosome slices per CTA, 1 | 2 (2 needs tile_n 128; 0 = auto) */
   int32_t device;         /* CUDA device ordinal                                            */
   void* stream;           /* cudaStream_t, or NULL for the legacy default stream           */
@@ -259,7 +261,7 @@ game_status game_selftest_timeout(game_ctx* ctx, int32_t wait_us, int32_t* waite
 typedef struct game_tile {
   int32_t n;          /* patterns per tile (MMA N)                            */
   int32_t stages;     /* pattern-tile ring depth                              */
-  int32_t cluster;    /* always 1 (no thread-block clusters)                  */
+  int32_t cluster;    /* 1: one CTA per work unit; 2: CTA pairs (cta_group::2) */
   int32_t prefetch;   /* 1: L2 prefetch of each CTA's next pattern tile       */
   int32_t slices;     /* 128-chromosome slices per CTA fed by each pattern tile */
   double ms;          /* median fitness time of this shape, milliseconds      */

@@ -254,7 +254,7 @@ static game_status validate(game_ctx* c, const game_config* cfg) {
   if (cfg->immigrants < 0 || cfg->immigrants > cfg->pop - (cfg->elitism < cfg->pop ? cfg->elitism : cfg->pop))
     return fail(c, GAME_ERR_INVALID_ARG, "immigrants must be in 0..pop - elitism");
   if ((cfg->tile_n != 0 && cfg->tile_n != 128 && cfg->tile_n != 256) || cfg->tile_stages < 0 ||
-      cfg->tile_cluster < 0 || cfg->tile_cluster > 1 || cfg->tile_slices < 0 || cfg->tile_slices > 2 ||
+      cfg->tile_cluster < 0 || cfg->tile_cluster > 2 || cfg->tile_slices < 0 || cfg->tile_slices > 2 ||
       (cfg->tile_slices == 2 && cfg->tile_n == 256))
     return fail(c, GAME_ERR_INVALID_ARG, "bad tile request");
   if (cfg->surrogate_pool < 0) return fail(c, GAME_ERR_INVALID_ARG, "bad surrogate_pool");

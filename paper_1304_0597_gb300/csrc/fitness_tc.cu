@@ -82,18 +82,21 @@ struct TcParams {
   int prefetch;           // L2 prefetch of the next tile's boxes
 };
 
-template <int BN, int PREC, bool FAST, int NA, int SP>
+template <int BN, int PREC, bool FAST, int NA, int SP, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_constant__ TcParams p) {
   static_assert(SP == 1 || (SP == 2 && BN == 128), "two slices per CTA use 128-pattern tiles");
-  if (p.in_evolve && p.state->stopped) return;
+  static_assert(!PAIR || SP == 1, "a CTA pair holds one slice per CTA");
+  if (p.in_evolve && p.state->stopped) return;   // (both CTAs of a pair read the same flag)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~(uintptr_t)1023);
-  constexpr int kTileB = BN * 128;
+  // A pair's CTA stages BN / 2 rows of each pattern tile (its half of the MMA's N).
+  constexpr int kRowsB = PAIR ? BN / 2 : BN;
+  constexpr int kTileB = kRowsB * 128;
   constexpr int kKB = PREC == GAME_FP8 ? 128 : 64;    // elements per 128-byte k-block
   constexpr int kKStep = PREC == GAME_FP8 ? 32 : 16;  // elements per MMA
   constexpr uint32_t kFmt = PREC == GAME_BF16 ? 1u : 0u;
-  constexpr uint32_t kIdesc = make_idesc(128, BN, kFmt);
+  constexpr uint32_t kIdesc = make_idesc(PAIR ? 256 : 128, BN, kFmt);
   const int S = p.stages;
   uint8_t* sA = smem;
   uint8_t* sB = sA + SP * NA * p.kblocks * kTileA;
@@ -110,8 +113,15 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   double* red = reinterpret_cast<double*>(sB);   // [SP][kColGroups][128], once the ring is idle
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int group = blockIdx.x % p.n_groups;      // slices group*SP .. group*SP+SP-1
-  const int member = blockIdx.x / p.n_groups;
+  // Work of this CTA: the slices slice0 .. slice0 + SP - 1 over the pattern tiles
+  // member, member + cps, ...  A pair (ranks 0 / 1 of a 2-CTA cluster) takes the two
+  // adjacent slices 2 g, 2 g + 1 over the same tiles.
+  const uint32_t crank = PAIR ? cluster_rank() : 0u;
+  const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int group = unit % p.n_groups;
+  const int member = unit / p.n_groups;
+  const int slice0 = PAIR ? 2 * group + (int)crank : group * SP;
+  const bool issuer = !PAIR || crank == 0;        // the CTA whose warp 1 issues the MMAs
   const int my_tiles = member < p.n_tiles ? (p.n_tiles - 1 - member) / p.cps + 1 : 0;
   constexpr uint32_t kTmemCols = 2 * SP * BN;      // [buffer][slice] accumulators of BN columns
 
@@ -124,7 +134,8 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(acc_full + b, 1);
-      mbar_init(acc_empty + b, kEpiWarps);
+      // a pair's leader waits for the epilogue warps of both CTAs
+      mbar_init(acc_empty + b, PAIR ? 2 * kEpiWarps : kEpiWarps);
     }
     mbar_init(fin, 1);
     *err = 0;
@@ -132,15 +143,30 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(kTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    if constexpr (PAIR) {
+      // one warp of each CTA of the pair allocates, together, the same TMEM columns in both
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(kTmemCols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(kTmemCols));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
   }
   fence_before();
   __syncthreads();
   fence_after();
+  // The peer completes bytes on and arrives at the leader's barriers: both CTAs'
+  // barriers exist before either CTA goes on.
+  if constexpr (PAIR) cluster_sync_all();
   const uint32_t tmem = *tmem_slot;
+  // shared::cluster addresses of the leader's barriers (the CTA's own for a single CTA)
+  auto lead = [&](uint64_t* bar) -> uint32_t {
+    return PAIR ? mapa_shared(smem_u32(bar), 0u) : smem_u32(bar);
+  };
   const int a_steps_total = p.kp / kKStep;
   F2Sum acc[SP];   // epilogue threads: each slice's chromosome error sum over its columns
 
@@ -148,18 +174,23 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     // ---- TMA producer: the whole warp follows one control flow, lane 0 issues ----
     if (lane == 0) {
       const uint32_t a_bytes = (uint32_t)SP * NA * p.kblocks * kTileA;
-      mbar_expect_tx(a_full, a_bytes);
+      // The leader expects its own and (pair) the peer's bytes on its barrier.
+      if (issuer) mbar_expect_tx(a_full, PAIR ? 2 * a_bytes : a_bytes);
       for (int sp = 0; sp < SP; ++sp)
         for (int pl = 0; pl < NA; ++pl)
-          for (int kb = 0; kb < p.kblocks; ++kb)
-            tma_load_2d(sA + ((sp * NA + pl) * p.kblocks + kb) * kTileA, &p.a[pl], kb * kKB,
-                        (group * SP + sp) * 128, a_full);
+          for (int kb = 0; kb < p.kblocks; ++kb) {
+            void* dst = sA + ((sp * NA + pl) * p.kblocks + kb) * kTileA;
+            if constexpr (PAIR)
+              tma_load_2d_pair(dst, &p.a[pl], kb * kKB, slice0 * 128, lead(a_full));
+            else
+              tma_load_2d(dst, &p.a[pl], kb * kKB, (slice0 + sp) * 128, a_full);
+          }
     }
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
     for (int it = 0; it < my_tiles && ok; ++it) {
-      const int row0 = (member + it * p.cps) * BN;
+      const int row0 = (member + it * p.cps) * BN + (int)crank * kRowsB;
       for (int kb = 0; kb < p.kblocks && ok; ++kb)
         for (int bp = 0; bp < p.n_bplanes; ++bp) {
           if (!warp_wait(b_empty + stage, phase ^ 1u, err, p.state, lane)) {
@@ -171,8 +202,13 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
             // warm L2 with the same box of this CTA's next tile
             if (it + 1 < my_tiles && p.prefetch)
               tma_prefetch_2d(&p.b[bp], kb * kKB, row0 + p.cps * BN);
-            mbar_expect_tx(b_full + stage, kTileB);
-            tma_load_2d(sB + stage * kTileB, &p.b[bp], kb * kKB, row0, b_full + stage);
+            if constexpr (PAIR) {
+              if (issuer) mbar_expect_tx(b_full + stage, 2 * kTileB);
+              tma_load_2d_pair(sB + stage * kTileB, &p.b[bp], kb * kKB, row0, lead(b_full + stage));
+            } else {
+              mbar_expect_tx(b_full + stage, kTileB);
+              tma_load_2d(sB + stage * kTileB, &p.b[bp], kb * kKB, row0, b_full + stage);
+            }
             last_par[stage] = (int)phase;
           }
           if (++stage == S) {
@@ -181,8 +217,10 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
           }
         }
     }
-    // Drain: every issued copy has landed before the CTA may exit.
-    if (lane == 0) {
+    // Drain: every issued copy has landed before the CTA may exit.  A pair's copies
+    // complete on the leader's barriers, which the leader drains (both CTAs issue the
+    // same stage sequence); the pair meets at a cluster barrier before either exits.
+    if (lane == 0 && issuer) {
       mbar_wait(a_full, 0, err, p.state);
       for (int s2 = 0; s2 < S; ++s2)
         if (last_par[s2] >= 0) {
@@ -194,7 +232,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     __syncwarp();
   } else if (warp == 1) {
     // ---- MMA issuer: warp-uniform loop (descriptors in uniform registers), lane 0 issues ----
-    if (warp_wait(a_full, 0, err, p.state, lane)) {
+    if (issuer && warp_wait(a_full, 0, err, p.state, lane)) {
       fence_after();
       int stage = 0;
       uint32_t phase = 0;
@@ -203,7 +241,9 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
       for (int it = 0; it < my_tiles; ++it) {
         const int buf = it & 1;
         const uint32_t ap = (uint32_t)((it >> 1) & 1);
-        if (!warp_wait(acc_empty + buf, ap ^ 1u, err, p.state, lane)) break;
+        const bool freed = PAIR ? warp_wait_cluster(acc_empty + buf, ap ^ 1u, err, p.state, lane)
+                                : warp_wait(acc_empty + buf, ap ^ 1u, err, p.state, lane);
+        if (!freed) break;
         fence_after();
         TC_STAMP(lane == 0, 2, it, 0);
         uint32_t accum = 0;   // the first k-step of a tile starts every slice's accumulator
@@ -231,14 +271,26 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
                 for (int k = 0; k < kKB / kKStep; ++k) {
                   if (k < steps) {
                     // +32 bytes along K inside the 128-byte swizzle row = +2 in the address field
-                    if (lane == 0) mma<PREC>(d, adesc + 2 * k, bdesc + 2 * k, kIdesc, acc_sp);
+                    if (lane == 0) {
+                      if constexpr (PAIR)
+                        mma_pair<PREC>(d, adesc + 2 * k, bdesc + 2 * k, kIdesc, acc_sp);
+                      else
+                        mma<PREC>(d, adesc + 2 * k, bdesc + 2 * k, kIdesc, acc_sp);
+                    }
                     acc_sp = 1;
                   }
                 }
               }
               if (sp == SP - 1) accum = acc_sp;
             }
-            if (lane == 0) mma_commit(b_empty + stage);
+            if (lane == 0) {
+              if constexpr (PAIR) {   // the stage is free in both CTAs
+                mma_commit_pair(smem_u32(b_empty + stage));
+                mma_commit_pair(mapa_shared(smem_u32(b_empty + stage), 1u));
+              } else {
+                mma_commit(b_empty + stage);
+              }
+            }
             if (++stage == S) {
               stage = 0;
               phase ^= 1u;
@@ -246,13 +298,23 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
           }
         }
         if (!ok) break;
-        if (lane == 0) mma_commit(acc_full + buf);
+        if (lane == 0) {
+          if constexpr (PAIR) {       // both CTAs' accumulators hold the tile
+            mma_commit_pair(smem_u32(acc_full + buf));
+            mma_commit_pair(mapa_shared(smem_u32(acc_full + buf), 1u));
+          } else {
+            mma_commit(acc_full + buf);
+          }
+        }
         TC_STAMP(lane == 0, 3, it, 0);
       }
     }
     // Drain: all issued MMAs complete before TMEM is released.
-    if (lane == 0) {
-      mma_commit(fin);
+    if (lane == 0 && issuer) {
+      if constexpr (PAIR)
+        mma_commit_pair(smem_u32(fin));
+      else
+        mma_commit(fin);
       const unsigned long long t0 = globaltimer();
       while (!mbar_try_wait(fin, 0) && globaltimer() - t0 < kWaitNs) {
       }
@@ -269,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     float bias[SP], rs[SP];
 #pragma unroll
     for (int sp = 0; sp < SP; ++sp) {
-      const int c = (group * SP + sp) * 128 + q * 32 + lane;
+      const int c = (slice0 + sp) * 128 + q * 32 + lane;
       bias[sp] = p.bias[c];
       rs[sp] = p.rscale[c];
     }
@@ -304,7 +366,12 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
       TC_STAMP(lane == 0 && (warp == 2 || warp == 17), warp == 2 ? 5 : 7, it, 0);
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty + buf);
+      if (lane == 0) {
+        if constexpr (PAIR)
+          mbar_arrive_cluster(lead(acc_empty + buf));   // the leader reuses the buffer
+        else
+          mbar_arrive(acc_empty + buf);
+      }
     }
   }
   // Every copy and MMA of this CTA has completed (drained above): the B ring is
@@ -312,9 +379,18 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   fence_before();
   __syncthreads();
   fence_after();
-  if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kTmemCols));
+  // A pair: the leader's MMAs (into both CTAs' TMEM) and copies (completing on the
+  // leader's barriers) are done and the peer has made its last arrival at the leader
+  // before either CTA releases TMEM or exits.
+  if constexpr (PAIR) cluster_sync_all();
+  if (warp == 1) {
+    if constexpr (PAIR)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(kTmemCols));
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                   "r"(kTmemCols));
+  }
   if (warp >= 2) {
 #pragma unroll
     for (int sp = 0; sp < SP; ++sp)
@@ -326,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     double tot = 0.0;
 #pragma unroll
     for (int g = 0; g < kColGroups; ++g) tot += red[(sp * kColGroups + g) * 128 + r];
-    p.partial[(long long)member * p.pop_pad + (group * SP + sp) * 128 + r] = tot;
+    p.partial[(long long)member * p.pop_pad + (slice0 + sp) * 128 + r] = tot;
   }
 }
 
@@ -372,15 +448,28 @@ int kblocks_of(const Shape& s) {
   return (s.kp + kkb - 1) / kkb;
 }
 
-template <int BN, int PREC, bool FAST, int NA, int SP>
+template <int BN, int PREC, bool FAST, int NA, int SP, bool PAIR>
 void* kernel_ptr() {
-  return reinterpret_cast<void*>(&fitness_tc_kernel<BN, PREC, FAST, NA, SP>);
+  return reinterpret_cast<void*>(&fitness_tc_kernel<BN, PREC, FAST, NA, SP, PAIR>);
 }
 
-void* pick_kernel(int bn, int prec, bool fast, int na, int sp) {
+// pair: 2-CTA clusters sharing each MMA (cta_group::2, M = 256 chromosomes)
+void* pick_kernel(int bn, int prec, bool fast, int na, int sp, bool pair = false) {
+#define GAME_TC_PAIR(BNV, PV, NAV)                                                          \
+  if (pair && bn == BNV && prec == PV && na == NAV && sp == 1)                               \
+    return fast ? kernel_ptr<BNV, PV, true, NAV, 1, true>()                                  \
+                : kernel_ptr<BNV, PV, false, NAV, 1, true>();
+  GAME_TC_PAIR(256, GAME_FP32, 2)
+  GAME_TC_PAIR(256, GAME_BF16, 2)
+  GAME_TC_PAIR(256, GAME_FP8, 2)
+  GAME_TC_PAIR(256, GAME_BF16, 1)
+  GAME_TC_PAIR(256, GAME_FP8, 1)
+#undef GAME_TC_PAIR
+  if (pair) return nullptr;
 #define GAME_TC_PICK(BNV, PV, NAV, SPV)                                                     \
   if (bn == BNV && prec == PV && na == NAV && sp == SPV)                                     \
-    return fast ? kernel_ptr<BNV, PV, true, NAV, SPV>() : kernel_ptr<BNV, PV, false, NAV, SPV>();
+    return fast ? kernel_ptr<BNV, PV, true, NAV, SPV, false>()                               \
+                : kernel_ptr<BNV, PV, false, NAV, SPV, false>();
   GAME_TC_PICK(256, GAME_FP32, 2, 1)
   GAME_TC_PICK(128, GAME_FP32, 2, 1)
   GAME_TC_PICK(256, GAME_BF16, 2, 1)
@@ -445,13 +534,14 @@ cudaError_t tc_init_attributes() {
     for (int prec : {GAME_FP32, GAME_BF16, GAME_FP8})
       for (bool fast : {false, true})
         for (int na : {1, 2})
-          for (int sp : {1, 2}) {
-            void* k = pick_kernel(bn, prec, fast, na, sp);
-            if (!k) continue;
-            cudaError_t e =
-                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-            if (e != cudaSuccess) return e;
-          }
+          for (int sp : {1, 2})
+            for (bool pair : {false, true}) {
+              void* k = pick_kernel(bn, prec, fast, na, sp, pair);
+              if (!k) continue;
+              cudaError_t e =
+                  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
+              if (e != cudaSuccess) return e;
+            }
   return cudaSuccess;
 }
 
@@ -462,11 +552,16 @@ bool tc_supported(const Shape& s) {
   return a_bytes + 2 * 128 * 128 + kSmemMisc <= kSmemMax;
 }
 
-static int max_stages(const Shape& s, int bn, int sp) {
+// Deepest pattern-tile ring next to the resident gene planes; rows = pattern rows a CTA
+// stages per tile (BN, or BN / 2 for a CTA of a pair).
+static int max_stages(const Shape& s, int rows, int sp) {
   const int room = kSmemMax - kSmemMisc - sp * s.gene_planes * kblocks_of(s) * kTileA;
-  int st = room / (bn * 128);
+  int st = room / (rows * 128);
   return st > 8 ? 8 : st;
 }
+
+// CTA pairs: 256-pattern tiles, one slice per CTA, an even number of slices.
+static bool pair_ok(const Shape& s) { return (s.pop_pad / 128) % 2 == 0; }
 
 void tc_candidates(const Shape& s, std::vector<TileReq>* out) {
   if (tc_narrow_shape(s)) {
@@ -477,11 +572,15 @@ void tc_candidates(const Shape& s, std::vector<TileReq>* out) {
   for (int sp : {1, 2})
     for (int bn : {256, 128}) {
       if (sp == 2 && (bn != 128 || n_slices % 2 != 0)) continue;
-      const int n_groups = n_slices / sp;
       const int ms = max_stages(s, bn, sp);
       for (int st = ms; st >= 2 && st >= ms - 1; --st)
         for (int pf : {1, 0}) out->push_back(TileReq{bn, st, 1, pf, sp});
     }
+  if (pair_ok(s)) {
+    const int ms = max_stages(s, 128, 1);
+    for (int st = ms; st >= 2 && st >= ms - 2; --st)
+      for (int pf : {1, 0}) out->push_back(TileReq{256, st, 2, pf, 1});
+  }
 }
 
 cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, TcPlan* plan,
@@ -491,37 +590,65 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
   t.kblocks = kblocks_of(s);
   const int n_bplanes = s.precision == GAME_FP32 ? 2 : 1;
   t.n_slices = s.pop_pad / 128;
+  // cluster 2: CTA pairs (cta_group::2), each CTA one slice, 256-pattern tiles
+  if (req.cluster < 0 || req.cluster > 2) return cudaErrorInvalidValue;
+  t.cluster = req.cluster == 2 ? 2 : 1;
+  const bool pair = t.cluster == 2;
+  if (pair && (!pair_ok(s) || (req.sp && req.sp != 1) || (req.n && req.n != 256)))
+    return cudaErrorInvalidValue;
   t.sp = req.sp ? req.sp : 1;
   if (t.sp != 1 && t.sp != 2) return cudaErrorInvalidValue;
   if (t.sp == 2 && (t.n_slices % 2 != 0 || (req.n && req.n != 128))) return cudaErrorInvalidValue;
-  t.n_groups = t.n_slices / t.sp;
+  // groups: units of work sharing the pattern tiles (a CTA's slices, or a pair's two)
+  t.n_groups = pair ? t.n_slices / 2 : t.n_slices / t.sp;
   const int a_bytes = t.sp * s.gene_planes * t.kblocks * kTileA;
   // Default shape: 256-pattern tiles when two stages fit, else 128
   // (128-pattern tiles cost as much per MMA instruction as 256-pattern ones).
-  t.bn = t.sp == 2 ? 128 : (req.n ? req.n : (max_stages(s, 256, 1) >= 2 ? 256 : 128));
+  t.bn = pair ? 256 : t.sp == 2 ? 128 : (req.n ? req.n : (max_stages(s, 256, 1) >= 2 ? 256 : 128));
   if (t.bn != 128 && t.bn != 256) return cudaErrorInvalidValue;
-  const int ms = max_stages(s, t.bn, t.sp);
+  const int rows = pair ? t.bn / 2 : t.bn;          // pattern rows a CTA stages per tile
+  const int ms = max_stages(s, rows, t.sp);
   t.stages = req.stages ? req.stages : ms;
   if (t.stages < 2 || t.stages > ms) return cudaErrorNotSupported;
-  // Every CTA loads its own pattern tiles (no thread-block clusters).
-  if (req.cluster > 1) return cudaErrorInvalidValue;
-  t.cluster = 1;
   t.prefetch = req.prefetch == 0 ? 0 : 1;
   t.n_tiles = (int)((s.n_train + t.bn - 1) / t.bn);
-  t.smem = (size_t)a_bytes + (size_t)t.stages * t.bn * 128 + kSmemMisc;
-  const int resident = n_sm;   // one CTA per SM (the shared memory of one fills it)
+  t.smem = (size_t)a_bytes + (size_t)t.stages * rows * 128 + kSmemMisc;
+  // Co-resident work units: one CTA per SM (its shared memory fills the SM); pairs must
+  // also find two SMs of one GPC, which the occupancy query counts.
+  int resident = n_sm;
+  if (pair) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * n_sm);      // large enough not to cap the count
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = t.smem;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n_clusters = 0;
+    const cudaError_t oe = cudaOccupancyMaxActiveClusters(
+        &n_clusters, pick_kernel(t.bn, s.precision, true, s.gene_planes, 1, true), &cfg);
+    if (oe != cudaSuccess || n_clusters < 1) {
+      cudaGetLastError();
+      return cudaErrorNotSupported;
+    }
+    resident = n_clusters;                           // pairs
+  }
   int cps = resident / t.n_groups;
   if (cps < 1) cps = 1;
   if (cps > t.n_tiles) cps = t.n_tiles;
   t.ctas_per_slice = cps;
-  t.grid = t.n_groups * cps;
+  t.grid = t.n_groups * cps * (pair ? 2 : 1);
   t.n_part = cps;
   cudaError_t err;
   if ((err = make_map(&t.a_map[0], p.ghi, s.precision, s.pop_pad, s.kp, 128)) != cudaSuccess) return err;
   if ((err = make_map(&t.a_map[1], p.glo, s.precision, s.pop_pad, s.kp, 128)) != cudaSuccess) return err;
-  if ((err = make_map(&t.b_map[0], e.p0, s.precision, s.n_train, s.kp, t.bn)) != cudaSuccess) return err;
+  if ((err = make_map(&t.b_map[0], e.p0, s.precision, s.n_train, s.kp, rows)) != cudaSuccess) return err;
   if (n_bplanes == 2) {
-    if ((err = make_map(&t.b_map[1], e.p1, s.precision, s.n_train, s.kp, t.bn)) != cudaSuccess) return err;
+    if ((err = make_map(&t.b_map[1], e.p1, s.precision, s.n_train, s.kp, rows)) != cudaSuccess) return err;
   } else {
     t.b_map[1] = t.b_map[0];
   }
@@ -558,10 +685,24 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
   p.prefetch = t.prefetch;
   const bool fast = f.pm1_targets && f.activation == GAME_TANH &&
                     (f.error == GAME_RMSE || f.error == GAME_MSE);
-  void* k = pick_kernel(t.bn, s.precision, fast, s.gene_planes, t.sp);
+  const bool pair = t.cluster == 2;
+  void* k = pick_kernel(t.bn, s.precision, fast, s.gene_planes, t.sp, pair);
   if (!k) return cudaErrorNotSupported;
   void* args[] = {&p};
-  return cudaLaunchKernel(k, dim3(t.grid), dim3(kThreads), args, t.smem, st);
+  if (!pair) return cudaLaunchKernel(k, dim3(t.grid), dim3(kThreads), args, t.smem, st);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = 2;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.gridDim = dim3(t.grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = t.smem;
+  cfg.stream = st;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, k, args);
 }
 
 #ifdef GAME_TC_TIMELINE

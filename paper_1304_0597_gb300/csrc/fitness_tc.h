@@ -22,7 +22,7 @@ struct TcPlan {
   int bn;                 // patterns per tile (MMA N)
   int kblocks;            // k-blocks of 128 bytes over kp
   int stages;             // B-operand pipeline depth
-  int cluster;            // always 1: every CTA loads its own pattern tiles
+  int cluster;            // 1, or 2: CTA pairs sharing each MMA (cta_group::2, M = 256)
   int prefetch = 1;       // L2 prefetch of each CTA's next pattern tile
   size_t smem;            // dynamic shared memory bytes
   int narrow = 0;         // 1: the swapped kernel (patterns on M, <= 32 chromosomes on N)

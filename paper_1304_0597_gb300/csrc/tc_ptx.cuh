@@ -168,6 +168,56 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity
   }
 }
 
+// ---- CTA pairs (cta_group::2): one MMA over the shared memory of two CTAs ----
+// A pair is a cluster of two CTAs; rank 0 (the leader) issues the MMAs.  An MMA of
+// M = 256 takes A rows 0-127 from the leader's and rows 128-255 from the peer's shared
+// memory, B rows (N) half from each, at the same offsets, and writes D rows 0-127 to
+// the leader's TMEM and rows 128-255 to the peer's.
+
+// TMA load into this CTA's shared memory whose bytes complete on the mbarrier at the
+// shared::cluster address bar_cl (the leader's barrier, also for the peer's loads).
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, int c0, int c1,
+                                                 uint32_t bar_cl) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      ".cta_group::2 [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(bar_cl)
+      : "memory");
+}
+
+template <int PREC>
+__device__ __forceinline__ void mma_pair(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  if (PREC == GAME_FP8) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum));
+  }
+}
+
+// Arrive on the mbarrier at shared::cluster address bar_cl (this CTA's or the peer's)
+// when every pair MMA this thread has issued so far has completed.
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar_cl) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar_cl)
+               : "memory");
+}
+
+// Warp-uniform bounded wait whose arrivals may come from the peer CTA (acquire at
+// cluster scope): lane 0 polls, the outcome is broadcast.
+__device__ __forceinline__ bool warp_wait_cluster(uint64_t* bar, uint32_t parity, volatile int* err,
+                                                  DevState* st, int lane) {
+  int ok = 0;
+  if (lane == 0) ok = mbar_wait_cluster(bar, parity, err, st) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (stride byte offset), descriptor version 1 (tcgen05).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {

@@ -402,11 +402,13 @@ def test_calls_out_of_order_are_state_errors():
 # ------------------------------------------------------------ tile shapes
 
 @pytest.mark.parametrize("tile", [(256, 3, 1, 1), (256, 2, 1, 1), (128, 5, 1, 1),
-                                  (128, 4, 1, 1), (128, 2, 1, 2), (128, 3, 0, 2)])
+                                  (128, 4, 1, 1), (128, 2, 1, 2), (128, 3, 0, 2),
+                                  (256, 6, 2, 1), (256, 4, 2, 1), (256, 2, 2, 1)])
 def test_tcgen05_tile_shapes_agree(tile):
-    """Every tile shape (patterns per tile, ring depth, cluster field, slices per CTA)
-    gives the oracle's fitness; population 1024 = 8 slices of 128 chromosomes, fed one
-    or two per CTA."""
+    """Every tile shape (patterns per tile, ring depth, cluster, slices per CTA) gives the
+    oracle's fitness; population 1024 = 8 slices of 128 chromosomes, fed one or two per
+    CTA, or (cluster 2) by CTA pairs whose MMAs of 256 chromosomes read both CTAs' halves
+    of each pattern tile."""
     game = lib()
     ds = synth.make_dataset(20011, 32, 8, seed=41, correlated=True)
     ocfg = _cfg(degree=8, pop=1024, seed=3)
@@ -418,14 +420,29 @@ def test_tcgen05_tile_shapes_agree(tile):
                                rtol=FIT_RTOL)
 
 
-def test_tile_cluster_above_one_is_rejected():
-    """Each CTA loads its own pattern tiles: a cluster request above 1 is INVALID_ARG."""
+def test_tile_cluster_above_two_is_rejected():
+    """Clusters are single CTAs or CTA pairs: a cluster request above 2 is INVALID_ARG."""
     game = lib()
     ds = synth.make_dataset(3001, 8, 4, seed=5)
     with pytest.raises(game.GameError) as e:
         make_game(_cfg(degree=4, pop=256, seed=1), ds.X, ds.t, ds.n_train,
-                  engine=game.ENGINE_TCGEN05, tile_cluster=2)
+                  engine=game.ENGINE_TCGEN05, tile_cluster=4)
     assert e.value.status == -1
+
+
+@pytest.mark.parametrize("pop,n", [(256, 5003), (1280, 40013), (384, 2000)])
+def test_cta_pairs_ragged_and_odd_slices(pop, n):
+    """CTA pairs on a ragged last tile (n_train not a multiple of 256) and few tiles;
+    pop 384 has an odd number of slices, where a pair request falls back to single CTAs."""
+    game = lib()
+    ds = synth.make_dataset(n, 16, 6, seed=44, correlated=True)
+    ocfg = _cfg(degree=6, pop=pop, seed=8)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=game.ENGINE_TCGEN05, tile_cluster=2)
+    fit, _ = g.evaluate()
+    P = o.expand(ds.X[:ds.n_train], "chebyshev", 6)
+    np.testing.assert_allclose(fit, o.fitness(P, ds.t[:ds.n_train], g.population(), ocfg),
+                               rtol=FIT_RTOL)
+    assert g.evolve(2) == 2
 
 
 def test_autotune_picks_a_valid_shape(tmp_path, monkeypatch):

@@ -120,6 +120,26 @@ def test_low_precision_two_slices_per_cta(fmt, planes):
 
 
 @pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+@pytest.mark.parametrize("planes", [1, 2])
+def test_low_precision_cta_pairs(fmt, planes):
+    """CTA pairs (cta_group::2: MMAs of 256 chromosomes over both CTAs' halves of each
+    256-pattern tile) give the oracle's fitness on the quantised operands; population
+    1024, training rows 21,007 (a ragged last tile)."""
+    game = lib()
+    ds = synth.make_dataset(30011, 32, 8, seed=37, correlated=True)
+    ocfg = o.Config(degree=8, pop=1024, seed=9)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=_prec(fmt), elite_rescore=0,
+                  engine=game.ENGINE_TCGEN05, gene_planes=planes, tile_cluster=2)
+    G = g.population()
+    fit, _ = g.evaluate()
+    Q, s = o.quantize_columns(o.expand(ds.X, "chebyshev", 8)[:, 1:], fmt)
+    Pq = np.concatenate([np.ones((ds.n_train, 1)), o.dequantize_columns(Q[:ds.n_train], s)], axis=1)
+    np.testing.assert_allclose(fit, o.fitness(Pq, ds.t[:ds.n_train],
+                                              o.quantize_genes(G, s, fmt, planes), ocfg),
+                               rtol=1e-5)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
 def test_low_precision_tanh_epilogue_within_its_bound(fmt):
     """42 training rows, too few for the per-element tanh.approx errors to average out.
     With eps = 2^-10 (twice the stated 2^-11) and y_k the oracle's output on the

@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--engine", choices=["auto", "tcgen05", "simt"], default="auto")
+    ap.add_argument("--engine", choices=["auto", "tcgen05", "simt", "on_the_fly"], default="auto")
     ap.add_argument("--n-patterns", type=int, default=1_000_000)
     ap.add_argument("--e2e-runs", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -75,6 +75,9 @@ def parse():
                     help="CTA-0 clock64 timeline of one tensor-core fitness launch per precision "
                          "(builds the -DGAME_TC_TIMELINE variant of the library)")
     ap.add_argument("--timeline-tiles", type=int, default=16)
+    ap.add_argument("--engine-table", action="store_true",
+                    help="fitness time per engine (stored tcgen05 / stored SIMT / on-the-fly) and "
+                         "device bytes of the stored expansion, on a few shapes")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args()
 
@@ -325,7 +328,7 @@ def run_ours(args):
     t_pin = torch.from_numpy(ds.t).pin_memory()
     stream = torch.cuda.current_stream()
     engine = {"auto": game.ENGINE_AUTO, "tcgen05": game.ENGINE_TCGEN05,
-              "simt": game.ENGINE_SIMT}[args.engine]
+              "simt": game.ENGINE_SIMT, "on_the_fly": game.ENGINE_ON_THE_FLY}[args.engine]
     prec = {"fp32": game.FP32, "bf16": game.BF16, "fp8": game.FP8}[args.precision]
     cfg = game.default_config(degree=8, pop=1024, seed=rank, stream=stream.cuda_stream,
                               engine=engine, device=local_rank, precision=prec,
@@ -395,7 +398,8 @@ def run_ours(args):
         achieved = flops / (fit_ms / 1e3) / 1e12
     else:
         # float32 FFMA: 152 SMs x 128 lanes x 2 flops x max SM clock
-        kfile, bound, punit = "fitness_simt.cu", "alu", "TFLOP/s"
+        kfile = "fitness_otf.cu" if engine_used == game.ENGINE_ON_THE_FLY else "fitness_simt.cu"
+        bound, punit = "alu", "TFLOP/s"
         peak = 152 * 128 * 2 * 2.07e9 / 1e12
         achieved = flops / (fit_ms / 1e3) / 1e12
     traffic = kernel_traffic(kfile, variant)
@@ -408,7 +412,7 @@ def run_ours(args):
         "config": dict(workload_config(args.n_patterns, args.precision), n_train=n_train,
                        precision=args.precision,
                        gene_planes=args.gene_planes if args.precision != "fp32" else None,
-                       engine={1: "tcgen05", 2: "simt"}.get(engine_used, "?"),
+                       engine={1: "tcgen05", 2: "simt", 3: "on_the_fly"}.get(engine_used, "?"),
                        tile=tile,
                        l2="inputs larger than L2 (expansion planes of the training rows: "
                           f"{2 * 2 * n_train * 256 / 1e6:.0f} MB)",
@@ -654,7 +658,7 @@ def paper_table(args):
             tot = time.perf_counter() - t0
             tm = g.timing()
             ms_gen = tm["ms_total"] / max(ran, 1)
-            engine = {1: "tcgen05", 2: "simt"}.get(tm["engine"], "?")
+            engine = {1: "tcgen05", 2: "simt", 3: "on_the_fly"}.get(tm["engine"], "?")
             g.close()
             paper_s = PAPER_TOT_S[d][PAPER_MB.index(mb)] * args.paper_iterations / 4000.0
             rows.append({"mb": mb, "patterns": int(ds.X.shape[0]), "degree": d,
@@ -719,6 +723,57 @@ def timeline(args):
                   flush=True)
 
 
+def engine_table(args):
+    """Stored expansion against the on-the-fly engine: median fitness time of 10
+    generations per engine (CUDA events) on shapes where P dominates the traffic to
+    ones where the contraction does, with the bytes the stored FP32 planes take."""
+    from paper_1304_0597_gb300 import game, synth
+    shapes = (
+        ("c2: 1M x 32, Chebyshev d=8, pop 1024", dict(n=1_000_000, F=32, d=8, basis="chebyshev",
+                                                     pop=1024, correlated=True)),
+        ("narrow: 1M x 40, trig d=10 (801 genes), pop 32", dict(n=1_000_000, F=40, d=10,
+                                                               basis="trig", pop=32)),
+        ("paper: 7.17M x 11, shared trig d=8, pop 23", dict(n=7_168_500, F=11, d=8, basis="trig",
+                                                           pop=23, shared=True)),
+        ("mid: 1M x 16, Chebyshev d=6, pop 128", dict(n=1_000_000, F=16, d=6, basis="chebyshev",
+                                                     pop=128)),
+    )
+    for label, sh in shapes:
+        if sh.get("shared"):
+            ds = synth.paper_kb(replicas=3413)
+        else:
+            ds = synth.make_dataset(sh["n"], sh["F"], sh["d"], sh["basis"], seed=synth.DATA_SEED,
+                                    correlated=sh.get("correlated", False))
+        row = {"shape": label, "n_train": ds.n_train}
+        for name, eng in (("tcgen05", game.ENGINE_TCGEN05), ("simt", game.ENGINE_SIMT),
+                          ("on_the_fly", game.ENGINE_ON_THE_FLY)):
+            cfg = game.default_config(
+                basis=game.CHEBYSHEV if sh["basis"] == "chebyshev" else game.TRIG, degree=sh["d"],
+                pop=sh["pop"], seed=0, engine=eng, stop_error=-1.0,
+                coefficients=game.COEF_SHARED if sh.get("shared") else game.COEF_PER_FEATURE)
+            try:
+                g = game.Game(cfg)
+                g.set_data(ds.X, ds.t, ds.n_train)
+            except game.GameError as e:
+                row[name] = f"unavailable: {e}"
+                continue
+            if eng == game.ENGINE_TCGEN05:
+                try:
+                    g.autotune(reps=2)
+                except game.GameError:
+                    pass
+            g.evolve(3)
+            g.set_timing(True)
+            g.evolve(10)
+            row[name + "_ms"] = g.timing()["ms_fitness"] / 10
+            g.close()
+        kb = (2 if sh["basis"] == "trig" else 1) * (1 if sh.get("shared") else sh["F"]) * sh["d"]
+        kp = (kb + 15) // 16 * 16
+        row["stored_fp32_planes_bytes"] = 4 * ds.n_patterns * kp
+        row["features_bytes"] = 4 * ds.X.size
+        print(json.dumps(row), flush=True)
+
+
 def main():
     args = parse()
     if args.surrogate:
@@ -738,6 +793,9 @@ def main():
         return
     if args.oracle_sample:
         oracle_sample_main(args)
+        return
+    if args.engine_table:
+        engine_table(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -52,6 +52,8 @@ struct game_ctx {
   int score_nb = 0;
   float* d_genes = nullptr;     // one chromosome (report)
   int engine = GAME_ENGINE_SIMT;
+  bool otf = false;             // on-the-fly engine: no stored expansion
+  const float* d_X = nullptr;   // the device copy of X (read by the on-the-fly engine)
   TcPlan tc{};
   // Precision form: FP32 copy of P and the FP32 re-score of the top elites.
   bool lowp = false;            // P stored in BF16 / FP8
@@ -245,7 +247,7 @@ static game_status validate(game_ctx* c, const game_config* cfg) {
     return fail(c, GAME_ERR_INVALID_ARG, "bad init mode");
   if (cfg->precision < GAME_FP32 || cfg->precision > GAME_FP8)
     return fail(c, GAME_ERR_INVALID_ARG, "bad precision");
-  if (cfg->engine < GAME_ENGINE_AUTO || cfg->engine > GAME_ENGINE_SIMT)
+  if (cfg->engine < GAME_ENGINE_AUTO || cfg->engine > GAME_ENGINE_ON_THE_FLY)
     return fail(c, GAME_ERR_INVALID_ARG, "bad engine");
   if (cfg->coefficients < GAME_COEF_PER_FEATURE || cfg->coefficients > GAME_COEF_SHARED)
     return fail(c, GAME_ERR_INVALID_ARG, "bad coefficients");
@@ -387,6 +389,11 @@ static void tune_cache_store(const Shape& s, const game_tile& t) {
 
 static game_status choose_engine(game_ctx* c, Shape& s, const ExpDev& e, const PopDev& p,
                                  int* engine, TcPlan* plan, int* n_part) {
+  if (c->otf) {
+    *engine = GAME_ENGINE_ON_THE_FLY;
+    *n_part = otf_partials(s, c->n_sm);
+    return GAME_OK;
+  }
   int want = c->cfg.engine;
   // Automatic: the narrow SIMT kernel for at most 32 chromosomes on 16 or 32 stored
   // columns (the paper's own settings); otherwise the tensor cores where a kernel
@@ -546,11 +553,33 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   unsigned int* dfmax = nullptr;   // per-feature max |x| (float bits)
   if ((r = dalloc(c, &dfmax, sizeof(unsigned int) * n_features)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->e.tcoef, sizeof(float) * tpad)) != GAME_OK) return r;
+  c->d_X = dX;
   const size_t esz = s.precision == GAME_FP32 ? 2 : (s.precision == GAME_BF16 ? 2 : 1);
   const size_t pbytes = esz * (size_t)n_patterns * s.kp;
-  if ((r = dalloc(c, &c->e.p0, pbytes)) != GAME_OK) return r;
-  if (s.precision == GAME_FP32) {
-    if ((r = dalloc(c, &c->e.p1, pbytes)) != GAME_OK) return r;
+  // On-the-fly engine: P is never stored.  Asked for by name, or chosen automatically
+  // in the FP32 form when the stored planes would not fit in the device's free memory
+  // (measured slower than the stored engines wherever P fits).
+  const size_t stored = pbytes * (s.precision == GAME_FP32 ? 2 : 3);   // + the FP32 copy
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    free_b = (size_t)-1;
+  }
+  c->otf = c->cfg.engine == GAME_ENGINE_ON_THE_FLY ||
+           (c->cfg.engine == GAME_ENGINE_AUTO && s.precision == GAME_FP32 &&
+            c->cfg.surrogate_pool == 0 && (double)stored > 0.85 * (double)free_b);
+  if (c->otf && (s.precision != GAME_FP32 || c->cfg.surrogate_pool > 0)) {
+    free_all(c);
+    return fail(c, GAME_ERR_UNSUPPORTED,
+                "the on-the-fly engine takes the FP32 form without the surrogate");
+  }
+  if (!c->otf) {
+    if ((r = dalloc(c, &c->e.p0, pbytes)) != GAME_OK) return r;
+    if (s.precision == GAME_FP32) {
+      if ((r = dalloc(c, &c->e.p1, pbytes)) != GAME_OK) return r;
+    }
+  } else {
+    c->e.p0 = c->e.p1 = nullptr;
   }
   if ((r = dalloc(c, &c->e.colscale, sizeof(float) * s.kp)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_scratch, sizeof(float) * s.kp)) != GAME_OK) return r;
@@ -564,7 +593,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   // host memory in the FP32 form, X comes over in chunks on a copy stream and each
   // chunk is expanded as soon as it lands (the rows are independent); the
   // quantised forms need the column maxima of all rows first.
-  if (!device_ptrs && s.precision == GAME_FP32) {
+  if (!device_ptrs && s.precision == GAME_FP32 && !c->otf) {
     if (!c->st_copy) CUDA_OK(c, cudaStreamCreateWithFlags(&c->st_copy, cudaStreamNonBlocking));
     const long long chunk = std::max<long long>(65536, ((long long)n_patterns + 7) / 8);
     const int n_chunks = (int)((n_patterns + chunk - 1) / chunk);
@@ -651,7 +680,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
     c->e.unit_scale32 = 0;
   }
   // (the host chunks of the FP32 form were expanded unscaled as they landed)
-  if (device_ptrs || s.precision != GAME_FP32 || scaled)
+  if ((device_ptrs || s.precision != GAME_FP32 || scaled) && !c->otf)
     CUDA_OK(c, launch_expand(dX, s, c->e, c->d_scratch, c->st));
   c->lowp = s.precision != GAME_FP32;
   c->s32 = s;
@@ -700,6 +729,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   }
   // Any tile shape uses at most one partial row per SM.
   c->part_rows = std::max(std::max(c->n_part, simt_partials(s, c->n_sm)), c->n_sm);
+  if (c->otf) c->part_rows = std::max(c->part_rows, otf_partials(s, c->n_sm));
   if ((r = dalloc(c, &c->d_partial, sizeof(double) * (size_t)c->part_rows * s.pop_pad)) != GAME_OK)
     return r;
   c->n_rescore = 0;
@@ -748,6 +778,9 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
 static game_status launch_fitness(game_ctx* c, const DevState* state) {
   if (c->engine == GAME_ENGINE_TCGEN05) {
     CUDA_OK(c, tc_launch(c->tc, c->s, c->fit, c->p, c->e, c->d_partial, state, c->st));
+  } else if (c->engine == GAME_ENGINE_ON_THE_FLY) {
+    CUDA_OK(c, launch_fitness_otf(c->s, c->fit, c->p, c->d_X, c->e, c->d_partial, c->n_part, state,
+                                  c->st));
   } else {
     CUDA_OK(c, launch_fitness_simt(c->s, c->fit, c->p, c->e, c->d_partial, c->n_part, state, c->st));
   }
@@ -1120,7 +1153,8 @@ extern "C" game_status game_get_expansion(game_ctx* c, float* out, int64_t row0,
   float* tmp = nullptr;
   const size_t bytes = sizeof(float) * (size_t)n_rows * c->s.kb;
   CUDA_OK(c, cudaMalloc(&tmp, bytes));
-  cudaError_t e = launch_expand_get(c->s, c->e, row0, n_rows, tmp, c->st);
+  cudaError_t e = c->otf ? launch_expand_get_otf(c->s, c->d_X, row0, n_rows, tmp, c->st)
+                         : launch_expand_get(c->s, c->e, row0, n_rows, tmp, c->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   cudaFree(tmp);
@@ -1136,8 +1170,12 @@ static game_status score(game_ctx* c, const float* genes_host_or_null, int split
   if (genes_host_or_null)
     CUDA_OK(c, cudaMemcpyAsync(c->d_genes, genes_host_or_null, sizeof(float) * c->s.n_genes,
                                cudaMemcpyHostToDevice, c->st));
-  CUDA_OK(c, launch_score(c->s32, c->fit, c->e32, c->d_genes, r0, r1, c->d_score_blocks,
-                          c->score_nb, c->d_score_out, c->st));
+  if (c->otf)
+    CUDA_OK(c, launch_score_otf(c->s, c->fit, c->d_X, c->e.t, c->d_genes, r0, r1, c->d_score_blocks,
+                                c->score_nb, c->d_score_out, c->st));
+  else
+    CUDA_OK(c, launch_score(c->s32, c->fit, c->e32, c->d_genes, r0, r1, c->d_score_blocks,
+                            c->score_nb, c->d_score_out, c->st));
   CUDA_OK(c, cudaMemcpyAsync(out, c->d_score_out, sizeof(double) * 5, cudaMemcpyDeviceToHost, c->st));
   CUDA_OK(c, cudaStreamSynchronize(c->st));
   return GAME_OK;
@@ -1395,7 +1433,7 @@ extern "C" game_status game_autotune(game_ctx* c, int32_t reps, game_tile* best,
   if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
   if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
   if (c->engine != GAME_ENGINE_TCGEN05)
-    return fail(c, GAME_ERR_UNSUPPORTED, "this shape runs on the SIMT engine; nothing to tune");
+    return fail(c, GAME_ERR_UNSUPPORTED, "this shape runs on a CUDA-core engine; nothing to tune");
   if (reps < 1) reps = 1;
   cudaSetDevice(c->dev);
   // Operand planes of the current population.
@@ -1674,6 +1712,12 @@ extern "C" game_status game_batch_set_data(game_batch* b, int32_t run, const flo
   batch_free_plan(b);
   game_status s = game_set_data(b->runs[run], X, t, n_patterns, n_features, n_train, device_ptrs);
   if (s != GAME_OK) b->err = b->runs[run]->err;
+  if (s == GAME_OK && b->runs[run]->otf) {
+    b->runs[run]->have_data = false;
+    return bfail(b, GAME_ERR_UNSUPPORTED,
+                 "the grouped launch reads stored expansions; a run on the on-the-fly engine "
+                 "cannot join a batch");
+  }
   return s;
 }
 

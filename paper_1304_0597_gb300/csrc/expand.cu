@@ -17,100 +17,12 @@
 //         2^15 (Chebyshev features beyond [-1, 1]), so that hi never overflows fp16
 //   BF16: bf16(v / s_g), s_g = max_k |P[k,g]|          (per-column scale)
 //   FP8 : e4m3(v / s_g), s_g = max_k |P[k,g]| / 448
+#include "basis.cuh"
 #include "game_internal.h"
 
 #include <algorithm>
 
 namespace game {
-
-// Error-free transformations on float32 (Dekker's product via FMA, Knuth's sum):
-// a*b = p + e and a+b = s + e exactly.
-__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
-  p = __fmul_rn(a, b);
-  e = fmaf(a, b, -p);
-}
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// Calls emit(b, v) with the float32 rounding of the b-th basis value of x.
-// Chebyshev: T_{k+1} = 2x T_k - T_{k-1} carried as a float-float pair (about
-// 44 significant bits, all on the float32 pipes).  Trig: one float64 sincos and
-// float64 angle addition.
-template <typename Emit>
-__device__ __forceinline__ void basis_values(int basis, int d, float x, Emit emit) {
-  if (basis == GAME_CHEBYSHEV) {
-    const float y = __fmul_rn(2.0f, x);          // exact
-    float mh = 1.0f, ml = 0.0f;                  // T_{k-1}
-    float th = x, tl = 0.0f;                     // T_k
-    for (int b = 0; b < d; ++b) {
-      emit(b, __fadd_rn(th, tl));
-      float p, pe, s, se;
-      two_prod(y, th, p, pe);
-      two_sum(p, -mh, s, se);
-      const float low = __fsub_rn(__fadd_rn(__fadd_rn(se, pe), __fmul_rn(y, tl)), ml);
-      const float nh = __fadd_rn(s, low);
-      const float nl = __fsub_rn(low, __fsub_rn(nh, s));
-      mh = th;
-      ml = tl;
-      th = nh;
-      tl = nl;
-    }
-  } else {
-    double s1, c1;
-    sincos((double)x, &s1, &c1);
-    double c = c1, s = s1;
-    for (int k = 0; k < d; ++k) {
-      emit(k, (float)c);
-      emit(d + k, (float)s);
-      const double cn = c * c1 - s * s1;
-      const double sn = s * c1 + c * s1;
-      c = cn;
-      s = sn;
-    }
-  }
-}
-
-// Calls emit(v) with the float32 basis values of x for b = b_lo .. b_hi - 1 in order
-// (0 <= b_lo < b_hi <= B*d): the same arithmetic as basis_values, stopped at b_hi.
-template <typename Emit>
-__device__ __forceinline__ void basis_range(int basis, int d, float x, int b_lo, int b_hi,
-                                            Emit emit) {
-  if (basis == GAME_CHEBYSHEV) {
-    const float y = __fmul_rn(2.0f, x);
-    float mh = 1.0f, ml = 0.0f, th = x, tl = 0.0f;
-    for (int b = 0; b < b_hi; ++b) {
-      if (b >= b_lo) emit(__fadd_rn(th, tl));
-      float p, pe, s2, se;
-      two_prod(y, th, p, pe);
-      two_sum(p, -mh, s2, se);
-      const float low = __fsub_rn(__fadd_rn(__fadd_rn(se, pe), __fmul_rn(y, tl)), ml);
-      const float nh = __fadd_rn(s2, low);
-      const float nl = __fsub_rn(low, __fsub_rn(nh, s2));
-      mh = th;
-      ml = tl;
-      th = nh;
-      tl = nl;
-    }
-  } else {
-    double s1, c1;
-    sincos((double)x, &s1, &c1);
-    // cos((k+1) x) for the columns below d, then sin((k+1) x) for those from d
-    for (int half = 0; half < 2; ++half) {
-      const int lo = half ? max(b_lo, d) - d : b_lo;
-      const int hi = half ? b_hi - d : min(b_hi, d);
-      double c = c1, sn = s1;
-      for (int k = 0; k < hi; ++k) {
-        if (k >= lo) emit((float)(half ? sn : c));
-        const double cn = c * c1 - sn * s1;
-        sn = sn * c1 + c * s1;
-        c = cn;
-      }
-    }
-  }
-}
 
 struct ExpArgs {
   const float* X;

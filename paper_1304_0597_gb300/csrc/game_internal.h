@@ -182,6 +182,18 @@ cudaError_t launch_fitness_simt(const Shape& s, const Fitness& f, const PopDev& 
                                 const ExpDev& e, double* partial, int n_part,
                                 const DevState* state, cudaStream_t st);
 
+// On-the-fly engine (fitness_otf.cu): P formed per tile from the features X, never
+// stored.  Same partial-sum layout as the SIMT engine, otf_partials rows.
+int otf_partials(const Shape& s, int n_sm);
+cudaError_t launch_fitness_otf(const Shape& s, const Fitness& f, const PopDev& p, const float* X,
+                               const ExpDev& e, double* partial, int n_part,
+                               const DevState* state, cudaStream_t st);
+cudaError_t launch_score_otf(const Shape& s, const Fitness& f, const float* X, const float* t,
+                             const float* genes, long long r0, long long r1, double* block_out,
+                             int n_blocks, double* result, cudaStream_t st);
+cudaError_t launch_expand_get_otf(const Shape& s, const float* X, long long row0, long long nrows,
+                                  float* out, cudaStream_t st);
+
 // Float64 score of one chromosome on rows [r0, r1).
 cudaError_t launch_score(const Shape& s, const Fitness& f, const ExpDev& e, const float* genes,
                          long long r0, long long r1, double* block_out, int n_blocks,

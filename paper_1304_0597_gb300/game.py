@@ -30,7 +30,7 @@ ELITE_TOP, ELITE_COPIES = 0, 1
 FP32, BF16, FP8 = 0, 1, 2
 COEF_PER_FEATURE, COEF_SHARED = 0, 1
 SEL_TOURNAMENT, SEL_ROULETTE, SEL_RANKING = 0, 1, 2
-ENGINE_AUTO, ENGINE_TCGEN05, ENGINE_SIMT = 0, 1, 2
+ENGINE_AUTO, ENGINE_TCGEN05, ENGINE_SIMT, ENGINE_ON_THE_FLY = 0, 1, 2, 3
 
 
 class GameConfig(C.Structure):

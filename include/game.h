@@ -322,6 +322,17 @@ game_status game_surrogate_monitor(game_ctx* ctx, double* rho_last, double* loss
                                    int32_t* fallback, double* history, int32_t cap,
                                    int32_t* n_history);
 
+/* The offspring pool of the last bred generation, for checks: its n_pool surrogate
+ * scores (host, n_pool floats), the pool rows selected into the population (host,
+ * pop - elitism int32: the pool indices whose scores are below the selection
+ * threshold, in index order, then those equal to it, in index order, up to pop -
+ * elitism), the pool's genes (host, n_pool x n_genes floats) and the score each row
+ * of the current population was selected with (host, pop floats; NaN for elites and
+ * rows bred without the network).  Any pointer may be NULL; *n_pool (may be NULL)
+ * receives the pool size.  Errors: STATE (no data, or no pool). */
+game_status game_surrogate_pool(game_ctx* ctx, float* scores, int32_t* selected, float* pool_genes,
+                                float* predictions, int32_t* n_pool);
+
 /* ---- batched form: many independent runs ----------------------------------- */
 
 /* A batch of independent GAME runs (no paper counterpart: the paper trains one

@@ -761,6 +761,19 @@ def adam_update(param: np.ndarray, grad: np.ndarray, m: np.ndarray, v: np.ndarra
     return param - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
+def surrogate_select(scores: np.ndarray, n_sel: int) -> np.ndarray:
+    """Pool rows kept by the learned-surrogate form (no paper counterpart): the n_sel
+    rows of lowest predicted fitness, ties at the cut going to lower pool indices
+    (NaN counts as +inf).  Listed as the kept rows strictly below the cut value in
+    pool order, then the kept rows equal to it in pool order."""
+    s = np.where(np.isnan(scores), np.inf, np.asarray(scores, dtype=np.float64))
+    idx = np.arange(len(s))
+    order = np.lexsort((idx, s))            # by value, then by index
+    kept = order[:n_sel]
+    cut = s[order[n_sel - 1]]
+    return np.concatenate([np.sort(kept[s[kept] < cut]), np.sort(kept[s[kept] == cut])])
+
+
 def spearman(a: np.ndarray, b: np.ndarray) -> float:
     """Spearman rank correlation (no ties expected): 1 - 6 sum d^2 / (n (n^2 - 1))."""
     n = len(a)

@@ -1573,6 +1573,33 @@ extern "C" game_status game_surrogate_monitor(game_ctx* c, double* rho_last, dou
   return GAME_OK;
 }
 
+extern "C" game_status game_surrogate_pool(game_ctx* c, float* scores, int32_t* selected,
+                                           float* pool_genes, float* predictions,
+                                           int32_t* n_pool) {
+  if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  if (c->cfg.surrogate_pool <= 0 || !c->d_pool)
+    return fail(c, GAME_ERR_STATE, "no offspring pool: surrogate_pool is 0");
+  cudaSetDevice(c->dev);
+  const int e = std::min(c->cfg.elitism, c->s.pop);
+  if (n_pool) *n_pool = c->n_pool;
+  if (scores)
+    CUDA_OK(c, cudaMemcpyAsync(scores, c->d_score, sizeof(float) * c->n_pool,
+                               cudaMemcpyDeviceToHost, c->st));
+  if (selected)
+    CUDA_OK(c, cudaMemcpyAsync(selected, c->d_sel, sizeof(int) * (c->s.pop - e),
+                               cudaMemcpyDeviceToHost, c->st));
+  if (pool_genes)
+    CUDA_OK(c, cudaMemcpy2DAsync(pool_genes, sizeof(float) * c->s.n_genes, c->d_pool,
+                                 sizeof(float) * c->s.kstride, sizeof(float) * c->s.n_genes,
+                                 c->n_pool, cudaMemcpyDeviceToHost, c->st));
+  if (predictions)
+    CUDA_OK(c, cudaMemcpyAsync(predictions, c->d_pred, sizeof(float) * c->s.pop,
+                               cudaMemcpyDeviceToHost, c->st));
+  CUDA_OK(c, cudaStreamSynchronize(c->st));
+  return GAME_OK;
+}
+
 extern "C" game_status game_selftest_timeout(game_ctx* c, int32_t wait_us, int32_t* waited_us) {
   if (!c) return fail(nullptr, GAME_ERR_INVALID_ARG, "ctx is NULL");
   if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");

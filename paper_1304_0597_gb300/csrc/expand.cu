@@ -193,21 +193,30 @@ __global__ void __launch_bounds__(256) expand_cheb_aligned_kernel(ExpArgs a) {
 
 // Shared coefficients (the paper's eq.2 / eq.9 form): column b of pattern k is the
 // sum over the features of the b-th basis value, the float32 values of the
-// per-feature expansion added in float64 and rounded once.
+// per-feature expansion added in float-float and rounded once.
 constexpr int kSharedRows = 64;   // patterns (threads) per block of the shared-form kernels
 
 // Column sums of one pattern in the shared form: acc[b * kSharedRows] (this
-// thread's slot of a column-major block array in shared memory) = the float64
-// sum over the features, in feature order, of the float32 b-th basis values.
-__device__ __forceinline__ void shared_row_sums(const ExpArgs& a, long long k, double* acc) {
-  for (int b = 0; b < a.kb; ++b) acc[b * kSharedRows] = 0.0;
+// thread's slot of a column-major block array in shared memory) = the sum over the
+// features, in feature order, of the float32 b-th basis values, kept as a float-float
+// pair (Knuth's TwoSum: about 48 bits, on the float32 pipes) and rounded once by the
+// caller.
+__device__ __forceinline__ void shared_row_sums(const ExpArgs& a, long long k, float2* acc) {
+  for (int b = 0; b < a.kb; ++b) acc[b * kSharedRows] = make_float2(0.0f, 0.0f);
   const float* x = a.X + k * a.F;
   for (int f = 0; f < a.F; ++f)
-    basis_values(a.basis, a.d, x[f], [&](int b, float v) { acc[b * kSharedRows] += (double)v; });
+    basis_values(a.basis, a.d, x[f], [&](int b, float v) {
+      float2 c = acc[b * kSharedRows];
+      float s, e;
+      two_sum(c.x, v, s, e);
+      acc[b * kSharedRows] = make_float2(s, __fadd_rn(c.y, e));
+    });
 }
 
+__device__ __forceinline__ float ff_round(float2 c) { return __fadd_rn(c.x, c.y); }
+
 __global__ void __launch_bounds__(kSharedRows) expand_shared_colmax_kernel(ExpArgs a) {
-  extern __shared__ double sacc[];   // [kb][kSharedRows]
+  extern __shared__ float2 sacc[];   // [kb][kSharedRows]
   __shared__ unsigned int cmax[64];  // kb <= 2 * 32
   for (int c = threadIdx.x; c < a.kb; c += blockDim.x) cmax[c] = 0u;
   __syncthreads();
@@ -215,11 +224,11 @@ __global__ void __launch_bounds__(kSharedRows) expand_shared_colmax_kernel(ExpAr
   for (long long k0 = (long long)blockIdx.x * kSharedRows; k0 < a.n;
        k0 += (long long)gridDim.x * kSharedRows) {
     const long long k = k0 + threadIdx.x;
-    double* acc = sacc + threadIdx.x;
+    float2* acc = sacc + threadIdx.x;
     if (k < a.n) shared_row_sums(a, k, acc);
     for (int b = 0; b < a.kb; ++b) {
       // non-negative floats order like their bit patterns
-      const unsigned int v = k < a.n ? __float_as_uint(fabsf((float)acc[b * kSharedRows])) : 0u;
+      const unsigned int v = k < a.n ? __float_as_uint(fabsf(ff_round(acc[b * kSharedRows]))) : 0u;
       const unsigned int m = __reduce_max_sync(0xffffffffu, v);
       if (lane == 0 && m) atomicMax(cmax + b, m);
     }
@@ -232,13 +241,13 @@ __global__ void __launch_bounds__(kSharedRows) expand_shared_colmax_kernel(ExpAr
 // One pattern per thread: the kb column sums, rounded once to float32, stored as
 // the run's planes 16 bytes at a time (kp is a multiple of 16, or of 32 for e4m3).
 __global__ void __launch_bounds__(kSharedRows) expand_shared_kernel(ExpArgs a) {
-  extern __shared__ double sacc[];   // [kb][kSharedRows]
+  extern __shared__ float2 sacc[];   // [kb][kSharedRows]
   const long long k = (long long)blockIdx.x * kSharedRows + threadIdx.x;
   if (k >= a.n) return;
-  const double* acc = sacc + threadIdx.x;
+  const float2* acc = sacc + threadIdx.x;
   shared_row_sums(a, k, sacc + threadIdx.x);
   const long long row = k * a.kp;
-  auto val = [&](int b) { return b < a.kb ? (float)acc[b * kSharedRows] : 0.0f; };
+  auto val = [&](int b) { return b < a.kb ? ff_round(acc[b * kSharedRows]) : 0.0f; };
   if (a.precision == GAME_FP32) {
     // the power-of-two column scale divides exactly
     auto vs = [&](int b) { return b < a.kb ? val(b) * (1.0f / a.colscale[b]) : 0.0f; };
@@ -366,7 +375,7 @@ cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax
   if (s.shared) {
     // one thread per pattern, F basis sequences each; column sums in shared memory
     if (s.kb > 64) return cudaErrorInvalidValue;   // B * d <= 2 * 32
-    const size_t smem = sizeof(double) * s.kb * kSharedRows;
+    const size_t smem = sizeof(float2) * s.kb * kSharedRows;
     const long long nblk = (s.n_patterns + kSharedRows - 1) / kSharedRows;
     if (s.precision != GAME_FP32) {   // FP32: the caller has set the power-of-two scales
       cudaError_t err = cudaMemsetAsync(qmax_scratch, 0, sizeof(float) * s.kp, st);

@@ -43,10 +43,10 @@ __device__ __forceinline__ float otf_error(float t, float s, int act, int err, f
 // columns).  Per-feature coefficients: one item per (row, feature touched by the
 // slab), each running its feature's recurrence up to the slab's last column.
 // Shared coefficients (the paper's eq.2 / eq.9 form, kb = B d): one thread per row
-// adds the features' values in feature order in float64 (dacc), then rounds once,
-// as the stored shared expansion does.
+// adds the features' values in feature order as float-float pairs (dacc), then rounds
+// once, as the stored shared expansion does.
 __device__ void otf_slab(const OtfArgs& a, long long m0, int k0, float (*Ps)[33],
-                         double (*dacc)[33]) {
+                         float2 (*dacc)[33]) {
   const int tid = threadIdx.x;
   const int c_end = min(k0 + 32, a.kb);
   if (!a.shared) {
@@ -75,15 +75,19 @@ __device__ void otf_slab(const OtfArgs& a, long long m0, int k0, float (*Ps)[33]
   } else if (tid < 64) {
     const int r = tid;
     const long long row = m0 + r;
-    for (int j = 0; j < 32; ++j) dacc[r][j] = 0.0;
+    for (int j = 0; j < 32; ++j) dacc[r][j] = make_float2(0.0f, 0.0f);
     if (row < a.m && k0 < c_end) {
       for (int f = 0; f < a.F; ++f) {
         int col = 0;
-        basis_range(a.basis, a.d, __ldg(a.X + row * a.F + f), k0, c_end,
-                    [&](float v) { dacc[r][col++] += (double)v; });
+        basis_range(a.basis, a.d, __ldg(a.X + row * a.F + f), k0, c_end, [&](float v) {
+          float s, e;
+          two_sum(dacc[r][col].x, v, s, e);
+          dacc[r][col] = make_float2(s, __fadd_rn(dacc[r][col].y, e));
+          ++col;
+        });
       }
     }
-    for (int j = 0; j < 32; ++j) Ps[r][j] = (float)dacc[r][j];   // zero past kb
+    for (int j = 0; j < 32; ++j) Ps[r][j] = __fadd_rn(dacc[r][j].x, dacc[r][j].y);   // zero past kb
   }
 }
 
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(256) fitness_otf_kernel(OtfArgs a) {
   __shared__ float Gs[64][33];
   __shared__ float red[16][65];
   __shared__ double acc64[64];
-  __shared__ double dacc[64][33];
+  __shared__ float2 dacc[64][33];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int c0 = blockIdx.y * 64;
   if (tid < 64) acc64[tid] = 0.0;
@@ -201,7 +205,7 @@ __global__ void score_otf_final_kernel(const double* block_out, int n_blocks, do
 }
 
 // Rows [row0, row0 + nrows) of P (basis columns) as float32, formed from X: one
-// thread per (row, feature) (per-feature coefficients) or per row (shared; float64
+// thread per (row, feature) (per-feature coefficients) or per row (shared; float-float
 // sums over the features, rounded once).
 __global__ void expand_get_otf_kernel(const float* __restrict__ X, int F, int d, int basis, int bd,
                                       int shared, int kb, long long row0, long long nrows,
@@ -216,14 +220,16 @@ __global__ void expand_get_otf_kernel(const float* __restrict__ X, int F, int d,
   } else {
     if (i >= nrows) return;
     for (int b = 0; b < kb; ++b) {
-      double s = 0.0;
+      float hi = 0.0f, lo = 0.0f;
       for (int f = 0; f < F; ++f) {
-        int col = 0;
         float v = 0.0f;
-        basis_range(basis, d, __ldg(X + (row0 + i) * F + f), b, b + 1, [&](float u) { v = u; ++col; });
-        s += (double)v;
+        basis_range(basis, d, __ldg(X + (row0 + i) * F + f), b, b + 1, [&](float u) { v = u; });
+        float s, e;
+        two_sum(hi, v, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, e);
       }
-      out[i * kb + b] = (float)s;
+      out[i * kb + b] = __fadd_rn(hi, lo);
     }
   }
 }

@@ -108,6 +108,7 @@ def _load() -> C.CDLL:
         "game_surrogate_train_step": (I32, [P, P, P, I32, F]),
         "game_surrogate_monitor": (I32, [P, C.POINTER(D), C.POINTER(D), C.POINTER(I32), P, I32,
                                          C.POINTER(I32)]),
+        "game_surrogate_pool": (I32, [P, P, P, P, P, C.POINTER(I32)]),
         "game_batch_create": (I32, [C.POINTER(GameConfig), I32, C.POINTER(P)]),
         "game_batch_set_data": (I32, [P, I32, P, P, I64, I32, I64, I32]),
         "game_batch_run": (P, [P, I32]),
@@ -343,6 +344,20 @@ class Game:
                                                hist.ctypes.data, cap, C.byref(n)), self.h)
         return {"rho": rho.value, "loss": loss.value, "fallback": fb.value,
                 "history": hist[:n.value].copy()}
+
+    def surrogate_pool(self) -> dict:
+        """The last bred generation's offspring pool: scores, selected rows, genes, and the
+        score each current row was selected with."""
+        n = C.c_int32()
+        self._check(lib.game_surrogate_pool(self.h, None, None, None, None, C.byref(n)), self.h)
+        e = min(self.cfg.elitism, self.pop)
+        scores = np.empty(n.value, dtype=np.float32)
+        sel = np.empty(self.pop - e, dtype=np.int32)
+        genes = np.empty((n.value, self.n_genes), dtype=np.float32)
+        pred = np.empty(self.pop, dtype=np.float32)
+        self._check(lib.game_surrogate_pool(self.h, scores.ctypes.data, sel.ctypes.data,
+                                            genes.ctypes.data, pred.ctypes.data, None), self.h)
+        return {"scores": scores, "selected": sel, "genes": genes, "predictions": pred}
 
     def set_timing(self, enabled: bool) -> None:
         self._check(lib.game_set_timing(self.h, int(bool(enabled))), self.h)

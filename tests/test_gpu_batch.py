@@ -72,12 +72,22 @@ def test_batch_fitness_against_oracle_and_autotune():
     assert g in (1, 2, 4, 8, 16) and ms > 0
     b.evolve(1)      # generation 0 of every run goes through the grouped launch
     for i, (ds, ocfg, cfg) in enumerate(specs):
-        if cfg.precision != game.FP32:
-            continue
         run = b.runs[i]
         G = run.population()
         fit, _ = run.fitness()    # computed by the grouped launch
-        P = o.expand(ds.X[:ds.n_train], ocfg.basis, ocfg.degree)
-        np.testing.assert_allclose(fit, o.fitness(P, ds.t[:ds.n_train], G, ocfg), rtol=1e-5)
+        if cfg.precision == game.FP32:
+            P = o.expand(ds.X[:ds.n_train], ocfg.basis, ocfg.degree)
+            want = o.fitness(P, ds.t[:ds.n_train], G, ocfg)
+        else:
+            # BF16 / FP8 runs: the oracle on the same quantised operands (column scales over
+            # every stored row, genes in the run's planes), oracle.quantize_columns and
+            # oracle.quantize_genes
+            fmt = "bf16" if cfg.precision == game.BF16 else "fp8"
+            Q, s = o.quantize_columns(o.expand(ds.X, ocfg.basis, ocfg.degree)[:, 1:], fmt)
+            Pq = np.concatenate([np.ones((ds.n_train, 1)),
+                                 o.dequantize_columns(Q[:ds.n_train], s)], axis=1)
+            want = o.fitness(Pq, ds.t[:ds.n_train], o.quantize_genes(G, s, fmt, cfg.gene_planes),
+                             ocfg)
+        np.testing.assert_allclose(fit, want, rtol=1e-5)
         _, fbest, _, _ = run.best()
         assert fbest == pytest.approx(fit.min(), rel=1e-12)

@@ -176,3 +176,30 @@ def test_surrogate_driven_evolution():
     assert len(rho) == 20 and np.isnan(rho[0])
     assert np.nanmean(rho[5:]) > 0.2
     assert hist_s[-1] <= hist_a[-1]
+
+
+@pytest.mark.parametrize("pop,pool", [(256, 8), (1000, 4)])
+def test_surrogate_selection_assembly_and_monitor_match_oracle(pop, pool):
+    """The last bred generation, checked row by row against the oracle: the kept pool
+    rows are oracle.surrogate_select of the pool's scores; the population after the
+    elites is those pool rows (genes bit for bit) with the scores they were kept with;
+    the monitor's correlation is oracle.spearman of those scores and the exact fitness
+    (both ranked in float32, ties to the lower row, as the kernel ranks them)."""
+    ds = synth.make_dataset(5000, 10, 4, seed=54)
+    ocfg = o.Config(degree=4, pop=pop, seed=9)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, surrogate_pool=pool, surrogate_batch=512,
+                  surrogate_steps=8)
+    assert g.evolve(6) == 6
+    e = ocfg.elitism
+    p = g.surrogate_pool()
+    sel = o.surrogate_select(p["scores"], pop - e)
+    np.testing.assert_array_equal(p["selected"], sel)
+    G = g.population()
+    np.testing.assert_array_equal(G[e:], p["genes"][sel])
+    pred = p["predictions"]
+    assert np.all(np.isnan(pred[:e]))
+    np.testing.assert_array_equal(pred[e:], p["scores"][sel])
+    fit, _ = g.fitness()
+    rho = g.surrogate_monitor()["rho"]
+    want = o.spearman(pred[e:].astype(np.float32), fit[e:].astype(np.float32))
+    assert rho == pytest.approx(want, abs=1e-12)

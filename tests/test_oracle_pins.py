@@ -717,6 +717,29 @@ def test_adam_first_step_moves_each_parameter_by_lr():
     np.testing.assert_allclose(p, -0.05 * np.sign(g), rtol=1e-10)
 
 
+def test_surrogate_select_against_brute_force():
+    """The kept set is the n_sel smallest (score, index) pairs, found here by trying every
+    row against every other; ties at the cut go to lower indices; the order is the rows
+    below the cut, then those at it, each in pool order."""
+    rng = np.random.default_rng(21)
+    for trial in range(200):
+        n = int(rng.integers(1, 40))
+        k = int(rng.integers(1, n + 1))
+        s = rng.integers(0, 6, size=n).astype(np.float32) * 0.5      # many ties
+        if trial % 7 == 0:
+            s[rng.integers(0, n)] = np.nan
+        got = o.surrogate_select(s, k)
+        key = [(np.inf if np.isnan(v) else float(v), i) for i, v in enumerate(s)]
+        below = [i for i in range(n) if sum(key[j] < key[i] for j in range(n)) < k]
+        assert sorted(got.tolist()) == sorted(below)
+        cut = max(key[i][0] for i in below)
+        assert got.tolist() == sorted(i for i in below if key[i][0] < cut) + \
+            sorted(i for i in below if key[i][0] == cut)
+    assert o.surrogate_select(np.zeros(5, np.float32), 3).tolist() == [0, 1, 2]
+    assert o.surrogate_select(np.array([3, 1, 2, 1], np.float32), 2).tolist() == [1, 3]
+    assert o.surrogate_select(np.array([0.5, 0.1, 0.5, 0.2], np.float32), 3).tolist() == [1, 3, 0]
+
+
 def test_spearman_known_values():
     a = np.arange(10.0)
     assert o.spearman(a, a) == pytest.approx(1.0)

@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--e2e-runs", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default tile (no trial launches before the steps)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the BF16 / FP8 precision-form record of the default line")
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32")
     ap.add_argument("--gene-planes", type=int, choices=[1, 2], default=2,
                     help="low precision: genes as one or two terms of P's format")
@@ -313,6 +317,36 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ our arm
 
+def forms_record(ds, X_pin, t_pin, stream, steps, warmup, bf16_peak):
+    """The precision form on the same workload, measured after the headline (outside its
+    timed region): P in BF16 and in FP8-E4M3 with one gene plane and the top-16 elites
+    re-scored in FP32 each generation.  Per-stage device times over `steps` generations
+    (CUDA events) and the fitness contraction's fraction of its dense peak (FP8: the
+    measured bf16 peak x 2, the nominal ratio)."""
+    from paper_1304_0597_gb300 import game
+    out = {}
+    flops = 2.0 * ds.n_train * 257 * 1024
+    for name, prec, ratio in (("bf16", game.BF16, 1.0), ("fp8", game.FP8, 2.0)):
+        cfg = game.default_config(degree=8, pop=1024, seed=0, stream=stream.cuda_stream,
+                                  precision=prec, gene_planes=1, elite_rescore=16)
+        with game.Game(cfg) as g:
+            g.set_data(X_pin, t_pin, ds.n_train)
+            tile, _ = g.autotune(reps=3)
+            g.evolve(warmup)
+            g.set_timing(True)
+            ran = g.evolve(steps)
+            tm = g.timing()
+        fit_ms = tm["ms_fitness"] / steps
+        out[name] = {"gene_planes": 1, "elite_rescore": 16, "tile": tile, "generations": ran,
+                     "ms_per_generation": tm["ms_total"] / steps,
+                     "stage_ms": {"breed_prepare": tm["ms_breed"] / steps, "fitness": fit_ms,
+                                  "reduce_rank_rescore": tm["ms_rank"] / steps},
+                     "evals_per_s": 1024 * ds.n_train / (tm["ms_total"] / steps / 1e3),
+                     "fitness_tflops": flops / (fit_ms / 1e3) / 1e12,
+                     "fitness_frac_of_peak": flops / (fit_ms / 1e3) / 1e12 / (bf16_peak * ratio)}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -336,7 +370,7 @@ def run_ours(args):
     g = game.Game(cfg)
     g.set_data(X_pin, t_pin, ds.n_train)
     tile = None
-    if g.timing()["engine"] == game.ENGINE_TCGEN05:
+    if g.timing()["engine"] == game.ENGINE_TCGEN05 and not args.no_autotune:
         tile, tile_cands = g.autotune(reps=3)     # library autotuner, outside the timed region
     K, W = args.steps, args.warmup
     g.evolve(W)
@@ -434,6 +468,8 @@ def run_ours(args):
         "clocks": clk.summary(),
         "best": {"train_rmse": fit_best, "test_rmse": test_rmse, "test_accuracy": test_acc},
     }
+    if rank == 0 and world == 1 and args.precision == "fp32" and not args.no_forms:
+        line["forms"] = forms_record(ds, X_pin, t_pin, stream, K, W, bf16_tf)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_record(args.cpu_seconds)
     g.close()

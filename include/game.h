@@ -50,7 +50,9 @@ typedef enum {
   GAME_ERR_NO_DEVICE = -5,    /* no usable sm_103a device                           */
   GAME_ERR_TIMEOUT = -6,      /* a bounded device-side wait gave up                 */
   GAME_ERR_NUMERIC = -7,      /* NaN / Inf in the input data                        */
-  GAME_ERR_UNSUPPORTED = -8   /* valid request outside this build's limits          */
+  GAME_ERR_UNSUPPORTED = -8,  /* valid request outside this build's limits          */
+  GAME_ERR_CHECK = -9         /* debug build (-DGAME_CHECKS): a device bounds check
+                                 failed; the access was skipped (no trap)           */
 } game_status;
 
 enum { GAME_CHEBYSHEV = 0, GAME_TRIG = 1 };                       /* basis g(x)     */

@@ -19,6 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libgame.so")
 LIB_TIMELINE = os.path.join(OUT_DIR, "libgame_timeline.so")
+LIB_CHECKS = os.path.join(OUT_DIR, "libgame_checks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
            "--expt-relaxed-constexpr", "-Xptxas", "-O3"]
@@ -43,13 +44,16 @@ def _compile(src: str, obj: str, extra: list[str]) -> str:
     return r.stderr
 
 
-def build(verbose: bool = False, extra: list[str] | None = None, timeline: bool = False) -> str:
+def build(verbose: bool = False, extra: list[str] | None = None, timeline: bool = False,
+          checks: bool = False) -> str:
     """Compile every csrc/*.cu and link libgame.so (or, with timeline, the profiling
-    variant libgame_timeline.so); returns the library path."""
+    variant libgame_timeline.so; with checks, the bounds-checked debug variant
+    libgame_checks.so built with -DGAME_CHECKS); returns the library path."""
     os.makedirs(OUT_DIR, exist_ok=True)
-    extra = list(extra or []) + (["-DGAME_TC_TIMELINE"] if timeline else [])
-    lib = LIB_TIMELINE if timeline else LIB
-    objdir = os.path.join(OUT_DIR, "obj_timeline" if timeline else "obj")
+    extra = list(extra or []) + (["-DGAME_TC_TIMELINE"] if timeline else []) + \
+        (["-DGAME_CHECKS"] if checks else [])
+    lib = LIB_TIMELINE if timeline else LIB_CHECKS if checks else LIB
+    objdir = os.path.join(OUT_DIR, "obj_timeline" if timeline else "obj_checks" if checks else "obj")
     os.makedirs(objdir, exist_ok=True)
     srcs = sources()
     objs = [os.path.join(objdir, os.path.basename(s)[:-3] + ".o") for s in srcs]

@@ -136,6 +136,22 @@ static game_status fail(game_ctx* c, game_status code, const char* fmt, ...) {
                   "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);     \
   } while (0)
 
+// Debug build (-DGAME_CHECKS): a device bounds check that failed since the last read
+// turns into GAME_ERR_CHECK, naming the file, the site and the offending index.
+static game_status collect_checks(game_ctx* c) {
+#ifdef GAME_CHECKS
+  const unsigned long long w[3] = {check_word_expand(), check_word_ga(), check_word_tc()};
+  static const char* const file[3] = {"expand.cu", "ga.cu", "fitness_tc.cu"};
+  for (int i = 0; i < 3; ++i)
+    if (w[i])
+      return fail(c, GAME_ERR_CHECK, "bounds check failed in %s: site %d, index %llu", file[i],
+                  (int)(w[i] >> 48), (unsigned long long)(w[i] & 0xFFFFFFFFFFFFull));
+#else
+  (void)c;
+#endif
+  return GAME_OK;
+}
+
 // Blocks from position alloc_next on are released (the sequence changed or ended).
 static void release_tail(game_ctx* c) {
   for (size_t i = c->alloc_next; i < c->allocs.size(); ++i) cudaFree(c->allocs[i].p);
@@ -708,6 +724,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   const size_t g32b = sizeof(float) * (size_t)s.pop_pad * s.kstride;
   for (int i = 0; i < 2; ++i)
     if ((r = dalloc(c, &c->p.g32[i], g32b)) != GAME_OK) return r;
+  c->p.pop_rows = s.pop;
   if ((r = dalloc(c, &c->p.geval, sizeof(float) * (size_t)s.pop_pad * s.kp)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->p.bias, sizeof(float) * s.pop_pad)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->p.rscale, sizeof(float) * s.pop_pad)) != GAME_OK) return r;
@@ -742,6 +759,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
     c->pr = PopDev{};
     c->pr.g32[0] = c->p.g32[0];
     c->pr.g32[1] = c->p.g32[1];
+    c->pr.pop_rows = s.pop;
     if ((r = dalloc(c, &c->pr.geval, sizeof(float) * 128 * (size_t)c->sr.kp)) != GAME_OK) return r;
     if ((r = dalloc(c, &c->pr.bias, sizeof(float) * 128)) != GAME_OK) return r;
     if ((r = dalloc(c, &c->pr.rscale, sizeof(float) * 128)) != GAME_OK) return r;
@@ -770,6 +788,7 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
   // The blocks of a longer earlier sequence are not needed.  X stays allocated (it
   // is no longer read once P exists) for the next data set of the same shape.
   release_tail(c);
+  if ((r = collect_checks(c)) != GAME_OK) return r;
   c->have_data = true;
   return GAME_OK;
 }
@@ -1046,6 +1065,7 @@ extern "C" game_status game_evolve(game_ctx* c, int32_t max_generations, int32_t
   c->timing.engine = c->engine;
   c->timing.launches = 1 + c->gen_kernels * max_generations;
   if (hs.status != 0) return fail(c, GAME_ERR_TIMEOUT, "device-side wait timed out (status %d)", hs.status);
+  if ((r = collect_checks(c)) != GAME_OK) return r;
   if (generations_run) *generations_run = hs.gens_run;
   return GAME_OK;
 }
@@ -1070,7 +1090,7 @@ extern "C" game_status game_evaluate(game_ctx* c, double* fitness, int32_t* rank
   if (rank)
     CUDA_OK(c, cudaMemcpyAsync(rank, c->d_rank, sizeof(int) * c->s.pop, cudaMemcpyDeviceToHost, c->st));
   CUDA_OK(c, cudaStreamSynchronize(c->st));
-  return GAME_OK;
+  return collect_checks(c);
 }
 
 extern "C" game_status game_get_fitness(game_ctx* c, double* fitness, int32_t* rank) {

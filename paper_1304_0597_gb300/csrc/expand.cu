@@ -18,6 +18,7 @@
 //   BF16: bf16(v / s_g), s_g = max_k |P[k,g]|          (per-column scale)
 //   FP8 : e4m3(v / s_g), s_g = max_k |P[k,g]| / 448
 #include "basis.cuh"
+#include "checks.cuh"
 #include "game_internal.h"
 
 #include <algorithm>
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(256) expand_chunk_kernel(ExpArgs a) {
   if (i >= a.n * n_chunks) return;
   const long long row = i / n_chunks;
   const int col0 = (int)(i % n_chunks) * kEpc;
+  if (!GAME_IN_BOUNDS_DBG(row < a.n && col0 + kEpc <= a.kp, kSiteExpandCol, i)) return;
   uint32_t w0[4] = {0u, 0u, 0u, 0u}, w1[4] = {0u, 0u, 0u, 0u};   // plane 0 / plane 1 words
   // shift the 128-bit chunk right by one element and put e (its low kBits) on top
   auto push = [&](uint32_t* w, uint32_t e) {
@@ -131,6 +133,7 @@ __global__ void __launch_bounds__(256) expand_cheb_aligned_kernel(ExpArgs a) {
   if (i >= a.n * n_chunks) return;
   const long long row = i / n_chunks;
   const int col0 = (int)(i % n_chunks) * kEpc;
+  if (!GAME_IN_BOUNDS_DBG(row < a.n && col0 + kEpc <= a.kp, kSiteExpandCol, i)) return;
   float v[kEpc];
   if (col0 < a.kb) {
     const int f = col0 / a.bd;
@@ -507,4 +510,8 @@ cudaError_t launch_predict(const float* X, long long n, int F, const float* gene
   return cudaGetLastError();
 }
 
+}  // namespace game
+
+namespace game {
+GAME_DEFINE_CHECK_READER(check_word_expand)
 }  // namespace game

@@ -30,6 +30,7 @@
 // MMAs of tile i+1.  Every mbarrier wait is bounded (2 s of %globaltimer); on
 // a timeout the CTA records GAME_ERR_TIMEOUT in the device state, drains its
 // outstanding copies and MMAs (again bounded), frees TMEM and exits.
+#include "checks.cuh"
 #include "fitness_tc.h"
 #include "tc_ptx.cuh"
 
@@ -402,7 +403,9 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     double tot = 0.0;
 #pragma unroll
     for (int g = 0; g < kColGroups; ++g) tot += red[(sp * kColGroups + g) * 128 + r];
-    p.partial[(long long)member * p.pop_pad + (slice0 + sp) * 128 + r] = tot;
+    const long long o = (long long)member * p.pop_pad + (slice0 + sp) * 128 + r;
+    if (GAME_IN_BOUNDS_DBG(member < p.cps && (slice0 + sp) * 128 + r < p.pop_pad, kSiteTcPartial, o))
+      p.partial[o] = tot;
   }
 }
 
@@ -716,5 +719,7 @@ extern "C" int game_tc_timeline_clear() {
   return (int)cudaMemcpyToSymbol(g_tc_timeline, zeros, sizeof(zeros));
 }
 #endif
+
+GAME_DEFINE_CHECK_READER(check_word_tc)
 
 }  // namespace game

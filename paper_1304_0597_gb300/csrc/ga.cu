@@ -8,6 +8,7 @@
 // generation criteria); Section 5 gives crossover, mutation, tournament and
 // elitism settings.  The paper keeps selection and the operators on the host;
 // here they run on the device so that a generation never leaves the GPU.
+#include "checks.cuh"
 #include "game_internal.h"
 #include "rng.cuh"
 
@@ -124,6 +125,7 @@ __global__ void breed_kernel(BreedArgs a) {
   } else if (warp < n_pairs + e) {
     const int slot = warp - n_pairs;
     const int src = (a.elite_mode == GAME_ELITE_TOP) ? a.rank[slot] : a.rank[0];
+    if (!GAME_IN_BOUNDS_DBG(src >= 0 && src < a.pop, kSiteBreedParent, src)) return;
     const float* __restrict__ r = G + (long long)src * a.kstride;
     float* o = out + (long long)slot * a.kstride;
     for (int g = lane; g < K; g += 32) o[g] = r[g];
@@ -258,6 +260,7 @@ struct PrepArgs {
   float* rscale;
   const DevState* state;
   int pop, pop_pad, kb, kp, kstride, precision, use_bred_flag, in_evolve;
+  int src_pop;            // rows of the source population (bounds of rows[])
 };
 
 __global__ void prepare_kernel(PrepArgs a) {
@@ -270,6 +273,7 @@ __global__ void prepare_kernel(PrepArgs a) {
   if (a.use_bred_flag && st->bred) buf ^= 1;
   const bool live = row < a.pop;
   const int src = (live && a.rows) ? a.rows[row] : row;
+  if (!GAME_IN_BOUNDS_DBG(!live || (src >= 0 && src < a.src_pop), kSitePrepareSrc, src)) return;
   const float* G = (buf ? a.g32_1 : a.g32_0) + (long long)src * a.kstride;
   float* ge = a.geval + (long long)row * a.kp;
   if (lane == 0) a.bias[row] = live ? G[0] : 0.0f;
@@ -346,6 +350,7 @@ cudaError_t launch_prepare(const Shape& s, const PopDev& p, const ExpDev& e, Dev
   a.precision = s.precision;
   a.use_bred_flag = use_bred_flag & 1;
   a.in_evolve = (use_bred_flag >> 1) & 1;
+  a.src_pop = (src && src->pop_rows) ? src->pop_rows : s.pop;
   const int threads = 256;
   const int blocks = (s.pop_pad * 32 + threads - 1) / threads;
   prepare_kernel<<<blocks, threads, 0, st>>>(a);
@@ -498,7 +503,8 @@ __global__ void __launch_bounds__(256) rank_count_kernel(RankArgs a) {
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
-  if (c < a.pop && lane == 0) a.rank[pos] = c;
+  if (c < a.pop && lane == 0 && GAME_IN_BOUNDS_DBG(pos >= 0 && pos < a.pop, kSiteRankIndex, pos))
+    a.rank[pos] = c;
 }
 
 // The state transition of a ranking (one thread), as in reduce_rank_kernel.
@@ -632,4 +638,8 @@ cudaError_t launch_state_op(DevState* state, int op, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+}  // namespace game
+
+namespace game {
+GAME_DEFINE_CHECK_READER(check_word_ga)
 }  // namespace game

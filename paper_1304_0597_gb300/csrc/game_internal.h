@@ -69,6 +69,7 @@ struct PopDev {
   void* glo;              // [pop_pad x kp] MMA operand plane (lo part)
   float* rscale;          // [pop_pad] per-chromosome scale of the planes (FP32: a power of
                           // two, 1 unless a gene times its column scale passes 2^15)
+  int pop_rows = 0;       // chromosomes in g32 (0: the shape's pop)
 };
 
 // Expansion matrix P (basis columns only; the bias column of ones is implicit).
@@ -136,6 +137,12 @@ cudaError_t launch_reduce_rank(const Shape& s, const game_config& cfg, const dou
                                int mode, cudaStream_t st);
 cudaError_t launch_state_op(DevState* state, int op, cudaStream_t st);
 cudaError_t ga_init_attributes();   // once per device, outside stream capture
+
+// Bounds-check words of the debug build (-DGAME_CHECKS): site << 48 | index of the
+// first failed check since the last read, per translation unit (0 in other builds).
+unsigned long long check_word_expand();
+unsigned long long check_word_ga();
+unsigned long long check_word_tc();
 
 // State ops.
 enum : int {

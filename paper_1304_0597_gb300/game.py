@@ -20,7 +20,7 @@ LIB_PATH = os.environ.get("GAME_LIB_PATH") or os.path.join(_HERE, "_lib", "libga
 
 GAME_OK = 0
 STATUS = {0: "OK", -1: "INVALID_ARG", -2: "STATE", -3: "OOM", -4: "CUDA", -5: "NO_DEVICE",
-          -6: "TIMEOUT", -7: "NUMERIC", -8: "UNSUPPORTED"}
+          -6: "TIMEOUT", -7: "NUMERIC", -8: "UNSUPPORTED", -9: "CHECK"}
 
 CHEBYSHEV, TRIG = 0, 1
 RMSE, MSE, TMSE, TMSE_SQ = 0, 1, 2, 3

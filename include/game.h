@@ -121,8 +121,14 @@ typedef struct game_config {
   int32_t tile_cluster;   /* tcgen05 tile: 1 = each CTA alone; 2 = CTA pairs sharing every MMA
                              (tcgen05 cta_group::2, M = 256 chromosomes: each CTA stages half of
                              each pattern tile; needs an even number of 128-chromosome slices);
-                             0 = tuned / 1.  Other values are INVALID_ARG.  No TMA multicast. */
+                             0 = tuned, else pairs for the FP32 form where they fit with two
+                             k-blocks per stage, else 1.  Other values are INVALID_ARG.  No
+                             TMA multicast.  A request that cannot be planned for the
+                             problem runs the default shape (game_get_tile says which). */
   int32_t tile_slices;    /* tcgen05 tile: 128-chromosome slices per CTA, 1 | 2 (2 needs tile_n 128; 0 = auto) */
+  int32_t tile_kgroup;    /* tcgen05 tile: 128-byte k-blocks per pattern-tile stage, 1 | 2 (2 fetches
+                             two k-blocks per TMA request; needs the stored genes to be whole
+                             k-blocks, 64 for FP32 / BF16, 128 for FP8; 0 = auto) */
   int32_t device;         /* CUDA device ordinal                                            */
   void* stream;           /* cudaStream_t, or NULL for the legacy default stream           */
 } game_config;
@@ -271,6 +277,7 @@ typedef struct game_tile {
   int32_t cluster;    /* 1: one CTA per work unit; 2: CTA pairs (cta_group::2) */
   int32_t prefetch;   /* 1: L2 prefetch of each CTA's next pattern tile       */
   int32_t slices;     /* 128-chromosome slices per CTA fed by each pattern tile */
+  int32_t kgroup;     /* 128-byte k-blocks of the pattern tile per ring stage (one TMA request) */
   double ms;          /* median fitness time of this shape, milliseconds      */
 } game_tile;
 
@@ -286,6 +293,14 @@ typedef struct game_tile {
  * runs on the SIMT engine). */
 game_status game_autotune(game_ctx* ctx, int32_t reps, game_tile* best, game_tile* candidates,
                           int32_t cap, int32_t* n_candidates);
+
+/* The tcgen05 tile shape this context's fitness launches use (ms = 0).  A tile
+ * request in the config that cannot be planned for the problem (too little
+ * shared memory for the genes, pairs on an odd number of slices, grouped
+ * k-blocks on genes that are not whole k-blocks) runs the default shape; this
+ * call says which one runs.  Errors: STATE (no data), UNSUPPORTED (the shape
+ * runs on a CUDA-core engine). */
+game_status game_get_tile(game_ctx* ctx, game_tile* out);
 
 /* enabled = 1: game_evolve records CUDA events around every stage of every
  * generation (on the context's stream) and game_get_timing reports their sums

@@ -273,7 +273,7 @@ static game_status validate(game_ctx* c, const game_config* cfg) {
     return fail(c, GAME_ERR_INVALID_ARG, "immigrants must be in 0..pop - elitism");
   if ((cfg->tile_n != 0 && cfg->tile_n != 128 && cfg->tile_n != 256) || cfg->tile_stages < 0 ||
       cfg->tile_cluster < 0 || cfg->tile_cluster > 2 || cfg->tile_slices < 0 || cfg->tile_slices > 2 ||
-      (cfg->tile_slices == 2 && cfg->tile_n == 256))
+      (cfg->tile_slices == 2 && cfg->tile_n == 256) || cfg->tile_kgroup < 0 || cfg->tile_kgroup > 2)
     return fail(c, GAME_ERR_INVALID_ARG, "bad tile request");
   if (cfg->surrogate_pool < 0) return fail(c, GAME_ERR_INVALID_ARG, "bad surrogate_pool");
   if (cfg->surrogate_steps < 0 || cfg->surrogate_batch < 0 || cfg->surrogate_batch > 65536 ||
@@ -377,15 +377,15 @@ static int ntrain_bucket(long long n) { return (int)floor(log2((double)(n > 0 ? 
 static bool tune_cache_lookup(const Shape& s, TileReq* out) {
   FILE* f = fopen(tune_cache_path().c_str(), "r");
   if (!f) return false;
-  int kp, pp, pr, nb, n, st, cl, pf, sp;
+  int kp, pp, pr, nb, n, st, cl, pf, sp, kg;
   double ms;
   bool found = false;
   char line[256];
   while (fgets(line, sizeof(line), f))
-    if (sscanf(line, "%d %d %d %d %d %d %d %d %d %lf", &kp, &pp, &pr, &nb, &n, &st, &cl, &pf, &sp,
-               &ms) == 10 &&
+    if (sscanf(line, "%d %d %d %d %d %d %d %d %d %d %lf", &kp, &pp, &pr, &nb, &n, &st, &cl, &pf,
+               &sp, &kg, &ms) == 11 &&
         kp == s.kp && pp == s.pop_pad && pr == s.precision && nb == ntrain_bucket(s.n_train)) {
-      *out = TileReq{n, st, cl, pf, sp};   // the last record for a bucket wins
+      *out = TileReq{n, st, cl, pf, sp, kg};   // the last record for a bucket wins
       found = true;
     }
   fclose(f);
@@ -398,8 +398,8 @@ static void tune_cache_store(const Shape& s, const game_tile& t) {
   if (slash != std::string::npos && slash > 0) mkdir(path.substr(0, slash).c_str(), 0755);
   FILE* f = fopen(path.c_str(), "a");
   if (!f) return;
-  fprintf(f, "%d %d %d %d %d %d %d %d %d %.6f\n", s.kp, s.pop_pad, s.precision,
-          ntrain_bucket(s.n_train), t.n, t.stages, t.cluster, t.prefetch, t.slices, t.ms);
+  fprintf(f, "%d %d %d %d %d %d %d %d %d %d %.6f\n", s.kp, s.pop_pad, s.precision,
+          ntrain_bucket(s.n_train), t.n, t.stages, t.cluster, t.prefetch, t.slices, t.kgroup, t.ms);
   fclose(f);
 }
 
@@ -426,8 +426,9 @@ static game_status choose_engine(game_ctx* c, Shape& s, const ExpDev& e, const P
   if (want == GAME_ENGINE_TCGEN05) {
     if (!tc_ok)
       return fail(c, GAME_ERR_UNSUPPORTED, "tcgen05 engine does not support this shape");
-    TileReq req{c->cfg.tile_n, c->cfg.tile_stages, c->cfg.tile_cluster, -1, c->cfg.tile_slices};
-    if (!req.n && !req.stages && !req.cluster && !req.sp) tune_cache_lookup(s, &req);
+    TileReq req{c->cfg.tile_n,      c->cfg.tile_stages, c->cfg.tile_cluster, -1,
+                c->cfg.tile_slices, c->cfg.tile_kgroup};
+    if (!req.n && !req.stages && !req.cluster && !req.sp && !req.kg) tune_cache_lookup(s, &req);
     cudaError_t err = tc_plan(s, e, p, c->n_sm, plan, req);
     if (err != cudaSuccess) {
       cudaGetLastError();
@@ -1410,7 +1411,7 @@ static game_status tune_shape(game_ctx* c, const Shape& s, const ExpDev& e, cons
   cudaEvent_t e0, e1;
   CUDA_OK(c, cudaEventCreate(&e0));
   CUDA_OK(c, cudaEventCreate(&e1));
-  *bt = game_tile{0, 0, 0, 0, 0, 1e30};
+  *bt = game_tile{0, 0, 0, 0, 0, 0, 1e30};
   for (const TileReq& rq : cands) {
     TcPlan plan{};
     if (tc_plan(s, e, pd, c->n_sm, &plan, rq) != cudaSuccess) {
@@ -1433,7 +1434,7 @@ static game_status tune_shape(game_ctx* c, const Shape& s, const ExpDev& e, cons
       return fail(c, GAME_ERR_CUDA, "autotune launch failed: %s", cudaGetErrorString(cudaGetLastError()));
     }
     std::sort(t.begin(), t.end());
-    const game_tile gt{plan.bn, plan.stages, plan.cluster, plan.prefetch, plan.sp,
+    const game_tile gt{plan.bn, plan.stages, plan.cluster, plan.prefetch, plan.sp, plan.kg,
                        t[t.size() / 2]};
     if (candidates && *n_done < cap) candidates[*n_done] = gt;
     ++*n_done;
@@ -1485,6 +1486,16 @@ extern "C" game_status game_autotune(game_ctx* c, int32_t reps, game_tile* best,
   }
   drop_graphs(c);
   if (best) *best = bt;
+  return GAME_OK;
+}
+
+extern "C" game_status game_get_tile(game_ctx* c, game_tile* out) {
+  if (!c || !out) return fail(c, GAME_ERR_INVALID_ARG, "ctx or out is NULL");
+  if (!c->have_data) return fail(c, GAME_ERR_STATE, "game_set_data must come first");
+  if (c->engine != GAME_ENGINE_TCGEN05)
+    return fail(c, GAME_ERR_UNSUPPORTED, "this shape runs on a CUDA-core engine");
+  const TcPlan& t = c->tc;
+  *out = game_tile{t.bn, t.stages, t.cluster, t.prefetch, t.sp, t.kg, 0.0};
   return GAME_OK;
 }
 

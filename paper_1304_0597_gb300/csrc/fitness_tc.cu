@@ -81,6 +81,7 @@ struct TcParams {
   int act, err, in_evolve;
   float R;
   int prefetch;           // L2 prefetch of the next tile's boxes
+  int kg;                 // k-blocks per pattern-tile stage (one 3-D TMA request when > 1)
 };
 
 template <int BN, int PREC, bool FAST, int NA, int SP, bool PAIR>
@@ -101,7 +102,9 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   const int S = p.stages;
   uint8_t* sA = smem;
   uint8_t* sB = sA + SP * NA * p.kblocks * kTileA;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + S * kTileB);
+  const int kg = p.kg;                                // k-blocks per stage
+  const int stage_bytes = kg * kTileB;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + S * stage_bytes);
   uint64_t* a_full = bars;
   uint64_t* b_full = bars + 1;
   uint64_t* b_empty = b_full + S;
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
     bool ok = true;
     for (int it = 0; it < my_tiles && ok; ++it) {
       const int row0 = (member + it * p.cps) * BN + (int)crank * kRowsB;
-      for (int kb = 0; kb < p.kblocks && ok; ++kb)
+      for (int kb = 0; kb < p.kblocks && ok; kb += kg)
         for (int bp = 0; bp < p.n_bplanes; ++bp) {
           if (!warp_wait(b_empty + stage, phase ^ 1u, err, p.state, lane)) {
             ok = false;
@@ -201,14 +204,21 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
           TC_STAMP(lane == 0 && bp == 0, 0, it, kb);
           if (lane == 0) {
             // warm L2 with the same box of this CTA's next tile
-            if (it + 1 < my_tiles && p.prefetch)
+            if (it + 1 < my_tiles && p.prefetch && kg == 1)
               tma_prefetch_2d(&p.b[bp], kb * kKB, row0 + p.cps * BN);
             if constexpr (PAIR) {
-              if (issuer) mbar_expect_tx(b_full + stage, 2 * kTileB);
-              tma_load_2d_pair(sB + stage * kTileB, &p.b[bp], kb * kKB, row0, lead(b_full + stage));
-            } else {
+              if (issuer) mbar_expect_tx(b_full + stage, 2 * stage_bytes);
+              if (kg == 1)
+                tma_load_2d_pair(sB + stage * kTileB, &p.b[bp], kb * kKB, row0, lead(b_full + stage));
+              else
+                tma_load_3d_pair(sB + stage * stage_bytes, &p.b[bp], 0, row0, kb, lead(b_full + stage));
+            } else if (kg == 1) {
               mbar_expect_tx(b_full + stage, kTileB);
               tma_load_2d(sB + stage * kTileB, &p.b[bp], kb * kKB, row0, b_full + stage);
+            } else {
+              // k-blocks kb .. kb + kg - 1 in one request (past the last: zero fill)
+              mbar_expect_tx(b_full + stage, stage_bytes);
+              tma_load_3d(sB + stage * stage_bytes, &p.b[bp], 0, row0, kb, b_full + stage);
             }
             last_par[stage] = (int)phase;
           }
@@ -249,40 +259,44 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
         TC_STAMP(lane == 0, 2, it, 0);
         uint32_t accum = 0;   // the first k-step of a tile starts every slice's accumulator
         bool ok = true;
-        for (int kb = 0; kb < p.kblocks && ok; ++kb) {
-          const int steps = min(kKB / kKStep, a_steps_total - kb * (kKB / kKStep));
+        for (int kb0 = 0; kb0 < p.kblocks && ok; kb0 += kg) {
           for (int bp = 0; bp < p.n_bplanes; ++bp) {
             if (!warp_wait(b_full + stage, phase, err, p.state, lane)) {
               ok = false;
               break;
             }
             fence_after();
-            TC_STAMP(lane == 0 && bp == 0, 1, it, kb);
-            const uint64_t bdesc = sw128_desc(b_addr + (uint32_t)(stage * kTileB));
-            // FP32 split: B = P_hi meets A = G_hi and G_lo; B = P_lo meets G_hi.
-            const int n_ap = (PREC == GAME_FP32 && bp == 1) ? 1 : NA;
+            TC_STAMP(lane == 0 && bp == 0, 1, it, kb0);
+            for (int g = 0; g < kg && kb0 + g < p.kblocks; ++g) {
+              const int kb = kb0 + g;
+              const int steps = min(kKB / kKStep, a_steps_total - kb * (kKB / kKStep));
+              const uint64_t bdesc =
+                  sw128_desc(b_addr + (uint32_t)(stage * stage_bytes + g * kTileB));
+              // FP32 split: B = P_hi meets A = G_hi and G_lo; B = P_lo meets G_hi.
+              const int n_ap = (PREC == GAME_FP32 && bp == 1) ? 1 : NA;
 #pragma unroll
-            for (int sp = 0; sp < SP; ++sp) {
-              const uint32_t d = tmem + (uint32_t)((buf * SP + sp) * BN);
-              uint32_t acc_sp = accum;
-              for (int ai = 0; ai < n_ap; ++ai) {
-                const uint64_t adesc =
-                    sw128_desc(a_addr + (uint32_t)(((sp * NA + ai) * p.kblocks + kb) * kTileA));
+              for (int sp = 0; sp < SP; ++sp) {
+                const uint32_t d = tmem + (uint32_t)((buf * SP + sp) * BN);
+                uint32_t acc_sp = accum;
+                for (int ai = 0; ai < n_ap; ++ai) {
+                  const uint64_t adesc =
+                      sw128_desc(a_addr + (uint32_t)(((sp * NA + ai) * p.kblocks + kb) * kTileA));
 #pragma unroll
-                for (int k = 0; k < kKB / kKStep; ++k) {
-                  if (k < steps) {
-                    // +32 bytes along K inside the 128-byte swizzle row = +2 in the address field
-                    if (lane == 0) {
-                      if constexpr (PAIR)
-                        mma_pair<PREC>(d, adesc + 2 * k, bdesc + 2 * k, kIdesc, acc_sp);
-                      else
-                        mma<PREC>(d, adesc + 2 * k, bdesc + 2 * k, kIdesc, acc_sp);
+                  for (int k = 0; k < kKB / kKStep; ++k) {
+                    if (k < steps) {
+                      // +32 bytes along K inside the 128-byte swizzle row = +2 in the address field
+                      if (lane == 0) {
+                        if constexpr (PAIR)
+                          mma_pair<PREC>(d, adesc + 2 * k, bdesc + 2 * k, kIdesc, acc_sp);
+                        else
+                          mma<PREC>(d, adesc + 2 * k, bdesc + 2 * k, kIdesc, acc_sp);
+                      }
+                      acc_sp = 1;
                     }
-                    acc_sp = 1;
                   }
                 }
+                if (sp == SP - 1) accum = acc_sp;
               }
-              if (sp == SP - 1) accum = acc_sp;
             }
             if (lane == 0) {
               if constexpr (PAIR) {   // the stage is free in both CTAs
@@ -443,6 +457,29 @@ cudaError_t make_map(CUtensorMap* m, const void* base, int precision, long long 
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// The same plane viewed as [k-block][row][128 bytes]: one box brings kg k-blocks of
+// box_rows rows, laid out in shared memory as kg 2-D boxes one after the other.
+// Needs cols to be whole k-blocks (else a k-block would run into the next row).
+cudaError_t make_map3(CUtensorMap* m, const void* base, int precision, long long rows, int cols,
+                      int box_rows, int kg) {
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const CUtensorMapDataType dt = precision == GAME_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                 : precision == GAME_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                          : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const int esz = precision == GAME_FP8 ? 1 : 2;
+  const int kb_elems = 128 / esz;
+  if (cols % kb_elems != 0) return cudaErrorInvalidValue;
+  cuuint64_t dims[3] = {(cuuint64_t)kb_elems, (cuuint64_t)rows, (cuuint64_t)(cols / kb_elems)};
+  cuuint64_t strides[2] = {(cuuint64_t)cols * esz, 128};
+  cuuint32_t box[3] = {(cuuint32_t)kb_elems, (cuuint32_t)box_rows, (cuuint32_t)kg};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(m, dt, 3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 constexpr int kSmemMax = 232448;     // 227 KB opt-in per block on sm_103
 constexpr int kSmemMisc = 1024 + 512;   // alignment slack + barriers
 
@@ -556,11 +593,17 @@ bool tc_supported(const Shape& s) {
 }
 
 // Deepest pattern-tile ring next to the resident gene planes; rows = pattern rows a CTA
-// stages per tile (BN, or BN / 2 for a CTA of a pair).
-static int max_stages(const Shape& s, int rows, int sp) {
+// stages per tile (BN, or BN / 2 for a CTA of a pair), kg = k-blocks per stage.
+static int max_stages(const Shape& s, int rows, int sp, int kg = 1) {
   const int room = kSmemMax - kSmemMisc - sp * s.gene_planes * kblocks_of(s) * kTileA;
-  int st = room / (rows * 128);
+  int st = room / (kg * rows * 128);
   return st > 8 ? 8 : st;
+}
+
+// Grouped k-blocks: whole k-blocks per row (the 3-D view) and more than one of them.
+static bool kg_ok(const Shape& s, int kg) {
+  const int kkb = s.precision == GAME_FP8 ? 128 : 64;
+  return kg == 1 || (kg == 2 && s.kp % kkb == 0 && kblocks_of(s) >= 2);
 }
 
 // CTA pairs: 256-pattern tiles, one slice per CTA, an even number of slices.
@@ -577,18 +620,35 @@ void tc_candidates(const Shape& s, std::vector<TileReq>* out) {
       if (sp == 2 && (bn != 128 || n_slices % 2 != 0)) continue;
       const int ms = max_stages(s, bn, sp);
       for (int st = ms; st >= 2 && st >= ms - 1; --st)
-        for (int pf : {1, 0}) out->push_back(TileReq{bn, st, 1, pf, sp});
+        for (int pf : {1, 0}) out->push_back(TileReq{bn, st, 1, pf, sp, 1});
+      if (kg_ok(s, 2))
+        for (int st = max_stages(s, bn, sp, 2); st >= 2; --st)
+          out->push_back(TileReq{bn, st, 1, 0, sp, 2});
     }
   if (pair_ok(s)) {
     const int ms = max_stages(s, 128, 1);
     for (int st = ms; st >= 2 && st >= ms - 2; --st)
-      for (int pf : {1, 0}) out->push_back(TileReq{256, st, 2, pf, 1});
+      for (int pf : {1, 0}) out->push_back(TileReq{256, st, 2, pf, 1, 1});
+    if (kg_ok(s, 2))
+      for (int st = max_stages(s, 128, 1, 2); st >= 2; --st)
+        out->push_back(TileReq{256, st, 2, 0, 1, 2});
   }
 }
 
 cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, TcPlan* plan,
                     TileReq req) {
   if (tc_narrow_shape(s)) return tc_narrow_plan(s, e, p, n_sm, plan, req);
+  // Default cluster for the FP32 form: CTA pairs with two k-blocks per request where
+  // nothing else is asked for and they fit (700k x 256 columns, pop 1024: single CTAs
+  // 0.739 ms, pairs 0.642 ms); single CTAs when the pair plan cannot be made.
+  if (req.cluster == 0 && s.precision == GAME_FP32 && pair_ok(s) && kg_ok(s, 2) &&
+      (!req.n || req.n == 256) && (!req.sp || req.sp == 1) && (!req.kg || req.kg == 2)) {
+    TileReq r2 = req;
+    r2.cluster = 2;
+    if (tc_plan(s, e, p, n_sm, plan, r2) == cudaSuccess) return cudaSuccess;
+    cudaGetLastError();
+    req.cluster = 1;
+  }
   TcPlan& t = *plan;
   t.kblocks = kblocks_of(s);
   const int n_bplanes = s.precision == GAME_FP32 ? 2 : 1;
@@ -610,12 +670,26 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
   t.bn = pair ? 256 : t.sp == 2 ? 128 : (req.n ? req.n : (max_stages(s, 256, 1) >= 2 ? 256 : 128));
   if (t.bn != 128 && t.bn != 256) return cudaErrorInvalidValue;
   const int rows = pair ? t.bn / 2 : t.bn;          // pattern rows a CTA stages per tile
-  const int ms = max_stages(s, rows, t.sp);
+  // Default k-grouping: two k-blocks per request wherever two such stages fit (at 700k x
+  // 256 columns, pop 1024: BF16 0.350 -> 0.274 ms, FP8 0.227 -> 0.213 ms, FP32 pairs
+  // 0.778 -> 0.642 ms); the FP32 form's two gene planes leave room for one only at
+  // 256-pattern tiles of single CTAs.
+  t.kg = req.kg;
+  if (!t.kg) {
+    t.kg = 1;
+    if (kg_ok(s, 2)) {
+      const int ms2 = max_stages(s, rows, t.sp, 2);
+      if (ms2 >= 2 && (!req.stages || req.stages <= ms2)) t.kg = 2;
+    }
+  }
+  if (!kg_ok(s, t.kg)) return cudaErrorInvalidValue;
+  const int ms = max_stages(s, rows, t.sp, t.kg);
   t.stages = req.stages ? req.stages : ms;
   if (t.stages < 2 || t.stages > ms) return cudaErrorNotSupported;
-  t.prefetch = req.prefetch == 0 ? 0 : 1;
+  // the prefetch addresses 2-D boxes; grouped stages go without it
+  t.prefetch = req.prefetch == 0 || t.kg > 1 ? 0 : 1;
   t.n_tiles = (int)((s.n_train + t.bn - 1) / t.bn);
-  t.smem = (size_t)a_bytes + (size_t)t.stages * rows * 128 + kSmemMisc;
+  t.smem = (size_t)a_bytes + (size_t)t.stages * t.kg * rows * 128 + kSmemMisc;
   // Co-resident work units: one CTA per SM (its shared memory fills the SM); pairs must
   // also find two SMs of one GPC, which the occupancy query counts.
   int resident = n_sm;
@@ -649,9 +723,13 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
   cudaError_t err;
   if ((err = make_map(&t.a_map[0], p.ghi, s.precision, s.pop_pad, s.kp, 128)) != cudaSuccess) return err;
   if ((err = make_map(&t.a_map[1], p.glo, s.precision, s.pop_pad, s.kp, 128)) != cudaSuccess) return err;
-  if ((err = make_map(&t.b_map[0], e.p0, s.precision, s.n_train, s.kp, rows)) != cudaSuccess) return err;
+  auto bmap = [&](CUtensorMap* m, const void* base) {
+    return t.kg == 1 ? make_map(m, base, s.precision, s.n_train, s.kp, rows)
+                     : make_map3(m, base, s.precision, s.n_train, s.kp, rows, t.kg);
+  };
+  if ((err = bmap(&t.b_map[0], e.p0)) != cudaSuccess) return err;
   if (n_bplanes == 2) {
-    if ((err = make_map(&t.b_map[1], e.p1, s.precision, s.n_train, s.kp, rows)) != cudaSuccess) return err;
+    if ((err = bmap(&t.b_map[1], e.p1)) != cudaSuccess) return err;
   } else {
     t.b_map[1] = t.b_map[0];
   }
@@ -686,6 +764,7 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
   p.R = f.tmse_R;
   p.in_evolve = state != nullptr;
   p.prefetch = t.prefetch;
+  p.kg = t.kg;
   const bool fast = f.pm1_targets && f.activation == GAME_TANH &&
                     (f.error == GAME_RMSE || f.error == GAME_MSE);
   const bool pair = t.cluster == 2;

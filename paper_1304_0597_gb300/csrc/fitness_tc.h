@@ -24,6 +24,7 @@ struct TcPlan {
   int stages;             // B-operand pipeline depth
   int cluster;            // 1, or 2: CTA pairs sharing each MMA (cta_group::2, M = 256)
   int prefetch = 1;       // L2 prefetch of each CTA's next pattern tile
+  int kg = 1;             // 128-byte k-blocks per stage (> 1: one 3-D TMA request each)
   size_t smem;            // dynamic shared memory bytes
   int narrow = 0;         // 1: the swapped kernel (patterns on M, <= 32 chromosomes on N)
 };
@@ -32,6 +33,7 @@ struct TcPlan {
 struct TileReq {
   int n = 0, stages = 0, cluster = 0, prefetch = -1;   // prefetch: -1 auto (on), 0 off, 1 on
   int sp = 0;                                          // slices per CTA: 0 auto (1), 1, 2
+  int kg = 0;                                          // k-blocks per stage: 0 auto (1), 1, 2
 };
 
 bool tc_supported(const Shape& s);

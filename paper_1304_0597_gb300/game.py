@@ -47,7 +47,8 @@ class GameConfig(C.Structure):
         ("surrogate_steps", C.c_int32), ("surrogate_batch", C.c_int32), ("surrogate_lr", C.c_float),
         ("surrogate_select", C.c_int32), ("surrogate_fp32", C.c_int32), ("engine", C.c_int32),
         ("tile_n", C.c_int32), ("tile_stages", C.c_int32), ("tile_cluster", C.c_int32),
-        ("tile_slices", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p),
+        ("tile_slices", C.c_int32), ("tile_kgroup", C.c_int32), ("device", C.c_int32),
+        ("stream", C.c_void_p),
     ]
 
 
@@ -59,7 +60,13 @@ class GameTiming(C.Structure):
 
 class GameTile(C.Structure):
     _fields_ = [("n", C.c_int32), ("stages", C.c_int32), ("cluster", C.c_int32),
-                ("prefetch", C.c_int32), ("slices", C.c_int32), ("ms", C.c_double)]
+                ("prefetch", C.c_int32), ("slices", C.c_int32), ("kgroup", C.c_int32),
+                ("ms", C.c_double)]
+
+
+def _tile_dict(t: "GameTile") -> dict:
+    return {"n": t.n, "stages": t.stages, "cluster": t.cluster, "prefetch": t.prefetch,
+            "slices": t.slices, "kgroup": t.kgroup, "ms": t.ms}
 
 
 class GameError(RuntimeError):
@@ -97,6 +104,7 @@ def _load() -> C.CDLL:
         "game_get_timing": (I32, [P, C.POINTER(GameTiming)]),
         "game_set_timing": (I32, [P, I32]),
         "game_selftest_timeout": (I32, [P, I32, C.POINTER(I32)]),
+        "game_get_tile": (I32, [P, C.POINTER(GameTile)]),
         "game_autotune": (I32, [P, I32, C.POINTER(GameTile), C.POINTER(GameTile), I32,
                                 C.POINTER(I32)]),
         "game_fitness_noalloc": (I32, [P, P, P, I64, I32, I32, I32, I32, F, P, P]),
@@ -297,9 +305,13 @@ class Game:
         cands = (GameTile * 64)()
         n = C.c_int32(0)
         self._check(lib.game_autotune(self.h, reps, C.byref(best), cands, 64, C.byref(n)), self.h)
-        tile = lambda t: {"n": t.n, "stages": t.stages, "cluster": t.cluster,
-                          "prefetch": t.prefetch, "slices": t.slices, "ms": t.ms}
-        return tile(best), [tile(cands[i]) for i in range(n.value)]
+        return _tile_dict(best), [_tile_dict(cands[i]) for i in range(n.value)]
+
+    def tile(self) -> dict:
+        """The tcgen05 tile shape the fitness launches use (see game_get_tile)."""
+        t = GameTile()
+        self._check(lib.game_get_tile(self.h, C.byref(t)), self.h)
+        return _tile_dict(t)
 
     # ---- learned surrogate ----
     def surrogate_params(self) -> np.ndarray:

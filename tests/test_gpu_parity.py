@@ -401,19 +401,46 @@ def test_calls_out_of_order_are_state_errors():
 
 # ------------------------------------------------------------ tile shapes
 
-@pytest.mark.parametrize("tile", [(256, 3, 1, 1), (256, 2, 1, 1), (128, 5, 1, 1),
-                                  (128, 4, 1, 1), (128, 2, 1, 2), (128, 3, 0, 2),
-                                  (256, 6, 2, 1), (256, 4, 2, 1), (256, 2, 2, 1)])
-def test_tcgen05_tile_shapes_agree(tile):
-    """Every tile shape (patterns per tile, ring depth, cluster, slices per CTA) gives the
-    oracle's fitness; population 1024 = 8 slices of 128 chromosomes, fed one or two per
-    CTA, or (cluster 2) by CTA pairs whose MMAs of 256 chromosomes read both CTAs' halves
-    of each pattern tile."""
+# (degree, (patterns per tile, ring depth, cluster, slices per CTA, k-blocks per stage));
+# 32 features: degree 8 stores 256 columns (4 k-blocks, both FP32 gene planes 128 KB of
+# shared memory per slice), degree 4 stores 128 (two slices per CTA fit).
+@pytest.mark.parametrize("degree,tile", [
+    (8, (256, 3, 1, 1, 1)), (8, (256, 2, 1, 1, 1)), (8, (128, 5, 1, 1, 1)),
+    (8, (128, 4, 1, 1, 1)), (4, (128, 2, 1, 2, 1)), (4, (128, 6, 0, 2, 0)),
+    (8, (256, 6, 2, 1, 1)), (8, (256, 4, 2, 1, 1)), (8, (256, 2, 2, 1, 1)),
+    (8, (128, 3, 1, 1, 2)), (8, (128, 2, 1, 1, 2)), (4, (256, 2, 1, 1, 2)),
+    (4, (128, 3, 1, 2, 2)), (8, (256, 3, 2, 1, 2)), (8, (256, 2, 2, 1, 2))])
+def test_tcgen05_tile_shapes_agree(degree, tile):
+    """Every tile shape (patterns per tile, ring depth, cluster, slices per CTA, k-blocks
+    per TMA request) gives the oracle's fitness, and is the shape that runs; population
+    1024 = 8 slices of 128 chromosomes, fed one or two per CTA, or (cluster 2) by CTA
+    pairs whose MMAs of 256 chromosomes read both CTAs' halves of each pattern tile."""
     game = lib()
-    ds = synth.make_dataset(20011, 32, 8, seed=41, correlated=True)
-    ocfg = _cfg(degree=8, pop=1024, seed=3)
-    g = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=game.ENGINE_TCGEN05, tile_n=tile[0],
-                  tile_stages=tile[1], tile_cluster=tile[2], tile_slices=tile[3])
+    ds = synth.make_dataset(20011, 32, degree, seed=41, correlated=True)
+    ocfg = _cfg(degree=degree, pop=1024, seed=3)
+    n, stages, cluster, slices, kgroup = tile
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=game.ENGINE_TCGEN05, tile_n=n,
+                  tile_stages=stages, tile_cluster=cluster, tile_slices=slices,
+                  tile_kgroup=kgroup)
+    got = g.tile()
+    assert (got["n"], got["stages"], got["cluster"], got["slices"], got["kgroup"]) == \
+        (n, stages, max(cluster, 1), slices, max(kgroup, 1)), got
+    fit, _ = g.evaluate()
+    P = o.expand(ds.X[:ds.n_train], "chebyshev", degree)
+    np.testing.assert_allclose(fit, o.fitness(P, ds.t[:ds.n_train], g.population(), ocfg),
+                               rtol=FIT_RTOL)
+
+
+def test_unplannable_tile_request_runs_the_default_shape():
+    """Two FP32 slices per CTA at 256 stored columns need 256 KB of gene planes: the
+    request cannot be planned, the default shape runs (and says so), and the fitness is
+    the oracle's."""
+    game = lib()
+    ds = synth.make_dataset(6007, 32, 8, seed=43, correlated=True)
+    ocfg = _cfg(degree=8, pop=512, seed=3)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=game.ENGINE_TCGEN05, tile_n=128,
+                  tile_slices=2)
+    assert g.tile()["slices"] == 1
     fit, _ = g.evaluate()
     P = o.expand(ds.X[:ds.n_train], "chebyshev", 8)
     np.testing.assert_allclose(fit, o.fitness(P, ds.t[:ds.n_train], g.population(), ocfg),
@@ -438,6 +465,7 @@ def test_cta_pairs_ragged_and_odd_slices(pop, n):
     ds = synth.make_dataset(n, 16, 6, seed=44, correlated=True)
     ocfg = _cfg(degree=6, pop=pop, seed=8)
     g = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=game.ENGINE_TCGEN05, tile_cluster=2)
+    assert g.tile()["cluster"] == (2 if (pop // 128) % 2 == 0 else 1)
     fit, _ = g.evaluate()
     P = o.expand(ds.X[:ds.n_train], "chebyshev", 6)
     np.testing.assert_allclose(fit, o.fitness(P, ds.t[:ds.n_train], g.population(), ocfg),

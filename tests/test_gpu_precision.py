@@ -104,12 +104,42 @@ def _two_plane_bound(Pq, t, G, s, fmt):
 def test_low_precision_two_slices_per_cta(fmt, planes):
     """Two 128-chromosome slices per CTA (both fed by each 128-pattern tile) give the
     same fitness as the oracle on the quantised operands; population 1280 = 10 slices
-    = 5 groups of two, training rows 21,007 (a ragged last tile)."""
+    = 5 groups of two, training rows 21,007 (a ragged last tile).  32 features at
+    degree 8 (256 stored columns), or degree 4 for two BF16 gene planes, whose two
+    slices at 256 columns would need 256 KB of shared memory."""
     game = lib()
-    ds = synth.make_dataset(30011, 32, 8, seed=35, correlated=True)
-    ocfg = o.Config(degree=8, pop=1280, seed=4)
+    d = 4 if (fmt == "bf16" and planes == 2) else 8
+    ds = synth.make_dataset(30011, 32, d, seed=35, correlated=True)
+    ocfg = o.Config(degree=d, pop=1280, seed=4)
     g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=_prec(fmt), elite_rescore=0,
                   engine=game.ENGINE_TCGEN05, gene_planes=planes, tile_n=128, tile_slices=2)
+    assert g.tile()["slices"] == 2 and g.tile()["n"] == 128
+    G = g.population()
+    fit, _ = g.evaluate()
+    Q, s = o.quantize_columns(o.expand(ds.X, "chebyshev", d)[:, 1:], fmt)
+    Pq = np.concatenate([np.ones((ds.n_train, 1)), o.dequantize_columns(Q[:ds.n_train], s)], axis=1)
+    np.testing.assert_allclose(fit, o.fitness(Pq, ds.t[:ds.n_train],
+                                              o.quantize_genes(G, s, fmt, planes), ocfg),
+                               rtol=1e-5)
+
+
+@pytest.mark.parametrize("fmt", ["bf16", "fp8"])
+@pytest.mark.parametrize("planes", [1, 2])
+@pytest.mark.parametrize("odd", [False, True])
+def test_low_precision_grouped_k_blocks(fmt, planes, odd):
+    """Two k-blocks per TMA request (the pattern plane read as [k-block][row][128 B], one
+    3-D box per ring stage) give the oracle's fitness on the quantised operands: 32
+    features x degree 8 = 256 stored columns = 4 BF16 / 2 FP8 k-blocks, or an odd count
+    whose last request is half zero fill (40 features: 5 BF16 k-blocks; 48: 3 FP8
+    k-blocks); training rows 21,007 (a ragged last tile)."""
+    game = lib()
+    F = (40 if fmt == "bf16" else 48) if odd else 32
+    ds = synth.make_dataset(30011, F, 8, seed=37, correlated=True)
+    ocfg = o.Config(degree=8, pop=512, seed=6)
+    n = 256 if planes == 1 else 128
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=_prec(fmt), elite_rescore=0,
+                  engine=game.ENGINE_TCGEN05, gene_planes=planes, tile_n=n, tile_kgroup=2)
+    assert g.tile()["kgroup"] == 2 and g.tile()["n"] == n
     G = g.population()
     fit, _ = g.evaluate()
     Q, s = o.quantize_columns(o.expand(ds.X, "chebyshev", 8)[:, 1:], fmt)
@@ -121,15 +151,18 @@ def test_low_precision_two_slices_per_cta(fmt, planes):
 
 @pytest.mark.parametrize("fmt", ["bf16", "fp8"])
 @pytest.mark.parametrize("planes", [1, 2])
-def test_low_precision_cta_pairs(fmt, planes):
+@pytest.mark.parametrize("kgroup", [1, 2])
+def test_low_precision_cta_pairs(fmt, planes, kgroup):
     """CTA pairs (cta_group::2: MMAs of 256 chromosomes over both CTAs' halves of each
-    256-pattern tile) give the oracle's fitness on the quantised operands; population
-    1024, training rows 21,007 (a ragged last tile)."""
+    256-pattern tile), one or two k-blocks per TMA request, give the oracle's fitness on
+    the quantised operands; population 1024, training rows 21,007 (a ragged last tile)."""
     game = lib()
     ds = synth.make_dataset(30011, 32, 8, seed=37, correlated=True)
     ocfg = o.Config(degree=8, pop=1024, seed=9)
     g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=_prec(fmt), elite_rescore=0,
-                  engine=game.ENGINE_TCGEN05, gene_planes=planes, tile_cluster=2)
+                  engine=game.ENGINE_TCGEN05, gene_planes=planes, tile_cluster=2,
+                  tile_kgroup=kgroup)
+    assert g.tile()["cluster"] == 2 and g.tile()["kgroup"] == kgroup
     G = g.population()
     fit, _ = g.evaluate()
     Q, s = o.quantize_columns(o.expand(ds.X, "chebyshev", 8)[:, 1:], fmt)

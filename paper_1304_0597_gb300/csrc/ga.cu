@@ -277,53 +277,83 @@ __global__ void prepare_kernel(PrepArgs a) {
   const float* G = (buf ? a.g32_1 : a.g32_0) + (long long)src * a.kstride;
   float* ge = a.geval + (long long)row * a.kp;
   if (lane == 0) a.bias[row] = live ? G[0] : 0.0f;
+  // Genes and column scales are read in batches of kPrepU per lane, all loads of a batch
+  // before its stores (a chain of load-store rounds costs a memory latency each).
+  constexpr int kPrepU = 8;
+  float m = 0.0f;
+  if (live)
+    for (int c0 = 0; c0 < a.kb; c0 += 32 * kPrepU) {
+      float v[kPrepU];
+#pragma unroll
+      for (int u = 0; u < kPrepU; ++u) {
+        const int c = c0 + lane + 32 * u;
+        v[u] = c < a.kb ? G[1 + c] * a.colscale[c] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < kPrepU; ++u) m = fmaxf(m, fabsf(v[u]));
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (a.precision == GAME_FP32) {
     __half* hi = (__half*)a.ghi + (long long)row * a.kp;
     __half* lo = (__half*)a.glo + (long long)row * a.kp;
-    float m = 0.0f;
-    for (int c = lane; c < a.kb; c += 32)
-      if (live) m = fmaxf(m, fabsf(G[1 + c] * a.colscale[c]));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     int ex = 0;
     frexpf(m, &ex);                                  // m < 2^ex
     const float r = ex > 15 ? ldexpf(1.0f, ex - 15) : 1.0f;
     const float inv_r = 1.0f / r;                    // powers of two: exact
-    for (int c = lane; c < a.kp; c += 32) {
-      const float v = (live && c < a.kb) ? G[1 + c] : 0.0f;
-      ge[c] = v;
-      const float w = c < a.kb ? (v * a.colscale[c]) * inv_r : 0.0f;
-      const __half h = __float2half_rn(w);
-      hi[c] = h;
-      lo[c] = __float2half_rn(__fsub_rn(w, __half2float(h)));
+    for (int c0 = 0; c0 < a.kp; c0 += 32 * kPrepU) {
+      float v[kPrepU], cs[kPrepU];
+#pragma unroll
+      for (int u = 0; u < kPrepU; ++u) {
+        const int c = c0 + lane + 32 * u;
+        v[u] = (live && c < a.kb) ? G[1 + c] : 0.0f;
+        cs[u] = c < a.kb ? a.colscale[c] : 0.0f;
+      }
+#pragma unroll
+      for (int u = 0; u < kPrepU; ++u) {
+        const int c = c0 + lane + 32 * u;
+        if (c >= a.kp) break;
+        ge[c] = v[u];
+        const float w = c < a.kb ? (v[u] * cs[u]) * inv_r : 0.0f;
+        const __half h = __float2half_rn(w);
+        hi[c] = h;
+        lo[c] = __float2half_rn(__fsub_rn(w, __half2float(h)));
+      }
     }
     if (lane == 0) a.rscale[row] = r;
     return;
   }
   const float qmax = a.precision == GAME_BF16 ? 1.0f : 448.0f;
-  float m = 0.0f;
-  for (int c = lane; c < a.kb; c += 32)
-    if (live) m = fmaxf(m, fabsf(G[1 + c] * a.colscale[c]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   const float r = m > 0.0f ? m / qmax : 1.0f;
   if (lane == 0) a.rscale[row] = r;
-  for (int c = lane; c < a.kp; c += 32) {
-    const float v = (live && c < a.kb) ? G[1 + c] : 0.0f;
-    ge[c] = v;
-    const float w = (c < a.kb) ? (v * a.colscale[c]) / r : 0.0f;
-    if (a.precision == GAME_BF16) {
-      __nv_bfloat16* hi = (__nv_bfloat16*)a.ghi + (long long)row * a.kp;
-      __nv_bfloat16* lo = (__nv_bfloat16*)a.glo + (long long)row * a.kp;
-      const __nv_bfloat16 h = __float2bfloat16_rn(w);
-      hi[c] = h;
-      lo[c] = __float2bfloat16_rn(w - __bfloat162float(h));
-    } else {
-      __nv_fp8_e4m3* hi = (__nv_fp8_e4m3*)a.ghi + (long long)row * a.kp;
-      __nv_fp8_e4m3* lo = (__nv_fp8_e4m3*)a.glo + (long long)row * a.kp;
-      const __nv_fp8_e4m3 h(w);
-      hi[c] = h;
-      lo[c] = __nv_fp8_e4m3(w - (float)h);
+  for (int c0 = 0; c0 < a.kp; c0 += 32 * kPrepU) {
+    float vv[kPrepU], cs[kPrepU];
+#pragma unroll
+    for (int u = 0; u < kPrepU; ++u) {
+      const int c = c0 + lane + 32 * u;
+      vv[u] = (live && c < a.kb) ? G[1 + c] : 0.0f;
+      cs[u] = c < a.kb ? a.colscale[c] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kPrepU; ++u) {
+      const int c = c0 + lane + 32 * u;
+      if (c >= a.kp) break;
+      const float v = vv[u];
+      ge[c] = v;
+      const float w = (c < a.kb) ? (v * cs[u]) / r : 0.0f;
+      if (a.precision == GAME_BF16) {
+        __nv_bfloat16* hi = (__nv_bfloat16*)a.ghi + (long long)row * a.kp;
+        __nv_bfloat16* lo = (__nv_bfloat16*)a.glo + (long long)row * a.kp;
+        const __nv_bfloat16 h = __float2bfloat16_rn(w);
+        hi[c] = h;
+        lo[c] = __float2bfloat16_rn(w - __bfloat162float(h));
+      } else {
+        __nv_fp8_e4m3* hi = (__nv_fp8_e4m3*)a.ghi + (long long)row * a.kp;
+        __nv_fp8_e4m3* lo = (__nv_fp8_e4m3*)a.glo + (long long)row * a.kp;
+        const __nv_fp8_e4m3 h(w);
+        hi[c] = h;
+        lo[c] = __nv_fp8_e4m3(w - (float)h);
+      }
     }
   }
 }
@@ -464,18 +494,76 @@ __global__ void __launch_bounds__(1024) reduce_rank_kernel(RankArgs a) {
 
 // ---- large populations: the same result without a single-CTA sort ----
 // fit[c] from the partial sums (many CTAs).
-__global__ void fit_reduce_kernel(RankArgs a) {
-  if (a.in_evolve && a.state->stopped) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= a.pop) return;
-  const double sse = sum_partials(a.partial, a.n_part, a.pop_pad, c);
-  const double mse = sse * a.inv_m;
-  a.fit[c] = (a.error == GAME_RMSE) ? sqrt(mse) : mse;
+// 256-thread blocks over 32 consecutive chromosomes: warp g adds partial rows g, g + 8,
+// g + 16, ... (each load coalesced over the 32 chromosomes, four in flight), then the
+// eight group sums are added in group order.  The order is fixed by n_part alone.
+constexpr int kRedGroups = 8;
+
+__device__ __forceinline__ double group_partial_sum(const double* __restrict__ partial,
+                                                    int n_part, long long stride, long long c,
+                                                    int g) {
+  double s = 0.0;
+  int b = g;
+  for (; b + 3 * kRedGroups < n_part; b += 4 * kRedGroups) {
+    double v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = partial[(long long)(b + i * kRedGroups) * stride + c];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s += v[i];
+  }
+  for (; b < n_part; b += kRedGroups) s += partial[(long long)b * stride + c];
+  return s;
+}
+
+// sse of chromosome blockIdx.x * 32 + lane, valid in warp 0 (n: chromosomes).
+__device__ __forceinline__ double block_sse(const double* __restrict__ partial, int n_part,
+                                            long long stride, int n, double (*part)[32]) {
+  const int l = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + l;
+  part[g][l] = c < n ? group_partial_sum(partial, n_part, stride, c, g) : 0.0;
+  __syncthreads();
+  double s = part[0][l];
+#pragma unroll
+  for (int i = 1; i < kRedGroups; ++i) s += part[i][l];
+  return s;
+}
+
+__global__ void __launch_bounds__(256) fit_reduce_kernel(RankArgs a) {
+  if (a.in_evolve && a.state->stopped) return;   // uniform over the block
+  __shared__ double part[kRedGroups][32];
+  const double sse = block_sse(a.partial, a.n_part, a.pop_pad, a.pop, part);
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (threadIdx.x < 32 && c < a.pop) {
+    const double mse = sse * a.inv_m;
+    a.fit[c] = (a.error == GAME_RMSE) ? sqrt(mse) : mse;
+  }
+}
+
+// The state transition of a ranking (one thread), as in reduce_rank_kernel; rank0 is
+// the chromosome at the first rank position.
+__device__ void apply_rank_state(const RankArgs& a, int rank0) {
+  DevState* st = a.state;
+  const double f0 = a.fit[rank0];
+  const double best = isnan(f0) ? CUDART_INF : f0;
+  st->best = best;
+  if (a.mode == kRankEvaluate) {
+    if (st->bred) {
+      st->cur ^= 1;
+      st->gen += 1;
+    }
+    st->bred = 0;
+    st->gens_run += 1;
+    st->evals += 1;
+  }
+  if (a.mode != kRankSortOnly && !a.no_stop && a.in_evolve && best <= a.stop_error)
+    st->stopped = 1;
+  st->evaluated = 1;
 }
 
 // Rank by counting: the position of chromosome c is the number of chromosomes
 // before it in the order (fitness, index) (NaN as +inf), so rank[pos] = c.  One
-// warp per c splits the comparisons; keys are staged per 1024.
+// warp per c splits the comparisons; keys are staged per 1024.  The last block to
+// finish (a fenced counter; nothing waits on it) applies the state transition.
 __global__ void __launch_bounds__(256) rank_count_kernel(RankArgs a) {
   if (a.in_evolve && a.state->stopped) return;
   __shared__ unsigned long long tile[1024];
@@ -505,27 +593,17 @@ __global__ void __launch_bounds__(256) rank_count_kernel(RankArgs a) {
   for (int o = 16; o > 0; o >>= 1) pos += __shfl_xor_sync(0xffffffffu, pos, o);
   if (c < a.pop && lane == 0 && GAME_IN_BOUNDS_DBG(pos >= 0 && pos < a.pop, kSiteRankIndex, pos))
     a.rank[pos] = c;
-}
-
-// The state transition of a ranking (one thread), as in reduce_rank_kernel.
-__global__ void rank_state_kernel(RankArgs a) {
-  DevState* st = a.state;
-  if (a.in_evolve && st->stopped) return;
-  const double f0 = a.fit[a.rank[0]];
-  const double best = isnan(f0) ? CUDART_INF : f0;
-  st->best = best;
-  if (a.mode == kRankEvaluate) {
-    if (st->bred) {
-      st->cur ^= 1;
-      st->gen += 1;
-    }
-    st->bred = 0;
-    st->gens_run += 1;
-    st->evals += 1;
+  // this block's rank writes are visible device-wide before it is counted
+  __threadfence();
+  __syncthreads();
+  __shared__ unsigned int done_before;
+  if (threadIdx.x == 0) done_before = atomicAdd(&a.state->rank_done, 1u);
+  __syncthreads();
+  if (threadIdx.x == 0 && done_before == gridDim.x - 1) {
+    __threadfence();
+    a.state->rank_done = 0;                       // ready for the next launch
+    apply_rank_state(a, __ldcg(a.rank));
   }
-  if (a.mode != kRankSortOnly && !a.no_stop && a.in_evolve && best <= a.stop_error)
-    st->stopped = 1;
-  st->evaluated = 1;
 }
 
 static int next_pow2(int n) {
@@ -553,9 +631,8 @@ cudaError_t launch_reduce_rank(const Shape& s, const game_config& cfg, const dou
   a.inv_m = 1.0 / (double)s.n_train;
   a.stop_error = cfg.stop_error;
   if (s.pop >= kRankCountMin) {
-    if (a.mode == kRankEvaluate) fit_reduce_kernel<<<(s.pop + 255) / 256, 256, 0, st>>>(a);
+    if (a.mode == kRankEvaluate) fit_reduce_kernel<<<(s.pop + 31) / 32, 256, 0, st>>>(a);
     rank_count_kernel<<<(s.pop + 7) / 8, 256, 0, st>>>(a);
-    rank_state_kernel<<<1, 1, 0, st>>>(a);
     return cudaGetLastError();
   }
   const size_t smem = (size_t)a.n2 * (sizeof(unsigned long long) + sizeof(int));
@@ -569,22 +646,26 @@ cudaError_t launch_reduce_rank(const Shape& s, const game_config& cfg, const dou
 
 // FP32 re-score of the elites: fitness of rank[i] (i < n) from the partial sums of
 // the FP32 engine over the gathered rows.
-__global__ void rescore_merge_kernel(const double* partial, int n_part, int pop_pad, int n,
-                                     const int* rank, double* fit, double inv_m, int error,
-                                     const DevState* st, int in_evolve) {
-  if (in_evolve && st->stopped) return;
-  const int i = threadIdx.x;
-  if (i >= n) return;
-  const double sse = sum_partials(partial, n_part, pop_pad, i);
-  const double mse = sse * inv_m;
-  fit[rank[i]] = error == GAME_RMSE ? sqrt(mse) : mse;
+__global__ void __launch_bounds__(256) rescore_merge_kernel(const double* partial, int n_part,
+                                                            int pop_pad, int n, const int* rank,
+                                                            double* fit, double inv_m, int error,
+                                                            const DevState* st, int in_evolve) {
+  if (in_evolve && st->stopped) return;          // uniform over the block
+  __shared__ double part[kRedGroups][32];
+  const double sse = block_sse(partial, n_part, pop_pad, n, part);
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  if (threadIdx.x < 32 && i < n) {
+    const double mse = sse * inv_m;
+    fit[rank[i]] = error == GAME_RMSE ? sqrt(mse) : mse;
+  }
 }
 
 cudaError_t launch_rescore_merge(const Shape& sr, const game_config& cfg, const double* partial,
                                  int n_part, const int* rank, double* fit, const DevState* state,
                                  int in_evolve, cudaStream_t st) {
-  rescore_merge_kernel<<<1, 128, 0, st>>>(partial, n_part, sr.pop_pad, sr.pop, rank, fit,
-                                          1.0 / (double)sr.n_train, cfg.error, state, in_evolve);
+  rescore_merge_kernel<<<(sr.pop + 31) / 32, 256, 0, st>>>(
+      partial, n_part, sr.pop_pad, sr.pop, rank, fit, 1.0 / (double)sr.n_train, cfg.error, state,
+      in_evolve);
   return cudaGetLastError();
 }
 

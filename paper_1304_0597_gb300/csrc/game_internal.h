@@ -38,6 +38,7 @@ struct DevState {
   int status;         // device-side error code (0 ok)
   int evals;          // populations evaluated since game_set_data (never reset)
   double best;        // best fitness of the last evaluated population
+  unsigned int rank_done;   // blocks of the running rank_count launch that finished (0 between)
 };
 
 // Everything a kernel needs to know about the problem and population shapes.

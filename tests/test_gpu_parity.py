@@ -221,10 +221,11 @@ def test_evolve_is_resumable():
     assert a.state() == b.state() == (8, 0)
 
 
-@pytest.mark.parametrize("pop,per_gen", [(50, 4), (1024, 6)])
+@pytest.mark.parametrize("pop,per_gen", [(50, 4), (1024, 5)])
 def test_launch_count_of_evolve(pop, per_gen):
     # breed, prepare, one fitness launch, then one fused reduce+rank kernel below 512
-    # chromosomes or reduce / rank-count / rank-state from 512 up; plus the state reset
+    # chromosomes or reduce / rank-count (whose last block makes the state transition)
+    # from 512 up; plus the state reset
     ds = synth.make_dataset(3000, 5, 3, seed=8)
     g = make_game(_cfg(degree=3, pop=pop), ds.X, ds.t, ds.n_train, engine=lib().ENGINE_TCGEN05)
     assert g.evolve(7) == 7

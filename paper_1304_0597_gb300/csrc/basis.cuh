@@ -112,14 +112,19 @@ __device__ __forceinline__ void ff_step(FF y, FF& prev, FF& cur) {
 // sin(m x) = sin x U_{m-1}(cos x) by the same three-term recurrence with y = 2 cos x,
 // from a float-float sincos, also on the float32 pipes (float64 is a narrow unit on
 // this part).
-template <typename Emit>
-__device__ __forceinline__ void basis_values(int basis, int d, float x, Emit emit) {
+// DC > 0 fixes the degree at compile time (the loops unroll and b is a constant in
+// emit); DC = 0 takes the run-time d.
+template <int DC = 0, typename Emit>
+__device__ __forceinline__ void basis_values(int basis, int d_rt, float x, Emit emit) {
+  const int d = DC > 0 ? DC : d_rt;
   if (basis == GAME_CHEBYSHEV) {
     const float y = __fmul_rn(2.0f, x);          // exact
     float mh = 1.0f, ml = 0.0f;                  // T_{k-1}
     float th = x, tl = 0.0f;                     // T_k
+#pragma unroll
     for (int b = 0; b < d; ++b) {
       emit(b, __fadd_rn(th, tl));
+      if (b + 1 == d) break;                     // no step past the last value
       float p, pe, s, se;
       two_prod(y, th, p, pe);
       two_sum(p, -mh, s, se);
@@ -137,9 +142,11 @@ __device__ __forceinline__ void basis_values(int basis, int d, float x, Emit emi
     ff_sincos(x, s1, c1);
     const FF y{__fmul_rn(2.0f, c1.hi), __fmul_rn(2.0f, c1.lo)};   // exact
     FF cm{1.0f, 0.0f}, cc = c1, sm{0.0f, 0.0f}, sc = s1;
+#pragma unroll
     for (int k = 0; k < d; ++k) {
       emit(k, cc.hi);
       emit(d + k, sc.hi);
+      if (k + 1 == d) break;                     // no step past the last value
       ff_step(y, cm, cc);
       ff_step(y, sm, sc);
     }

@@ -64,7 +64,8 @@ __global__ void expand_scale_kernel(const unsigned int* colmax_bits, float* cols
 
 // Vectorised expansion: one thread per (pattern row, 16-byte chunk of the stored row),
 // consecutive threads on consecutive chunks of a row, so that every store is a full
-// coalesced 16-byte vector.  A chunk holds EPC = 16 / element-size columns; the thread
+// coalesced 16-byte vector.  Blocks are (chunks of a row) x (rows): threadIdx.x is the
+// chunk, so no thread divides by the chunk count.  A chunk holds EPC = 16 / element-size columns; the thread
 // runs the recurrence of each feature its columns belong to (from T_1 / m = 1, stopping
 // at the chunk's last column) and shifts every value into packed registers in column
 // order.  Columns past kb are zero.
@@ -73,12 +74,10 @@ __global__ void __launch_bounds__(256) expand_chunk_kernel(ExpArgs a) {
   constexpr int kEsz = PREC == GAME_FP8 ? 1 : 2;
   constexpr int kEpc = 16 / kEsz;
   constexpr int kBits = 8 * kEsz;
-  const int n_chunks = a.kp / kEpc;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n * n_chunks) return;
-  const long long row = i / n_chunks;
-  const int col0 = (int)(i % n_chunks) * kEpc;
-  if (!GAME_IN_BOUNDS_DBG(row < a.n && col0 + kEpc <= a.kp, kSiteExpandCol, i)) return;
+  const long long row = (long long)blockIdx.x * blockDim.y + threadIdx.y;
+  const int col0 = (int)(blockIdx.y * blockDim.x + threadIdx.x) * kEpc;
+  if (row >= a.n || col0 >= a.kp) return;
+  if (!GAME_IN_BOUNDS_DBG(col0 + kEpc <= a.kp, kSiteExpandCol, row)) return;
   uint32_t w0[4] = {0u, 0u, 0u, 0u}, w1[4] = {0u, 0u, 0u, 0u};   // plane 0 / plane 1 words
   // shift the 128-bit chunk right by one element and put e (its low kBits) on top
   auto push = [&](uint32_t* w, uint32_t e) {
@@ -128,70 +127,111 @@ template <int PREC>
 __global__ void __launch_bounds__(256) expand_cheb_aligned_kernel(ExpArgs a) {
   constexpr int kEsz = PREC == GAME_FP8 ? 1 : 2;
   constexpr int kEpc = 16 / kEsz;
-  const int n_chunks = a.kp / kEpc;
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n * n_chunks) return;
-  const long long row = i / n_chunks;
-  const int col0 = (int)(i % n_chunks) * kEpc;
-  if (!GAME_IN_BOUNDS_DBG(row < a.n && col0 + kEpc <= a.kp, kSiteExpandCol, i)) return;
-  float v[kEpc];
-  if (col0 < a.kb) {
-    const int f = col0 / a.bd;
-    const int b0 = col0 - f * a.bd;
-    const float x = __ldg(a.X + row * a.F + f);
-    const float y = __fmul_rn(2.0f, x);
-    float mh = 1.0f, ml = 0.0f, th = x, tl = 0.0f;
-    auto step = [&]() {
-      float p, pe, s2, se;
-      two_prod(y, th, p, pe);
-      two_sum(p, -mh, s2, se);
-      const float low = __fsub_rn(__fadd_rn(__fadd_rn(se, pe), __fmul_rn(y, tl)), ml);
-      const float nh = __fadd_rn(s2, low);
-      const float nl = __fsub_rn(low, __fsub_rn(nh, s2));
-      mh = th;
-      ml = tl;
-      th = nh;
-      tl = nl;
-    };
-    for (int b = 0; b < b0; ++b) step();
+  constexpr int kRows = 2;   // rows per thread: two independent recurrences in flight
+  const int col0 = (int)(blockIdx.y * blockDim.x + threadIdx.x) * kEpc;
+  if (col0 >= a.kp) return;
+  if (!GAME_IN_BOUNDS_DBG(col0 + kEpc <= a.kp, kSiteExpandCol, col0)) return;
+  // per-thread constants: the chunk's feature, its first basis index, its column scales
+  const bool val = col0 < a.kb;
+  int f = 0, b0 = 0;
+  float sc[kEpc];
 #pragma unroll
-    for (int j = 0; j < kEpc; ++j) {
-      v[j] = __fadd_rn(th, tl);
-      if (j + 1 < kEpc) step();
-    }
+  for (int j = 0; j < kEpc; ++j) sc[j] = 1.0f;
+  if (val) {
+    f = col0 / a.bd;
+    b0 = col0 - f * a.bd;
     if (PREC != GAME_FP32 || !a.unit_scale) {
 #pragma unroll
       for (int j = 0; j < kEpc; ++j)
-        v[j] = PREC == GAME_FP32 ? v[j] * (1.0f / __ldg(a.colscale + col0 + j))
-                                 : v[j] / __ldg(a.colscale + col0 + j);
+        sc[j] = PREC == GAME_FP32 ? 1.0f / __ldg(a.colscale + col0 + j)   // powers of two
+                                  : __ldg(a.colscale + col0 + j);
+    }
+  }
+  const long long rbase = (long long)blockIdx.x * blockDim.y * kRows + threadIdx.y;
+  float v[kRows][kEpc];
+  float x[kRows];
+#pragma unroll
+  for (int u = 0; u < kRows; ++u) {
+    const long long row = rbase + (long long)u * blockDim.y;
+    x[u] = val && row < a.n ? __ldg(a.X + row * a.F + f) : 0.0f;
+  }
+  if (val) {
+    // T_{b+1}(x) for b = b0 .. b0 + EPC - 1 by the float-float recurrence, both rows
+    // advanced in the same loop
+    float y[kRows], mh[kRows], ml[kRows], th[kRows], tl[kRows];
+#pragma unroll
+    for (int u = 0; u < kRows; ++u) {
+      y[u] = __fmul_rn(2.0f, x[u]);
+      mh[u] = 1.0f;
+      ml[u] = 0.0f;
+      th[u] = x[u];
+      tl[u] = 0.0f;
+    }
+    auto step = [&](int u) {
+      float p, pe, s2, se;
+      two_prod(y[u], th[u], p, pe);
+      two_sum(p, -mh[u], s2, se);
+      const float low = __fsub_rn(__fadd_rn(__fadd_rn(se, pe), __fmul_rn(y[u], tl[u])), ml[u]);
+      const float nh = __fadd_rn(s2, low);
+      const float nl = __fsub_rn(low, __fsub_rn(nh, s2));
+      mh[u] = th[u];
+      ml[u] = tl[u];
+      th[u] = nh;
+      tl[u] = nl;
+    };
+    for (int b = 0; b < b0; ++b) {
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) step(u);
+    }
+#pragma unroll
+    for (int j = 0; j < kEpc; ++j) {
+#pragma unroll
+      for (int u = 0; u < kRows; ++u) {
+        v[u][j] = __fadd_rn(th[u], tl[u]);
+        if (j + 1 < kEpc) step(u);
+      }
+    }
+    if (PREC != GAME_FP32 || !a.unit_scale) {
+#pragma unroll
+      for (int u = 0; u < kRows; ++u)
+#pragma unroll
+        for (int j = 0; j < kEpc; ++j)
+          v[u][j] = PREC == GAME_FP32 ? v[u][j] * sc[j] : v[u][j] / sc[j];
     }
   } else {
 #pragma unroll
-    for (int j = 0; j < kEpc; ++j) v[j] = 0.0f;
+    for (int u = 0; u < kRows; ++u)
+#pragma unroll
+      for (int j = 0; j < kEpc; ++j) v[u][j] = 0.0f;
   }
-  uint32_t w0[4], w1[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    if (PREC == GAME_FP32) {
-      const __half h0 = __float2half_rn(v[2 * q]), h1 = __float2half_rn(v[2 * q + 1]);
-      const __half l0 = __float2half_rn(__fsub_rn(v[2 * q], __half2float(h0)));
-      const __half l1 = __float2half_rn(__fsub_rn(v[2 * q + 1], __half2float(h1)));
-      w0[q] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-      w1[q] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
-    } else if (PREC == GAME_BF16) {
-      w0[q] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[2 * q])) |
-              ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[2 * q + 1])) << 16);
-    } else {
-      uint32_t w = 0;
+  for (int u = 0; u < kRows; ++u) {
+    const long long row = rbase + (long long)u * blockDim.y;
+    if (row >= a.n) break;
+    uint32_t w0[4], w1[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) w |= (uint32_t)__nv_fp8_e4m3(v[4 * q + j]).__x << (8 * j);
-      w0[q] = w;
+    for (int q = 0; q < 4; ++q) {
+      if (PREC == GAME_FP32) {
+        const __half h0 = __float2half_rn(v[u][2 * q]), h1 = __float2half_rn(v[u][2 * q + 1]);
+        const __half l0 = __float2half_rn(__fsub_rn(v[u][2 * q], __half2float(h0)));
+        const __half l1 = __float2half_rn(__fsub_rn(v[u][2 * q + 1], __half2float(h1)));
+        w0[q] = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+        w1[q] = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+      } else if (PREC == GAME_BF16) {
+        w0[q] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[u][2 * q])) |
+                ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v[u][2 * q + 1])) << 16);
+      } else {
+        uint32_t w = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w |= (uint32_t)__nv_fp8_e4m3(v[u][4 * q + j]).__x << (8 * j);
+        w0[q] = w;
+      }
     }
+    const long long o = (row * a.kp + col0) * kEsz;
+    *reinterpret_cast<uint4*>((uint8_t*)a.p0 + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+    if (PREC == GAME_FP32)
+      *reinterpret_cast<uint4*>((uint8_t*)a.p1 + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
   }
-  const long long o = (row * a.kp + col0) * kEsz;
-  *reinterpret_cast<uint4*>((uint8_t*)a.p0 + o) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-  if (PREC == GAME_FP32)
-    *reinterpret_cast<uint4*>((uint8_t*)a.p1 + o) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
 }
 
 // Shared coefficients (the paper's eq.2 / eq.9 form): column b of pattern k is the
@@ -301,6 +341,83 @@ __global__ void __launch_bounds__(kSharedRows) expand_shared_kernel(ExpArgs a) {
   }
 }
 
+// The same for a degree fixed at compile time (D <= 8, the paper's settings): the
+// column sums live in registers (b is a constant in every emit) instead of shared
+// memory, and the kernel stores the same bytes as expand_shared_kernel.  kp <= 32.
+template <int D>
+__global__ void __launch_bounds__(128) expand_shared_reg_kernel(ExpArgs a) {
+  constexpr int kB = 2 * D;                      // room for both bases (trig: 2 d columns)
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= a.n) return;
+  float2 acc[kB];
+#pragma unroll
+  for (int b = 0; b < kB; ++b) acc[b] = make_float2(0.0f, 0.0f);
+  const float* x = a.X + k * a.F;
+  for (int f = 0; f < a.F; ++f)
+    basis_values<D>(a.basis, D, __ldg(x + f), [&](int b, float v) {
+      float s, e;
+      two_sum(acc[b].x, v, s, e);
+      acc[b] = make_float2(s, __fadd_rn(acc[b].y, e));
+    });
+  const long long row = k * a.kp;
+  auto val = [&](int b) { return b < kB && b < a.kb ? ff_round(acc[b < kB ? b : 0]) : 0.0f; };
+  if (a.precision == GAME_FP32) {
+#pragma unroll
+    for (int b0 = 0; b0 < 16; b0 += 8) {
+      if (b0 >= a.kp) break;
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int b = b0 + 2 * i;
+        // the power-of-two column scale divides exactly
+        const float v0 = b < a.kb ? val(b) * (1.0f / a.colscale[b]) : 0.0f;
+        const float v1 = b + 1 < a.kb ? val(b + 1) * (1.0f / a.colscale[b + 1]) : 0.0f;
+        const __half h0 = __float2half_rn(v0), h1 = __float2half_rn(v1);
+        const __half l0 = __float2half_rn(__fsub_rn(v0, __half2float(h0)));
+        const __half l1 = __float2half_rn(__fsub_rn(v1, __half2float(h1)));
+        const __half2 hh = __halves2half2(h0, h1), ll = __halves2half2(l0, l1);
+        hw[i] = *reinterpret_cast<const uint32_t*>(&hh);
+        lw[i] = *reinterpret_cast<const uint32_t*>(&ll);
+      }
+      *reinterpret_cast<uint4*>((__half*)a.p0 + row + b0) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4*>((__half*)a.p1 + row + b0) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+  } else if (a.precision == GAME_BF16) {
+#pragma unroll
+    for (int b0 = 0; b0 < 16; b0 += 8) {
+      if (b0 >= a.kp) break;
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int b = b0 + 2 * i;
+        const __nv_bfloat162 q =
+            __halves2bfloat162(__float2bfloat16_rn(b < a.kb ? val(b) / a.colscale[b] : 0.0f),
+                               __float2bfloat16_rn(b + 1 < a.kb ? val(b + 1) / a.colscale[b + 1] : 0.0f));
+        w[i] = *reinterpret_cast<const uint32_t*>(&q);
+      }
+      *reinterpret_cast<uint4*>((__nv_bfloat16*)a.p0 + row + b0) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  } else {
+#pragma unroll
+    for (int b0 = 0; b0 < 32; b0 += 16) {
+      if (b0 >= a.kp) break;
+      uint32_t w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int b = b0 + 4 * i + j;
+          const __nv_fp8_e4m3 q(b < a.kb ? val(b) / a.colscale[b] : 0.0f);
+          word |= (uint32_t)q.__x << (8 * j);
+        }
+        w[i] = word;
+      }
+      *reinterpret_cast<uint4*>((__nv_fp8_e4m3*)a.p0 + row + b0) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
 __global__ void target_coef_kernel(const float* t, float* c, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) c[i] = 2.8853900817779268f * t[i];   // 2 log2(e) t
@@ -388,6 +505,25 @@ cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax
       expand_scale_kernel<<<(s.kp + 255) / 256, 256, 0, st>>>(
           a.colmax_bits, e.colscale, s.kb, s.kp, s.precision == GAME_BF16 ? 1.0f : 448.0f);
     }
+    // degrees up to 8: the register form (kp <= 16 for 16-bit storage, <= 32 for e4m3)
+    const unsigned rblk = (unsigned)((s.n_patterns + 127) / 128);
+    switch (s.degree) {
+#define GAME_SHARED_REG(DV)                                          \
+  case DV:                                                           \
+    expand_shared_reg_kernel<DV><<<rblk, 128, 0, st>>>(a);           \
+    return cudaGetLastError();
+      GAME_SHARED_REG(1)
+      GAME_SHARED_REG(2)
+      GAME_SHARED_REG(3)
+      GAME_SHARED_REG(4)
+      GAME_SHARED_REG(5)
+      GAME_SHARED_REG(6)
+      GAME_SHARED_REG(7)
+      GAME_SHARED_REG(8)
+#undef GAME_SHARED_REG
+      default:
+        break;
+    }
     expand_shared_kernel<<<(unsigned)nblk, kSharedRows, smem, st>>>(a);
     return cudaGetLastError();
   }
@@ -401,25 +537,31 @@ cudaError_t launch_expand(const float* X, const Shape& s, ExpDev& e, float* qmax
     expand_scale_kernel<<<(s.kp + 255) / 256, 256, 0, st>>>(
         a.colmax_bits, e.colscale, s.kb, s.kp, s.precision == GAME_BF16 ? 1.0f : 448.0f);
   }
+  // Blocks of (chunks of a row) x (rows): x = min(chunks, 256) consecutive chunks, y = rows,
+  // grid y over the chunk groups of wider rows.
   const int epc = s.precision == GAME_FP8 ? 16 : 8;
-  const long long items = s.n_patterns * (s.kp / epc);
-  const unsigned cb = (unsigned)((items + threads - 1) / threads);
+  const int nc = s.kp / epc;
+  const int bx = nc < threads ? nc : threads;
+  const int by = threads / bx;
+  const unsigned gy = (unsigned)((nc + bx - 1) / bx);
   a.unit_scale = e.unit_scale32;
   if (s.basis == GAME_CHEBYSHEV && s.bd % epc == 0) {
+    const dim3 grid((unsigned)((s.n_patterns + 2LL * by - 1) / (2LL * by)), gy);   // 2 rows/thread
     if (s.precision == GAME_FP32)
-      expand_cheb_aligned_kernel<GAME_FP32><<<cb, threads, 0, st>>>(a);
+      expand_cheb_aligned_kernel<GAME_FP32><<<grid, dim3(bx, by), 0, st>>>(a);
     else if (s.precision == GAME_BF16)
-      expand_cheb_aligned_kernel<GAME_BF16><<<cb, threads, 0, st>>>(a);
+      expand_cheb_aligned_kernel<GAME_BF16><<<grid, dim3(bx, by), 0, st>>>(a);
     else
-      expand_cheb_aligned_kernel<GAME_FP8><<<cb, threads, 0, st>>>(a);
+      expand_cheb_aligned_kernel<GAME_FP8><<<grid, dim3(bx, by), 0, st>>>(a);
     return cudaGetLastError();
   }
+  const dim3 grid((unsigned)((s.n_patterns + by - 1) / by), gy);
   if (s.precision == GAME_FP32)
-    expand_chunk_kernel<GAME_FP32><<<cb, threads, 0, st>>>(a);
+    expand_chunk_kernel<GAME_FP32><<<grid, dim3(bx, by), 0, st>>>(a);
   else if (s.precision == GAME_BF16)
-    expand_chunk_kernel<GAME_BF16><<<cb, threads, 0, st>>>(a);
+    expand_chunk_kernel<GAME_BF16><<<grid, dim3(bx, by), 0, st>>>(a);
   else
-    expand_chunk_kernel<GAME_FP8><<<cb, threads, 0, st>>>(a);
+    expand_chunk_kernel<GAME_FP8><<<grid, dim3(bx, by), 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -71,6 +71,8 @@ struct game_ctx {
   // Learned surrogate (cfg.surrogate_pool > 0 drives the generation; the network
   // also exists on demand for the checking calls).
   bool sg_alloc = false;
+  cudaStream_t st_sg = nullptr;        // the surrogate training step's second stream
+  cudaEvent_t ev_sg[2] = {};           // its fork / join events
   Surrogate sg{};
   int n_pool = 0;               // children bred per generation
   int sg_steps = 4, sg_batch = 1024;
@@ -337,6 +339,12 @@ extern "C" void game_destroy(game_ctx* c) {
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   for (cudaEvent_t e : c->copy_ev) cudaEventDestroy(e);
   if (c->st_copy) cudaStreamDestroy(c->st_copy);
+  if (c->st_sg) {
+    cudaStreamSynchronize(c->st_sg);
+    cudaStreamDestroy(c->st_sg);
+    cudaEventDestroy(c->ev_sg[0]);
+    cudaEventDestroy(c->ev_sg[1]);
+  }
   delete c;
 }
 
@@ -497,6 +505,14 @@ static game_status alloc_surrogate(game_ctx* c) {
     if ((r = dalloc(c, &tcbuf, sg.tc_bytes(sg.max_rows, c->sg_batch))) != GAME_OK) return r;
     sg.state = c->d_state;
     sg.tc_carve(tcbuf, c->sg_batch);
+    if (!c->st_sg) {
+      CUDA_OK(c, cudaStreamCreateWithFlags(&c->st_sg, cudaStreamNonBlocking));
+      CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_sg[0], cudaEventDisableTiming));
+      CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_sg[1], cudaEventDisableTiming));
+    }
+    sg.side = c->st_sg;
+    sg.ev_fork = c->ev_sg[0];
+    sg.ev_join = c->ev_sg[1];
   }
   if ((r = dalloc(c, &c->d_pool, sizeof(float) * (size_t)c->n_pool * s.kstride)) != GAME_OK) return r;
   if ((r = dalloc(c, &c->d_score, sizeof(float) * c->n_pool)) != GAME_OK) return r;

@@ -82,6 +82,7 @@ struct TcParams {
   float R;
   int prefetch;           // L2 prefetch of the next tile's boxes
   int kg;                 // k-blocks per pattern-tile stage (one 3-D TMA request when > 1)
+  int a_rows;             // gene rows held per A tile (128, or the live rows of one slice)
 };
 
 template <int BN, int PREC, bool FAST, int NA, int SP, bool PAIR>
@@ -101,7 +102,13 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   constexpr uint32_t kIdesc = make_idesc(PAIR ? 256 : 128, BN, kFmt);
   const int S = p.stages;
   uint8_t* sA = smem;
-  uint8_t* sB = sA + SP * NA * p.kblocks * kTileA;
+  // A tiles hold a_rows rows (a multiple of 8): 128, or, for a single slice of at most
+  // 120 chromosomes, its live rows only.  The MMA still spans 128 rows; the 8-row groups
+  // past a_rows read whatever shared memory follows (the next A tile or the ring, all
+  // inside the CTA's allocation) and feed only padded chromosomes, whose sums are never
+  // read; the epilogue skips the lane quadrants that hold no live row.
+  const int a_tile = p.a_rows * 128;
+  uint8_t* sB = sA + SP * NA * p.kblocks * a_tile;
   const int kg = p.kg;                                // k-blocks per stage
   const int stage_bytes = kg * kTileB;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sB + S * stage_bytes);
@@ -177,13 +184,13 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
   if (warp == 0) {
     // ---- TMA producer: the whole warp follows one control flow, lane 0 issues ----
     if (lane == 0) {
-      const uint32_t a_bytes = (uint32_t)SP * NA * p.kblocks * kTileA;
+      const uint32_t a_bytes = (uint32_t)SP * NA * p.kblocks * a_tile;
       // The leader expects its own and (pair) the peer's bytes on its barrier.
       if (issuer) mbar_expect_tx(a_full, PAIR ? 2 * a_bytes : a_bytes);
       for (int sp = 0; sp < SP; ++sp)
         for (int pl = 0; pl < NA; ++pl)
           for (int kb = 0; kb < p.kblocks; ++kb) {
-            void* dst = sA + ((sp * NA + pl) * p.kblocks + kb) * kTileA;
+            void* dst = sA + ((sp * NA + pl) * p.kblocks + kb) * a_tile;
             if constexpr (PAIR)
               tma_load_2d_pair(dst, &p.a[pl], kb * kKB, slice0 * 128, lead(a_full));
             else
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
                 uint32_t acc_sp = accum;
                 for (int ai = 0; ai < n_ap; ++ai) {
                   const uint64_t adesc =
-                      sw128_desc(a_addr + (uint32_t)(((sp * NA + ai) * p.kblocks + kb) * kTileA));
+                      sw128_desc(a_addr + (uint32_t)(((sp * NA + ai) * p.kblocks + kb) * a_tile));
 #pragma unroll
                   for (int k = 0; k < kKB / kKStep; ++k) {
                     if (k < steps) {
@@ -369,6 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1) fitness_tc_kernel(const __grid_co
       TC_STAMP(lane == 0 && (warp == 2 || warp == 17), warp == 2 ? 4 : 6, it, 0);
 #pragma unroll
       for (int sp = 0; sp < SP; ++sp) {
+        if (q * 32 >= p.a_rows) continue;   // no live chromosome in this lane quadrant
         const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) +
                                (uint32_t)((buf * SP + sp) * BN + h * kCols);
 #pragma unroll
@@ -592,10 +600,19 @@ bool tc_supported(const Shape& s) {
   return a_bytes + 2 * 128 * 128 + kSmemMisc <= kSmemMax;
 }
 
+// Gene rows held per A tile: a single slice (at most 128 chromosomes) of a single CTA
+// keeps only its live rows, rounded up to a whole 8-row group (the elites' FP32
+// re-score: 16 of 128), which frees shared memory for a deeper pattern-tile ring.
+static int a_rows_of(const Shape& s, bool pair, int sp) {
+  if (pair || sp != 1 || s.pop_pad != 128) return 128;
+  const int r = (s.pop + 7) / 8 * 8;
+  return r < 8 ? 8 : r;
+}
+
 // Deepest pattern-tile ring next to the resident gene planes; rows = pattern rows a CTA
 // stages per tile (BN, or BN / 2 for a CTA of a pair), kg = k-blocks per stage.
-static int max_stages(const Shape& s, int rows, int sp, int kg = 1) {
-  const int room = kSmemMax - kSmemMisc - sp * s.gene_planes * kblocks_of(s) * kTileA;
+static int max_stages(const Shape& s, int rows, int sp, int kg = 1, int a_rows = 128) {
+  const int room = kSmemMax - kSmemMisc - sp * s.gene_planes * kblocks_of(s) * a_rows * 128;
   int st = room / (kg * rows * 128);
   return st > 8 ? 8 : st;
 }
@@ -618,12 +635,14 @@ void tc_candidates(const Shape& s, std::vector<TileReq>* out) {
   for (int sp : {1, 2})
     for (int bn : {256, 128}) {
       if (sp == 2 && (bn != 128 || n_slices % 2 != 0)) continue;
-      const int ms = max_stages(s, bn, sp);
+      const int ar = a_rows_of(s, false, sp);
+      const int ms = max_stages(s, bn, sp, 1, ar);
       for (int st = ms; st >= 2 && st >= ms - 1; --st)
         for (int pf : {1, 0}) out->push_back(TileReq{bn, st, 1, pf, sp, 1});
-      if (kg_ok(s, 2))
-        for (int st = max_stages(s, bn, sp, 2); st >= 2; --st)
-          out->push_back(TileReq{bn, st, 1, 0, sp, 2});
+      if (kg_ok(s, 2)) {
+        const int ms2 = max_stages(s, bn, sp, 2, ar);
+        for (int st = ms2; st >= 2 && st >= ms2 - 2; --st) out->push_back(TileReq{bn, st, 1, 0, sp, 2});
+      }
     }
   if (pair_ok(s)) {
     const int ms = max_stages(s, 128, 1);
@@ -664,10 +683,12 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
   if (t.sp == 2 && (t.n_slices % 2 != 0 || (req.n && req.n != 128))) return cudaErrorInvalidValue;
   // groups: units of work sharing the pattern tiles (a CTA's slices, or a pair's two)
   t.n_groups = pair ? t.n_slices / 2 : t.n_slices / t.sp;
-  const int a_bytes = t.sp * s.gene_planes * t.kblocks * kTileA;
+  t.a_rows = a_rows_of(s, pair, t.sp);
+  const int a_bytes = t.sp * s.gene_planes * t.kblocks * t.a_rows * 128;
   // Default shape: 256-pattern tiles when two stages fit, else 128
   // (128-pattern tiles cost as much per MMA instruction as 256-pattern ones).
-  t.bn = pair ? 256 : t.sp == 2 ? 128 : (req.n ? req.n : (max_stages(s, 256, 1) >= 2 ? 256 : 128));
+  t.bn = pair ? 256 : t.sp == 2 ? 128
+                               : (req.n ? req.n : (max_stages(s, 256, 1, 1, t.a_rows) >= 2 ? 256 : 128));
   if (t.bn != 128 && t.bn != 256) return cudaErrorInvalidValue;
   const int rows = pair ? t.bn / 2 : t.bn;          // pattern rows a CTA stages per tile
   // Default k-grouping: two k-blocks per request wherever two such stages fit (at 700k x
@@ -678,12 +699,12 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
   if (!t.kg) {
     t.kg = 1;
     if (kg_ok(s, 2)) {
-      const int ms2 = max_stages(s, rows, t.sp, 2);
+      const int ms2 = max_stages(s, rows, t.sp, 2, t.a_rows);
       if (ms2 >= 2 && (!req.stages || req.stages <= ms2)) t.kg = 2;
     }
   }
   if (!kg_ok(s, t.kg)) return cudaErrorInvalidValue;
-  const int ms = max_stages(s, rows, t.sp, t.kg);
+  const int ms = max_stages(s, rows, t.sp, t.kg, t.a_rows);
   t.stages = req.stages ? req.stages : ms;
   if (t.stages < 2 || t.stages > ms) return cudaErrorNotSupported;
   // the prefetch addresses 2-D boxes; grouped stages go without it
@@ -721,8 +742,8 @@ cudaError_t tc_plan(const Shape& s, const ExpDev& e, const PopDev& p, int n_sm, 
   t.grid = t.n_groups * cps * (pair ? 2 : 1);
   t.n_part = cps;
   cudaError_t err;
-  if ((err = make_map(&t.a_map[0], p.ghi, s.precision, s.pop_pad, s.kp, 128)) != cudaSuccess) return err;
-  if ((err = make_map(&t.a_map[1], p.glo, s.precision, s.pop_pad, s.kp, 128)) != cudaSuccess) return err;
+  if ((err = make_map(&t.a_map[0], p.ghi, s.precision, s.pop_pad, s.kp, t.a_rows)) != cudaSuccess) return err;
+  if ((err = make_map(&t.a_map[1], p.glo, s.precision, s.pop_pad, s.kp, t.a_rows)) != cudaSuccess) return err;
   auto bmap = [&](CUtensorMap* m, const void* base) {
     return t.kg == 1 ? make_map(m, base, s.precision, s.n_train, s.kp, rows)
                      : make_map3(m, base, s.precision, s.n_train, s.kp, rows, t.kg);
@@ -765,6 +786,7 @@ cudaError_t tc_launch(const TcPlan& t, const Shape& s, const Fitness& f, const P
   p.in_evolve = state != nullptr;
   p.prefetch = t.prefetch;
   p.kg = t.kg;
+  p.a_rows = t.a_rows;
   const bool fast = f.pm1_targets && f.activation == GAME_TANH &&
                     (f.error == GAME_RMSE || f.error == GAME_MSE);
   const bool pair = t.cluster == 2;

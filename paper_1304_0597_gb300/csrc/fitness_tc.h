@@ -25,6 +25,7 @@ struct TcPlan {
   int cluster;            // 1, or 2: CTA pairs sharing each MMA (cta_group::2, M = 256)
   int prefetch = 1;       // L2 prefetch of each CTA's next pattern tile
   int kg = 1;             // 128-byte k-blocks per stage (> 1: one 3-D TMA request each)
+  int a_rows = 128;       // gene rows per resident A tile (fewer for one small slice)
   size_t smem;            // dynamic shared memory bytes
   int narrow = 0;         // 1: the swapped kernel (patterns on M, <= 32 chromosomes on N)
 };

@@ -85,12 +85,20 @@ struct Surrogate {
   // dZ1^T, [gW2 | gb2] and [gW1 | gb1] of the batch just run forward with targets,
   // as split-K planes in gws, added into g when sum_planes
   cudaError_t tc_backward_gemms(int B, cudaStream_t st, bool sum_planes = true);
+  // its three GEMMs: dZ1^T (needs dZ2), then [gW1 | gb1]; [gW2 | gb2] (needs dZ2 only)
+  cudaError_t tc_backward_b1(int B, cudaStream_t st);
+  cudaError_t tc_grad_w1(int B, cudaStream_t st);
+  cudaError_t tc_grad_w2(int B, cudaStream_t st);
   // gw3, gb3 and the loss of that batch
   cudaError_t tc_out_grads(int B, cudaStream_t st);
   // Adam step that also refreshes the bf16 GEMM copies and the step counter; with
   // from_planes it adds the split-K planes of the last tc_backward_gemms itself
   cudaError_t tc_adam(float lr, cudaStream_t st, bool from_planes = false);
   int grad_splits = 0;       // split-K planes written by the last tc_backward_gemms
+  // Optional second stream and events (owned by the caller): a training step runs the
+  // W2 gradient and the output-layer gradients beside dZ1 and the W1 gradient.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 cudaError_t surrogate_tc_init_attributes();

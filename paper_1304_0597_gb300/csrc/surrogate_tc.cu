@@ -726,9 +726,23 @@ cudaError_t Surrogate::tc_forward(const float* X, long long ldx, int M, float* y
 cudaError_t Surrogate::tc_train_step(int B, const float* t, float lr, cudaStream_t st) {
   cudaError_t e;
   if ((e = tc_layers(B, yb, t, st)) != cudaSuccess) return e;
-  if ((e = tc_out_grads(B, st)) != cudaSuccess) return e;
-  // the Adam launch adds the split-K planes itself: one launch fewer per step
-  if ((e = tc_backward_gemms(B, st, false)) != cudaSuccess) return e;
+  // After the forward pass (which leaves dZ2) the output-layer gradients and the W2
+  // gradient depend on nothing else: with a second stream they run beside dZ1 and the
+  // W1 gradient.  The Adam launch adds the split-K planes itself.
+  const bool fork = side && ev_fork && ev_join;
+  cudaStream_t s2 = fork ? side : st;
+  if (fork) {
+    if ((e = cudaEventRecord(ev_fork, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(side, ev_fork, 0)) != cudaSuccess) return e;
+  }
+  if ((e = tc_out_grads(B, s2)) != cudaSuccess) return e;
+  if ((e = tc_grad_w2(B, s2)) != cudaSuccess) return e;
+  if ((e = tc_backward_b1(B, st)) != cudaSuccess) return e;
+  if ((e = tc_grad_w1(B, st)) != cudaSuccess) return e;
+  if (fork) {
+    if ((e = cudaEventRecord(ev_join, side)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(st, ev_join, 0)) != cudaSuccess) return e;
+  }
   return tc_adam(lr, st, true);
 }
 
@@ -801,6 +815,18 @@ cudaError_t Surrogate::tc_adam(float lr, cudaStream_t st, bool from_planes) {
 
 cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st, bool sum_planes) {
   cudaError_t e;
+  if ((e = tc_backward_b1(B, st)) != cudaSuccess) return e;
+  if ((e = tc_grad_w2(B, st)) != cudaSuccess) return e;
+  if ((e = tc_grad_w1(B, st)) != cudaSuccess) return e;
+  if (sum_planes) {
+    const long long n12 = (long long)H * D + H + (long long)H * H + H;
+    grad_sum_kernel<<<ceil_div(n12, 256), 256, 0, st>>>(gws, grad_splits, n12, g);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t Surrogate::tc_backward_b1(int B, cudaStream_t st) {
+  cudaError_t e;
   MlpParams a = {};
   a.state = state;
   a.ldt = ldt;
@@ -814,16 +840,24 @@ cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st, bool sum_planes
   a.kblocks = H / 64;
   a.out_t = dZ1Tb;
   a.gp = gp1;
-  e = bn == 128 ? launch_mlp<128, kEpiB1>(a, gm, H / 128, st)
-                : launch_mlp<64, kEpiB1>(a, gm, H / 64, st);
-  if (e != cudaSuccess) return e;
-  // The weight gradients reduce over the batch (K = B): split K into up to
-  // kGradSplits slices, each writing a partial plane laid out like the flat
-  // parameters [W1 | b1 | W2 | b2] (workspace gws), then add the planes in order.
+  return bn == 128 ? launch_mlp<128, kEpiB1>(a, gm, H / 128, st)
+                   : launch_mlp<64, kEpiB1>(a, gm, H / 64, st);
+}
+
+// The weight gradients reduce over the batch (K = B): K is split into up to kGradSplits
+// slices, each writing a partial plane laid out like the flat parameters [W1 | b1 | W2 |
+// b2] (workspace gws); the planes are added in order later (grad_sum_kernel or Adam).
+static void grad_split_plan(int B, int* kblocks, int* kbps, int* splits) {
+  *kblocks = ceil_div(B, 64);
+  *kbps = ceil_div(*kblocks, kGradSplits);
+  *splits = ceil_div(*kblocks, *kbps);
+}
+
+cudaError_t Surrogate::tc_grad_w2(int B, cudaStream_t st) {
+  cudaError_t e;
   const long long n12 = (long long)H * D + H + (long long)H * H + H;
-  const int kblocks = ceil_div(B, 64);
-  const int kbps = ceil_div(kblocks, kGradSplits);
-  const int splits = ceil_div(kblocks, kbps);
+  int kblocks, kbps, splits;
+  grad_split_plan(B, &kblocks, &kbps, &splits);
   grad_splits = splits;
   float *wW1, *wb1, *wW2, *wb2, *ww3, *wb3;
   views(gws, &wW1, &wb1, &wW2, &wb2, &ww3, &wb3);
@@ -841,11 +875,24 @@ cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st, bool sum_planes
   w.g_bias = wb2;
   w.n_main = H;
   w.ld_main = H;
-  if ((e = launch_mlp<128, kEpiGrad>(w, ceil_div(H, 128), ceil_div(H + 1, 128), st, splits)) !=
-      cudaSuccess)
-    return e;
+  return launch_mlp<128, kEpiGrad>(w, ceil_div(H, 128), ceil_div(H + 1, 128), st, splits);
+}
+
+cudaError_t Surrogate::tc_grad_w1(int B, cudaStream_t st) {
+  cudaError_t e;
+  const long long n12 = (long long)H * D + H + (long long)H * H + H;
+  int kblocks, kbps, splits;
+  grad_split_plan(B, &kblocks, &kbps, &splits);
+  grad_splits = splits;
+  float *wW1, *wb1, *wW2, *wb2, *ww3, *wb3;
+  views(gws, &wW1, &wb1, &wW2, &wb2, &ww3, &wb3);
   // [gW1 | gb1] = dZ1^T [X | 1] : A = dZ1^T [H x B], B operand = [X^T ; 1] [(D + 1) x B]
-  MlpParams v = w;
+  MlpParams v = {};
+  v.state = state;
+  v.M = H;
+  v.kblocks = kblocks;
+  v.kbps = kbps;
+  v.zstride = n12;
   if ((e = map_a(v, dZ1Tb, H, B, ldt)) != cudaSuccess) return e;
   if ((e = map_b(v, XTb, D + 1, B, ldt, 128)) != cudaSuccess) return e;
   v.N = D + 1;
@@ -853,11 +900,7 @@ cudaError_t Surrogate::tc_backward_gemms(int B, cudaStream_t st, bool sum_planes
   v.g_bias = wb1;
   v.n_main = D;
   v.ld_main = D;
-  if ((e = launch_mlp<128, kEpiGrad>(v, ceil_div(H, 128), ceil_div(D + 1, 128), st, splits)) !=
-      cudaSuccess)
-    return e;
-  if (sum_planes) grad_sum_kernel<<<ceil_div(n12, 256), 256, 0, st>>>(gws, splits, n12, g);
-  return cudaGetLastError();
+  return launch_mlp<128, kEpiGrad>(v, ceil_div(H, 128), ceil_div(D + 1, 128), st, splits);
 }
 
 }  // namespace game

@@ -10,6 +10,12 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built libgame.so")
+    # Contexts without a tile request read the autotuner's cache file; the tests get a
+    # private one, so that what runs is the default plan unless a test tunes or asks.
+    if "GAME_TUNE_CACHE" not in os.environ:
+        import tempfile
+        os.environ["GAME_TUNE_CACHE"] = os.path.join(tempfile.mkdtemp(prefix="game_tiles_"),
+                                                     "tiles.txt")
 
 
 def pytest_collection_modifyitems(config, items):

@@ -432,6 +432,22 @@ def test_tcgen05_tile_shapes_agree(degree, tile):
                                rtol=FIT_RTOL)
 
 
+def test_fp32_pairs_odd_k_blocks():
+    """The FP32 form's default plan (CTA pairs, two k-blocks per TMA request) on 40
+    features x degree 8 = 320 stored columns: five k-blocks, so the last request is half
+    zero fill; training rows 14,008 (a ragged last tile)."""
+    game = lib()
+    ds = synth.make_dataset(20011, 40, 8, seed=45, correlated=True)
+    ocfg = _cfg(degree=8, pop=512, seed=5)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=game.ENGINE_TCGEN05)
+    got = g.tile()
+    assert (got["cluster"], got["kgroup"]) == (2, 2), got
+    fit, _ = g.evaluate()
+    P = o.expand(ds.X[:ds.n_train], "chebyshev", 8)
+    np.testing.assert_allclose(fit, o.fitness(P, ds.t[:ds.n_train], g.population(), ocfg),
+                               rtol=FIT_RTOL)
+
+
 def test_unplannable_tile_request_runs_the_default_shape():
     """Two FP32 slices per CTA at 256 stored columns need 256 KB of gene planes: the
     request cannot be planned, the default shape runs (and says so), and the fitness is

@@ -149,6 +149,37 @@ def test_low_precision_grouped_k_blocks(fmt, planes, odd):
                                rtol=1e-5)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+@pytest.mark.parametrize("pop", [8, 44, 120])
+def test_small_single_slice_trimmed_gene_tiles(prec, pop):
+    """A population in one 128-row slice keeps only its live gene rows (rounded up to 8)
+    per resident tile; the MMA's other 8-row groups read the shared memory after them and
+    feed only padded chromosomes, and the lane quadrants with no live row skip the
+    epilogue.  8 rows (one group), 44 (a partly padded group, two quadrants) and 120;
+    the fitness of every real chromosome is the oracle's (on the quantised operands for
+    BF16 / FP8).  FP32 populations of up to 32 take the narrow kernel, so pop 8 there
+    runs it instead (and is checked the same way)."""
+    game = lib()
+    ds = synth.make_dataset(30011, 24, 6, seed=47, correlated=True)
+    ocfg = o.Config(degree=6, pop=pop, seed=12)
+    kw = dict(engine=game.ENGINE_TCGEN05, elite_rescore=0)
+    if prec != "fp32":
+        kw.update(precision=_prec(prec), gene_planes=1)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, **kw)
+    G = g.population()
+    fit, _ = g.evaluate()
+    if prec == "fp32":
+        P = o.expand(ds.X[:ds.n_train], "chebyshev", 6)
+        want = o.fitness(P, ds.t[:ds.n_train], G, ocfg)
+    else:
+        Q, s = o.quantize_columns(o.expand(ds.X, "chebyshev", 6)[:, 1:], prec)
+        Pq = np.concatenate([np.ones((ds.n_train, 1)), o.dequantize_columns(Q[:ds.n_train], s)],
+                            axis=1)
+        want = o.fitness(Pq, ds.t[:ds.n_train], o.quantize_genes(G, s, prec, 1), ocfg)
+    assert fit.shape == (pop,) and np.all(np.isfinite(fit))
+    np.testing.assert_allclose(fit, want, rtol=1e-5)
+
+
 @pytest.mark.parametrize("fmt", ["bf16", "fp8"])
 @pytest.mark.parametrize("planes", [1, 2])
 @pytest.mark.parametrize("kgroup", [1, 2])

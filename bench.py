@@ -738,25 +738,26 @@ def timeline(args):
                 raise RuntimeError("reading the timeline failed")
         T = buf.reshape(8, 32, 8)
         nkb = {"fp32": 4, "bf16": 4, "fp8": 2}[name]
+        ks = list(range(0, nkb, max(1, tile.get("kgroup", 1))))   # stamped: one per ring stage
         ran = [it for it in range(32) if T[2, it, 0] != 0]      # tiles CTA 0 ran
         n = min(args.timeline_tiles, len(ran))
         t0 = T[2, 0, 0]
         print(f"{name}: tile {tile}, CTA 0 ran {len(ran)} stamped tiles")
-        print("tile | producer issues k-block 0..   | MMA past ring wait k-block 0..  "
+        print("tile | producer issues stage (k-block) .. | MMA past ring wait .. "
               "| MMA start  commit | epi w2 start end | epi w17 start end")
         for it in range(n):
             rel = lambda e, k=0: int(T[e, it, k] - t0)
             print("%4d | %s | %s | %6d %6d | %6d %6d | %6d %6d" % (
-                it, " ".join("%6d" % rel(0, k) for k in range(nkb)),
-                " ".join("%6d" % rel(1, k) for k in range(nkb)),
+                it, " ".join("%6d" % rel(0, k) for k in ks),
+                " ".join("%6d" % rel(1, k) for k in ks),
                 rel(2), rel(3), rel(4), rel(5), rel(6), rel(7)), flush=True)
         if n > 3:
             period = np.diff(T[2, 2:n, 0]).mean()
-            gaps = np.diff(T[1, 2:n, :nkb], axis=1).mean()
+            gaps = np.diff(T[1, 2:n][:, ks], axis=1).mean() if len(ks) > 1 else float("nan")
             epi = (T[5, 2:n, 0] - T[4, 2:n, 0]).mean()
-            print(f"{name}: tile period {period:.0f} cycles, MMA ring waits {gaps:.0f} cycles "
-                  f"apart within a tile, epilogue warp 2 busy {epi:.0f} cycles per tile\n",
-                  flush=True)
+            print(f"{name}: tile period {period:.0f} cycles, MMA ring waits (first plane of each "
+                  f"stage) {gaps:.0f} cycles apart within a tile, epilogue warp 2 busy "
+                  f"{epi:.0f} cycles per tile\n", flush=True)
 
 
 def engine_table(args):

@@ -66,9 +66,12 @@ enum { GAME_FP32 = 0, GAME_BF16 = 1, GAME_FP8 = 2 };              /* storage of 
 /* Fitness engine.  TCGEN05: the tensor-core contraction (128-chromosome tiles, or
  * for at most 32 FP32 chromosomes the kernel with patterns on the MMA's M side).
  * SIMT: CUDA-core FMAs (for at most 32 chromosomes on 16 or 32 stored columns, one
- * pattern per thread).  ON_THE_FLY: CUDA-core FMAs on slabs of the expansion formed
- * in shared memory from the features, so that the expansion matrix is never stored
- * (device memory of X instead of P; FP32 form only, no surrogate, not in batches).
+ * pattern per thread).  ON_THE_FLY: the expansion matrix is never stored (device
+ * memory of X instead of P; FP32 form only, no surrogate, not in batches): with
+ * per-feature coefficients, warps of the tensor-core kernel form each k-block of P in
+ * shared memory from the features for the MMAs; with shared coefficients (or genes
+ * beyond what that kernel keeps in shared memory), CUDA-core FMAs on slabs formed the
+ * same way.
  * AUTO: SIMT for the narrow shapes (the paper's own population of 2N + 1) and where
  * the genes exceed what the tensor-core kernels keep in shared memory, TCGEN05
  * otherwise; ON_THE_FLY only when the stored FP32 planes would not fit in the

@@ -45,6 +45,8 @@ struct game_ctx {
   double* d_partial = nullptr;
   int n_part = 0;          // partial rows used by the engine in use
   int part_rows = 0;       // partial rows allocated
+  OtfTcPlan otf_tc;        // on-the-fly engine: the tensor-core kernel's plan ...
+  bool otf_tc_ok = false;  // ... when it takes the shape (else the CUDA-core kernel)
   DevState* d_state = nullptr;
   float* d_scratch = nullptr;   // expansion column maxima
   double* d_score_blocks = nullptr;
@@ -320,6 +322,7 @@ extern "C" game_status game_create(const game_config* cfg, game_ctx** out) {
   cudaSetDevice(c->dev);
   cudaError_t e = ga_init_attributes();
   if (e == cudaSuccess) e = tc_init_attributes();
+  if (e == cudaSuccess) e = otf_tc_init_attributes();
   if (e == cudaSuccess) e = batch_init_attributes();
   if (e == cudaSuccess) e = surrogate_ga_init_attributes();
   if (e == cudaSuccess) e = surrogate_tc_init_attributes();
@@ -415,7 +418,11 @@ static game_status choose_engine(game_ctx* c, Shape& s, const ExpDev& e, const P
                                  int* engine, TcPlan* plan, int* n_part) {
   if (c->otf) {
     *engine = GAME_ENGINE_ON_THE_FLY;
-    *n_part = otf_partials(s, c->n_sm);
+    // the tensor-core form where it takes the shape (FP32, per-feature coefficients,
+    // the gene planes and two ring stages in shared memory), else the CUDA-core one
+    c->otf_tc_ok = otf_tc_supported(s) && otf_tc_plan(s, p, c->n_sm, &c->otf_tc) == cudaSuccess;
+    if (!c->otf_tc_ok) cudaGetLastError();
+    *n_part = c->otf_tc_ok ? c->otf_tc.cps : otf_partials(s, c->n_sm);
     return GAME_OK;
   }
   int want = c->cfg.engine;
@@ -814,6 +821,9 @@ extern "C" game_status game_set_data(game_ctx* c, const float* X, const float* t
 static game_status launch_fitness(game_ctx* c, const DevState* state) {
   if (c->engine == GAME_ENGINE_TCGEN05) {
     CUDA_OK(c, tc_launch(c->tc, c->s, c->fit, c->p, c->e, c->d_partial, state, c->st));
+  } else if (c->engine == GAME_ENGINE_ON_THE_FLY && c->otf_tc_ok) {
+    CUDA_OK(c, otf_tc_launch(c->otf_tc, c->s, c->fit, c->p, c->e, c->d_X, c->d_partial, c->d_state,
+                             state != nullptr, c->st));
   } else if (c->engine == GAME_ENGINE_ON_THE_FLY) {
     CUDA_OK(c, launch_fitness_otf(c->s, c->fit, c->p, c->d_X, c->e, c->d_partial, c->n_part, state,
                                   c->st));

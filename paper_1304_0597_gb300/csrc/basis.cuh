@@ -192,3 +192,110 @@ __device__ __forceinline__ void basis_range(int basis, int d, float x, int b_lo,
 }
 
 }  // namespace game
+
+namespace game {
+
+// One 16-byte chunk of a pattern's FP32 expansion planes: the basis columns
+// [col0, col0 + 8) (zero from kb on) of the pattern whose features start at x, divided
+// by their power-of-two column scales (skipped when every scale is 1), each value v
+// split as hi = fp16(v), lo = fp16(v - hi).  hi[i] / lo[i] hold columns col0 + 2i (low
+// half) and col0 + 2i + 1 (high half), the stored planes' byte order.  The same
+// recurrences and rounding as the stored expansion, so the halves are the stored ones.
+__device__ __forceinline__ void fp32_planes_chunk(const float* __restrict__ x, int basis, int d,
+                                                  int bd, int kb, int col0,
+                                                  const float* __restrict__ colscale,
+                                                  bool unit_scale, uint32_t hi[4], uint32_t lo[4]) {
+  float v[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = 0.0f;
+  int n = 0;   // values written so far
+  const int c_end = min(col0 + 8, kb);
+  int col = col0;
+  while (col < c_end) {
+    const int f = col / bd;
+    const int b_lo = col - f * bd;
+    const int b_hi = min(bd, c_end - f * bd);
+    basis_range(basis, d, __ldg(x + f), b_lo, b_hi, [&](float val) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j == n) v[j] = val;
+      ++n;
+    });
+    col = f * bd + b_hi;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float a = v[2 * i], b = v[2 * i + 1];
+    if (!unit_scale) {
+      if (col0 + 2 * i < kb) a = a * (1.0f / __ldg(colscale + col0 + 2 * i));
+      if (col0 + 2 * i + 1 < kb) b = b * (1.0f / __ldg(colscale + col0 + 2 * i + 1));
+    }
+    const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+    const __half la = __float2half_rn(__fsub_rn(a, __half2float(ha)));
+    const __half lb = __float2half_rn(__fsub_rn(b, __half2float(hb)));
+    hi[i] = (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
+    lo[i] = (uint32_t)__half_as_ushort(la) | ((uint32_t)__half_as_ushort(lb) << 16);
+  }
+}
+
+}  // namespace game
+
+namespace game {
+
+// T_{b0+1}(x) .. T_{b0+8}(x) for N patterns at once (N independent float-float
+// recurrences advanced in the same loop, so that their latencies overlap): the same
+// arithmetic, step by step, as the stored expansion's Chebyshev kernels.
+template <int N>
+__device__ __forceinline__ void cheb8_rows(const float (&x)[N], int b0, float (&v)[N][8]) {
+  float y[N], mh[N], ml[N], th[N], tl[N];
+#pragma unroll
+  for (int u = 0; u < N; ++u) {
+    y[u] = __fmul_rn(2.0f, x[u]);
+    mh[u] = 1.0f;
+    ml[u] = 0.0f;
+    th[u] = x[u];
+    tl[u] = 0.0f;
+  }
+  auto step = [&](int u) {
+    float p, pe, s2, se;
+    two_prod(y[u], th[u], p, pe);
+    two_sum(p, -mh[u], s2, se);
+    const float low = __fsub_rn(__fadd_rn(__fadd_rn(se, pe), __fmul_rn(y[u], tl[u])), ml[u]);
+    const float nh = __fadd_rn(s2, low);
+    const float nl = __fsub_rn(low, __fsub_rn(nh, s2));
+    mh[u] = th[u];
+    ml[u] = tl[u];
+    th[u] = nh;
+    tl[u] = nl;
+  };
+  for (int b = 0; b < b0; ++b) {
+#pragma unroll
+    for (int u = 0; u < N; ++u) step(u);
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+#pragma unroll
+    for (int u = 0; u < N; ++u) {
+      v[u][j] = __fadd_rn(th[u], tl[u]);
+      if (j + 1 < 8) step(u);
+    }
+  }
+}
+
+// hi / lo fp16 planes of 8 consecutive float32 values (times the column scales' inverses
+// inv[j], powers of two), packed as the stored planes are.
+__device__ __forceinline__ void fp32_split8(const float (&v)[8], const float (&inv)[8],
+                                            bool unit_scale, uint32_t hi[4], uint32_t lo[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float a = unit_scale ? v[2 * i] : v[2 * i] * inv[2 * i];
+    const float b = unit_scale ? v[2 * i + 1] : v[2 * i + 1] * inv[2 * i + 1];
+    const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+    const __half la = __float2half_rn(__fsub_rn(a, __half2float(ha)));
+    const __half lb = __float2half_rn(__fsub_rn(b, __half2float(hb)));
+    hi[i] = (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
+    lo[i] = (uint32_t)__half_as_ushort(la) | ((uint32_t)__half_as_ushort(lb) << 16);
+  }
+}
+
+}  // namespace game

@@ -65,6 +65,23 @@ cudaError_t tc_timeout_selftest(DevState* st, unsigned long long wait_ns, int* o
 cudaError_t tc_make_map(CUtensorMap* m, const void* base, int precision, long long rows, int cols,
                         int box_rows);
 
+// ---- on-the-fly tensor-core engine (fitness_tc_otf.cu) ------------------------
+// The FP32 form with per-feature coefficients: expansion warps form each k-block of P
+// in shared memory from X, the MMA warp contracts it with the resident gene planes.
+struct OtfTcPlan {
+  CUtensorMap a_map[2];   // gene planes (hi, lo)
+  int kblocks = 0, stages = 0, cps = 0, grid = 0, n_tiles = 0;
+  size_t smem = 0;
+};
+bool otf_tc_supported(const Shape& s);
+cudaError_t otf_tc_plan(const Shape& s, const PopDev& p, int n_sm, OtfTcPlan* plan);
+// dev_state: the context's device state (timeouts are recorded there; with in_evolve
+// the launch returns at once once the run has stopped); partial rows [plan.cps x pop_pad]
+cudaError_t otf_tc_launch(const OtfTcPlan& t, const Shape& s, const Fitness& f, const PopDev& p,
+                          const ExpDev& e, const float* X, double* partial, DevState* dev_state,
+                          int in_evolve, cudaStream_t st);
+cudaError_t otf_tc_init_attributes();
+
 // ---- batched form: many runs in one persistent grouped launch ----------------
 
 // Everything the grouped kernel needs about one run (device-resident; the tensor

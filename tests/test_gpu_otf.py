@@ -39,6 +39,20 @@ def test_otf_fitness_matches_oracle(basis, F, d, pop, n):
     np.testing.assert_array_equal(rank, o.rank(fit))
 
 
+def test_otf_features_beyond_unit_interval():
+    """Chebyshev features to +-3 at d = 8 (T_8 reaches 6.7e5): the FP32 planes' power-of-two
+    column scales apply to the tiles formed in shared memory as to the stored planes;
+    16 features x 8 = whole 8-column chunks (the tensor-core kernel's Chebyshev path)."""
+    ds = synth.make_dataset(20011, 16, 8, seed=73)
+    X = (ds.X * 3.0).astype(np.float32)
+    ocfg = o.Config(degree=8, pop=256, seed=5)
+    g = _otf(ocfg, X, ds.t, ds.n_train)
+    fit, _ = g.evaluate()
+    P = o.expand(X[:ds.n_train], "chebyshev", 8)
+    np.testing.assert_allclose(fit, o.fitness(P, ds.t[:ds.n_train], g.population(), ocfg),
+                               rtol=FIT_RTOL)
+
+
 @pytest.mark.parametrize("err,act", [("mse", "tanh"), ("tmse", "linear"), ("rmse", "linear")])
 def test_otf_error_forms_and_shared_coefficients(err, act):
     """The paper's own form: shared polytrigo coefficients (eq.9), 0/1 targets."""

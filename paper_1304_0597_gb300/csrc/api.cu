@@ -322,6 +322,7 @@ extern "C" game_status game_create(const game_config* cfg, game_ctx** out) {
   cudaSetDevice(c->dev);
   cudaError_t e = ga_init_attributes();
   if (e == cudaSuccess) e = tc_init_attributes();
+  if (e == cudaSuccess) e = simt_init_attributes();
   if (e == cudaSuccess) e = otf_tc_init_attributes();
   if (e == cudaSuccess) e = batch_init_attributes();
   if (e == cudaSuccess) e = surrogate_ga_init_attributes();
@@ -828,7 +829,8 @@ static game_status launch_fitness(game_ctx* c, const DevState* state) {
     CUDA_OK(c, launch_fitness_otf(c->s, c->fit, c->p, c->d_X, c->e, c->d_partial, c->n_part, state,
                                   c->st));
   } else {
-    CUDA_OK(c, launch_fitness_simt(c->s, c->fit, c->p, c->e, c->d_partial, c->n_part, state, c->st));
+    CUDA_OK(c, launch_fitness_simt(c->s, c->fit, c->p, c->e, c->d_partial, c->n_part, state,
+                                   c->d_state, c->st));
   }
   return GAME_OK;
 }
@@ -844,7 +846,7 @@ static game_status enqueue_rescore(game_ctx* c, int in_evolve) {
     CUDA_OK(c, tc_launch(c->tc_r, c->sr, c->fit, c->pr, c->e32, c->d_partial_r, st, c->st));
   } else {
     CUDA_OK(c, launch_fitness_simt(c->sr, c->fit, c->pr, c->e32, c->d_partial_r, c->n_part_r, st,
-                                   c->st));
+                                   c->d_state, c->st));
   }
   CUDA_OK(c, launch_rescore_merge(c->sr, c->cfg, c->d_partial_r, c->n_part_r, c->d_rank, c->d_fit,
                                   c->d_state, in_evolve, c->st));

@@ -186,9 +186,12 @@ __device__ __forceinline__ double sum_partials(const double* __restrict__ partia
 // kp 16 or 32), which the automatic engine choice prefers to the tensor cores.
 bool simt_narrow(const Shape& s);
 int simt_partials(const Shape& s, int n_sm);
+// state: read (stop flag) only inside game_evolve, else null; dev_state: the
+// context's device state, where a timed-out wait records its status.
 cudaError_t launch_fitness_simt(const Shape& s, const Fitness& f, const PopDev& p,
                                 const ExpDev& e, double* partial, int n_part,
-                                const DevState* state, cudaStream_t st);
+                                const DevState* state, DevState* dev_state, cudaStream_t st);
+cudaError_t simt_init_attributes();   // the narrow kernel's shared-memory ring
 
 // On-the-fly engine (fitness_otf.cu): P formed per tile from the features X, never
 // stored.  Same partial-sum layout as the SIMT engine, otf_partials rows.

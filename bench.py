@@ -55,6 +55,9 @@ def parse():
                     help="keep the library's default tile (no trial launches before the steps)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the BF16 / FP8 precision-form record of the default line")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="skip the one-seed learned-surrogate time-to-target record of the "
+                         "default line")
     ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="fp32")
     ap.add_argument("--gene-planes", type=int, choices=[1, 2], default=2,
                     help="low precision: genes as one or two terms of P's format")
@@ -470,6 +473,8 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and args.precision == "fp32" and not args.no_forms:
         line["forms"] = forms_record(ds, X_pin, t_pin, stream, K, W, bf16_tf)
+    if rank == 0 and world == 1 and args.precision == "fp32" and not args.no_surrogate:
+        line["surrogate"] = surrogate_record()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_record(args.cpu_seconds)
     g.close()
@@ -570,6 +575,71 @@ def batched(args):
     print(json.dumps(line), flush=True)
 
 
+def ttt_seed(ds, seed, budget, contenders, tuned):
+    """One seed of the time-to-target comparison on the learned-surrogate workload: the
+    plain FP32 GA runs `budget` generations and sets the target (its final best train
+    RMSE); each contender runs in steps of 5 generations until it reaches the target (at
+    most 2 x budget).  Device time from the library's CUDA events around each generation."""
+    from paper_1304_0597_gb300 import game
+
+    def make(**kw):
+        g = game.Game(game.default_config(degree=6, pop=4096, seed=seed, **kw))
+        g.set_data(ds.X, ds.t, ds.n_train)
+        key = (kw.get("precision", game.FP32), kw.get("gene_planes", 2))
+        if key not in tuned and g.timing()["engine"] == game.ENGINE_TCGEN05:
+            g.autotune(reps=2)      # the tile cache serves the later contexts
+            tuned.add(key)
+        g.set_timing(False)
+        return g
+
+    plain = make()
+    plain.evolve(budget)
+    t_plain = plain.timing()["ms_total"]
+    _, target, _, acc_plain = plain.best()
+    plain.close()
+    row = {"seed": seed, "target_rmse": target, "plain_fp32": {"ms": t_plain,
+           "generations": budget, "test_accuracy": acc_plain}}
+    for name, kw in contenders:
+        g = make(**kw)
+        ms, gens, hit = 0.0, 0, False
+        while gens < 2 * budget:
+            g.evolve(5)
+            ms += g.timing()["ms_total"]
+            gens += 5
+            _, best, _, acc = g.best()
+            if best <= target:
+                hit = True
+                break
+        rec = {"ms": ms, "generations": gens, "reached": hit, "best_rmse": best,
+               "test_accuracy": acc, "speedup_vs_plain": t_plain / ms if hit else None}
+        if kw.get("surrogate_pool"):
+            rho = g.surrogate_monitor()["history"]
+            rec["spearman_mean"] = float(np.nanmean(rho)) if len(rho) else None
+        row[name] = rec
+        g.close()
+    return row
+
+
+def surrogate_record(budget: int = 200) -> dict:
+    """The learned-surrogate form for the default line: one seed (0) of the time-to-target
+    comparison, plain FP32 GA against surrogate + FP8 P (8x pool, top-16 elites re-scored in
+    FP32), on the 2,000,000 x 48 (Chebyshev d=6, pop 4096) workload."""
+    from paper_1304_0597_gb300 import game, synth
+    ds = synth.surrogate_scale(n_patterns=2_000_000)
+    contenders = (("surrogate_fp8", dict(surrogate_pool=8, precision=game.FP8, gene_planes=1,
+                                         elite_rescore=16)),)
+    row = ttt_seed(ds, 0, budget, contenders, set())
+    sur = row["surrogate_fp8"]
+    return {"workload": "learned-surrogate form: 2,000,000 patterns x 48 features, Chebyshev "
+                        "d=6, 289 genes, pop 4096, 8x pool, MLP 289-256-256-1",
+            "seed": 0, "budget_generations": budget, "target_rmse": row["target_rmse"],
+            "plain_fp32": row["plain_fp32"], "surrogate_fp8": sur,
+            "time_to_target_speedup": sur["speedup_vs_plain"],
+            "test_accuracy_delta": sur["test_accuracy"] - row["plain_fp32"]["test_accuracy"],
+            "note": "one seed; bench.py --surrogate gives the median over seeds and the other "
+                    "contenders"}
+
+
 def surrogate_ttt(args):
     """Time to target RMSE on 2,000,000 patterns x 48 features (Chebyshev d=6, 289 genes),
     population 4096.  Target = final best train RMSE of the plain FP32 GA after --budget
@@ -578,7 +648,6 @@ def surrogate_ttt(args):
     re-scored in FP32); the same with a 4x pool; FP8 P alone (no surrogate); and the
     ablation (plain children of the same 8x pools) for the gain of the network itself.
     Every contender is timed on the device (CUDA events around each generation)."""
-    import torch
     from paper_1304_0597_gb300 import game, synth
     ds = synth.surrogate_scale(n_patterns=args.n_patterns if args.n_patterns != 1_000_000
                                else 2_000_000)
@@ -592,43 +661,8 @@ def surrogate_ttt(args):
     )
     tuned = set()
     results = []
-    base = dict(degree=6, pop=4096)
     for seed in range(args.seeds):
-        def make(**kw):
-            g = game.Game(game.default_config(**base, seed=seed, **kw))
-            g.set_data(ds.X, ds.t, ds.n_train)
-            key = (kw.get("precision", game.FP32), kw.get("gene_planes", 2))
-            if key not in tuned and g.timing()["engine"] == game.ENGINE_TCGEN05:
-                g.autotune(reps=2)      # the tile cache serves the later contexts
-                tuned.add(key)
-            g.set_timing(False)
-            return g
-
-        plain = make()
-        plain.evolve(args.budget)
-        t_plain = plain.timing()["ms_total"]
-        _, target, _, acc_plain = plain.best()
-        plain.close()
-        row = {"seed": seed, "target_rmse": target, "plain_fp32": {"ms": t_plain,
-               "generations": args.budget, "test_accuracy": acc_plain}}
-        for name, kw in contenders:
-            g = make(**kw)
-            ms, gens, hit = 0.0, 0, False
-            while gens < 2 * args.budget:
-                g.evolve(5)
-                ms += g.timing()["ms_total"]
-                gens += 5
-                _, best, _, acc = g.best()
-                if best <= target:
-                    hit = True
-                    break
-            rec = {"ms": ms, "generations": gens, "reached": hit, "best_rmse": best,
-                   "test_accuracy": acc, "speedup_vs_plain": t_plain / ms if hit else None}
-            if kw.get("surrogate_pool"):
-                rho = g.surrogate_monitor()["history"]
-                rec["spearman_mean"] = float(np.nanmean(rho)) if len(rho) else None
-            row[name] = rec
-            g.close()
+        row = ttt_seed(ds, seed, args.budget, contenders, tuned)
         results.append(row)
         print(json.dumps(row), flush=True)
 

@@ -71,8 +71,14 @@ def _hidden(rng: np.random.Generator, X: np.ndarray, basis: str, degree: int) ->
         else:
             a = rng.uniform(-1.0, 1.0, size=degree)
             b = rng.uniform(-1.0, 1.0, size=degree)
+            # cos(kx), sin(kx) by angle addition from cos x, sin x (float64; the
+            # values agree with np.cos(k x) / np.sin(k x) to ~1e-15)
+            c1, s1 = np.cos(x), np.sin(x)
+            ck, sk = c1, s1
             for k in range(1, degree + 1):
-                v += a[k - 1] * np.cos(k * x) + b[k - 1] * np.sin(k * x)
+                if k > 1:
+                    ck, sk = ck * c1 - sk * s1, sk * c1 + ck * s1
+                v += a[k - 1] * ck + b[k - 1] * sk
     return v
 
 

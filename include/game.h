@@ -65,8 +65,9 @@ enum { GAME_SEL_TOURNAMENT = 0, GAME_SEL_ROULETTE = 1, GAME_SEL_RANKING = 2 };  
 enum { GAME_FP32 = 0, GAME_BF16 = 1, GAME_FP8 = 2 };              /* storage of P    */
 /* Fitness engine.  TCGEN05: the tensor-core contraction (128-chromosome tiles, or
  * for at most 32 FP32 chromosomes the kernel with patterns on the MMA's M side).
- * SIMT: CUDA-core FMAs (for at most 32 chromosomes on 16 or 32 stored columns, one
- * pattern per thread).  ON_THE_FLY: the expansion matrix is never stored (device
+ * SIMT: no tcgen05.  For at most 32 chromosomes on 16 or 32 stored columns, the
+ * narrow kernels (FP32 on warp-level MMAs, BF16 / FP8 on CUDA-core FMAs); otherwise
+ * CUDA-core FMA tiles.  ON_THE_FLY: the expansion matrix is never stored (device
  * memory of X instead of P; FP32 form only, no surrogate, not in batches): with
  * per-feature coefficients, warps of the tensor-core kernel form each k-block of P in
  * shared memory from the features for the MMAs; with shared coefficients (or genes
@@ -387,9 +388,9 @@ void game_batch_destroy(game_batch* b);
 /* ---- fitness without device allocation ------------------------------------ */
 
 /* Population fitness for callers that cannot allocate device memory.  The
- * paper has no counterpart: this is a packaging of the fitness step (the same
- * float32 CUDA-core kernel as GAME_ENGINE_SIMT) for code that must not call
- * cudaMalloc -- a service whose device memory is a fixed arena owned by another
+ * paper has no counterpart: this is a packaging of the fitness step (float32
+ * CUDA-core tiles, as in the tiled kernel of GAME_ENGINE_SIMT) for code that must
+ * not call cudaMalloc -- a service whose device memory is a fixed arena owned by another
  * allocator, a plugin inside a program that owns every device allocation, or a
  * latency-critical path that cannot afford cudaMalloc's device-wide
  * synchronisation.  It calls no cudaMalloc, cudaFree or allocating library

@@ -462,19 +462,13 @@ __device__ __forceinline__ unsigned long long mma_error2(const float d0, const f
     return tc::add2(acc, tc::pack2(u0, u1));
   }
   const unsigned long long dd = tc::fma2(tc::pack2(d0, d1), nr2, tc::pack2(t, t));   // t - Out
-  if (ERR == GAME_TMSE || ERR == GAME_TMSE_SQ) {   // a compare and a predicated add each
-    float x0, x1, a0, a1;
+  if (ERR == GAME_TMSE || ERR == GAME_TMSE_SQ) {   // branch-free: d, or 0 below the threshold
+    float x0, x1;
     tc::unpack2(dd, x0, x1);
-    tc::unpack2(acc, a0, a1);
-    if (ERR == GAME_TMSE) {
-      if (fabsf(x0) > R) a0 = fmaf(x0, x0, a0);
-      if (fabsf(x1) > R) a1 = fmaf(x1, x1, a1);
-    } else {
-      const float e0 = x0 * x0, e1 = x1 * x1;
-      if (e0 > R) a0 += e0;
-      if (e1 > R) a1 += e1;
-    }
-    return tc::pack2(a0, a1);
+    const bool k0 = ERR == GAME_TMSE_SQ ? x0 * x0 > R : fabsf(x0) > R;
+    const bool k1 = ERR == GAME_TMSE_SQ ? x1 * x1 > R : fabsf(x1) > R;
+    const unsigned long long z = tc::pack2(k0 ? x0 : 0.0f, k1 ? x1 : 0.0f);
+    return tc::fma2(z, z, acc);
   }
   return tc::fma2(dd, dd, acc);
 }
@@ -582,12 +576,21 @@ __global__ void __launch_bounds__(kNarrowThreads, 2) fitness_narrow_mma_kernel(S
           al[mb][ks][h] = *reinterpret_cast<const uint2*>(sp + (W + r) * RB + 32 * ks + 8 * qi);
         }
       }
+    }
+    if (full) {   // targets: from the stage, or for the ragged last pass from global memory
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int rr = 16 * mb + gq + 8 * h;
-        t[mb][h] = full ? reinterpret_cast<const float*>(sp + 2 * W * RB)[rr]
-                        : (k0 + rr < a.m ? a.t[k0 + rr] : 0.0f);
-      }
+      for (int mb = 0; mb < MB; ++mb)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          t[mb][h] = reinterpret_cast<const float*>(sp + 2 * W * RB)[16 * mb + gq + 8 * h];
+    } else {
+#pragma unroll
+      for (int mb = 0; mb < MB; ++mb)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int rr = 16 * mb + gq + 8 * h;
+          t[mb][h] = k0 + rr < a.m ? a.t[k0 + rr] : 0.0f;
+        }
     }
     stage = stage + 1 == kNarrowStages ? 0 : stage + 1;
 
@@ -605,12 +608,20 @@ __global__ void __launch_bounds__(kNarrowThreads, 2) fitness_narrow_mma_kernel(S
           mma_f16_16816(d[nb], ah[mb][ks][0], ah[mb][ks][1], bl[nb][ks]);
           mma_f16_16816(d[nb], al[mb][ks][0], al[mb][ks][1], bh[nb][ks]);
         }
-      const bool v0 = full || k0 + 16 * mb + gq < a.m;
-      const bool v1 = full || k0 + 16 * mb + gq + 8 < a.m;
+      if (full) {   // every pass but the last: no row checks
 #pragma unroll
-      for (int nb = 0; nb < NB; ++nb) {
-        if (v0) acc[nb] = mma_error2<ERR, TANH>(d[nb][0], d[nb][1], nr2[nb], t[mb][0], a.R, acc[nb]);
-        if (v1) acc[nb] = mma_error2<ERR, TANH>(d[nb][2], d[nb][3], nr2[nb], t[mb][1], a.R, acc[nb]);
+        for (int nb = 0; nb < NB; ++nb) {
+          acc[nb] = mma_error2<ERR, TANH>(d[nb][0], d[nb][1], nr2[nb], t[mb][0], a.R, acc[nb]);
+          acc[nb] = mma_error2<ERR, TANH>(d[nb][2], d[nb][3], nr2[nb], t[mb][1], a.R, acc[nb]);
+        }
+      } else {
+        const bool v0 = k0 + 16 * mb + gq < a.m;
+        const bool v1 = k0 + 16 * mb + gq + 8 < a.m;
+#pragma unroll
+        for (int nb = 0; nb < NB; ++nb) {
+          if (v0) acc[nb] = mma_error2<ERR, TANH>(d[nb][0], d[nb][1], nr2[nb], t[mb][0], a.R, acc[nb]);
+          if (v1) acc[nb] = mma_error2<ERR, TANH>(d[nb][2], d[nb][3], nr2[nb], t[mb][1], a.R, acc[nb]);
+        }
       }
     }
     __syncwarp();   // the stage's values are used: refill it with the pass kNarrowStages ahead

@@ -45,7 +45,7 @@ def test_batch_matches_single_runs():
     gens = b.evolve(5)
     assert list(gens) == [5] * len(specs)
     for i, (ds, ocfg, cfg) in enumerate(specs):
-        # the 20-chromosome run alone would take the narrow SIMT kernel: ask for the
+        # the 20-chromosome run alone would take the narrow kernels: ask for the
         # tensor cores, as in the grouped launch (801 genes stay on SIMT either way)
         eng = game.ENGINE_TCGEN05 if ocfg.pop <= 32 else game.ENGINE_AUTO
         single = game.Game(game_config(ocfg, precision=cfg.precision,

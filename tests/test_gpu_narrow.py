@@ -44,7 +44,7 @@ def test_narrow_fitness_matches_oracle(shape, engine):
     eng = {"auto": game.ENGINE_AUTO, "simt": game.ENGINE_SIMT,
            "tcgen05": game.ENGINE_TCGEN05}[engine]
     g = make_game(ocfg, ds.X, ds.t, ds.n_train, engine=eng)
-    # 16 / 32 stored columns: the automatic choice is the narrow SIMT kernel
+    # 16 / 32 stored columns: the automatic choice is the narrow kernels (fitness_narrow.cu)
     assert g.timing()["engine"] == (game.ENGINE_TCGEN05 if engine == "tcgen05" else game.ENGINE_SIMT)
     G = g.population()
     fit, rank = g.evaluate()
@@ -110,7 +110,7 @@ def test_narrow_many_blocks_per_thread(engine):
 
 
 def test_narrow_engines_agree():
-    """The swapped tensor-core kernel and the narrow SIMT kernel give the same fitness
+    """The swapped tensor-core kernel and the narrow kernel give the same fitness
     to 2e-5 (each within 1e-5 of the oracle)."""
     game = lib()
     ds = synth.make_dataset(9000, 6, 4, seed=31)

@@ -493,33 +493,37 @@ def run_ours(args):
 def precision_table(args):
     """Fitness error against the float64 report, and test accuracy, per storage precision
     (the plain small workload: 2,000 x 7, Chebyshev d=4, pop 20, 100 generations; top-16
-    elites re-scored in FP32 for BF16 / FP8)."""
-    import torch
+    elites re-scored in FP32 for BF16 / FP8), on the automatic engine (for this population
+    of 20 the narrow kernels, whose BF16 / FP8 form keeps the genes in float32) and on the
+    tensor-core engine (genes in 1 or 2 planes of P's format)."""
     from paper_1304_0597_gb300 import game, synth
     ds = synth.plain_small()
     rows = []
-    for name, prec in (("fp32", game.FP32), ("bf16", game.BF16), ("fp8", game.FP8)):
-        for rescore, planes in (((0, 2),) if prec == game.FP32 else
-                                ((0, 2), (16, 2), (0, 1), (16, 1))):
-            g = game.Game(game.default_config(degree=4, pop=20, seed=0, precision=prec,
-                                              elite_rescore=rescore, gene_planes=planes))
-            g.set_data(ds.X, ds.t, ds.n_train)
-            G = g.population()
-            fit, _ = g.evaluate()
-            exact = np.array([g.score(G[i], 0)["rmse"] for i in range(20)])
-            rel = np.abs(fit - exact) / exact
-            g.set_timing(True)
-            g.evolve(100)
-            tm = g.timing()
-            genes, fbest, test_rmse, acc = g.best()
-            exact_best = g.score(genes, 0)["rmse"]
-            rows.append({"precision": name, "elite_rescore": rescore, "gene_planes": planes,
-                         "gen0_fitness_rel_err_vs_fp64": {"max": float(rel.max()),
-                                                          "median": float(np.median(rel))},
-                         "best_train_rmse_reported": fbest, "best_train_rmse_fp64": exact_best,
-                         "test_rmse": test_rmse, "test_accuracy": acc,
-                         "ms_per_generation": tm["ms_total"] / 100})
-            g.close()
+    for ename, eng in (("auto", game.ENGINE_AUTO), ("tcgen05", game.ENGINE_TCGEN05)):
+        for name, prec in (("fp32", game.FP32), ("bf16", game.BF16), ("fp8", game.FP8)):
+            for rescore, planes in (((0, 2),) if prec == game.FP32 else
+                                    ((0, 2), (16, 2), (0, 1), (16, 1))):
+                g = game.Game(game.default_config(degree=4, pop=20, seed=0, precision=prec,
+                                                  elite_rescore=rescore, gene_planes=planes,
+                                                  engine=eng))
+                g.set_data(ds.X, ds.t, ds.n_train)
+                G = g.population()
+                fit, _ = g.evaluate()
+                exact = np.array([g.score(G[i], 0)["rmse"] for i in range(20)])
+                rel = np.abs(fit - exact) / exact
+                g.set_timing(True)
+                g.evolve(100)
+                tm = g.timing()
+                genes, fbest, test_rmse, acc = g.best()
+                exact_best = g.score(genes, 0)["rmse"]
+                rows.append({"engine": ename, "precision": name, "elite_rescore": rescore,
+                             "gene_planes": planes,
+                             "gen0_fitness_rel_err_vs_fp64": {"max": float(rel.max()),
+                                                              "median": float(np.median(rel))},
+                             "best_train_rmse_reported": fbest, "best_train_rmse_fp64": exact_best,
+                             "test_rmse": test_rmse, "test_accuracy": acc,
+                             "ms_per_generation": tm["ms_total"] / 100})
+                g.close()
     print(json.dumps({"table": "precision form on the plain small workload", "rows": rows}))
 
 

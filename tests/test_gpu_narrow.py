@@ -30,6 +30,7 @@ def _cfg(**kw):
 
 @pytest.mark.parametrize("shape", [
     dict(n=5003, F=5, d=3, pop=23, basis="chebyshev"),   # 15 columns -> 16 stored, ragged rows
+    dict(n=6007, F=4, d=4, pop=29, basis="chebyshev"),   # 16 columns, 25-32 chromosomes
     dict(n=4099, F=8, d=4, pop=32, basis="chebyshev"),   # 32 columns, a full warp of chromosomes
     dict(n=3001, F=7, d=4, pop=2, basis="chebyshev"),    # the smallest population
     dict(n=777, F=3, d=5, pop=9, basis="trig"),          # 30 columns, fewer rows than one CTA

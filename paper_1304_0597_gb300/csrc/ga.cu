@@ -195,7 +195,12 @@ __global__ void __launch_bounds__(1024) selection_weights_kernel(const double* f
 cudaError_t launch_selection_weights(const game_config& cfg, const Shape& s, const double* fit,
                                      const int* rank, unsigned long long* cum, cudaStream_t st) {
   if (cfg.selection == GAME_SEL_TOURNAMENT) return cudaSuccess;
-  selection_weights_kernel<<<1, 1024, 0, st>>>(fit, rank, s.pop, cfg.selection, cum);
+  // a power-of-two block no wider than the population needs (the paper's 23 chromosomes:
+  // one warp, so 5 + 10 barrier steps instead of 10 + 20); integer weights and a maximum,
+  // so the result does not depend on the block size
+  int nt = 32;
+  while (nt < s.pop && nt < 1024) nt <<= 1;
+  selection_weights_kernel<<<1, nt, 0, st>>>(fit, rank, s.pop, cfg.selection, cum);
   return cudaGetLastError();
 }
 
@@ -425,14 +430,23 @@ __global__ void __launch_bounds__(1024) reduce_rank_kernel(RankArgs a) {
     }
     __syncthreads();
   } else if (a.mode == kRankEvaluate) {
-    // many (one per CTA of the narrow SIMT kernel): one warp per chromosome, lane l
+    // many (one per CTA of the narrow kernels): one warp per chromosome, lane l
     // adds rows l, l + 32, ... in order, then a fixed butterfly adds the 32 lane
     // sums (deterministic; the lanes' loads overlap instead of forming one chain
     // of memory latencies)
     const int lane = tid & 31;
     for (int c = tid >> 5; c < a.pop; c += blockDim.x >> 5) {
+      // eight rows are loaded before they are added, in the same order as one at a time
       double sse = 0.0;
-      for (int b = lane; b < a.n_part; b += 32) sse += a.partial[(long long)b * a.pop_pad + c];
+      int b = lane;
+      for (; b + 32 * 7 < a.n_part; b += 32 * 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = a.partial[(long long)(b + 32 * u) * a.pop_pad + c];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sse += v[u];
+      }
+      for (; b < a.n_part; b += 32) sse += a.partial[(long long)b * a.pop_pad + c];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sse += __shfl_xor_sync(0xffffffffu, sse, o);
       if (lane == 0) {

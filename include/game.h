@@ -66,7 +66,7 @@ enum { GAME_FP32 = 0, GAME_BF16 = 1, GAME_FP8 = 2 };              /* storage of 
 /* Fitness engine.  TCGEN05: the tensor-core contraction (128-chromosome tiles, or
  * for at most 32 FP32 chromosomes the kernel with patterns on the MMA's M side).
  * SIMT: no tcgen05.  For at most 32 chromosomes on 16 or 32 stored columns, the
- * narrow kernels (FP32 on warp-level MMAs, BF16 / FP8 on CUDA-core FMAs); otherwise
+ * narrow kernels (FP32 and BF16 on warp-level MMAs, FP8 on CUDA-core FMAs); otherwise
  * CUDA-core FMA tiles.  ON_THE_FLY: the expansion matrix is never stored (device
  * memory of X instead of P; FP32 form only, no surrogate, not in batches): with
  * per-feature coefficients, warps of the tensor-core kernel form each k-block of P in

@@ -12,13 +12,13 @@
 // two-stage ring in shared memory, and the float32 error sums of a lane cover
 // at most 32 patterns before they are added across lanes and into float64
 // (fixed assignment and order, so the result is deterministic).
-// * FP32 form (fitness_narrow_mma_kernel): warp-level MMAs; each stage is three
-//   bulk copies (hi plane, lo plane, targets) issued by one lane and completed
-//   on an mbarrier.
-// * BF16 / FP8 forms (fitness_narrow_kernel), whose genes stay float32: CUDA
-//   cores; each stage is 16-byte cp.async copies, consecutive in global memory
-//   and stored chunk-major (chunk j of row r at (j * rows + r) * 16), so that
-//   each thread later reads its own rows without bank conflicts.
+// * FP32 and BF16 forms (fitness_narrow_mma_kernel): warp-level MMAs; each stage
+//   is bulk copies (the P planes, then the targets) issued by one lane and
+//   completed on an mbarrier.
+// * FP8 form (fitness_narrow_kernel), whose genes stay float32: CUDA cores; each
+//   stage is 16-byte cp.async copies, consecutive in global memory and stored
+//   chunk-major (chunk j of row r at (j * rows + r) * 16), so that each thread
+//   later reads its own rows without bank conflicts.
 #include "simt.h"
 #include "tc_ptx.cuh"
 
@@ -116,21 +116,12 @@ __device__ __forceinline__ void narrow_stage(const SimtArgs& a, long long k0, ui
   }
 }
 
-// Values 8j .. 8j+7 of row r of a BF16 / FP8 stage (the column scales are
-// folded into the genes).
+// Values 8j .. 8j+7 of row r of an FP8 stage (the column scales are folded into
+// the genes).
 template <int PREC, int KP, int W>
 __device__ __forceinline__ void narrow_values8(const uint8_t* stage, int r, int j, float v[8]) {
   using Gm = NarrowGeom<PREC, KP, W>;
-  if (PREC == GAME_BF16) {
-    const uint4 w = *reinterpret_cast<const uint4*>(stage + (j * Gm::kWarpRows + r) * 16);
-    const __nv_bfloat162* b = reinterpret_cast<const __nv_bfloat162*>(&w);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float2 f = __bfloat1622float2(b[i]);
-      v[2 * i] = f.x;
-      v[2 * i + 1] = f.y;
-    }
-  } else {   // e4m3: 16 values a chunk, this is its half j % 2
+  {   // e4m3: 16 values a chunk, this is its half j % 2
     const uint2 w = *reinterpret_cast<const uint2*>(
         stage + ((j >> 1) * Gm::kWarpRows + r) * 16 + 8 * (j & 1));
     const __nv_fp8x2_storage_t* b = reinterpret_cast<const __nv_fp8x2_storage_t*>(&w);
@@ -151,7 +142,7 @@ __device__ __forceinline__ float narrow_error(float t, float s, int err, float R
   return e;
 }
 
-// CUDA-core form (BF16 / FP8 P, float32 genes x column scales).  A thread takes
+// CUDA-core form (FP8 P, float32 genes x column scales).  A thread takes
 // kRows patterns a pass.  The genes sit transposed in shared memory; each
 // 16-byte read is a broadcast of four chromosomes that feeds kRows patterns, two
 // chromosomes per packed f32x2 FMA.  The loop runs over the columns outside and
@@ -162,7 +153,7 @@ __device__ __forceinline__ float narrow_error(float t, float s, int err, float R
 // leaves lane c with chromosome c's block total.
 template <int PREC, int KP, int NG, bool TANH>
 __global__ void __launch_bounds__(kNarrowThreads, 2) fitness_narrow_kernel(SimtArgs a) {
-  static_assert(PREC != GAME_FP32, "the FP32 form runs on fitness_narrow_mma_kernel");
+  static_assert(PREC == GAME_FP8, "the FP32 and BF16 forms run on fitness_narrow_mma_kernel");
   if (a.in_evolve && a.state->stopped) return;
   constexpr int kRows = narrow_rows(KP, NG);
   using Gm = NarrowGeom<PREC, KP, 32 * kRows>;
@@ -364,7 +355,7 @@ cudaError_t attributes_prec() {
 
 
 // ---------------------------------------------------------------------------
-// FP32 form on warp-level MMAs.  The contraction of a 23-chromosome population
+// FP32 and BF16 forms on warp-level MMAs.  The contraction of a 23-chromosome population
 // is 16 x 23 FMAs a pattern, which keeps the FMA pipe of the CUDA-core form
 // above busy for longer than HBM takes to deliver the rows; here the tensor
 // cores take it through mma.sync m16n8k16 (f16 operands, f32 accumulate), fed
@@ -379,7 +370,10 @@ cudaError_t attributes_prec() {
 // * FP32 from fp16 pieces, as in the tensor-core kernel: P = P_hi + P_lo
 //   exactly, g' = g s_col / r_c = G_hi + G_lo; D = P_hi G_hi + P_hi G_lo +
 //   P_lo G_hi, three products on one accumulator that starts at a_0 / r_c, so
-//   Out = r_c D.
+//   Out = r_c D.  BF16: one P plane; the float32 genes times the column scales
+//   are split into three bf16 pieces that add up to them exactly, so the three
+//   products P w1 + P w2 + P w3 give what float32 genes would (each product is
+//   exact in float32; only the order of the sums differs).
 // * A thread ends with rows lane/4 and lane/4 + 8 of each 16-row block for
 //   chromosomes 2i, 2i+1 of each 8-chromosome block: it sums their errors in
 //   float32 pairs over 32 patterns, then the 8 lanes that share i add theirs
@@ -395,23 +389,24 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       : "memory");
 }
 
-// FP32 stage of the warp-MMA kernel: rows [k0, k0 + W) of the hi plane, then of
-// the lo plane (row-major, 2 KP bytes a row), then their targets; three bulk
+// Stage of the warp-MMA kernel: rows [k0, k0 + W) of each plane (FP32: hi, then
+// lo; BF16: the one plane; row-major, 2 KP bytes a row), then their targets; bulk
 // copies issued by one lane.  A ragged last pass copies its rows only (a
 // multiple of 16 bytes) and leaves its targets to be read from global memory;
 // the stale rows past m feed only outputs that are never summed.
-template <int KP, int W>
+template <int PREC, int KP, int W>
 __device__ __forceinline__ void mma_stage(const SimtArgs& a, long long k0, uint32_t stage,
                                           uint64_t* bar) {
   constexpr uint32_t RB = 2 * KP;
+  constexpr uint32_t kPlanes = PREC == GAME_FP32 ? 2 : 1;
   const long long rows = a.m - k0 < W ? a.m - k0 : W;
   const uint32_t bp = (uint32_t)rows * RB;
   const bool full = rows == W;
-  tc::mbar_expect_tx(bar, 2 * bp + (full ? 4 * W : 0));
+  tc::mbar_expect_tx(bar, kPlanes * bp + (full ? 4 * W : 0));
   const uint32_t b = tc::smem_u32(bar);
   bulk_g2s(stage, static_cast<const uint8_t*>(a.p0) + k0 * RB, bp, b);
-  bulk_g2s(stage + W * RB, static_cast<const uint8_t*>(a.p1) + k0 * RB, bp, b);
-  if (full) bulk_g2s(stage + 2 * W * RB, a.t + k0, 4 * W, b);
+  if (kPlanes == 2) bulk_g2s(stage + W * RB, static_cast<const uint8_t*>(a.p1) + k0 * RB, bp, b);
+  if (full) bulk_g2s(stage + kPlanes * W * RB, a.t + k0, 4 * W, b);
 }
 
 // Bounded wait that ignores the CTA's error flag: after a timeout the warp still
@@ -433,23 +428,59 @@ constexpr int mma_blocks(int kp, int nb) {
   return kp == 16 ? (nb <= 3 ? 4 : 2) : (nb <= 3 ? 2 : 1);
 }
 
-__device__ __forceinline__ void mma_f16_16816_c(float d[4], const uint2 a_r0, const uint2 a_r1,
-                                                const uint2 b, float c0, float c1) {
+// m16n8k16 with f32 accumulate; BF: bf16 operands, else f16.  a_r0 = {a0a1, a4a5}
+// (row lane/4), a_r1 = {a2a3, a6a7} (row lane/4 + 8).
+template <bool BF>
+__device__ __forceinline__ void mma_16816_c(float d[4], const uint2 a_r0, const uint2 a_r1,
+                                            const uint2 b, float c0, float c1) {
   // d = A B + (c0, c1, c0, c1): the accumulator starts from registers held for the pass
-  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-      "{%8, %9}, {%10, %11, %10, %11};"
-      : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-      : "r"(a_r0.x), "r"(a_r1.x), "r"(a_r0.y), "r"(a_r1.y), "r"(b.x), "r"(b.y), "f"(c0), "f"(c1));
+  if (BF)
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+        "{%4, %5, %6, %7}, {%8, %9}, {%10, %11, %10, %11};"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a_r0.x), "r"(a_r1.x), "r"(a_r0.y), "r"(a_r1.y), "r"(b.x), "r"(b.y), "f"(c0),
+          "f"(c1));
+  else
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, "
+        "{%4, %5, %6, %7}, {%8, %9}, {%10, %11, %10, %11};"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a_r0.x), "r"(a_r1.x), "r"(a_r0.y), "r"(a_r1.y), "r"(b.x), "r"(b.y), "f"(c0),
+          "f"(c1));
 }
 
-__device__ __forceinline__ void mma_f16_16816(float d[4], const uint2 a_r0, const uint2 a_r1,
-                                              const uint2 b) {
-  // a_r0 = {a0a1, a4a5} (row lane/4), a_r1 = {a2a3, a6a7} (row lane/4 + 8)
-  asm(
-      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
-      "{%8, %9}, {%0, %1, %2, %3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a_r0.x), "r"(a_r1.x), "r"(a_r0.y), "r"(a_r1.y), "r"(b.x), "r"(b.y));
+template <bool BF>
+__device__ __forceinline__ void mma_16816(float d[4], const uint2 a_r0, const uint2 a_r1,
+                                          const uint2 b) {
+  if (BF)
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+        "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a_r0.x), "r"(a_r1.x), "r"(a_r0.y), "r"(a_r1.y), "r"(b.x), "r"(b.y));
+  else
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, "
+        "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a_r0.x), "r"(a_r1.x), "r"(a_r0.y), "r"(a_r1.y), "r"(b.x), "r"(b.y));
+}
+
+// Four float32 gene values as three bf16 pieces that add up to them exactly: each
+// remainder is exact in float32, and the third piece has at most 8 significant bits.
+__device__ __forceinline__ void bf16_pieces4(const float w[4], uint2& p1, uint2& p2, uint2& p3) {
+  __nv_bfloat16 h1[4], h2[4], h3[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    h1[e] = __float2bfloat16_rn(w[e]);
+    const float r1 = w[e] - __bfloat162float(h1[e]);
+    h2[e] = __float2bfloat16_rn(r1);
+    h3[e] = __float2bfloat16_rn(r1 - __bfloat162float(h2[e]));
+  }
+  auto pack = [](__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    const __nv_bfloat162 v = __halves2bfloat162(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+  };
+  p1 = make_uint2(pack(h1[0], h1[1]), pack(h1[2], h1[3]));
+  p2 = make_uint2(pack(h2[0], h2[1]), pack(h2[2], h2[3]));
+  p3 = make_uint2(pack(h3[0], h3[1]), pack(h3[2], h3[3]));
 }
 
 template <int ERR, bool TANH>
@@ -479,13 +510,15 @@ __device__ __forceinline__ unsigned long long mma_error2(const float d0, const f
   return tc::fma2(dd, dd, acc);
 }
 
-template <int KP, int NB, int ERR, bool TANH>
+template <int PREC, int KP, int NB, int ERR, bool TANH>
 __global__ void __launch_bounds__(kNarrowThreads, 2) fitness_narrow_mma_kernel(SimtArgs a) {
   if (a.in_evolve && a.state->stopped) return;
   constexpr int MB = mma_blocks(KP, NB);   // 16-row blocks a warp and pass
   constexpr int W = 16 * MB;
   constexpr int KS = KP / 16;              // k-steps of 16 columns
-  using Gm = NarrowGeom<GAME_FP32, KP, W>;
+  constexpr bool BF = PREC == GAME_BF16;
+  constexpr int kPlanes = BF ? 1 : 2;
+  using Gm = NarrowGeom<PREC, KP, W>;
   constexpr int RB = 2 * KP;               // bytes of a row of one plane
   extern __shared__ __align__(16) uint8_t narrow_ring[];   // [warp][stage][kStageBytes]
   __shared__ double red[kNarrowWarps][kNarrowPop];
@@ -509,28 +542,44 @@ __global__ void __launch_bounds__(kNarrowThreads, 2) fitness_narrow_mma_kernel(S
   uint32_t phase = 0;     // parity of each stage's next completion
   for (int s = 0; s < kNarrowStages; ++s)
     if (k0 + s * step < a.m) {
-      if (lane == 0) mma_stage<KP, W>(a, k0 + s * step, ring_s + s * Gm::kStageBytes, &full_bar[warp][s]);
+      if (lane == 0)
+        mma_stage<PREC, KP, W>(a, k0 + s * step, ring_s + s * Gm::kStageBytes, &full_bar[warp][s]);
       pending |= 1u << s;
     }
-  // B fragments: chromosome 8 nb + lane/4, stored columns 16 ks + 4i .. +3 of each
-  // gene plane (rows past pop are zero).  Accumulator start a_0 / r_c and the
-  // epilogue factor -r_c for chromosomes 8 nb + 2i, 8 nb + 2i + 1.
-  uint2 bh[NB][KS], bl[NB][KS];
+  // B fragments: chromosome 8 nb + lane/4, stored columns 16 ks + 4i .. +3.  FP32:
+  // prepare_kernel's gene planes (hi, lo; rows past pop are zero), accumulator start
+  // a_0 / r_c and epilogue factor -r_c.  BF16: the float32 genes times the column
+  // scales as three bf16 pieces, accumulator start a_0 and factor -1.
+  uint2 b0[NB][KS], b1[NB][KS], b2[NB][KS];
   float cb[NB][2];
   unsigned long long nr2[NB];
 #pragma unroll
   for (int nb = 0; nb < NB; ++nb) {
-    const long long row = (long long)(8 * nb + gq) * a.kp;
+    const int cg = 8 * nb + gq;
+    const long long row = (long long)cg * a.kp;
 #pragma unroll
     for (int ks = 0; ks < KS; ++ks) {
-      bh[nb][ks] = *reinterpret_cast<const uint2*>(static_cast<const __half*>(a.ghi) + row + 16 * ks + 4 * qi);
-      bl[nb][ks] = *reinterpret_cast<const uint2*>(static_cast<const __half*>(a.glo) + row + 16 * ks + 4 * qi);
+      if (BF) {
+        float w[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int col = 16 * ks + 4 * qi + e;
+          w[e] = (cg < a.pop && col < a.kb) ? a.geval[row + col] * a.colscale[col] : 0.0f;
+        }
+        bf16_pieces4(w, b0[nb][ks], b1[nb][ks], b2[nb][ks]);
+      } else {
+        b0[nb][ks] = *reinterpret_cast<const uint2*>(static_cast<const __half*>(a.ghi) + row +
+                                                     16 * ks + 4 * qi);
+        b1[nb][ks] = *reinterpret_cast<const uint2*>(static_cast<const __half*>(a.glo) + row +
+                                                     16 * ks + 4 * qi);
+        b2[nb][ks] = make_uint2(0u, 0u);
+      }
     }
     float r[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int c = 8 * nb + 2 * qi + h;
-      r[h] = c < a.pop ? a.rscale[c] : 1.0f;
+      r[h] = (!BF && c < a.pop) ? a.rscale[c] : 1.0f;
       cb[nb][h] = c < a.pop ? a.bias[c] / r[h] : 0.0f;   // r: a power of two, exact
     }
     nr2[nb] = tc::pack2(-r[0], -r[1]);
@@ -579,7 +628,8 @@ __global__ void __launch_bounds__(kNarrowThreads, 2) fitness_narrow_mma_kernel(S
         for (int h = 0; h < 2; ++h) {
           const int r = 16 * mb + gq + 8 * h;   // columns 16 ks + 4i .. + 3
           ah[mb][ks][h] = *reinterpret_cast<const uint2*>(sp + r * RB + 32 * ks + 8 * qi);
-          al[mb][ks][h] = *reinterpret_cast<const uint2*>(sp + (W + r) * RB + 32 * ks + 8 * qi);
+          if (!BF)
+            al[mb][ks][h] = *reinterpret_cast<const uint2*>(sp + (W + r) * RB + 32 * ks + 8 * qi);
         }
       }
     }
@@ -588,7 +638,7 @@ __global__ void __launch_bounds__(kNarrowThreads, 2) fitness_narrow_mma_kernel(S
       for (int mb = 0; mb < MB; ++mb)
 #pragma unroll
         for (int h = 0; h < 2; ++h)
-          t[mb][h] = reinterpret_cast<const float*>(sp + 2 * W * RB)[16 * mb + gq + 8 * h];
+          t[mb][h] = reinterpret_cast<const float*>(sp + kPlanes * W * RB)[16 * mb + gq + 8 * h];
     } else {
 #pragma unroll
       for (int mb = 0; mb < MB; ++mb)
@@ -607,12 +657,16 @@ __global__ void __launch_bounds__(kNarrowThreads, 2) fitness_narrow_mma_kernel(S
       for (int ks = 0; ks < KS; ++ks)
 #pragma unroll
         for (int nb = 0; nb < NB; ++nb) {
+          // FP32: P_hi G_hi + P_hi G_lo + P_lo G_hi.  BF16: P (w1 + w2 + w3).
           if (ks == 0)
-            mma_f16_16816_c(d[nb], ah[mb][0][0], ah[mb][0][1], bh[nb][0], cb[nb][0], cb[nb][1]);
+            mma_16816_c<BF>(d[nb], ah[mb][0][0], ah[mb][0][1], b0[nb][0], cb[nb][0], cb[nb][1]);
           else
-            mma_f16_16816(d[nb], ah[mb][ks][0], ah[mb][ks][1], bh[nb][ks]);
-          mma_f16_16816(d[nb], ah[mb][ks][0], ah[mb][ks][1], bl[nb][ks]);
-          mma_f16_16816(d[nb], al[mb][ks][0], al[mb][ks][1], bh[nb][ks]);
+            mma_16816<BF>(d[nb], ah[mb][ks][0], ah[mb][ks][1], b0[nb][ks]);
+          mma_16816<BF>(d[nb], ah[mb][ks][0], ah[mb][ks][1], b1[nb][ks]);
+          if (BF)
+            mma_16816<BF>(d[nb], ah[mb][ks][0], ah[mb][ks][1], b2[nb][ks]);
+          else
+            mma_16816<BF>(d[nb], al[mb][ks][0], al[mb][ks][1], b0[nb][ks]);
         }
       if (full) {   // every pass but the last: no row checks
 #pragma unroll
@@ -633,7 +687,7 @@ __global__ void __launch_bounds__(kNarrowThreads, 2) fitness_narrow_mma_kernel(S
     __syncwarp();   // the stage's values are used: refill it with the pass kNarrowStages ahead
     if (k0 + kNarrowStages * step < a.m) {
       if (lane == 0)
-        mma_stage<KP, W>(a, k0 + kNarrowStages * step, ring_s + cur * Gm::kStageBytes,
+        mma_stage<PREC, KP, W>(a, k0 + kNarrowStages * step, ring_s + cur * Gm::kStageBytes,
                          &full_bar[warp][cur]);
       pending |= 1u << cur;
     }
@@ -654,40 +708,40 @@ __global__ void __launch_bounds__(kNarrowThreads, 2) fitness_narrow_mma_kernel(S
   }
 }
 
-template <int KP, int NB, int ERR>
+template <int PREC, int KP, int NB, int ERR>
 void launch_mma_err(const SimtArgs& a, int grid, bool tanh_act, cudaStream_t st) {
-  constexpr int smem = NarrowGeom<GAME_FP32, KP, 16 * mma_blocks(KP, NB)>::kSmem;
+  constexpr int smem = NarrowGeom<PREC, KP, 16 * mma_blocks(KP, NB)>::kSmem;
   if (tanh_act)
-    fitness_narrow_mma_kernel<KP, NB, ERR, true><<<grid, kNarrowThreads, smem, st>>>(a);
+    fitness_narrow_mma_kernel<PREC, KP, NB, ERR, true><<<grid, kNarrowThreads, smem, st>>>(a);
   else
-    fitness_narrow_mma_kernel<KP, NB, ERR, false><<<grid, kNarrowThreads, smem, st>>>(a);
+    fitness_narrow_mma_kernel<PREC, KP, NB, ERR, false><<<grid, kNarrowThreads, smem, st>>>(a);
 }
 
-template <int KP, int NB>
+template <int PREC, int KP, int NB>
 void launch_mma_nb(const SimtArgs& a, int grid, bool tanh_act, cudaStream_t st) {
   if (a.err == GAME_TMSE)
-    launch_mma_err<KP, NB, GAME_TMSE>(a, grid, tanh_act, st);
+    launch_mma_err<PREC, KP, NB, GAME_TMSE>(a, grid, tanh_act, st);
   else if (a.err == GAME_TMSE_SQ)
-    launch_mma_err<KP, NB, GAME_TMSE_SQ>(a, grid, tanh_act, st);
+    launch_mma_err<PREC, KP, NB, GAME_TMSE_SQ>(a, grid, tanh_act, st);
   else
-    launch_mma_err<KP, NB, GAME_MSE>(a, grid, tanh_act, st);
+    launch_mma_err<PREC, KP, NB, GAME_MSE>(a, grid, tanh_act, st);
 }
 
-template <int KP>
+template <int PREC, int KP>
 void launch_mma(const SimtArgs& a, int grid, bool tanh_act, cudaStream_t st) {
   switch ((a.pop + 7) / 8) {
-    case 1: launch_mma_nb<KP, 1>(a, grid, tanh_act, st); break;
-    case 2: launch_mma_nb<KP, 2>(a, grid, tanh_act, st); break;
-    case 3: launch_mma_nb<KP, 3>(a, grid, tanh_act, st); break;
-    default: launch_mma_nb<KP, 4>(a, grid, tanh_act, st); break;
+    case 1: launch_mma_nb<PREC, KP, 1>(a, grid, tanh_act, st); break;
+    case 2: launch_mma_nb<PREC, KP, 2>(a, grid, tanh_act, st); break;
+    case 3: launch_mma_nb<PREC, KP, 3>(a, grid, tanh_act, st); break;
+    default: launch_mma_nb<PREC, KP, 4>(a, grid, tanh_act, st); break;
   }
 }
 
-template <int KP, int NB, int ERR>
+template <int PREC, int KP, int NB, int ERR>
 cudaError_t mma_attributes_err() {
-  constexpr int smem = NarrowGeom<GAME_FP32, KP, 16 * mma_blocks(KP, NB)>::kSmem;
-  for (auto k : {fitness_narrow_mma_kernel<KP, NB, ERR, true>,
-                 fitness_narrow_mma_kernel<KP, NB, ERR, false>}) {
+  constexpr int smem = NarrowGeom<PREC, KP, 16 * mma_blocks(KP, NB)>::kSmem;
+  for (auto k : {fitness_narrow_mma_kernel<PREC, KP, NB, ERR, true>,
+                 fitness_narrow_mma_kernel<PREC, KP, NB, ERR, false>}) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -697,23 +751,22 @@ cudaError_t mma_attributes_err() {
   return cudaSuccess;
 }
 
-template <int KP, int NB>
+template <int PREC, int KP, int NB>
 cudaError_t mma_attributes_nb() {
-  cudaError_t e = mma_attributes_err<KP, NB, GAME_MSE>();
-  if (e == cudaSuccess) e = mma_attributes_err<KP, NB, GAME_TMSE>();
-  if (e == cudaSuccess) e = mma_attributes_err<KP, NB, GAME_TMSE_SQ>();
+  cudaError_t e = mma_attributes_err<PREC, KP, NB, GAME_MSE>();
+  if (e == cudaSuccess) e = mma_attributes_err<PREC, KP, NB, GAME_TMSE>();
+  if (e == cudaSuccess) e = mma_attributes_err<PREC, KP, NB, GAME_TMSE_SQ>();
   return e;
 }
 
-template <int KP>
+template <int PREC, int KP>
 cudaError_t mma_attributes() {
-  cudaError_t e = mma_attributes_nb<KP, 1>();
-  if (e == cudaSuccess) e = mma_attributes_nb<KP, 2>();
-  if (e == cudaSuccess) e = mma_attributes_nb<KP, 3>();
-  if (e == cudaSuccess) e = mma_attributes_nb<KP, 4>();
+  cudaError_t e = mma_attributes_nb<PREC, KP, 1>();
+  if (e == cudaSuccess) e = mma_attributes_nb<PREC, KP, 2>();
+  if (e == cudaSuccess) e = mma_attributes_nb<PREC, KP, 3>();
+  if (e == cudaSuccess) e = mma_attributes_nb<PREC, KP, 4>();
   return e;
 }
-
 }  // namespace
 
 bool narrow_shape_ok(int pop, int kp) {
@@ -723,9 +776,9 @@ bool narrow_shape_ok(int pop, int kp) {
 bool simt_narrow(const Shape& s) { return narrow_shape_ok(s.pop, s.kp); }
 
 int narrow_partials(const Shape& s, int n_sm) {
-  const int rows = s.precision == GAME_FP32
-                       ? kNarrowWarps * 16 * mma_blocks(s.kp, (s.pop + 7) / 8)
-                       : kNarrowThreads * narrow_rows(s.kp, narrow_groups(s.pop));
+  const int rows = s.precision == GAME_FP8
+                       ? kNarrowThreads * narrow_rows(s.kp, narrow_groups(s.pop))
+                       : kNarrowWarps * 16 * mma_blocks(s.kp, (s.pop + 7) / 8);
   const long long need = (s.n_train + rows - 1) / rows;
   const long long g = 2LL * n_sm;
   return (int)(need < 1 ? 1 : need < g ? need : g);
@@ -735,30 +788,26 @@ cudaError_t launch_narrow(const SimtArgs& a, const Shape& s, int grid, cudaStrea
   const bool th = a.act == GAME_TANH;
   if (s.precision == GAME_FP32) {   // warp-level MMAs
     if (s.kp == 16)
-      launch_mma<16>(a, grid, th, st);
+      launch_mma<GAME_FP32, 16>(a, grid, th, st);
     else
-      launch_mma<32>(a, grid, th, st);
-    return cudaGetLastError();
-  }
-  if (s.kp == 16) {
-    if (s.precision == GAME_BF16)
-      launch_prec<GAME_BF16, 16>(a, grid, th, st);
+      launch_mma<GAME_FP32, 32>(a, grid, th, st);
+  } else if (s.precision == GAME_BF16) {
+    if (s.kp == 16)
+      launch_mma<GAME_BF16, 16>(a, grid, th, st);
     else
-      return cudaErrorInvalidValue;   // e4m3 rows are padded to 32 columns
+      launch_mma<GAME_BF16, 32>(a, grid, th, st);
   } else {
-    if (s.precision == GAME_BF16)
-      launch_prec<GAME_BF16, 32>(a, grid, th, st);
-    else
-      launch_prec<GAME_FP8, 32>(a, grid, th, st);
+    if (s.kp != 32) return cudaErrorInvalidValue;   // e4m3 rows are padded to 32 columns
+    launch_prec<GAME_FP8, 32>(a, grid, th, st);
   }
   return cudaGetLastError();
 }
 
 cudaError_t simt_init_attributes() {
-  cudaError_t e = mma_attributes<16>();
-  if (e == cudaSuccess) e = mma_attributes<32>();
-  if (e == cudaSuccess) e = attributes_prec<GAME_BF16, 16>();
-  if (e == cudaSuccess) e = attributes_prec<GAME_BF16, 32>();
+  cudaError_t e = mma_attributes<GAME_FP32, 16>();
+  if (e == cudaSuccess) e = mma_attributes<GAME_FP32, 32>();
+  if (e == cudaSuccess) e = mma_attributes<GAME_BF16, 16>();
+  if (e == cudaSuccess) e = mma_attributes<GAME_BF16, 32>();
   if (e == cudaSuccess) e = attributes_prec<GAME_FP8, 32>();
   return e;
 }

@@ -32,9 +32,8 @@ constexpr int kNarrowStages = 2;
 
 // CUDA-core form: chromosome groups of four the kernel carries (the population
 // rounded up to 8), and rows per thread and pass (each gene read from shared
-// memory feeds this many patterns; two rows of 16 columns with up to 24
-// chromosomes fit the 128 registers that two resident CTAs of 256 threads
-// leave, more would spill).
+// memory feeds this many patterns; two rows fit 128 registers only at 16
+// columns with up to 24 chromosomes, so the FP8 form's 32-column rows take one).
 constexpr int narrow_groups(int pop) { return (pop + 7) / 8 * 2; }
 constexpr int narrow_rows(int kp, int ng) { return kp == 16 && ng <= 6 ? 2 : 1; }
 

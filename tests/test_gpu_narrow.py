@@ -93,6 +93,22 @@ def test_narrow_low_precision(fmt, F, d):
                                rtol=FIT_RTOL)
 
 
+@pytest.mark.parametrize("pop", [5, 29])
+def test_narrow_bf16_chromosome_blocks(pop):
+    """BF16 on the warp-MMA narrow kernel with one and with four 8-chromosome blocks
+    (16 stored columns), against the oracle on the quantised P with exact genes."""
+    game = lib()
+    ds = synth.make_dataset(5003, 4, 4, seed=29)
+    ocfg = _cfg(degree=4, pop=pop)
+    g = make_game(ocfg, ds.X, ds.t, ds.n_train, precision=game.BF16, elite_rescore=0)
+    assert g.timing()["engine"] == game.ENGINE_SIMT
+    fit, _ = g.evaluate()
+    Q, sc = o.quantize_columns(o.expand(ds.X[:ds.n_train], "chebyshev", 4)[:, 1:], "bf16")
+    Pq = np.concatenate([np.ones((ds.n_train, 1)), o.dequantize_columns(Q, sc)], axis=1)
+    np.testing.assert_allclose(fit, o.fitness(Pq, ds.t[:ds.n_train], g.population(), ocfg),
+                               rtol=FIT_RTOL)
+
+
 @pytest.mark.parametrize("engine", ["simt", "tcgen05"])
 def test_narrow_many_blocks_per_thread(engine):
     """Enough rows that every thread folds several 32-pattern blocks into its float64
